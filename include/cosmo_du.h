@@ -1,0 +1,291 @@
+/*
+ * cosmo_du.h -- C ABI of the B300 (sm_103a) library for one unrolled COSMO
+ * ADMM iteration and its backward, batched over many conic programs.
+ *
+ * Problem (Sec. 2.1, Eq. conic-standard), one per instance i:
+ *     minimize 1/2 x'Px + q'x   s.t.  A x + s = b,  s in K
+ * K is a product of zero, nonnegative, box, second-order (SOC) and PSD cones
+ * listed in row order.  PSD blocks are stored in svec form: upper triangle,
+ * column by column, off-diagonals times sqrt(2) (an isometry, so projections
+ * and their adjoints need no extra factors).
+ *
+ * Iteration k (Sec. 2.2, Eqs. cosmo_linear_system .. cosmo_projection) with
+ * per-row penalties rho^k (rectified to the block mean on SOC/PSD blocks,
+ * App. E), relaxation alpha^k per instance and sigma_k:
+ *     (P + sigma I + A'D(rho)A) x~ = sigma x - q + A'(y + rho o (b - s))   (Sec. 2.3, reduced form)
+ *     s~ = b - A x~                         (equal to s - (y + nu~)/rho)
+ *     x+ = alpha x~ + (1 - alpha) x
+ *     s+ = Pi_K(alpha s~ + (1 - alpha) s + y / rho)
+ *     y+ = y + rho o (alpha s~ + (1 - alpha) s - s+)
+ * The linear system is solved matrix-free by Jacobi-preconditioned CG (App. D),
+ * warm-started at the previous x~.  The backward uses the adjoint CG rule of
+ * Sec. 2.3 (Eq. grad_rho) and the Daleckii-Krein rule of Sec. 2.4
+ * (Eqs. psd-cotangent-dk, lowner).
+ *
+ * Conventions
+ *  - Every function returns a cosmo_status; no C++ exception crosses the ABI.
+ *    On failure cosmo_last_error() returns a thread-local message.
+ *  - "dev" pointers are caller-owned device memory (e.g. PyTorch tensors),
+ *    "host" pointers caller-owned host memory.  The library never frees
+ *    caller memory; it owns only the opaque batch and what the batch
+ *    allocates (problem copy, tape, workspace).
+ *  - Real-valued device arrays ("real") are float for COSMO_PREC_MIXED and
+ *    double for COSMO_PREC_FP64.  Reductions (norms, losses, CG inner
+ *    products, eigenvalue-gap tests) are done in double in both modes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered and do not synchronise unless the
+ *    name says so (cosmo_status_sync, cosmo_step_host).
+ *  - Batched arrays concatenate instances: x, q have n_total entries, s, y,
+ *    b have m_total; instance i owns the column range [col_off[i],
+ *    col_off[i+1]) and the row range [row_off[i], row_off[i+1]).
+ *  - Conditions found on the device (CG cap reached, non-finite values,
+ *    eigensolver sweep cap, invalid rho/alpha) set per-instance flag bits
+ *    read by cosmo_status_sync; they never trap.
+ */
+#ifndef COSMO_DU_H
+#define COSMO_DU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  COSMO_OK = 0,
+  COSMO_E_INVAL = 1,      /* invalid argument or problem data */
+  COSMO_E_NOMEM = 2,      /* device or host allocation failed */
+  COSMO_E_CUDA = 3,       /* a CUDA runtime call failed */
+  COSMO_E_NOTCONV = 4,    /* (flag) CG reached its iteration cap */
+  COSMO_E_NONFINITE = 5,  /* (flag) a non-finite iterate was produced */
+  COSMO_E_TIMEOUT = 6,    /* reserved: bounded device wait gave up */
+  COSMO_E_STATE = 7,      /* call out of order (e.g. backward without tape) */
+  COSMO_E_NODEVICE = 8    /* no CUDA device */
+} cosmo_status;
+
+/* cone types (Sec. 2.4 lists zero, orthant, SOC, PSD; box is an addition) */
+enum {
+  COSMO_CONE_ZERO = 0,
+  COSMO_CONE_NONNEG = 1,
+  COSMO_CONE_BOX = 2,
+  COSMO_CONE_SOC = 3,
+  COSMO_CONE_PSD = 4
+};
+
+/* precision modes */
+enum {
+  COSMO_PREC_MIXED = 0, /* float iterates and values, double reductions */
+  COSMO_PREC_FP64 = 1   /* double everywhere */
+};
+
+/* storage of the matrix values of P and A in COSMO_PREC_MIXED */
+enum { COSMO_VAL_F32 = 0, COSMO_VAL_BF16 = 1 };
+
+/* per-instance flag bits reported by cosmo_status_sync */
+enum {
+  COSMO_FLAG_CG_CAP = 1,        /* forward CG hit cg_max_iter */
+  COSMO_FLAG_ADJ_CG_CAP = 2,    /* adjoint CG hit cg_max_iter */
+  COSMO_FLAG_EIG_CAP = 4,       /* eigensolver hit its sweep/iteration cap */
+  COSMO_FLAG_NONFINITE = 8,     /* non-finite iterate or cotangent */
+  COSMO_FLAG_BAD_PARAM = 16     /* rho <= 0, non-finite, or alpha outside (0, 2) */
+};
+
+/* One cone: type and dimension.  For PSD, dim = p and the cone occupies
+ * p(p+1)/2 rows; for every other type it occupies dim rows. */
+typedef struct {
+  int32_t type;
+  int32_t dim;
+} cosmo_cone;
+
+/* Problem batch, all HOST memory, read during cosmo_batch_create only
+ * (the library copies what it needs).  CSR arrays are batch-global: rows of
+ * A are the concatenated constraint rows, columns are global variable
+ * indices; every row of instance i must only reference columns of instance i
+ * (the batch is block diagonal).  P holds both triangles of each symmetric
+ * block; P_rowptr may be NULL for P = 0. */
+typedef struct {
+  int32_t ninst;
+  const int64_t* col_off;   /* [ninst+1], col_off[0] = 0, nondecreasing */
+  const int64_t* row_off;   /* [ninst+1] */
+  const int64_t* P_rowptr;  /* [n_total+1] or NULL */
+  const int32_t* P_col;     /* [nnzP] */
+  const double* P_val;      /* [nnzP] */
+  const int64_t* A_rowptr;  /* [m_total+1] */
+  const int32_t* A_col;     /* [nnzA] */
+  const double* A_val;      /* [nnzA] */
+  const double* q;          /* [n_total] */
+  const double* b;          /* [m_total] */
+  const double* box_l;      /* [m_total] or NULL (required if a box cone exists) */
+  const double* box_u;      /* [m_total] or NULL */
+  const int32_t* cone_count;/* [ninst] cones of each instance */
+  const cosmo_cone* cones;  /* [sum cone_count], instance by instance, row order */
+} cosmo_problem;
+
+typedef struct {
+  int32_t precision;        /* COSMO_PREC_MIXED or COSMO_PREC_FP64 */
+  int32_t value_type;       /* COSMO_VAL_F32 / COSMO_VAL_BF16 (MIXED only) */
+  double cg_tol;            /* stop when ||r|| <= cg_tol * ||rhs|| (App. D: 1e-8) */
+  int32_t cg_max_iter;      /* CG cap per solve; flag COSMO_FLAG_*CG_CAP */
+  int32_t checkpoint_every; /* 0: keep the whole tape; c > 0: keep states every
+                               c steps and recompute segments in the backward */
+  double dk_gap_tau;        /* Loewner-matrix gap threshold, relative:
+                               tau = dk_gap_tau * max(1, max|lambda|) */
+  int32_t eig_jacobi_max_p; /* PSD blocks with p <= this use the cyclic Jacobi
+                               solver, larger ones tridiagonalisation + QL;
+                               <= 0 selects the built-in default */
+  int32_t eig_max_sweeps;   /* Jacobi sweep cap (flag COSMO_FLAG_EIG_CAP) */
+  double eig_tol;           /* Jacobi stop: off(A) <= eig_tol * ||A||_F */
+  int32_t use_graph;        /* capture forward/backward into CUDA graphs */
+  int32_t device;           /* CUDA device ordinal the batch lives on */
+} cosmo_options;
+
+typedef struct {
+  int32_t ninst;
+  int32_t precision;
+  int64_t n_total, m_total;
+  int64_t nnzA, nnzP;
+  int32_t n_soc, n_psd, max_psd_p;
+  int64_t psd_u_entries;    /* sum of p^2 over PSD blocks */
+  int64_t device_bytes;     /* device memory the batch currently owns */
+  int32_t last_K;           /* K of the last forward (0 if none) */
+  int32_t tape_valid;       /* 1 if a backward can run now */
+  int64_t kernels_launched; /* kernels this batch launched so far (graph replays
+                               count their kernels) */
+} cosmo_batch_info;
+
+typedef struct cosmo_batch cosmo_batch;
+
+/* Library version and the number of kernels launched by all batches. */
+const char* cosmo_version(void);
+int64_t cosmo_kernel_launch_count(void);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* cosmo_last_error(void);
+
+/* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
+ * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; Jacobi up to p = 64
+ * (MIXED) / 48 (FP64); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
+ * use_graph 1; device 0.  Returns COSMO_E_INVAL for an unknown precision. */
+cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
+
+/* Validate a problem on the host without touching the device (CSR bounds and
+ * block-diagonal structure, cone rows summing to each instance's row count,
+ * PSD dims, box bounds l <= u, finite data).  COSMO_OK or COSMO_E_INVAL. */
+cosmo_status cosmo_problem_validate(const cosmo_problem* prob);
+
+/* Create a batch on opt->device: validates (as above, before any CUDA call),
+ * builds A' in CSR, the cone schedule and the Jacobi-preconditioner
+ * ingredients, and uploads them.  *out is owned by the caller and released
+ * with cosmo_batch_destroy.  Errors: E_INVAL, E_NODEVICE, E_NOMEM, E_CUDA. */
+cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* opt,
+                                cosmo_batch** out);
+cosmo_status cosmo_batch_destroy(cosmo_batch* batch);
+cosmo_status cosmo_batch_get_info(const cosmo_batch* batch, cosmo_batch_info* out);
+
+/* Unroll K iterations from (x0, s0, y0) (NULL = zero start).
+ *   sigma_host: host [K] (NULL = 1e-6 every step, the value of Sec. 2.2)
+ *   rho:   dev real [K][m_total], per-row penalties before rectification
+ *   alpha: dev real [K][ninst]
+ *   xK, sK, yK: dev real outputs (NULL = not wanted)
+ *   loss:  dev double [ninst] output ||A x^K + s^K - b||^2 + ||P x^K + q - A'y^K||^2
+ *          (NULL = not wanted; required if a backward will seed from it)
+ *   record_tape: 1 keeps what cosmo_backward needs (the tape), 0 does not.
+ * Errors: E_INVAL (K < 1, NULL rho/alpha), E_NOMEM, E_CUDA. */
+cosmo_status cosmo_forward(cosmo_batch* batch, int32_t K, const double* sigma_host,
+                           const void* rho, const void* alpha, const void* x0,
+                           const void* s0, const void* y0, void* xK, void* sK, void* yK,
+                           double* loss, int32_t record_tape, void* stream);
+
+/* Reverse pass of the last taped forward.  Cotangents (dev, NULL = 0):
+ *   gxK, gsK, gyK: real [n_total]/[m_total]/[m_total] for x^K, s^K, y^K
+ *   gloss: double [ninst] cotangent of the forward's loss
+ * Outputs (dev, NULL = not wanted):
+ *   grho: real [K][m_total] w.r.t. the unrectified rho
+ *   galpha: real [K][ninst]
+ *   gx0, gs0, gy0: real cotangents of the starting point.
+ * Errors: E_STATE (no tape, or the tape was overwritten), E_INVAL, E_CUDA. */
+cosmo_status cosmo_backward(cosmo_batch* batch, const void* gxK, const void* gsK,
+                            const void* gyK, const double* gloss, void* grho, void* galpha,
+                            void* gx0, void* gs0, void* gy0, void* stream);
+
+/* Residuals of App. E at a point: rp2[i] = ||A x + s - b||^2,
+ * rd2[i] = ||P x + q - A'y||^2, obj[i] = 1/2 x'Px + q'x (dev double [ninst],
+ * each NULL = not wanted).  x, s, y: dev real. */
+cosmo_status cosmo_residuals(cosmo_batch* batch, const void* x, const void* s, const void* y,
+                             double* rp2, double* rd2, double* obj, void* stream);
+
+/* Learnable per-iteration penalty (one scalar per step, shared by all rows and
+ * instances) mapped to per-row values: rho[k][r] = exp(log_rho[k]) * w_r with
+ * w_r = eq_scale on zero-cone rows and 1 elsewhere (the COSMO/OSQP equality
+ * scaling, App. E).  log_rho: dev double [K]; rho: dev real [K][m_total]. */
+cosmo_status cosmo_rho_from_log(cosmo_batch* batch, int32_t K, const double* log_rho,
+                                double eq_scale, void* rho, void* stream);
+/* Adjoint of cosmo_rho_from_log: glog[k] = sum_r grho[k][r] * rho[k][r]
+ * (dev double [K], fixed-order reduction). */
+cosmo_status cosmo_rho_from_log_backward(cosmo_batch* batch, int32_t K, const void* rho,
+                                         const void* grho, double* glog, void* stream);
+/* alpha[k][i] = alpha_k[k]  and its adjoint galpha_k[k] = sum_i galpha[k][i]. */
+cosmo_status cosmo_alpha_broadcast(cosmo_batch* batch, int32_t K, const double* alpha_k,
+                                   void* alpha, void* stream);
+cosmo_status cosmo_alpha_reduce(cosmo_batch* batch, int32_t K, const void* galpha,
+                                double* galpha_k, void* stream);
+
+/* One end-to-end differentiable step on HOST buffers: copies the per-step
+ * parameters (and warm start) host->device, runs cosmo_rho_from_log,
+ * cosmo_alpha_broadcast, the forward with the residual loss, the backward
+ * seeded with d(sum_i loss_i) = 1, the parameter adjoints, and copies the
+ * loss and gradients device->host; synchronises the stream before returning.
+ *   log_rho_host, alpha_k_host: host double [K]
+ *   x0_host, s0_host, y0_host: host real (NULL = zero start)
+ *   loss_host: host double [ninst]; glog_rho_host, galpha_k_host: host double [K]
+ *   gx0_host, gs0_host, gy0_host: host real (NULL = not wanted)
+ * Pinned host memory makes the copies asynchronous; pageable memory works. */
+cosmo_status cosmo_step_host(cosmo_batch* batch, int32_t K, double sigma, double eq_scale,
+                             const double* log_rho_host, const double* alpha_k_host,
+                             const void* x0_host, const void* s0_host, const void* y0_host,
+                             double* loss_host, double* glog_rho_host, double* galpha_k_host,
+                             void* gx0_host, void* gs0_host, void* gy0_host, void* stream);
+
+/* Kernel timing with CUDA events on the launching stream (not a part of the
+ * method; for measurement).  kernel = NULL times every launch, "" turns
+ * timing off, otherwise only launches of that kernel class are timed.
+ * Classes: rho_check rho_rectify alpha_check precond rhs pcg post soc_fwd
+ * psd_fwd residuals loss_seed bwd_gproj soc_bwd psd_bwd bwd_relax pcg_adj
+ * bwd_solve rect_adjoint.  Timing applies to direct launches only
+ * (options.use_graph = 0); launches replayed from a CUDA graph are not timed. */
+cosmo_status cosmo_profile_enable(cosmo_batch* batch, const char* kernel);
+/* Sum of the timed durations (ms) and number of timed launches of `kernel`
+ * (NULL = all classes) since the last reset; synchronises on the recorded
+ * events.  reset = 1 clears the accumulators. */
+cosmo_status cosmo_profile_read(cosmo_batch* batch, const char* kernel, double* total_ms,
+                                int64_t* launches, int32_t reset);
+
+/* Copy per-instance flag bits (COSMO_FLAG_*) accumulated since the last
+ * cosmo_status_sync into flags_host [ninst] and clear them.  Synchronises the
+ * device.  Returns COSMO_OK even when flags are set. */
+cosmo_status cosmo_status_sync(cosmo_batch* batch, int32_t* flags_host);
+
+/* ---- standalone kernels (each is one step of the path, usable alone) ---- */
+
+/* Batched PSD projection, Eq. (psd-proj), on nblk blocks given in svec form.
+ * Block j has order p[j] and starts at svec offset off[j] of v and out
+ * (dev real, sum of p(p+1)/2 entries).  lam (dev real, sum p, may be NULL)
+ * and U (dev real, sum p^2, column-major per block, may be NULL) receive the
+ * eigen-decomposition.  p_host/off_host: host int32/int64 [nblk].
+ * precision selects float or double.  Allocates and frees its own workspace. */
+cosmo_status cosmo_psd_project(int32_t precision, int32_t nblk, const int32_t* p_host,
+                               const int64_t* off_host, const void* v, void* out,
+                               void* lam, void* U, void* stream);
+
+/* Daleckii-Krein backward, Eq. (psd-cotangent-dk): out = svec(U (L o (U' smat(g) U)) U')
+ * per block, with L the Loewner matrix of max(x, 0) at lam (gap threshold as
+ * dk_gap_tau).  Layouts as cosmo_psd_project.  Allocates nothing. */
+cosmo_status cosmo_psd_dk_backward(int32_t precision, int32_t nblk, const int32_t* p_host,
+                                   const int64_t* off_host, const void* lam, const void* U,
+                                   const void* g, void* out, double dk_gap_tau, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COSMO_DU_H */

@@ -1,0 +1,127 @@
+"""ctypes declarations of the C ABI in ``include/cosmo_du.h``.
+
+Argument marshalling only: every computation happens in ``libcosmo_du.so``.
+Loading fails loudly if the library is missing; there is no fallback path.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcosmo_du.so")
+HEADER_PATH = os.path.join(os.path.dirname(HERE), "include", "cosmo_du.h")
+
+COSMO_OK, COSMO_E_INVAL, COSMO_E_NOMEM, COSMO_E_CUDA = 0, 1, 2, 3
+COSMO_E_NOTCONV, COSMO_E_NONFINITE, COSMO_E_TIMEOUT, COSMO_E_STATE, COSMO_E_NODEVICE = 4, 5, 6, 7, 8
+STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NOTCONV",
+                5: "E_NONFINITE", 6: "E_TIMEOUT", 7: "E_STATE", 8: "E_NODEVICE"}
+PREC_MIXED, PREC_FP64 = 0, 1
+VAL_F32, VAL_BF16 = 0, 1
+FLAG_CG_CAP, FLAG_ADJ_CG_CAP, FLAG_EIG_CAP, FLAG_NONFINITE, FLAG_BAD_PARAM = 1, 2, 4, 8, 16
+
+
+class CosmoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Cone(ctypes.Structure):
+    _fields_ = [("type", c_int32), ("dim", c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("ninst", c_int32),
+                ("col_off", POINTER(c_int64)), ("row_off", POINTER(c_int64)),
+                ("P_rowptr", POINTER(c_int64)), ("P_col", POINTER(c_int32)),
+                ("P_val", POINTER(c_double)),
+                ("A_rowptr", POINTER(c_int64)), ("A_col", POINTER(c_int32)),
+                ("A_val", POINTER(c_double)),
+                ("q", POINTER(c_double)), ("b", POINTER(c_double)),
+                ("box_l", POINTER(c_double)), ("box_u", POINTER(c_double)),
+                ("cone_count", POINTER(c_int32)), ("cones", POINTER(Cone))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("value_type", c_int32), ("cg_tol", c_double),
+                ("cg_max_iter", c_int32), ("checkpoint_every", c_int32),
+                ("dk_gap_tau", c_double), ("eig_jacobi_max_p", c_int32),
+                ("eig_max_sweeps", c_int32), ("eig_tol", c_double), ("use_graph", c_int32),
+                ("device", c_int32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("ninst", c_int32), ("precision", c_int32), ("n_total", c_int64),
+                ("m_total", c_int64), ("nnzA", c_int64), ("nnzP", c_int64),
+                ("n_soc", c_int32), ("n_psd", c_int32), ("max_psd_p", c_int32),
+                ("psd_u_entries", c_int64), ("device_bytes", c_int64), ("last_K", c_int32),
+                ("tape_valid", c_int32), ("kernels_launched", c_int64)]
+
+
+_SIGS = {
+    "cosmo_version": (c_char_p, []),
+    "cosmo_kernel_launch_count": (c_int64, []),
+    "cosmo_last_error": (c_char_p, []),
+    "cosmo_options_default": (c_int32, [POINTER(Options), c_int32]),
+    "cosmo_problem_validate": (c_int32, [POINTER(Problem)]),
+    "cosmo_batch_create": (c_int32, [POINTER(Problem), POINTER(Options), POINTER(c_void_p)]),
+    "cosmo_batch_destroy": (c_int32, [c_void_p]),
+    "cosmo_batch_get_info": (c_int32, [c_void_p, POINTER(BatchInfo)]),
+    "cosmo_forward": (c_int32, [c_void_p, c_int32, POINTER(c_double), c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_int32, c_void_p]),
+    "cosmo_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cosmo_residuals": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p]),
+    "cosmo_rho_from_log": (c_int32, [c_void_p, c_int32, c_void_p, c_double, c_void_p, c_void_p]),
+    "cosmo_rho_from_log_backward": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
+                                              c_void_p]),
+    "cosmo_alpha_broadcast": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "cosmo_alpha_reduce": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "cosmo_step_host": (c_int32, [c_void_p, c_int32, c_double, c_double, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cosmo_status_sync": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "cosmo_profile_enable": (c_int32, [c_void_p, c_char_p]),
+    "cosmo_profile_read": (c_int32, [c_void_p, c_char_p, POINTER(c_double), POINTER(c_int64),
+                                     c_int32]),
+    "cosmo_psd_project": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cosmo_psd_dk_backward": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
+                                        c_void_p, c_void_p, c_void_p, c_void_p, c_double,
+                                        c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2606_13825_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != COSMO_OK:
+        msg = lib().cosmo_last_error().decode(errors="replace")
+        raise CosmoError(status, msg)
+    return status
+
+
+def header_functions():
+    """Names of the functions declared in include/cosmo_du.h."""
+    import re
+    txt = open(HEADER_PATH).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cosmo_[a-z0-9_]+)\s*\(", txt)))

@@ -1,0 +1,607 @@
+// Sparse and elementwise kernels of the unrolled COSMO iteration
+// (Sec. 2.2-2.3) and of its reverse pass.
+//
+// Layout: instances are concatenated; x-like vectors have n_total entries,
+// s/y-like vectors m_total.  A is CSR over rows, A' is a second CSR (rows =
+// variables) so that every product is a gather (coalesced over rows, no
+// atomics, bitwise reproducible).  Per-row loops use one thread per row:
+// the rows of the paper's problem classes hold few nonzeros.
+#pragma once
+
+#include "common.cuh"
+
+namespace cosmo {
+
+// ---------------------------------------------------------------------------
+// a1: rho preparation (App. E rectification), parameter checks, and the
+//     Jacobi preconditioner d = diag(P) + sigma + (A o A)' rho (App. D)
+// ---------------------------------------------------------------------------
+template <class T, class V>
+__global__ void k_rho_copy_check(Prob<T, V> P, int32_t K, const T* __restrict__ rho_in,
+                                 T* __restrict__ rho_rect, int32_t* flags) {
+  const int64_t tot = (int64_t)K * P.m_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T v = rho_in[e];
+    if (!(v > T(0)) || !finite_(v)) {
+      atomicOr(&flags[P.row_inst[e % P.m_total]], F_BAD_PARAM);
+    }
+    rho_rect[e] = v;
+  }
+}
+
+// one warp per (step, SOC/PSD block): replace the rows by their mean
+template <class T, class V>
+__global__ void k_rho_rectify(Prob<T, V> P, int32_t K, const T* __restrict__ rho_in,
+                              T* __restrict__ rho_rect) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)K * P.nrect) return;
+  const int32_t k = (int32_t)(w / P.nrect), c = (int32_t)(w % P.nrect);
+  const int64_t r0 = P.rect_row0[c];
+  const int32_t nr = P.rect_rows[c];
+  const T* src = rho_in + (int64_t)k * P.m_total + r0;
+  double acc = 0.0;
+  for (int32_t i = lane; i < nr; i += 32) acc += (double)src[i];
+  acc = warp_sum(acc);
+  const T mean = (T)(acc / (double)nr);
+  T* dst = rho_rect + (int64_t)k * P.m_total + r0;
+  for (int32_t i = lane; i < nr; i += 32) dst[i] = mean;
+}
+
+template <class T, class V>
+__global__ void k_alpha_check(Prob<T, V> P, int32_t K, const T* __restrict__ alpha,
+                              int32_t* flags) {
+  const int64_t tot = (int64_t)K * P.ninst;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T a = alpha[e];
+    if (!(a > T(0) && a < T(2))) atomicOr(&flags[e % P.ninst], F_BAD_PARAM);
+  }
+}
+
+// dinv[k][j] = 1 / (P_jj + sigma_k + sum_r A_rj^2 rho_k[r])
+template <class T, class V>
+__global__ void k_precond(Prob<T, V> P, int32_t K, const double* __restrict__ sigma,
+                          const T* __restrict__ rho_rect, T* __restrict__ dinv) {
+  const int64_t tot = (int64_t)K * P.n_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = (int32_t)(e / P.n_total);
+    const int64_t j = e % P.n_total;
+    const T* rho = rho_rect + (int64_t)k * P.m_total;
+    T acc = P.Pdiag[j] + (T)sigma[k];
+    for (int64_t q = P.AT_rp[j]; q < P.AT_rp[j + 1]; ++q) {
+      T a = (T)ldv(P.AT_v, q);
+      acc += a * a * rho[P.AT_ci[q]];
+    }
+    dinv[e] = T(1) / acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3: xi = sigma x - q + A'(y + rho o (b - s))      (Sec. 2.3, Eq. reduced)
+// ---------------------------------------------------------------------------
+template <class T, class V>
+__global__ void k_rhs(Prob<T, V> P, double sigma, const T* __restrict__ x,
+                      const T* __restrict__ s, const T* __restrict__ y,
+                      const T* __restrict__ rho, T* __restrict__ xi) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.n_total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    T acc = (T)sigma * x[j] - P.q[j];
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) {
+      const int32_t r = P.AT_ci[e];
+      acc += (T)ldv(P.AT_v, e) * (y[r] + rho[r] * (P.b[r] - s[r]));
+    }
+    xi[j] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a4 / b5: Jacobi-preconditioned CG on M = P + sigma I + A'D(rho)A, one CTA
+// per instance, persistent over the CG iterations (no host round trip, no
+// inter-CTA waits).  Inner products and the stopping test are in double.
+// Stops when ||r||_2 <= tol ||rhs||_2 (recursively updated residual) or at
+// maxit (flag bit).  x holds the warm start on entry unless zero_start.
+// ---------------------------------------------------------------------------
+template <class T>
+struct CgArgs {
+  const T* rhs;      // [n_total]
+  T* x;              // [n_total] out: solution
+  const T* x0;       // [n_total] warm start copied into x first (null: x holds it)
+  const T* rho;      // [m_total] rectified
+  const T* dinv;     // [n_total]
+  double sigma;
+  T* r; T* p; T* u;  // [n_total] workspace
+  T* t;              // [m_total] workspace
+  double tol;
+  int32_t maxit;
+  int32_t zero_start;
+  int32_t flag_bit;
+  int32_t* flags;
+  int32_t* iters;    // [ninst] CG iterations used (may be null)
+};
+
+// u = M v on the columns [c0, c1) of one instance (rows [r0, r1)); CTA-wide.
+template <class T, class V>
+__device__ __forceinline__ void cta_matvec(const Prob<T, V>& P, const CgArgs<T>& a,
+                                           const T* __restrict__ v, T* __restrict__ u,
+                                           int64_t c0, int64_t c1, int64_t r0, int64_t r1) {
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    T acc = T(0);
+    for (int64_t e = P.A_rp[r]; e < P.A_rp[r + 1]; ++e) acc += (T)ldv(P.A_v, e) * v[P.A_ci[e]];
+    a.t[r] = a.rho[r] * acc;
+  }
+  __syncthreads();
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+    T acc = (T)a.sigma * v[j];
+    if (P.P_rp) {
+      for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e) acc += (T)ldv(P.P_v, e) * v[P.P_ci[e]];
+    }
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) acc += (T)ldv(P.AT_v, e) * a.t[P.AT_ci[e]];
+    u[j] = acc;
+  }
+  __syncthreads();
+}
+
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
+  __shared__ double sm[3 * (NT / 32)];
+  const int32_t inst = P.inst_sched[blockIdx.x];
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  if (c1 == c0) return;
+  T* __restrict__ x = a.x;
+  T* __restrict__ r = a.r;
+  T* __restrict__ p = a.p;
+  T* __restrict__ u = a.u;
+  if (a.zero_start) {
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) x[j] = T(0);
+  } else {
+    if (a.x0 && a.x0 != a.x)
+      for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) x[j] = a.x0[j];
+    __syncthreads();
+    cta_matvec(P, a, x, u, c0, c1, r0, r1);
+  }
+  double s3[3] = {0.0, 0.0, 0.0};   // rz, rr, bb
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+    const T bj = a.rhs[j];
+    const T rj = a.zero_start ? bj : bj - u[j];
+    const T zj = a.dinv[j] * rj;
+    r[j] = rj;
+    p[j] = zj;
+    s3[0] += (double)rj * (double)zj;
+    s3[1] += (double)rj * (double)rj;
+    s3[2] += (double)bj * (double)bj;
+  }
+  block_sum<3>(s3, sm);
+  double rz = s3[0], rr = s3[1];
+  const double thr = a.tol * a.tol * s3[2];
+  int32_t it = 0;
+  if (s3[2] == 0.0) {
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) x[j] = T(0);
+    rr = 0.0;
+  }
+  while (rr > thr && it < a.maxit) {
+    cta_matvec(P, a, p, u, c0, c1, r0, r1);
+    double s1[1] = {0.0};
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) s1[0] += (double)p[j] * (double)u[j];
+    block_sum<1>(s1, sm);
+    if (!(s1[0] > 0.0)) break;  // breakdown (p = 0 or non-finite): stop, flagged below
+    const T al = (T)(rz / s1[0]);
+    double s2[2] = {0.0, 0.0};
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+      x[j] += al * p[j];
+      const T rj = r[j] - al * u[j];
+      r[j] = rj;
+      const T zj = a.dinv[j] * rj;
+      s2[0] += (double)rj * (double)zj;
+      s2[1] += (double)rj * (double)rj;
+    }
+    block_sum<2>(s2, sm);
+    const T be = (T)(s2[0] / rz);
+    rz = s2[0];
+    rr = s2[1];
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) p[j] = a.dinv[j] * r[j] + be * p[j];
+    __syncthreads();
+    ++it;
+  }
+  if (threadIdx.x == 0) {
+    if (rr > thr) atomicOr(&a.flags[inst], a.flag_bit);
+    if (!(rr == rr)) atomicOr(&a.flags[inst], F_NONFINITE);
+    if (a.iters) a.iters[inst] = it;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a5, a6 (separable cones), a8: s~ = b - A x~, relaxation, projection of
+// v = alpha s~ + (1-alpha) s + y/rho on zero / orthant / box rows, dual update;
+// x+ = alpha x~ + (1 - alpha) x.  SOC and PSD rows only store s~ here.
+// ---------------------------------------------------------------------------
+template <class T>
+struct StepPtrs {
+  const T* x; const T* s; const T* y;   // z^k
+  T* xn; T* sn; T* yn;                  // z^{k+1}
+  const T* rho;                         // rectified rho^k [m_total]
+  const T* alpha;                       // [ninst]
+  const T* xt;                          // x~ [n_total]
+  T* st;                                // s~ [m_total] (tape)
+  T* lam; T* U;                         // PSD eigen tape slot
+  int32_t* flags;
+};
+
+template <class T, class V>
+__global__ void k_post(Prob<T, V> P, StepPtrs<T> q) {
+  const int64_t tot = P.m_total + P.n_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < P.m_total) {
+      const int64_t r = e;
+      T acc = T(0);
+      for (int64_t k = P.A_rp[r]; k < P.A_rp[r + 1]; ++k) acc += (T)ldv(P.A_v, k) * q.xt[P.A_ci[k]];
+      const T st = P.b[r] - acc;
+      q.st[r] = st;
+      const uint8_t kind = P.row_kind[r];
+      if (kind <= K_BOX) {
+        const T al = q.alpha[P.row_inst[r]];
+        const T rh = q.rho[r];
+        const T sh = al * st + (T(1) - al) * q.s[r];
+        const T v = sh + q.y[r] / rh;
+        T sp;
+        if (kind == K_ZERO) sp = T(0);
+        else if (kind == K_NONNEG) sp = v > T(0) ? v : T(0);
+        else sp = fmin(fmax(v, P.box_l[r]), P.box_u[r]);
+        const T yn = q.y[r] + rh * (sh - sp);
+        q.sn[r] = sp;
+        q.yn[r] = yn;
+        if (!finite_(yn) || !finite_(sp)) atomicOr(&q.flags[P.row_inst[r]], F_NONFINITE);
+      }
+    } else {
+      const int64_t j = e - P.m_total;
+      const T al = q.alpha[P.col_inst[j]];
+      q.xn[j] = al * q.xt[j] + (T(1) - al) * q.x[j];
+    }
+  }
+}
+
+// a6 (SOC): one warp per cone {(t, u): ||u|| <= t}
+template <class T, class V>
+__global__ void k_soc_fwd(Prob<T, V> P, StepPtrs<T> q) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= P.nsoc) return;
+  const int64_t r0 = P.soc_row0[w];
+  const int32_t d = P.soc_dim[w];
+  const int32_t inst = P.row_inst[r0];
+  const T al = q.alpha[inst], rh = q.rho[r0];
+  double nu2 = 0.0;
+  for (int32_t i = 1 + lane; i < d; i += 32) {
+    const int64_t r = r0 + i;
+    const T v = al * q.st[r] + (T(1) - al) * q.s[r] + q.y[r] / rh;
+    nu2 += (double)v * (double)v;
+  }
+  nu2 = warp_sum(nu2);
+  const T t = al * q.st[r0] + (T(1) - al) * q.s[r0] + q.y[r0] / rh;
+  const double nu = sqrt(nu2);
+  int mode;  // 0 identity, 1 zero, 2 boundary projection
+  if (nu <= (double)t) mode = 0;
+  else if (nu <= -(double)t) mode = 1;
+  else mode = 2;
+  const T scale = mode == 2 ? (T)(0.5 * (1.0 + (double)t / nu)) : T(0);
+  for (int32_t i = lane; i < d; i += 32) {
+    const int64_t r = r0 + i;
+    const T sh = al * q.st[r] + (T(1) - al) * q.s[r];
+    const T v = sh + q.y[r] / rh;
+    T sp;
+    if (mode == 0) sp = v;
+    else if (mode == 1) sp = T(0);
+    else sp = scale * (i == 0 ? (T)nu : v);
+    const T yn = q.y[r] + rh * (sh - sp);
+    q.sn[r] = sp;
+    q.yn[r] = yn;
+    if (!finite_(yn)) atomicOr(&q.flags[inst], F_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a9: residuals r_p = A x + s - b, r_d = P x + q - A'y (App. E; sign fixed by
+// the fixed point of Sec. 2.2), per-instance ||r_p||^2, ||r_d||^2 and the
+// objective 1/2 x'Px + q'x; one CTA per instance, double accumulation.
+// ---------------------------------------------------------------------------
+template <class T>
+struct ResArgs {
+  const T* x; const T* s; const T* y;
+  T* rp; T* rd;        // stored residual vectors (may be null)
+  double* rp2; double* rd2; double* obj; double* loss;  // [ninst] each, may be null
+};
+
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_residuals(Prob<T, V> P, ResArgs<T> a) {
+  __shared__ double sm[3 * (NT / 32)];
+  const int32_t inst = blockIdx.x;
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
+    T v = a.s[r] - P.b[r];
+    for (int64_t e = P.A_rp[r]; e < P.A_rp[r + 1]; ++e) v += (T)ldv(P.A_v, e) * a.x[P.A_ci[e]];
+    if (a.rp) a.rp[r] = v;
+    acc[0] += (double)v * (double)v;
+  }
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    T px = T(0);
+    if (P.P_rp) {
+      for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e) px += (T)ldv(P.P_v, e) * a.x[P.P_ci[e]];
+    }
+    T aty = T(0);
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) aty += (T)ldv(P.AT_v, e) * a.y[P.AT_ci[e]];
+    const T v = px + P.q[j] - aty;
+    if (a.rd) a.rd[j] = v;
+    acc[1] += (double)v * (double)v;
+    acc[2] += 0.5 * (double)a.x[j] * (double)px + (double)P.q[j] * (double)a.x[j];
+  }
+  block_sum<3>(acc, sm);
+  if (threadIdx.x == 0) {
+    if (a.rp2) a.rp2[inst] = acc[0];
+    if (a.rd2) a.rd2[inst] = acc[1];
+    if (a.obj) a.obj[inst] = acc[2];
+    if (a.loss) a.loss[inst] = acc[0] + acc[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// b1: loss backward.  d/dx = 2 (A'r_p + P r_d), d/ds = 2 r_p, d/dy = -2 A r_d,
+// each times the per-instance loss cotangent, plus the caller's cotangents.
+// ---------------------------------------------------------------------------
+template <class T>
+struct SeedArgs {
+  const T* rp; const T* rd; const double* gloss;   // gloss may be null
+  const T* gx; const T* gs; const T* gy;           // may be null
+  T* xb; T* sb; T* yb;
+};
+
+template <class T, class V>
+__global__ void k_loss_seed(Prob<T, V> P, SeedArgs<T> a) {
+  const int64_t tot = P.m_total + P.n_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < P.m_total) {
+      const int64_t r = e;
+      const T g = a.gloss ? (T)a.gloss[P.row_inst[r]] : T(0);
+      T ys = a.gy ? a.gy[r] : T(0);
+      T ss = a.gs ? a.gs[r] : T(0);
+      if (a.gloss) {
+        T ard = T(0);
+        for (int64_t k = P.A_rp[r]; k < P.A_rp[r + 1]; ++k) ard += (T)ldv(P.A_v, k) * a.rd[P.A_ci[k]];
+        ys -= T(2) * g * ard;
+        ss += T(2) * g * a.rp[r];
+      }
+      a.yb[r] = ys;
+      a.sb[r] = ss;
+    } else {
+      const int64_t j = e - P.m_total;
+      T xs = a.gx ? a.gx[j] : T(0);
+      if (a.gloss) {
+        const T g = (T)a.gloss[P.col_inst[j]];
+        T acc = T(0);
+        for (int64_t k = P.AT_rp[j]; k < P.AT_rp[j + 1]; ++k) acc += (T)ldv(P.AT_v, k) * a.rp[P.AT_ci[k]];
+        if (P.P_rp) {
+          for (int64_t k = P.P_rp[j]; k < P.P_rp[j + 1]; ++k) acc += (T)ldv(P.P_v, k) * a.rd[P.P_ci[k]];
+        }
+        xs += T(2) * g * acc;
+      }
+      a.xb[j] = xs;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse pass of one iteration.  Cotangents of z^{k+1} come in (xb, sb, yb);
+// those of z^k go out (xb2, sb2, yb2), together with rho-bar (per row, before
+// the rectification adjoint) and alpha-bar (per instance).
+// ---------------------------------------------------------------------------
+template <class T>
+struct BwdPtrs {
+  const T* x; const T* s; const T* y;   // z^k
+  const T* sn;                          // s^{k+1}
+  const T* rho; const T* alpha; double sigma;
+  const T* xt; const T* st;             // tape
+  const T* lam; const T* U;
+  const T* xb; const T* sb; const T* yb;   // cotangents of z^{k+1}
+  T* xb2; T* sb2; T* yb2;                  // cotangents of z^k
+  T* gproj;  // [m_total] cotangent reaching the projection output
+  T* vbar;   // [m_total] cotangent of the projection input v
+  T* adjrhs; // [n_total] -x~bar
+  const T* lamt; // [n_total] adjoint solution lambda~
+  T* grho;   // [m_total] rho-bar of this step (unrectified later)
+  T* galpha; // [ninst]
+  int32_t* flags;
+  double dk_tau;
+};
+
+// b2 (first half) + b3 separable: g = s+bar - rho y+bar; vbar = mask(v) g
+template <class T, class V>
+__global__ void k_bwd_gproj(Prob<T, V> P, BwdPtrs<T> q) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.m_total;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const T rh = q.rho[r];
+    const T g = q.sb[r] - rh * q.yb[r];
+    q.gproj[r] = g;
+    const uint8_t kind = P.row_kind[r];
+    if (kind <= K_BOX) {
+      const T al = q.alpha[P.row_inst[r]];
+      const T v = al * q.st[r] + (T(1) - al) * q.s[r] + q.y[r] / rh;
+      bool pass;
+      if (kind == K_ZERO) pass = false;
+      else if (kind == K_NONNEG) pass = v > T(0);
+      else pass = (v > P.box_l[r]) && (v < P.box_u[r]);
+      q.vbar[r] = pass ? g : T(0);
+    }
+  }
+}
+
+// b3 (SOC): vbar = J' g with the closed-form Jacobian of the SOC projection
+template <class T, class V>
+__global__ void k_soc_bwd(Prob<T, V> P, BwdPtrs<T> q) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= P.nsoc) return;
+  const int64_t r0 = P.soc_row0[w];
+  const int32_t d = P.soc_dim[w];
+  const int32_t inst = P.row_inst[r0];
+  const T al = q.alpha[inst], rh = q.rho[r0];
+  double nu2 = 0.0, ug = 0.0;
+  for (int32_t i = 1 + lane; i < d; i += 32) {
+    const int64_t r = r0 + i;
+    const T v = al * q.st[r] + (T(1) - al) * q.s[r] + q.y[r] / rh;
+    nu2 += (double)v * (double)v;
+    ug += (double)v * (double)q.gproj[r];
+  }
+  nu2 = warp_sum(nu2);
+  ug = warp_sum(ug);
+  const T t = al * q.st[r0] + (T(1) - al) * q.s[r0] + q.y[r0] / rh;
+  const double nu = sqrt(nu2);
+  int mode;
+  if (nu <= (double)t) mode = 0;
+  else if (nu <= -(double)t) mode = 1;
+  else mode = 2;
+  const double g0 = (double)q.gproj[r0];
+  const double uhg = mode == 2 ? ug / nu : 0.0;     // u^' g_u
+  const double tn = mode == 2 ? (double)t / nu : 0.0;
+  for (int32_t i = lane; i < d; i += 32) {
+    const int64_t r = r0 + i;
+    T out;
+    if (mode == 0) out = q.gproj[r];
+    else if (mode == 1) out = T(0);
+    else if (i == 0) out = (T)(0.5 * (g0 + uhg));
+    else {
+      const T v = al * q.st[r] + (T(1) - al) * q.s[r] + q.y[r] / rh;
+      const double uh = (double)v / nu;
+      out = (T)(0.5 * (g0 * uh + (1.0 + tn) * (double)q.gproj[r] - tn * uh * uhg));
+    }
+    q.vbar[r] = out;
+  }
+}
+
+// b2 (rest) + b4: per instance (one CTA), fixed-order alpha-bar reduction.
+//   shat_bar = rho y+bar + vbar ;  s~bar = alpha shat_bar
+//   ybar_part = y+bar + vbar / rho ; sbar_part = (1-alpha) shat_bar
+//   rhobar_part = y+bar (shat - s+) - vbar y / rho^2
+//   x~bar = alpha x+bar - A' s~bar ; xbar_part = (1-alpha) x+bar
+//   alpha_bar = <shat_bar, s~ - s> + <x+bar, x~ - x>
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
+  __shared__ double sm[NT / 32];
+  const int32_t inst = blockIdx.x;
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  const T al = q.alpha[inst];
+  double acc[1] = {0.0};
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
+    const T rh = q.rho[r];
+    const T yb = q.yb[r], vb = q.vbar[r];
+    const T shb = rh * yb + vb;
+    const T s = q.s[r], st = q.st[r], y = q.y[r];
+    const T sh = al * st + (T(1) - al) * s;
+    q.yb2[r] = yb + vb / rh;
+    q.sb2[r] = (T(1) - al) * shb;
+    q.grho[r] = yb * (sh - q.sn[r]) - vb * y / (rh * rh);
+    acc[0] += (double)shb * (double)(st - s);
+    if (!finite_(shb)) atomicOr(&q.flags[inst], F_NONFINITE);
+  }
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    const T xb = q.xb[j];
+    T acc2 = al * xb;
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) {
+      const int32_t r = P.AT_ci[e];
+      acc2 -= (T)ldv(P.AT_v, e) * (al * (q.rho[r] * q.yb[r] + q.vbar[r]));
+    }
+    q.adjrhs[j] = -acc2;
+    q.xb2[j] = (T(1) - al) * xb;
+    acc[0] += (double)xb * (double)(q.xt[j] - q.x[j]);
+  }
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) q.galpha[inst] = (T)acc[0];
+}
+
+// b5 (after the adjoint CG): w = A lambda~;  rho-bar += w o (s - s~)
+// (the implicit rule (A lam)(A x~) plus the RHS chain), y-bar -= w,
+// s-bar += rho w, x-bar -= sigma lambda~.
+template <class T, class V>
+__global__ void k_bwd_solve(Prob<T, V> P, BwdPtrs<T> q) {
+  const int64_t tot = P.m_total + P.n_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < P.m_total) {
+      const int64_t r = e;
+      T w = T(0);
+      for (int64_t k = P.A_rp[r]; k < P.A_rp[r + 1]; ++k) w += (T)ldv(P.A_v, k) * q.lamt[P.A_ci[k]];
+      q.grho[r] += w * (q.s[r] - q.st[r]);
+      q.yb2[r] -= w;
+      q.sb2[r] += q.rho[r] * w;
+    } else {
+      const int64_t j = e - P.m_total;
+      q.xb2[j] -= (T)q.sigma * q.lamt[j];
+    }
+  }
+}
+
+// b6: adjoint of the rectification over all K steps: every row of a SOC/PSD
+// block receives the block mean of rho-bar.  One warp per (step, block).
+template <class T, class V>
+__global__ void k_rect_adjoint(Prob<T, V> P, int32_t K, T* __restrict__ g) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)K * P.nrect) return;
+  const int32_t k = (int32_t)(w / P.nrect), c = (int32_t)(w % P.nrect);
+  T* dst = g + (int64_t)k * P.m_total + P.rect_row0[c];
+  const int32_t nr = P.rect_rows[c];
+  double acc = 0.0;
+  for (int32_t i = lane; i < nr; i += 32) acc += (double)dst[i];
+  acc = warp_sum(acc);
+  __syncwarp();
+  const T mean = (T)(acc / (double)nr);
+  for (int32_t i = lane; i < nr; i += 32) dst[i] = mean;
+}
+
+// ---------------------------------------------------------------------------
+// parameter maps for per-iteration learnable scalars
+// ---------------------------------------------------------------------------
+template <class T, class V>
+__global__ void k_rho_from_log(Prob<T, V> P, int32_t K, const double* __restrict__ logr,
+                               double eq_scale, T* __restrict__ rho) {
+  const int64_t tot = (int64_t)K * P.m_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = (int32_t)(e / P.m_total);
+    const int64_t r = e % P.m_total;
+    const double base = exp(logr[k]);
+    rho[e] = (T)(P.row_kind[r] == K_ZERO ? eq_scale * base : base);
+  }
+}
+
+// glog[k] = sum_r grho[k][r] rho[k][r]; one CTA per step, fixed order.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_rowsum_prod(int64_t m, const T* __restrict__ a,
+                                                    const T* __restrict__ b,
+                                                    double* __restrict__ out) {
+  __shared__ double sm[NT / 32];
+  const int32_t k = blockIdx.x;
+  double acc[1] = {0.0};
+  const T* ak = a + (int64_t)k * m;
+  const T* bk = b ? b + (int64_t)k * m : nullptr;
+  for (int64_t r = threadIdx.x; r < m; r += NT) acc[0] += (double)ak[r] * (bk ? (double)bk[r] : 1.0);
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) out[k] = acc[0];
+}
+
+template <class T>
+__global__ void k_broadcast(int32_t K, int32_t w, const double* __restrict__ src,
+                            T* __restrict__ dst) {
+  const int64_t tot = (int64_t)K * w;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e / w];
+}
+
+}  // namespace cosmo

@@ -1,0 +1,1217 @@
+// Host runtime of the C ABI declared in include/cosmo_du.h: problem
+// validation, batch construction (A' in CSR, cone schedules, row/column
+// instance maps), the tape of the unrolled iteration (with checkpoint
+// segments), the forward/backward launch sequences, and CUDA-graph capture.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/cosmo_du.h"
+#include "common.cuh"
+#include "kernels_psd.cuh"
+#include "kernels_vec.cuh"
+
+using namespace cosmo;
+
+// ------------------------------------------------------------ errors ----
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+static cosmo_status fail(cosmo_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(COSMO_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                            \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    cosmo_status s_ = (expr);         \
+    if (s_ != COSMO_OK) return s_;    \
+  } while (0)
+
+static int grid_for(int64_t work, int threads, int cap = 148 * 16) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+static int64_t svec_rows(int64_t p) { return p * (p + 1) / 2; }
+static int64_t cone_rows(const cosmo_cone& c) {
+  return c.type == COSMO_CONE_PSD ? svec_rows(c.dim) : (int64_t)c.dim;
+}
+
+// --------------------------------------------------------- validation ---
+static cosmo_status validate(const cosmo_problem* pr) {
+  if (!pr) return fail(COSMO_E_INVAL, "problem is NULL");
+  if (pr->ninst < 1) return fail(COSMO_E_INVAL, "ninst must be >= 1");
+  if (!pr->col_off || !pr->row_off || !pr->A_rowptr || !pr->cone_count || !pr->q || !pr->b)
+    return fail(COSMO_E_INVAL, "required problem array is NULL");
+  const int32_t ni = pr->ninst;
+  if (pr->col_off[0] != 0 || pr->row_off[0] != 0)
+    return fail(COSMO_E_INVAL, "col_off[0] and row_off[0] must be 0");
+  for (int32_t i = 0; i < ni; ++i) {
+    if (pr->col_off[i + 1] < pr->col_off[i] || pr->row_off[i + 1] < pr->row_off[i])
+      return fail(COSMO_E_INVAL, "offsets of instance %d decrease", i);
+    if (pr->cone_count[i] < 0) return fail(COSMO_E_INVAL, "negative cone count");
+  }
+  const int64_t n = pr->col_off[ni], m = pr->row_off[ni];
+  if (n > INT32_MAX || m > INT32_MAX) return fail(COSMO_E_INVAL, "n or m exceeds int32 indexing");
+  // A: CSR bounds and block-diagonal structure
+  if (pr->A_rowptr[0] != 0) return fail(COSMO_E_INVAL, "A_rowptr[0] != 0");
+  int64_t nnzA = pr->A_rowptr[m];
+  if (nnzA < 0) return fail(COSMO_E_INVAL, "bad A nnz");
+  if (nnzA > 0 && (!pr->A_col || !pr->A_val)) return fail(COSMO_E_INVAL, "A_col/A_val NULL");
+  for (int32_t i = 0; i < ni; ++i) {
+    for (int64_t r = pr->row_off[i]; r < pr->row_off[i + 1]; ++r) {
+      if (pr->A_rowptr[r + 1] < pr->A_rowptr[r]) return fail(COSMO_E_INVAL, "A_rowptr decreases at row %lld", (long long)r);
+      for (int64_t e = pr->A_rowptr[r]; e < pr->A_rowptr[r + 1]; ++e) {
+        const int64_t c = pr->A_col[e];
+        if (c < pr->col_off[i] || c >= pr->col_off[i + 1])
+          return fail(COSMO_E_INVAL, "A row %lld references column %lld outside instance %d", (long long)r, (long long)c, i);
+        if (!std::isfinite(pr->A_val[e])) return fail(COSMO_E_INVAL, "non-finite A value");
+      }
+    }
+  }
+  if (pr->P_rowptr) {
+    if (pr->P_rowptr[0] != 0) return fail(COSMO_E_INVAL, "P_rowptr[0] != 0");
+    const int64_t nnzP = pr->P_rowptr[n];
+    if (nnzP > 0 && (!pr->P_col || !pr->P_val)) return fail(COSMO_E_INVAL, "P_col/P_val NULL");
+    for (int32_t i = 0; i < ni; ++i)
+      for (int64_t j = pr->col_off[i]; j < pr->col_off[i + 1]; ++j) {
+        if (pr->P_rowptr[j + 1] < pr->P_rowptr[j]) return fail(COSMO_E_INVAL, "P_rowptr decreases");
+        for (int64_t e = pr->P_rowptr[j]; e < pr->P_rowptr[j + 1]; ++e) {
+          const int64_t c = pr->P_col[e];
+          if (c < pr->col_off[i] || c >= pr->col_off[i + 1])
+            return fail(COSMO_E_INVAL, "P row %lld references column %lld outside instance %d", (long long)j, (long long)c, i);
+          if (!std::isfinite(pr->P_val[e])) return fail(COSMO_E_INVAL, "non-finite P value");
+        }
+      }
+  }
+  for (int64_t j = 0; j < n; ++j)
+    if (!std::isfinite(pr->q[j])) return fail(COSMO_E_INVAL, "non-finite q");
+  for (int64_t r = 0; r < m; ++r)
+    if (!std::isfinite(pr->b[r])) return fail(COSMO_E_INVAL, "non-finite b");
+  // cones
+  int64_t ci = 0;
+  bool has_box = false;
+  for (int32_t i = 0; i < ni; ++i) {
+    int64_t rows = 0;
+    for (int32_t c = 0; c < pr->cone_count[i]; ++c, ++ci) {
+      if (!pr->cones) return fail(COSMO_E_INVAL, "cones NULL");
+      const cosmo_cone& cn = pr->cones[ci];
+      if (cn.type < COSMO_CONE_ZERO || cn.type > COSMO_CONE_PSD)
+        return fail(COSMO_E_INVAL, "unknown cone type %d", cn.type);
+      if (cn.dim < 1) return fail(COSMO_E_INVAL, "cone dimension must be >= 1");
+      if (cn.type == COSMO_CONE_PSD && cn.dim > 1024) return fail(COSMO_E_INVAL, "PSD order above 1024");
+      if (cn.type == COSMO_CONE_BOX) has_box = true;
+      rows += cone_rows(cn);
+    }
+    if (rows != pr->row_off[i + 1] - pr->row_off[i])
+      return fail(COSMO_E_INVAL, "cones of instance %d cover %lld rows, instance has %lld", i,
+                  (long long)rows, (long long)(pr->row_off[i + 1] - pr->row_off[i]));
+  }
+  if (has_box) {
+    if (!pr->box_l || !pr->box_u) return fail(COSMO_E_INVAL, "box cone without bounds");
+    ci = 0;
+    for (int32_t i = 0; i < ni; ++i) {
+      int64_t r = pr->row_off[i];
+      for (int32_t c = 0; c < pr->cone_count[i]; ++c, ++ci) {
+        const cosmo_cone& cn = pr->cones[ci];
+        const int64_t k = cone_rows(cn);
+        if (cn.type == COSMO_CONE_BOX)
+          for (int64_t t = r; t < r + k; ++t)
+            if (!(pr->box_l[t] <= pr->box_u[t])) return fail(COSMO_E_INVAL, "box bound l > u at row %lld", (long long)t);
+        r += k;
+      }
+    }
+  }
+  return COSMO_OK;
+}
+
+// --------------------------------------------------------- allocation ---
+struct DevArena {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  ~DevArena() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+  template <class X>
+  cosmo_status alloc(X** out, int64_t count) {
+    *out = nullptr;
+    if (count <= 0) return COSMO_OK;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(X));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(COSMO_E_NOMEM, "cudaMalloc of %lld bytes failed: %s",
+                  (long long)(count * (int64_t)sizeof(X)), cudaGetErrorString(e));
+    }
+    ptrs.push_back(p);
+    bytes += count * (int64_t)sizeof(X);
+    *out = reinterpret_cast<X*>(p);
+    return COSMO_OK;
+  }
+  template <class X>
+  cosmo_status upload(X** out, const std::vector<X>& h) {
+    TRY(alloc(out, (int64_t)h.size()));
+    if (!h.empty()) CU(cudaMemcpy(*out, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice));
+    return COSMO_OK;
+  }
+};
+
+// ------------------------------------------------------ host structure ---
+struct HostPlan {
+  int32_t ninst = 0;
+  int64_t n = 0, m = 0;
+  std::vector<int64_t> col_off, row_off;
+  std::vector<int32_t> row_inst, col_inst;
+  std::vector<uint8_t> row_kind;
+  std::vector<int64_t> A_rp, AT_rp, P_rp;
+  std::vector<int32_t> A_ci, AT_ci, P_ci;
+  std::vector<double> A_v, AT_v, P_v, Pdiag, q, b, bl, bu;
+  bool has_P = false, has_box = false;
+  std::vector<int64_t> soc_row0; std::vector<int32_t> soc_dim;
+  std::vector<int64_t> psd_row0, psd_loff, psd_uoff; std::vector<int32_t> psd_p, psd_sched;
+  std::vector<int64_t> rect_row0; std::vector<int32_t> rect_rows;
+  std::vector<int32_t> inst_sched;
+  int64_t sum_p = 0, sum_p2 = 0;
+  int32_t max_p = 0;
+};
+
+static void build_plan(const cosmo_problem* pr, HostPlan& h) {
+  const int32_t ni = pr->ninst;
+  h.ninst = ni;
+  h.n = pr->col_off[ni];
+  h.m = pr->row_off[ni];
+  h.col_off.assign(pr->col_off, pr->col_off + ni + 1);
+  h.row_off.assign(pr->row_off, pr->row_off + ni + 1);
+  h.row_inst.resize(h.m);
+  h.col_inst.resize(h.n);
+  for (int32_t i = 0; i < ni; ++i) {
+    for (int64_t r = h.row_off[i]; r < h.row_off[i + 1]; ++r) h.row_inst[r] = i;
+    for (int64_t j = h.col_off[i]; j < h.col_off[i + 1]; ++j) h.col_inst[j] = i;
+  }
+  // A and its transpose (stable counting sort by column: entries of each A'
+  // row come in increasing row order)
+  const int64_t nnzA = pr->A_rowptr[h.m];
+  h.A_rp.assign(pr->A_rowptr, pr->A_rowptr + h.m + 1);
+  h.A_ci.assign(pr->A_col, pr->A_col + nnzA);
+  h.A_v.assign(pr->A_val, pr->A_val + nnzA);
+  h.AT_rp.assign(h.n + 1, 0);
+  for (int64_t e = 0; e < nnzA; ++e) h.AT_rp[h.A_ci[e] + 1]++;
+  for (int64_t j = 0; j < h.n; ++j) h.AT_rp[j + 1] += h.AT_rp[j];
+  h.AT_ci.resize(nnzA);
+  h.AT_v.resize(nnzA);
+  {
+    std::vector<int64_t> pos(h.AT_rp.begin(), h.AT_rp.end() - 1);
+    for (int64_t r = 0; r < h.m; ++r)
+      for (int64_t e = h.A_rp[r]; e < h.A_rp[r + 1]; ++e) {
+        const int64_t c = h.A_ci[e];
+        h.AT_ci[pos[c]] = (int32_t)r;
+        h.AT_v[pos[c]] = h.A_v[e];
+        pos[c]++;
+      }
+  }
+  h.Pdiag.assign(h.n, 0.0);
+  if (pr->P_rowptr && pr->P_rowptr[h.n] > 0) {
+    h.has_P = true;
+    const int64_t nnzP = pr->P_rowptr[h.n];
+    h.P_rp.assign(pr->P_rowptr, pr->P_rowptr + h.n + 1);
+    h.P_ci.assign(pr->P_col, pr->P_col + nnzP);
+    h.P_v.assign(pr->P_val, pr->P_val + nnzP);
+    for (int64_t j = 0; j < h.n; ++j)
+      for (int64_t e = h.P_rp[j]; e < h.P_rp[j + 1]; ++e)
+        if (h.P_ci[e] == j) h.Pdiag[j] += h.P_v[e];
+  }
+  h.q.assign(pr->q, pr->q + h.n);
+  h.b.assign(pr->b, pr->b + h.m);
+  // cones
+  h.row_kind.resize(h.m);
+  int64_t ci = 0;
+  for (int32_t i = 0; i < ni; ++i) {
+    int64_t r = h.row_off[i];
+    for (int32_t c = 0; c < pr->cone_count[i]; ++c, ++ci) {
+      const cosmo_cone& cn = pr->cones[ci];
+      const int64_t k = cone_rows(cn);
+      for (int64_t t = r; t < r + k; ++t) h.row_kind[t] = (uint8_t)cn.type;
+      if (cn.type == COSMO_CONE_BOX) h.has_box = true;
+      if (cn.type == COSMO_CONE_SOC) {
+        h.soc_row0.push_back(r);
+        h.soc_dim.push_back(cn.dim);
+      }
+      if (cn.type == COSMO_CONE_PSD) {
+        h.psd_row0.push_back(r);
+        h.psd_p.push_back(cn.dim);
+        h.psd_loff.push_back(h.sum_p);
+        h.psd_uoff.push_back(h.sum_p2);
+        h.sum_p += cn.dim;
+        h.sum_p2 += (int64_t)cn.dim * cn.dim;
+        h.max_p = std::max(h.max_p, cn.dim);
+      }
+      if (cn.type == COSMO_CONE_SOC || cn.type == COSMO_CONE_PSD) {
+        h.rect_row0.push_back(r);
+        h.rect_rows.push_back((int32_t)k);
+      }
+      r += k;
+    }
+  }
+  if (h.has_box) {
+    h.bl.assign(pr->box_l, pr->box_l + h.m);
+    h.bu.assign(pr->box_u, pr->box_u + h.m);
+  }
+  // schedules: largest PSD blocks first; instances with the most work first
+  h.psd_sched.resize(h.psd_p.size());
+  std::iota(h.psd_sched.begin(), h.psd_sched.end(), 0);
+  std::stable_sort(h.psd_sched.begin(), h.psd_sched.end(),
+                   [&](int a, int b) { return h.psd_p[a] > h.psd_p[b]; });
+  std::vector<int64_t> work(ni);
+  for (int32_t i = 0; i < ni; ++i)
+    work[i] = (h.A_rp[h.row_off[i + 1]] - h.A_rp[h.row_off[i]]) * 2 +
+              (h.has_P ? h.P_rp[h.col_off[i + 1]] - h.P_rp[h.col_off[i]] : 0) +
+              (h.col_off[i + 1] - h.col_off[i]) + (h.row_off[i + 1] - h.row_off[i]);
+  h.inst_sched.resize(ni);
+  std::iota(h.inst_sched.begin(), h.inst_sched.end(), 0);
+  std::stable_sort(h.inst_sched.begin(), h.inst_sched.end(),
+                   [&](int a, int b) { return work[a] > work[b]; });
+}
+
+// ------------------------------------------------------- implementation ---
+struct Impl {
+  virtual ~Impl() {}
+  virtual cosmo_status forward(int32_t K, const double* sigma, const void* rho, const void* alpha,
+                               const void* x0, const void* s0, const void* y0, void* xK, void* sK,
+                               void* yK, double* loss, int32_t tape, cudaStream_t st) = 0;
+  virtual cosmo_status backward(const void* gx, const void* gs, const void* gy, const double* gl,
+                                void* grho, void* galpha, void* gx0, void* gs0, void* gy0,
+                                cudaStream_t st) = 0;
+  virtual cosmo_status residuals(const void* x, const void* s, const void* y, double* rp2,
+                                 double* rd2, double* obj, cudaStream_t st) = 0;
+  virtual cosmo_status rho_from_log(int32_t K, const double* lr, double eq, void* rho,
+                                    cudaStream_t st) = 0;
+  virtual cosmo_status rho_from_log_bwd(int32_t K, const void* rho, const void* grho,
+                                        double* glog, cudaStream_t st) = 0;
+  virtual cosmo_status alpha_bcast(int32_t K, const double* a, void* alpha, cudaStream_t st) = 0;
+  virtual cosmo_status alpha_reduce(int32_t K, const void* ga, double* gk, cudaStream_t st) = 0;
+  virtual cosmo_status flags_sync(int32_t* out) = 0;
+  virtual void info(cosmo_batch_info* o) const = 0;
+  virtual cosmo_status profile_enable(const char* tag) = 0;
+  virtual cosmo_status profile_read(const char* tag, double* ms, int64_t* n, int32_t reset) = 0;
+  virtual size_t real_size() const = 0;
+};
+
+// device staging of cosmo_step_host, owned by the batch so repeated steps
+// allocate nothing
+struct HostStepBufs {
+  int32_t K = 0;
+  DevArena a;
+  double *lr = nullptr, *ak = nullptr, *glr = nullptr, *gak = nullptr, *loss = nullptr,
+         *gloss = nullptr;
+  void *rho = nullptr, *alpha = nullptr, *grho = nullptr, *galpha = nullptr;
+  void *x0 = nullptr, *s0 = nullptr, *y0 = nullptr, *gx0 = nullptr, *gs0 = nullptr, *gy0 = nullptr;
+};
+
+struct cosmo_batch {
+  cosmo_options opt;
+  HostPlan plan;
+  std::unique_ptr<Impl> impl;
+  std::unique_ptr<HostStepBufs> hostbufs;
+};
+
+template <class T, class V>
+struct ImplT : Impl {
+  cosmo_options opt;
+  HostPlan& h;
+  DevArena arena;   // K-independent
+  DevArena tarena;  // K-dependent (tape, staging)
+  Prob<T, V> P{};
+  cudaStream_t cap = nullptr;
+  int32_t* flags = nullptr;
+  // K-independent workspace
+  T *xi = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_u = nullptr, *cg_t = nullptr;
+  T *xb[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr}, *yb[2] = {nullptr, nullptr};
+  T *gproj = nullptr, *vbar = nullptr, *adjrhs = nullptr, *lamt = nullptr, *rp = nullptr,
+    *rd = nullptr;
+  double *loss_buf = nullptr, *gloss_buf = nullptr;
+  T *gx_in = nullptr, *gs_in = nullptr, *gy_in = nullptr;
+  // tape (segment buffers) and per-step parameters
+  int32_t K = 0, cK = 0, nseg = 0, seg_in_buffer = -1;
+  bool tape_valid = false, loss_valid = false;
+  T *xs = nullptr, *ss = nullptr, *ys = nullptr;        // (cK+1) states
+  T *xts = nullptr, *sts = nullptr, *lams = nullptr, *Us = nullptr;  // cK slots
+  T *ck_x = nullptr, *ck_s = nullptr, *ck_y = nullptr, *ck_xt = nullptr;  // nseg
+  T *rho_in = nullptr, *rho_rect = nullptr, *dinv = nullptr, *alpha_in = nullptr;
+  T *grho_all = nullptr, *galpha_all = nullptr;
+  double* sigma_dev = nullptr;
+  std::vector<double> sigma_h;
+  // graphs
+  cudaGraphExec_t gfwd = nullptr, gbwd = nullptr;
+  int32_t gfwd_key[3] = {-1, -1, -1};
+  std::vector<double> gfwd_sigma, gbwd_sigma;
+  int64_t gfwd_nk = 0, gbwd_nk = 0;
+  int64_t launched = 0;
+  int64_t seq_kernels = 0;  // kernels enqueued by the sequence being built
+  int psd_nt = 256;
+  // optional CUDA-event timing of launches (direct mode only)
+  int prof_mode = 0;            // 0 off, 1 every kernel, 2 kernels whose tag == prof_tag
+  std::string prof_tag;
+  bool capturing = false;
+  struct Rec { const char* tag; cudaEvent_t e0, e1; };
+  std::vector<Rec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<std::string, std::pair<double, int64_t>>> prof_acc;
+
+  explicit ImplT(const cosmo_options& o, HostPlan& hp) : opt(o), h(hp) {}
+  ~ImplT() override {
+    for (auto& r : prof_pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    if (gfwd) cudaGraphExecDestroy(gfwd);
+    if (gbwd) cudaGraphExecDestroy(gbwd);
+    if (cap) cudaStreamDestroy(cap);
+  }
+  size_t real_size() const override { return sizeof(T); }
+
+  template <class X>
+  static std::vector<X> conv(const std::vector<double>& v) {
+    std::vector<X> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (X)v[i];
+    return o;
+  }
+  static std::vector<__nv_bfloat16> conv_bf16(const std::vector<double>& v) {
+    std::vector<__nv_bfloat16> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = __float2bfloat16((float)v[i]);
+    return o;
+  }
+  std::vector<V> convV(const std::vector<double>& v) {
+    if constexpr (std::is_same<V, __nv_bfloat16>::value) return conv_bf16(v);
+    else return conv<V>(v);
+  }
+
+  cosmo_status init() {
+    CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int64_t *col_off, *row_off, *A_rp, *AT_rp, *P_rp = nullptr, *soc_row0, *psd_row0, *psd_loff,
+        *psd_uoff, *rect_row0;
+    int32_t *row_inst, *col_inst, *A_ci, *AT_ci, *P_ci = nullptr, *soc_dim, *psd_p, *psd_sched,
+        *rect_rows, *inst_sched;
+    uint8_t* row_kind;
+    V *A_v, *AT_v, *P_v = nullptr;
+    T *Pdiag, *q, *b, *bl = nullptr, *bu = nullptr;
+    TRY(arena.upload(&col_off, h.col_off));
+    TRY(arena.upload(&row_off, h.row_off));
+    TRY(arena.upload(&row_inst, h.row_inst));
+    TRY(arena.upload(&col_inst, h.col_inst));
+    TRY(arena.upload(&row_kind, h.row_kind));
+    TRY(arena.upload(&A_rp, h.A_rp));
+    TRY(arena.upload(&A_ci, h.A_ci));
+    TRY(arena.upload(&A_v, convV(h.A_v)));
+    TRY(arena.upload(&AT_rp, h.AT_rp));
+    TRY(arena.upload(&AT_ci, h.AT_ci));
+    TRY(arena.upload(&AT_v, convV(h.AT_v)));
+    if (h.has_P) {
+      TRY(arena.upload(&P_rp, h.P_rp));
+      TRY(arena.upload(&P_ci, h.P_ci));
+      TRY(arena.upload(&P_v, convV(h.P_v)));
+    }
+    TRY(arena.upload(&Pdiag, conv<T>(h.Pdiag)));
+    TRY(arena.upload(&q, conv<T>(h.q)));
+    TRY(arena.upload(&b, conv<T>(h.b)));
+    if (h.has_box) {
+      TRY(arena.upload(&bl, conv<T>(h.bl)));
+      TRY(arena.upload(&bu, conv<T>(h.bu)));
+    }
+    TRY(arena.upload(&soc_row0, h.soc_row0));
+    TRY(arena.upload(&soc_dim, h.soc_dim));
+    TRY(arena.upload(&psd_row0, h.psd_row0));
+    TRY(arena.upload(&psd_p, h.psd_p));
+    TRY(arena.upload(&psd_loff, h.psd_loff));
+    TRY(arena.upload(&psd_uoff, h.psd_uoff));
+    TRY(arena.upload(&psd_sched, h.psd_sched));
+    TRY(arena.upload(&rect_row0, h.rect_row0));
+    TRY(arena.upload(&rect_rows, h.rect_rows));
+    TRY(arena.upload(&inst_sched, h.inst_sched));
+    P.ninst = h.ninst;
+    P.n_total = h.n;
+    P.m_total = h.m;
+    P.col_off = col_off; P.row_off = row_off; P.row_inst = row_inst; P.col_inst = col_inst;
+    P.row_kind = row_kind;
+    P.A_rp = A_rp; P.A_ci = A_ci; P.A_v = A_v;
+    P.AT_rp = AT_rp; P.AT_ci = AT_ci; P.AT_v = AT_v;
+    P.P_rp = P_rp; P.P_ci = P_ci; P.P_v = P_v;
+    P.Pdiag = Pdiag; P.q = q; P.b = b; P.box_l = bl; P.box_u = bu;
+    P.nsoc = (int32_t)h.soc_row0.size(); P.soc_row0 = soc_row0; P.soc_dim = soc_dim;
+    P.npsd = (int32_t)h.psd_p.size(); P.psd_row0 = psd_row0; P.psd_p = psd_p;
+    P.psd_loff = psd_loff; P.psd_uoff = psd_uoff; P.psd_sched = psd_sched;
+    P.nrect = (int32_t)h.rect_row0.size(); P.rect_row0 = rect_row0; P.rect_rows = rect_rows;
+    P.inst_sched = inst_sched;
+    const int64_t n = h.n, m = h.m;
+    TRY(arena.alloc(&flags, h.ninst));
+    CU(cudaMemset(flags, 0, sizeof(int32_t) * h.ninst));
+    TRY(arena.alloc(&xi, n)); TRY(arena.alloc(&cg_r, n)); TRY(arena.alloc(&cg_p, n));
+    TRY(arena.alloc(&cg_u, n)); TRY(arena.alloc(&cg_t, m));
+    for (int i = 0; i < 2; ++i) {
+      TRY(arena.alloc(&xb[i], n)); TRY(arena.alloc(&sb[i], m)); TRY(arena.alloc(&yb[i], m));
+    }
+    TRY(arena.alloc(&gproj, m)); TRY(arena.alloc(&vbar, m)); TRY(arena.alloc(&adjrhs, n));
+    TRY(arena.alloc(&lamt, n)); TRY(arena.alloc(&rp, m)); TRY(arena.alloc(&rd, n));
+    TRY(arena.alloc(&gx_in, n)); TRY(arena.alloc(&gs_in, m)); TRY(arena.alloc(&gy_in, m));
+    TRY(arena.alloc(&loss_buf, h.ninst)); TRY(arena.alloc(&gloss_buf, h.ninst));
+    if (P.npsd > 0) {
+      const size_t fs = psd_fwd_smem<T>(h.max_p, psd_nt), bs = psd_bwd_smem<T>(h.max_p, psd_nt);
+      int dev = 0, maxs = 0;
+      CU(cudaGetDevice(&dev));
+      CU(cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      if ((int64_t)fs > maxs || (int64_t)bs > maxs)
+        return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
+                    h.max_p, std::max(fs, bs), maxs);
+      CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+      CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
+    }
+    return COSMO_OK;
+  }
+
+  // (re)allocate the tape for K steps with checkpoint interval c
+  cosmo_status ensure_tape(int32_t newK) {
+    int32_t c = opt.checkpoint_every > 0 ? std::min(opt.checkpoint_every, newK) : newK;
+    if (newK == K && c == cK && xs) return COSMO_OK;
+    if (gfwd) { cudaGraphExecDestroy(gfwd); gfwd = nullptr; }
+    if (gbwd) { cudaGraphExecDestroy(gbwd); gbwd = nullptr; }
+    CU(cudaDeviceSynchronize());
+    tarena.release();
+    tape_valid = false;
+    K = newK;
+    cK = c;
+    nseg = (K + cK - 1) / cK;
+    const int64_t n = h.n, m = h.m, ni = h.ninst;
+    TRY(tarena.alloc(&xs, (cK + 1) * n)); TRY(tarena.alloc(&ss, (cK + 1) * m));
+    TRY(tarena.alloc(&ys, (cK + 1) * m));
+    TRY(tarena.alloc(&xts, (int64_t)cK * n)); TRY(tarena.alloc(&sts, (int64_t)cK * m));
+    TRY(tarena.alloc(&lams, (int64_t)cK * h.sum_p)); TRY(tarena.alloc(&Us, (int64_t)cK * h.sum_p2));
+    TRY(tarena.alloc(&ck_x, nseg * n)); TRY(tarena.alloc(&ck_s, nseg * m));
+    TRY(tarena.alloc(&ck_y, nseg * m)); TRY(tarena.alloc(&ck_xt, nseg * n));
+    TRY(tarena.alloc(&rho_in, (int64_t)K * m)); TRY(tarena.alloc(&rho_rect, (int64_t)K * m));
+    TRY(tarena.alloc(&dinv, (int64_t)K * n)); TRY(tarena.alloc(&alpha_in, (int64_t)K * ni));
+    TRY(tarena.alloc(&grho_all, (int64_t)K * m)); TRY(tarena.alloc(&galpha_all, (int64_t)K * ni));
+    TRY(tarena.alloc(&sigma_dev, K));
+    return COSMO_OK;
+  }
+
+  // ----------------------------------------------------------- launches --
+  cudaEvent_t get_event() {
+    if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+
+  template <class Kern, class... Args>
+  void launch(const char* tag, Kern kern, int grid, int block, size_t smem, cudaStream_t st,
+              Args... args) {
+    const bool rec = prof_mode != 0 && !capturing && (prof_mode == 1 || prof_tag == tag);
+    Rec r{tag, nullptr, nullptr};
+    if (rec) {
+      r.e0 = get_event();
+      r.e1 = get_event();
+      cudaEventRecord(r.e0, st);
+    }
+    kern<<<grid, block, smem, st>>>(args...);
+    ++seq_kernels;
+    if (rec) {
+      cudaEventRecord(r.e1, st);
+      prof_pending.push_back(r);
+    }
+  }
+
+  cosmo_status profile_enable(const char* tag) override {
+    TRY(profile_collect());
+    if (!tag) { prof_mode = 1; prof_tag.clear(); }
+    else if (!*tag) { prof_mode = 0; prof_tag.clear(); }
+    else { prof_mode = 2; prof_tag = tag; }
+    return COSMO_OK;
+  }
+  cosmo_status profile_collect() {
+    for (auto& r : prof_pending) {
+      CU(cudaEventSynchronize(r.e1));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, r.e0, r.e1));
+      bool found = false;
+      for (auto& a : prof_acc)
+        if (a.first == r.tag) { a.second.first += ms; a.second.second += 1; found = true; }
+      if (!found) prof_acc.push_back(std::make_pair(std::string(r.tag), std::make_pair((double)ms, (int64_t)1)));
+      ev_pool.push_back(r.e0);
+      ev_pool.push_back(r.e1);
+    }
+    prof_pending.clear();
+    return COSMO_OK;
+  }
+  cosmo_status profile_read(const char* tag, double* ms, int64_t* n, int32_t reset) override {
+    TRY(profile_collect());
+    *ms = 0.0;
+    *n = 0;
+    for (auto& a : prof_acc)
+      if (!tag || a.first == tag) { *ms += a.second.first; *n += a.second.second; }
+    if (reset) prof_acc.clear();
+    return COSMO_OK;
+  }
+
+  T* st_x(int slot) { return xs + (int64_t)slot * h.n; }
+  T* st_s(int slot) { return ss + (int64_t)slot * h.m; }
+  T* st_y(int slot) { return ys + (int64_t)slot * h.m; }
+
+  void enqueue_prep(cudaStream_t st) {
+    const int64_t Km = (int64_t)K * h.m;
+    launch("rho_check", k_rho_copy_check<T, V>, grid_for(Km, 256), 256, 0, st, P, K, (const T*)rho_in, rho_rect, flags);
+    if (P.nrect) launch("rho_rectify", k_rho_rectify<T, V>, grid_for((int64_t)K * P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, K, (const T*)rho_in, rho_rect);
+    launch("alpha_check", k_alpha_check<T, V>, grid_for((int64_t)K * h.ninst, 256), 256, 0, st, P, K, (const T*)alpha_in, flags);
+    launch("precond", k_precond<T, V>, grid_for((int64_t)K * h.n, 256), 256, 0, st, P, K, (const double*)sigma_dev, (const T*)rho_rect, dinv);
+  }
+
+  // one forward step k; state slot `slot` -> slot+1, tape slot `slot`
+  void enqueue_step(int32_t k, int slot, const T* xt_warm, cudaStream_t st) {
+    const T* rho = rho_rect + (int64_t)k * h.m;
+    const T* alpha = alpha_in + (int64_t)k * h.ninst;
+    const double sig = sigma_h[k];
+    T* xt = xts + (int64_t)slot * h.n;
+    T* stt = sts + (int64_t)slot * h.m;
+    launch("rhs", k_rhs<T, V>, grid_for(h.n, 256), 256, 0, st, P, sig, (const T*)st_x(slot),
+           (const T*)st_s(slot), (const T*)st_y(slot), rho, xi);
+    CgArgs<T> ca{};
+    ca.rhs = xi; ca.x = xt; ca.x0 = xt_warm; ca.rho = rho; ca.dinv = dinv + (int64_t)k * h.n;
+    ca.sigma = sig; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = opt.cg_tol;
+    ca.maxit = opt.cg_max_iter; ca.zero_start = xt_warm ? 0 : 1; ca.flag_bit = F_CG_CAP;
+    ca.flags = flags; ca.iters = nullptr;
+    launch("pcg", k_pcg<T, V, 256>, h.ninst, 256, 0, st, P, ca);
+    StepPtrs<T> sp{};
+    sp.x = st_x(slot); sp.s = st_s(slot); sp.y = st_y(slot);
+    sp.xn = st_x(slot + 1); sp.sn = st_s(slot + 1); sp.yn = st_y(slot + 1);
+    sp.rho = rho; sp.alpha = alpha; sp.xt = xt; sp.st = stt;
+    sp.lam = lams + (int64_t)slot * h.sum_p; sp.U = Us + (int64_t)slot * h.sum_p2; sp.flags = flags;
+    launch("post", k_post<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, sp);
+    if (P.nsoc) launch("soc_fwd", k_soc_fwd<T, V>, grid_for((int64_t)P.nsoc * 32, 256, INT32_MAX), 256, 0, st, P, sp);
+    if (P.npsd) {
+      PsdIterIO<T> io{stt, st_s(slot), st_y(slot), rho, alpha, st_s(slot + 1), st_y(slot + 1), P.row_inst};
+      launch("psd_fwd", k_psd_fwd<T, V, 256>, P.npsd, 256, psd_fwd_smem<T>(h.max_p, 256), st, P, io,
+             sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags);
+    }
+  }
+
+  // run steps [k0, k1) of segment seg (slot 0 holds z^{k0})
+  void enqueue_segment(int32_t seg, cudaStream_t st) {
+    const int32_t k0 = seg * cK, k1 = std::min(K, k0 + cK);
+    for (int32_t k = k0; k < k1; ++k) {
+      const int slot = k - k0;
+      const T* warm = nullptr;
+      if (k > 0) warm = slot == 0 ? ck_xt + (int64_t)seg * h.n : xts + (int64_t)(slot - 1) * h.n;
+      enqueue_step(k, slot, warm, st);
+    }
+  }
+
+  void copy_state(T* dx, T* ds, T* dy, const T* sx, const T* s_, const T* sy, cudaStream_t st) {
+    cudaMemcpyAsync(dx, sx, sizeof(T) * h.n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(ds, s_, sizeof(T) * h.m, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(dy, sy, sizeof(T) * h.m, cudaMemcpyDeviceToDevice, st);
+  }
+
+  int32_t last_len() const { return K - (nseg - 1) * cK; }
+
+  // whole forward: prep, all segments with checkpoints, optional loss
+  void enqueue_forward(bool want_loss, cudaStream_t st) {
+    enqueue_prep(st);
+    for (int32_t seg = 0; seg < nseg; ++seg) {
+      if (seg > 0) {
+        // slot cK of the previous segment is z^{seg*cK}; x~ of its last step warms CG
+        copy_state(st_x(0), st_s(0), st_y(0), st_x(cK), st_s(cK), st_y(cK), st);
+        cudaMemcpyAsync(ck_xt + (int64_t)seg * h.n, xts + (int64_t)(cK - 1) * h.n,
+                        sizeof(T) * h.n, cudaMemcpyDeviceToDevice, st);
+      }
+      copy_state(ck_x + (int64_t)seg * h.n, ck_s + (int64_t)seg * h.m, ck_y + (int64_t)seg * h.m,
+                 st_x(0), st_s(0), st_y(0), st);
+      enqueue_segment(seg, st);
+    }
+    if (want_loss) {
+      const int fs = last_len();
+      ResArgs<T> ra{st_x(fs), st_s(fs), st_y(fs), rp, rd, nullptr, nullptr, nullptr, loss_buf};
+      launch("residuals", k_residuals<T, V, 256>, h.ninst, 256, 0, st, P, ra);
+    }
+  }
+
+  void enqueue_bwd_step(int32_t k, int slot, int cur, cudaStream_t st) {
+    BwdPtrs<T> q{};
+    q.x = st_x(slot); q.s = st_s(slot); q.y = st_y(slot); q.sn = st_s(slot + 1);
+    q.rho = rho_rect + (int64_t)k * h.m; q.alpha = alpha_in + (int64_t)k * h.ninst;
+    q.sigma = sigma_h[k];
+    q.xt = xts + (int64_t)slot * h.n; q.st = sts + (int64_t)slot * h.m;
+    q.lam = lams + (int64_t)slot * h.sum_p; q.U = Us + (int64_t)slot * h.sum_p2;
+    q.xb = xb[cur]; q.sb = sb[cur]; q.yb = yb[cur];
+    q.xb2 = xb[cur ^ 1]; q.sb2 = sb[cur ^ 1]; q.yb2 = yb[cur ^ 1];
+    q.gproj = gproj; q.vbar = vbar; q.adjrhs = adjrhs; q.lamt = lamt;
+    q.grho = grho_all + (int64_t)k * h.m; q.galpha = galpha_all + (int64_t)k * h.ninst;
+    q.flags = flags; q.dk_tau = opt.dk_gap_tau;
+    launch("bwd_gproj", k_bwd_gproj<T, V>, grid_for(h.m, 256), 256, 0, st, P, q);
+    if (P.nsoc) launch("soc_bwd", k_soc_bwd<T, V>, grid_for((int64_t)P.nsoc * 32, 256, INT32_MAX), 256, 0, st, P, q);
+    if (P.npsd) {
+      PsdBwdIO<T> io{gproj, vbar, P.row_inst};
+      launch("psd_bwd", k_psd_bwd<T, V, 256>, P.npsd, 256, psd_bwd_smem<T>(h.max_p, 256), st, P, io,
+             (const T*)q.lam, (const T*)q.U, opt.dk_gap_tau);
+    }
+    launch("bwd_relax", k_bwd_relax<T, V, 256>, h.ninst, 256, 0, st, P, q);
+    CgArgs<T> ca{};
+    ca.rhs = adjrhs; ca.x = lamt; ca.x0 = nullptr; ca.rho = q.rho;
+    ca.dinv = dinv + (int64_t)k * h.n; ca.sigma = q.sigma; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u;
+    ca.t = cg_t; ca.tol = opt.cg_tol; ca.maxit = opt.cg_max_iter; ca.zero_start = 1;
+    ca.flag_bit = F_ADJ_CG_CAP; ca.flags = flags; ca.iters = nullptr;
+    launch("pcg_adj", k_pcg<T, V, 256>, h.ninst, 256, 0, st, P, ca);
+    launch("bwd_solve", k_bwd_solve<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, q);
+  }
+
+  // whole backward (cotangents staged in gx_in/gs_in/gy_in/gloss_buf)
+  void enqueue_backward(bool use_gloss, cudaStream_t st) {
+    const int fs = last_len();
+    SeedArgs<T> sa{rp, rd, use_gloss ? gloss_buf : nullptr, gx_in, gs_in, gy_in, xb[0], sb[0], yb[0]};
+    (void)fs;
+    launch("loss_seed", k_loss_seed<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, sa);
+    int cur = 0;
+    for (int32_t seg = nseg - 1; seg >= 0; --seg) {
+      if (seg != nseg - 1) {
+        copy_state(st_x(0), st_s(0), st_y(0), ck_x + (int64_t)seg * h.n, ck_s + (int64_t)seg * h.m,
+                   ck_y + (int64_t)seg * h.m, st);
+        enqueue_segment(seg, st);
+      }
+      const int32_t k0 = seg * cK, k1 = std::min(K, k0 + cK);
+      for (int32_t k = k1 - 1; k >= k0; --k) {
+        enqueue_bwd_step(k, k - k0, cur, st);
+        cur ^= 1;
+      }
+    }
+    if (P.nrect) launch("rect_adjoint", k_rect_adjoint<T, V>, grid_for((int64_t)K * P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, K, grho_all);
+    final_cot = cur;
+  }
+  int final_cot = 0;
+
+  // run `fn` either captured into a cached graph or directly on st
+  template <class Fn>
+  cosmo_status run_seq(cudaGraphExec_t& exec, int64_t& nk, bool reuse, Fn fn, cudaStream_t st) {
+    if (!opt.use_graph) {
+      seq_kernels = 0;
+      fn(st);
+      CU(cudaGetLastError());
+      launched += seq_kernels;
+      g_launches += seq_kernels;
+      return COSMO_OK;
+    }
+    if (!(exec && reuse)) {
+      if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+      seq_kernels = 0;
+      CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      capturing = true;
+      fn(cap);
+      capturing = false;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cap, &g);
+      if (e != cudaSuccess) return fail(COSMO_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { exec = nullptr; return fail(COSMO_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e)); }
+      nk = seq_kernels;
+    }
+    CU(cudaGraphLaunch(exec, st));
+    launched += nk;
+    g_launches += nk;
+    return COSMO_OK;
+  }
+
+  cosmo_status forward(int32_t K_, const double* sigma, const void* rho, const void* alpha,
+                       const void* x0, const void* s0, const void* y0, void* xK, void* sK,
+                       void* yK, double* loss, int32_t tape, cudaStream_t st) override {
+    if (K_ < 1) return fail(COSMO_E_INVAL, "K must be >= 1");
+    if (!rho || !alpha) return fail(COSMO_E_INVAL, "rho and alpha are required");
+    TRY(ensure_tape(K_));
+    std::vector<double> sg(K, 1e-6);
+    if (sigma)
+      for (int32_t k = 0; k < K; ++k) {
+        if (!(sigma[k] > 0.0) || !std::isfinite(sigma[k])) return fail(COSMO_E_INVAL, "sigma must be > 0");
+        sg[k] = sigma[k];
+      }
+    sigma_h = sg;
+    const int64_t n = h.n, m = h.m;
+    CU(cudaMemcpyAsync(sigma_dev, sg.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(rho_in, rho, sizeof(T) * K * m, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(alpha_in, alpha, sizeof(T) * K * h.ninst, cudaMemcpyDeviceToDevice, st));
+    if (x0) CU(cudaMemcpyAsync(st_x(0), x0, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+    else CU(cudaMemsetAsync(st_x(0), 0, sizeof(T) * n, st));
+    if (s0) CU(cudaMemcpyAsync(st_s(0), s0, sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    else CU(cudaMemsetAsync(st_s(0), 0, sizeof(T) * m, st));
+    if (y0) CU(cudaMemcpyAsync(st_y(0), y0, sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    else CU(cudaMemsetAsync(st_y(0), 0, sizeof(T) * m, st));
+    const bool want_loss = loss != nullptr || tape;
+    const bool reuse = gfwd_key[0] == K && gfwd_key[1] == (int)want_loss && gfwd_sigma == sg;
+    TRY(run_seq(gfwd, gfwd_nk, reuse, [&](cudaStream_t s) { enqueue_forward(want_loss, s); }, st));
+    gfwd_key[0] = K; gfwd_key[1] = (int)want_loss; gfwd_sigma = sg;
+    seg_in_buffer = nseg - 1;
+    tape_valid = tape != 0;
+    loss_valid = want_loss;
+    const int fs = last_len();
+    if (xK) CU(cudaMemcpyAsync(xK, st_x(fs), sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+    if (sK) CU(cudaMemcpyAsync(sK, st_s(fs), sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    if (yK) CU(cudaMemcpyAsync(yK, st_y(fs), sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    if (loss) CU(cudaMemcpyAsync(loss, loss_buf, sizeof(double) * h.ninst, cudaMemcpyDeviceToDevice, st));
+    return COSMO_OK;
+  }
+
+  cosmo_status backward(const void* gx, const void* gs, const void* gy, const double* gl,
+                        void* grho, void* galpha, void* gx0, void* gs0, void* gy0,
+                        cudaStream_t st) override {
+    if (!tape_valid) return fail(COSMO_E_STATE, "backward needs a forward with record_tape=1");
+    const int64_t n = h.n, m = h.m;
+    // the last segment must be in the buffer (a previous backward may have replaced it)
+    if (seg_in_buffer != nseg - 1) {
+      const int32_t seg = nseg - 1;
+      seq_kernels = 0;
+      copy_state(st_x(0), st_s(0), st_y(0), ck_x + (int64_t)seg * n, ck_s + (int64_t)seg * m,
+                 ck_y + (int64_t)seg * m, st);
+      enqueue_segment(seg, st);
+      CU(cudaGetLastError());
+      launched += seq_kernels;
+      g_launches += seq_kernels;
+      seg_in_buffer = seg;
+    }
+    if (gx) CU(cudaMemcpyAsync(gx_in, gx, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+    else CU(cudaMemsetAsync(gx_in, 0, sizeof(T) * n, st));
+    if (gs) CU(cudaMemcpyAsync(gs_in, gs, sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    else CU(cudaMemsetAsync(gs_in, 0, sizeof(T) * m, st));
+    if (gy) CU(cudaMemcpyAsync(gy_in, gy, sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    else CU(cudaMemsetAsync(gy_in, 0, sizeof(T) * m, st));
+    if (gl) {
+      if (!loss_valid) return fail(COSMO_E_STATE, "gloss given but the forward computed no loss");
+      CU(cudaMemcpyAsync(gloss_buf, gl, sizeof(double) * h.ninst, cudaMemcpyDeviceToDevice, st));
+    } else {
+      CU(cudaMemsetAsync(gloss_buf, 0, sizeof(double) * h.ninst, st));
+    }
+    // rp / rd must exist for the seed kernel even without a loss cotangent
+    if (!loss_valid) {
+      CU(cudaMemsetAsync(rp, 0, sizeof(T) * m, st));
+      CU(cudaMemsetAsync(rd, 0, sizeof(T) * n, st));
+    }
+    const bool reuse = gbwd_sigma == sigma_h && gbwd != nullptr;
+    TRY(run_seq(gbwd, gbwd_nk, reuse, [&](cudaStream_t s) { enqueue_backward(true, s); }, st));
+    gbwd_sigma = sigma_h;
+    seg_in_buffer = nseg > 1 ? 0 : nseg - 1;
+    const int c = final_cot;  // each reverse step swaps the cotangent buffers
+    if (grho) CU(cudaMemcpyAsync(grho, grho_all, sizeof(T) * K * m, cudaMemcpyDeviceToDevice, st));
+    if (galpha) CU(cudaMemcpyAsync(galpha, galpha_all, sizeof(T) * K * h.ninst, cudaMemcpyDeviceToDevice, st));
+    if (gx0) CU(cudaMemcpyAsync(gx0, xb[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+    if (gs0) CU(cudaMemcpyAsync(gs0, sb[c], sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    if (gy0) CU(cudaMemcpyAsync(gy0, yb[c], sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
+    return COSMO_OK;
+  }
+
+  cosmo_status residuals(const void* x, const void* s, const void* y, double* rp2, double* rd2,
+                         double* obj, cudaStream_t st) override {
+    if (!x || !s || !y) return fail(COSMO_E_INVAL, "x, s, y are required");
+    ResArgs<T> ra{(const T*)x, (const T*)s, (const T*)y, nullptr, nullptr, rp2, rd2, obj, nullptr};
+    seq_kernels = 0;
+    launch("residuals", k_residuals<T, V, 256>, h.ninst, 256, 0, st, P, ra);
+    CU(cudaGetLastError());
+    launched += 1; g_launches += 1;
+    return COSMO_OK;
+  }
+
+  cosmo_status rho_from_log(int32_t K_, const double* lr, double eq, void* rho, cudaStream_t st) override {
+    if (K_ < 1 || !lr || !rho) return fail(COSMO_E_INVAL, "bad arguments to rho_from_log");
+    k_rho_from_log<T, V><<<grid_for((int64_t)K_ * h.m, 256), 256, 0, st>>>(P, K_, lr, eq, (T*)rho);
+    CU(cudaGetLastError());
+    launched += 1; g_launches += 1;
+    return COSMO_OK;
+  }
+  cosmo_status rho_from_log_bwd(int32_t K_, const void* rho, const void* grho, double* glog,
+                                cudaStream_t st) override {
+    if (K_ < 1 || !rho || !grho || !glog) return fail(COSMO_E_INVAL, "bad arguments to rho_from_log_backward");
+    k_rowsum_prod<T, 256><<<K_, 256, 0, st>>>(h.m, (const T*)grho, (const T*)rho, glog);
+    CU(cudaGetLastError());
+    launched += 1; g_launches += 1;
+    return COSMO_OK;
+  }
+  cosmo_status alpha_bcast(int32_t K_, const double* a, void* alpha, cudaStream_t st) override {
+    if (K_ < 1 || !a || !alpha) return fail(COSMO_E_INVAL, "bad arguments to alpha_broadcast");
+    k_broadcast<T><<<grid_for((int64_t)K_ * h.ninst, 256), 256, 0, st>>>(K_, h.ninst, a, (T*)alpha);
+    CU(cudaGetLastError());
+    launched += 1; g_launches += 1;
+    return COSMO_OK;
+  }
+  cosmo_status alpha_reduce(int32_t K_, const void* ga, double* gk, cudaStream_t st) override {
+    if (K_ < 1 || !ga || !gk) return fail(COSMO_E_INVAL, "bad arguments to alpha_reduce");
+    k_rowsum_prod<T, 256><<<K_, 256, 0, st>>>(h.ninst, (const T*)ga, (const T*)nullptr, gk);
+    CU(cudaGetLastError());
+    launched += 1; g_launches += 1;
+    return COSMO_OK;
+  }
+  cosmo_status flags_sync(int32_t* out) override {
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(out, flags, sizeof(int32_t) * h.ninst, cudaMemcpyDeviceToHost));
+    CU(cudaMemset(flags, 0, sizeof(int32_t) * h.ninst));
+    return COSMO_OK;
+  }
+  void info(cosmo_batch_info* o) const override {
+    o->ninst = h.ninst;
+    o->n_total = h.n;
+    o->m_total = h.m;
+    o->nnzA = (int64_t)h.A_ci.size();
+    o->nnzP = (int64_t)h.P_ci.size();
+    o->n_soc = (int32_t)h.soc_row0.size();
+    o->n_psd = (int32_t)h.psd_p.size();
+    o->max_psd_p = h.max_p;
+    o->psd_u_entries = h.sum_p2;
+    o->device_bytes = arena.bytes + tarena.bytes;
+    o->last_K = K;
+    o->tape_valid = tape_valid ? 1 : 0;
+    o->kernels_launched = launched;
+  }
+};
+
+// ------------------------------------------------------------------ ABI ---
+extern "C" {
+
+const char* cosmo_version(void) { return "cosmo_du 0.1 (sm_103a)"; }
+int64_t cosmo_kernel_launch_count(void) { return g_launches.load(); }
+const char* cosmo_last_error(void) { return g_err.c_str(); }
+
+cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
+  if (!o) return fail(COSMO_E_INVAL, "options pointer is NULL");
+  if (precision != COSMO_PREC_MIXED && precision != COSMO_PREC_FP64)
+    return fail(COSMO_E_INVAL, "unknown precision %d", precision);
+  std::memset(o, 0, sizeof(*o));
+  o->precision = precision;
+  o->value_type = COSMO_VAL_F32;
+  o->cg_tol = precision == COSMO_PREC_FP64 ? 1e-10 : 1e-8;
+  o->cg_max_iter = 500;
+  o->checkpoint_every = 0;
+  o->dk_gap_tau = 1e-12;
+  o->eig_jacobi_max_p = precision == COSMO_PREC_FP64 ? 48 : 64;
+  o->eig_max_sweeps = 30;
+  o->eig_tol = precision == COSMO_PREC_FP64 ? 1e-14 : 1e-6;
+  o->use_graph = 1;
+  o->device = 0;
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_problem_validate(const cosmo_problem* prob) {
+  g_err.clear();
+  return validate(prob);
+}
+
+cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* opt,
+                                cosmo_batch** out) {
+  g_err.clear();
+  if (!out) return fail(COSMO_E_INVAL, "out is NULL");
+  *out = nullptr;
+  cosmo_options o;
+  if (opt) o = *opt;
+  else cosmo_options_default(&o, COSMO_PREC_MIXED);
+  if (o.precision != COSMO_PREC_MIXED && o.precision != COSMO_PREC_FP64)
+    return fail(COSMO_E_INVAL, "unknown precision %d", o.precision);
+  if (o.value_type != COSMO_VAL_F32 && o.value_type != COSMO_VAL_BF16)
+    return fail(COSMO_E_INVAL, "unknown value type %d", o.value_type);
+  if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
+      o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0))
+    return fail(COSMO_E_INVAL, "invalid options");
+  TRY(validate(prob));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(COSMO_E_NODEVICE, "no CUDA device");
+  }
+  if (o.device < 0 || o.device >= ndev) return fail(COSMO_E_INVAL, "device %d out of range", o.device);
+  CU(cudaSetDevice(o.device));
+  std::unique_ptr<cosmo_batch> b(new cosmo_batch());
+  b->opt = o;
+  build_plan(prob, b->plan);
+  cosmo_status st;
+  if (o.precision == COSMO_PREC_FP64) {
+    auto* im = new ImplT<double, double>(o, b->plan);
+    b->impl.reset(im);
+    st = im->init();
+  } else if (o.value_type == COSMO_VAL_BF16) {
+    auto* im = new ImplT<float, __nv_bfloat16>(o, b->plan);
+    b->impl.reset(im);
+    st = im->init();
+  } else {
+    auto* im = new ImplT<float, float>(o, b->plan);
+    b->impl.reset(im);
+    st = im->init();
+  }
+  if (st != COSMO_OK) return st;
+  *out = b.release();
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_batch_destroy(cosmo_batch* b) {
+  if (!b) return COSMO_OK;
+  cudaSetDevice(b->opt.device);
+  cudaDeviceSynchronize();
+  delete b;
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_batch_get_info(const cosmo_batch* b, cosmo_batch_info* out) {
+  if (!b || !out) return fail(COSMO_E_INVAL, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->precision = b->opt.precision;
+  b->impl->info(out);
+  return COSMO_OK;
+}
+
+#define BATCH_GUARD(b)                                           \
+  do {                                                           \
+    g_err.clear();                                               \
+    if (!(b)) return fail(COSMO_E_INVAL, "batch is NULL");       \
+    CU(cudaSetDevice((b)->opt.device));                          \
+  } while (0)
+
+cosmo_status cosmo_forward(cosmo_batch* b, int32_t K, const double* sigma_host, const void* rho,
+                           const void* alpha, const void* x0, const void* s0, const void* y0,
+                           void* xK, void* sK, void* yK, double* loss, int32_t record_tape,
+                           void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->forward(K, sigma_host, rho, alpha, x0, s0, y0, xK, sK, yK, loss, record_tape,
+                          (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_backward(cosmo_batch* b, const void* gxK, const void* gsK, const void* gyK,
+                            const double* gloss, void* grho, void* galpha, void* gx0, void* gs0,
+                            void* gy0, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->backward(gxK, gsK, gyK, gloss, grho, galpha, gx0, gs0, gy0, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_residuals(cosmo_batch* b, const void* x, const void* s, const void* y,
+                             double* rp2, double* rd2, double* obj, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->residuals(x, s, y, rp2, rd2, obj, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_rho_from_log(cosmo_batch* b, int32_t K, const double* log_rho, double eq_scale,
+                                void* rho, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->rho_from_log(K, log_rho, eq_scale, rho, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_rho_from_log_backward(cosmo_batch* b, int32_t K, const void* rho,
+                                         const void* grho, double* glog, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->rho_from_log_bwd(K, rho, grho, glog, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_alpha_broadcast(cosmo_batch* b, int32_t K, const double* alpha_k, void* alpha,
+                                   void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->alpha_bcast(K, alpha_k, alpha, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_alpha_reduce(cosmo_batch* b, int32_t K, const void* galpha, double* galpha_k,
+                                void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->alpha_reduce(K, galpha, galpha_k, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_profile_enable(cosmo_batch* b, const char* kernel) {
+  BATCH_GUARD(b);
+  return b->impl->profile_enable(kernel);
+}
+
+cosmo_status cosmo_profile_read(cosmo_batch* b, const char* kernel, double* total_ms,
+                                int64_t* launches, int32_t reset) {
+  BATCH_GUARD(b);
+  if (!total_ms || !launches) return fail(COSMO_E_INVAL, "NULL output");
+  return b->impl->profile_read(kernel, total_ms, launches, reset);
+}
+
+cosmo_status cosmo_status_sync(cosmo_batch* b, int32_t* flags_host) {
+  BATCH_GUARD(b);
+  if (!flags_host) return fail(COSMO_E_INVAL, "flags_host is NULL");
+  return b->impl->flags_sync(flags_host);
+}
+
+
+
+cosmo_status cosmo_step_host(cosmo_batch* b, int32_t K, double sigma, double eq_scale,
+                             const double* lr_h, const double* ak_h, const void* x0_h,
+                             const void* s0_h, const void* y0_h, double* loss_h, double* glr_h,
+                             double* gak_h, void* gx0_h, void* gs0_h, void* gy0_h, void* stream) {
+  BATCH_GUARD(b);
+  if (K < 1 || !lr_h || !ak_h || !loss_h || !glr_h || !gak_h)
+    return fail(COSMO_E_INVAL, "bad arguments to cosmo_step_host");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!b->hostbufs) b->hostbufs.reset(new HostStepBufs());
+  HostStepBufs* hb = b->hostbufs.get();
+  const HostPlan& h = b->plan;
+  const size_t rs = b->impl->real_size();
+  if (hb->K != K) {
+    CU(cudaDeviceSynchronize());
+    hb->a.release();
+    hb->K = K;
+    char* p;
+    TRY(hb->a.alloc(&hb->lr, K)); TRY(hb->a.alloc(&hb->ak, K)); TRY(hb->a.alloc(&hb->glr, K));
+    TRY(hb->a.alloc(&hb->gak, K)); TRY(hb->a.alloc(&hb->loss, h.ninst));
+    TRY(hb->a.alloc(&hb->gloss, h.ninst));
+    TRY(hb->a.alloc(&p, (int64_t)rs * K * h.m)); hb->rho = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * K * h.m)); hb->grho = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * K * h.ninst)); hb->alpha = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * K * h.ninst)); hb->galpha = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * h.n)); hb->x0 = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * h.m)); hb->s0 = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * h.m)); hb->y0 = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * h.n)); hb->gx0 = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * h.m)); hb->gs0 = p;
+    TRY(hb->a.alloc(&p, (int64_t)rs * h.m)); hb->gy0 = p;
+    std::vector<double> ones(h.ninst, 1.0);
+    CU(cudaMemcpy(hb->gloss, ones.data(), sizeof(double) * h.ninst, cudaMemcpyHostToDevice));
+  }
+  CU(cudaMemcpyAsync(hb->lr, lr_h, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(hb->ak, ak_h, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+  if (x0_h) CU(cudaMemcpyAsync(hb->x0, x0_h, rs * h.n, cudaMemcpyHostToDevice, st));
+  if (s0_h) CU(cudaMemcpyAsync(hb->s0, s0_h, rs * h.m, cudaMemcpyHostToDevice, st));
+  if (y0_h) CU(cudaMemcpyAsync(hb->y0, y0_h, rs * h.m, cudaMemcpyHostToDevice, st));
+  TRY(b->impl->rho_from_log(K, hb->lr, eq_scale, hb->rho, st));
+  TRY(b->impl->alpha_bcast(K, hb->ak, hb->alpha, st));
+  std::vector<double> sg(K, sigma);
+  TRY(b->impl->forward(K, sg.data(), hb->rho, hb->alpha, x0_h ? hb->x0 : nullptr,
+                       s0_h ? hb->s0 : nullptr, y0_h ? hb->y0 : nullptr, nullptr, nullptr, nullptr,
+                       hb->loss, 1, st));
+  TRY(b->impl->backward(nullptr, nullptr, nullptr, hb->gloss, hb->grho, hb->galpha,
+                        gx0_h ? hb->gx0 : nullptr, gs0_h ? hb->gs0 : nullptr,
+                        gy0_h ? hb->gy0 : nullptr, st));
+  TRY(b->impl->rho_from_log_bwd(K, hb->rho, hb->grho, hb->glr, st));
+  TRY(b->impl->alpha_reduce(K, hb->galpha, hb->gak, st));
+  CU(cudaMemcpyAsync(loss_h, hb->loss, sizeof(double) * h.ninst, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(glr_h, hb->glr, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(gak_h, hb->gak, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+  if (gx0_h) CU(cudaMemcpyAsync(gx0_h, hb->gx0, rs * h.n, cudaMemcpyDeviceToHost, st));
+  if (gs0_h) CU(cudaMemcpyAsync(gs0_h, hb->gs0, rs * h.m, cudaMemcpyDeviceToHost, st));
+  if (gy0_h) CU(cudaMemcpyAsync(gy0_h, hb->gy0, rs * h.m, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return COSMO_OK;
+}
+
+}  // extern "C"
+
+// ---- standalone PSD kernels ----
+template <class T>
+static cosmo_status psd_project_t(int32_t nblk, const int32_t* p_h, const int64_t* off_h,
+                                  const void* v, void* out, void* lam, void* U, cudaStream_t st) {
+  std::vector<int32_t> p(p_h, p_h + nblk);
+  std::vector<int64_t> off(off_h, off_h + nblk), loff(nblk), uoff(nblk);
+  int64_t sl = 0, su = 0;
+  int maxp = 0;
+  for (int32_t j = 0; j < nblk; ++j) {
+    if (p[j] < 1 || p[j] > 1024) return fail(COSMO_E_INVAL, "PSD order out of range");
+    loff[j] = sl; uoff[j] = su; sl += p[j]; su += (int64_t)p[j] * p[j];
+    maxp = std::max(maxp, p[j]);
+  }
+  const size_t smem = psd_fwd_smem<T>(maxp, 256);
+  int dev = 0, maxs = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if ((int64_t)smem > maxs) return fail(COSMO_E_INVAL, "PSD order %d too large for one CTA", maxp);
+  CU(cudaFuncSetAttribute(k_psd_project_batch<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DevArena a;
+  int32_t *dp, *dflag;
+  int64_t *doff, *dloff, *duoff;
+  TRY(a.upload(&dp, p)); TRY(a.upload(&doff, off)); TRY(a.upload(&dloff, loff));
+  TRY(a.upload(&duoff, uoff)); TRY(a.alloc(&dflag, 1));
+  CU(cudaMemsetAsync(dflag, 0, sizeof(int32_t), st));
+  PsdBatch<T> B{nblk, dp, doff, dloff, duoff};
+  const double tol = sizeof(T) == 8 ? 1e-14 : 1e-6;
+  k_psd_project_batch<T, 256><<<nblk, 256, smem, st>>>(B, (const T*)v, (T*)out, (T*)lam, (T*)U, tol, 30, dflag);
+  CU(cudaGetLastError());
+  g_launches += 1;
+  CU(cudaStreamSynchronize(st));
+  return COSMO_OK;
+}
+
+template <class T>
+static cosmo_status psd_dk_t(int32_t nblk, const int32_t* p_h, const int64_t* off_h,
+                             const void* lam, const void* U, const void* g, void* out, double tau,
+                             cudaStream_t st) {
+  std::vector<int32_t> p(p_h, p_h + nblk);
+  std::vector<int64_t> off(off_h, off_h + nblk), loff(nblk), uoff(nblk);
+  int64_t sl = 0, su = 0;
+  int maxp = 0;
+  for (int32_t j = 0; j < nblk; ++j) {
+    if (p[j] < 1 || p[j] > 1024) return fail(COSMO_E_INVAL, "PSD order out of range");
+    loff[j] = sl; uoff[j] = su; sl += p[j]; su += (int64_t)p[j] * p[j];
+    maxp = std::max(maxp, p[j]);
+  }
+  const size_t smem = psd_bwd_smem<T>(maxp, 256);
+  int dev = 0, maxs = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if ((int64_t)smem > maxs) return fail(COSMO_E_INVAL, "PSD order %d too large for one CTA", maxp);
+  CU(cudaFuncSetAttribute(k_psd_dk_batch<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DevArena a;
+  int32_t* dp;
+  int64_t *doff, *dloff, *duoff;
+  TRY(a.upload(&dp, p)); TRY(a.upload(&doff, off)); TRY(a.upload(&dloff, loff)); TRY(a.upload(&duoff, uoff));
+  PsdBatch<T> B{nblk, dp, doff, dloff, duoff};
+  k_psd_dk_batch<T, 256><<<nblk, 256, smem, st>>>(B, (const T*)lam, (const T*)U, (const T*)g, (T*)out, tau);
+  CU(cudaGetLastError());
+  g_launches += 1;
+  CU(cudaStreamSynchronize(st));
+  return COSMO_OK;
+}
+
+extern "C" {
+
+cosmo_status cosmo_psd_project(int32_t precision, int32_t nblk, const int32_t* p_host,
+                               const int64_t* off_host, const void* v, void* out, void* lam,
+                               void* U, void* stream) {
+  g_err.clear();
+  if (nblk < 0 || (nblk > 0 && (!p_host || !off_host || !v || !out)))
+    return fail(COSMO_E_INVAL, "bad arguments to cosmo_psd_project");
+  if (nblk == 0) return COSMO_OK;
+  if (precision == COSMO_PREC_FP64)
+    return psd_project_t<double>(nblk, p_host, off_host, v, out, lam, U, (cudaStream_t)stream);
+  if (precision == COSMO_PREC_MIXED)
+    return psd_project_t<float>(nblk, p_host, off_host, v, out, lam, U, (cudaStream_t)stream);
+  return fail(COSMO_E_INVAL, "unknown precision");
+}
+
+cosmo_status cosmo_psd_dk_backward(int32_t precision, int32_t nblk, const int32_t* p_host,
+                                   const int64_t* off_host, const void* lam, const void* U,
+                                   const void* g, void* out, double tau, void* stream) {
+  g_err.clear();
+  if (nblk < 0 || (nblk > 0 && (!p_host || !off_host || !lam || !U || !g || !out)))
+    return fail(COSMO_E_INVAL, "bad arguments to cosmo_psd_dk_backward");
+  if (nblk == 0) return COSMO_OK;
+  if (precision == COSMO_PREC_FP64)
+    return psd_dk_t<double>(nblk, p_host, off_host, lam, U, g, out, tau, (cudaStream_t)stream);
+  if (precision == COSMO_PREC_MIXED)
+    return psd_dk_t<float>(nblk, p_host, off_host, lam, U, g, out, tau, (cudaStream_t)stream);
+  return fail(COSMO_E_INVAL, "unknown precision");
+}
+
+}  // extern "C"

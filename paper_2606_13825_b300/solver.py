@@ -1,0 +1,381 @@
+"""Python binding of the unrolled COSMO library: a batch object holding the
+library handle, and ``torch.autograd.Function`` wrappers whose forward and
+backward are single calls into ``libcosmo_du.so``.
+
+Only argument marshalling happens here (packing instances into the batch
+CSR layout, taking tensor pointers and the current CUDA stream).  PyTorch
+provides device memory and streams; every step of the method runs in the
+library's CUDA kernels.
+"""
+import ctypes
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import scipy.sparse as sp
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+CONE_PSD = 4
+
+
+def _svec_rows(ctype, dim):
+    return dim * (dim + 1) // 2 if ctype == CONE_PSD else dim
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(POINTER(ctype)) if a is not None else None
+
+
+def _tp(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensors passed to the library must be contiguous CUDA tensors"
+    return c_void_p(t.data_ptr())
+
+
+def _stream():
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Packed:
+    """Batch layout of the C ABI (host numpy arrays)."""
+    col_off: np.ndarray
+    row_off: np.ndarray
+    P: sp.csr_matrix
+    A: sp.csr_matrix
+    q: np.ndarray
+    b: np.ndarray
+    box_l: Optional[np.ndarray]
+    box_u: Optional[np.ndarray]
+    cone_count: np.ndarray
+    cones: np.ndarray   # (ncones, 2) int32 (type, dim)
+
+
+def pack(problems: Sequence) -> Packed:
+    """Concatenate problems (objects with P, q, A, b, cones and optional
+    box_l / box_u) into the block-diagonal batch layout."""
+    ns = [pr.A.shape[1] for pr in problems]
+    ms = [pr.A.shape[0] for pr in problems]
+    col_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    row_off = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    A = sp.block_diag([sp.csr_matrix(pr.A) for pr in problems], format="csr")
+    P = sp.block_diag([sp.csr_matrix(pr.P) for pr in problems], format="csr")
+    A.sort_indices()
+    P.sort_indices()
+    q = np.concatenate([np.asarray(pr.q, np.float64) for pr in problems])
+    b = np.concatenate([np.asarray(pr.b, np.float64) for pr in problems])
+    has_box = any(getattr(pr, "box_l", None) is not None for pr in problems)
+    box_l = box_u = None
+    if has_box:
+        box_l = np.concatenate([np.asarray(pr.box_l, np.float64) if getattr(pr, "box_l", None) is not None
+                                else np.zeros(m) for pr, m in zip(problems, ms)])
+        box_u = np.concatenate([np.asarray(pr.box_u, np.float64) if getattr(pr, "box_u", None) is not None
+                                else np.zeros(m) for pr, m in zip(problems, ms)])
+    cone_count = np.array([len(pr.cones) for pr in problems], np.int32)
+    cones = np.array([c for pr in problems for c in pr.cones], np.int32).reshape(-1, 2)
+    return Packed(col_off, row_off, P, A, q, b, box_l, box_u, cone_count, cones)
+
+
+def _problem_struct(pk: Packed):
+    """ctypes Problem plus the arrays it points into (kept alive by the caller)."""
+    keep = []
+
+    def arr(x, dt):
+        a = np.ascontiguousarray(x, dtype=dt)
+        keep.append(a)
+        return a
+
+    A, P = pk.A, pk.P
+    pr = _abi.Problem()
+    pr.ninst = len(pk.cone_count)
+    pr.col_off = _ptr(arr(pk.col_off, np.int64), c_int64)
+    pr.row_off = _ptr(arr(pk.row_off, np.int64), c_int64)
+    if P.nnz > 0:
+        pr.P_rowptr = _ptr(arr(P.indptr, np.int64), c_int64)
+        pr.P_col = _ptr(arr(P.indices, np.int32), c_int32)
+        pr.P_val = _ptr(arr(P.data, np.float64), c_double)
+    pr.A_rowptr = _ptr(arr(A.indptr, np.int64), c_int64)
+    pr.A_col = _ptr(arr(A.indices, np.int32), c_int32)
+    pr.A_val = _ptr(arr(A.data, np.float64), c_double)
+    pr.q = _ptr(arr(pk.q, np.float64), c_double)
+    pr.b = _ptr(arr(pk.b, np.float64), c_double)
+    if pk.box_l is not None:
+        pr.box_l = _ptr(arr(pk.box_l, np.float64), c_double)
+        pr.box_u = _ptr(arr(pk.box_u, np.float64), c_double)
+    pr.cone_count = _ptr(arr(pk.cone_count, np.int32), c_int32)
+    cones = (_abi.Cone * max(1, len(pk.cones)))()
+    for i, (t, d) in enumerate(pk.cones):
+        cones[i].type, cones[i].dim = int(t), int(d)
+    keep.append(cones)
+    pr.cones = ctypes.cast(cones, POINTER(_abi.Cone))
+    return pr, keep
+
+
+def validate(problems) -> None:
+    """Host-only validation through the library (no device needed)."""
+    pr, keep = _problem_struct(pack(problems))
+    check(lib().cosmo_problem_validate(byref(pr)))
+
+
+def default_options(precision="mixed") -> _abi.Options:
+    o = _abi.Options()
+    check(lib().cosmo_options_default(byref(o), _abi.PREC_FP64 if precision == "fp64" else _abi.PREC_MIXED))
+    return o
+
+
+class CosmoBatch:
+    """A batch of conic programs resident on one GPU.
+
+    precision: "mixed" (float iterates, double reductions) or "fp64".
+    value_type: "f32" or "bf16" storage of P and A values (mixed only).
+    Remaining keyword arguments override fields of the C options struct.
+    """
+
+    def __init__(self, problems, precision="mixed", value_type="f32", device=0, **opts):
+        self.packed = pack(problems)
+        o = default_options(precision)
+        o.value_type = _abi.VAL_BF16 if value_type == "bf16" else _abi.VAL_F32
+        o.device = int(device)
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.options = o
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.device = torch.device("cuda", int(device))
+        pr, keep = _problem_struct(self.packed)
+        h = c_void_p()
+        check(lib().cosmo_batch_create(byref(pr), byref(o), byref(h)))
+        self._h = h
+        self.ninst = len(self.packed.cone_count)
+        self.n_total = int(self.packed.col_off[-1])
+        self.m_total = int(self.packed.row_off[-1])
+        self.K = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                lib().cosmo_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    # ------------------------------------------------------------------
+    def info(self):
+        inf = _abi.BatchInfo()
+        check(lib().cosmo_batch_get_info(self._h, byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def zeros(self, *shape, dtype=None):
+        return torch.zeros(*shape, dtype=dtype or self.dtype, device=self.device)
+
+    def forward(self, K, rho, alpha, x0=None, s0=None, y0=None, sigma=None, tape=True,
+                want_loss=True):
+        """Unroll K steps; returns (xK, sK, yK, loss) tensors (loss double)."""
+        K = int(K)
+        xK = self.zeros(self.n_total)
+        sK = self.zeros(self.m_total)
+        yK = self.zeros(self.m_total)
+        loss = self.zeros(self.ninst, dtype=torch.float64) if want_loss else None
+        sig = None
+        if sigma is not None:
+            sarr = np.broadcast_to(np.asarray(sigma, np.float64), (K,)).copy()
+            sig = sarr.ctypes.data_as(POINTER(c_double))
+        rho = rho.contiguous()
+        alpha = alpha.contiguous()
+        check(lib().cosmo_forward(self._h, K, sig, _tp(rho), _tp(alpha), _tp(x0), _tp(s0), _tp(y0),
+                                  _tp(xK), _tp(sK), _tp(yK), _tp(loss), 1 if tape else 0, _stream()))
+        self.K = K
+        return xK, sK, yK, loss
+
+    def backward(self, gxK=None, gsK=None, gyK=None, gloss=None, want_start=True):
+        K = self.K or 1   # without a forward the library reports E_STATE
+        grho = self.zeros(K, self.m_total)
+        galpha = self.zeros(K, self.ninst)
+        gx0 = self.zeros(self.n_total) if want_start else None
+        gs0 = self.zeros(self.m_total) if want_start else None
+        gy0 = self.zeros(self.m_total) if want_start else None
+        c = lambda t: None if t is None else t.contiguous()
+        check(lib().cosmo_backward(self._h, _tp(c(gxK)), _tp(c(gsK)), _tp(c(gyK)), _tp(c(gloss)),
+                                   _tp(grho), _tp(galpha), _tp(gx0), _tp(gs0), _tp(gy0), _stream()))
+        return {"grho": grho, "galpha": galpha, "gx0": gx0, "gs0": gs0, "gy0": gy0}
+
+    def residuals(self, x, s, y):
+        """(||r_p||^2, ||r_d||^2, objective) per instance, double tensors."""
+        rp2 = self.zeros(self.ninst, dtype=torch.float64)
+        rd2 = self.zeros(self.ninst, dtype=torch.float64)
+        obj = self.zeros(self.ninst, dtype=torch.float64)
+        check(lib().cosmo_residuals(self._h, _tp(x.contiguous()), _tp(s.contiguous()),
+                                    _tp(y.contiguous()), _tp(rp2), _tp(rd2), _tp(obj), _stream()))
+        return rp2, rd2, obj
+
+    def rho_from_log(self, log_rho, eq_scale=1e3):
+        K = log_rho.numel()
+        rho = self.zeros(K, self.m_total)
+        lr = log_rho.to(torch.float64).contiguous()
+        check(lib().cosmo_rho_from_log(self._h, K, _tp(lr), float(eq_scale), _tp(rho), _stream()))
+        return rho
+
+    def rho_from_log_backward(self, rho, grho):
+        K = rho.shape[0]
+        out = self.zeros(K, dtype=torch.float64)
+        check(lib().cosmo_rho_from_log_backward(self._h, K, _tp(rho.contiguous()),
+                                                _tp(grho.contiguous()), _tp(out), _stream()))
+        return out
+
+    def alpha_broadcast(self, alpha_k):
+        K = alpha_k.numel()
+        out = self.zeros(K, self.ninst)
+        a = alpha_k.to(torch.float64).contiguous()
+        check(lib().cosmo_alpha_broadcast(self._h, K, _tp(a), _tp(out), _stream()))
+        return out
+
+    def alpha_reduce(self, galpha):
+        K = galpha.shape[0]
+        out = self.zeros(K, dtype=torch.float64)
+        check(lib().cosmo_alpha_reduce(self._h, K, _tp(galpha.contiguous()), _tp(out), _stream()))
+        return out
+
+    KERNEL_CLASSES = ("rho_check", "rho_rectify", "alpha_check", "precond", "rhs", "pcg", "post",
+                      "soc_fwd", "psd_fwd", "residuals", "loss_seed", "bwd_gproj", "soc_bwd",
+                      "psd_bwd", "bwd_relax", "pcg_adj", "bwd_solve", "rect_adjoint")
+
+    def profile(self, kernel=None, enable=True):
+        """Time launches with CUDA events: kernel=None every class, a class
+        name only that class; enable=False turns timing off."""
+        arg = (kernel.encode() if kernel else None) if enable else b""
+        check(lib().cosmo_profile_enable(self._h, arg))
+
+    def profile_read(self, kernel=None, reset=True):
+        """(total ms, launches) of the timed launches of a class (None = all)."""
+        ms = c_double()
+        n = c_int64()
+        check(lib().cosmo_profile_read(self._h, kernel.encode() if kernel else None, byref(ms),
+                                       byref(n), 1 if reset else 0))
+        return ms.value, n.value
+
+    def status(self):
+        flags = np.zeros(self.ninst, np.int32)
+        check(lib().cosmo_status_sync(self._h, flags.ctypes.data_as(POINTER(c_int32))))
+        return flags
+
+    def step_host(self, K, log_rho, alpha_k, sigma=1e-6, eq_scale=1e3, x0=None, s0=None,
+                  y0=None, want_start_grads=False, stream=None):
+        """One end-to-end differentiable step through host buffers (numpy,
+        pinned or pageable).  Returns (loss[ninst], glog_rho[K], galpha_k[K])."""
+        K = int(K)
+        lr = np.ascontiguousarray(log_rho, np.float64)
+        ak = np.ascontiguousarray(alpha_k, np.float64)
+        loss = np.zeros(self.ninst)
+        glr = np.zeros(K)
+        gak = np.zeros(K)
+        p = lambda a: None if a is None else c_void_p(a.ctypes.data)
+        st = c_void_p(stream) if stream is not None else _stream()
+        check(lib().cosmo_step_host(self._h, K, float(sigma), float(eq_scale), p(lr), p(ak),
+                                    p(x0), p(s0), p(y0), p(loss), p(glr), p(gak),
+                                    None, None, None, st))
+        return loss, glr, gak
+
+
+# ---------------------------------------------------------------------------
+class CosmoUnroll(torch.autograd.Function):
+    """(rho[K, m], alpha[K, ninst], x0, s0, y0) -> (x^K, s^K, y^K, loss[ninst])."""
+
+    @staticmethod
+    def forward(ctx, batch, K, sigma, rho, alpha, x0, s0, y0):
+        xK, sK, yK, loss = batch.forward(K, rho, alpha, x0, s0, y0, sigma=sigma, tape=True)
+        ctx.batch = batch
+        ctx.has_start = (x0 is not None, s0 is not None, y0 is not None)
+        return xK, sK, yK, loss
+
+    @staticmethod
+    def backward(ctx, gx, gs, gy, gloss):
+        g = ctx.batch.backward(gx, gs, gy, gloss)
+        hx, hs, hy = ctx.has_start
+        return (None, None, None, g["grho"], g["galpha"], g["gx0"] if hx else None,
+                g["gs0"] if hs else None, g["gy0"] if hy else None)
+
+
+class RhoFromLog(torch.autograd.Function):
+    """log_rho[K] -> rho[K, m_total] with the equality-row scaling."""
+
+    @staticmethod
+    def forward(ctx, batch, log_rho, eq_scale):
+        rho = batch.rho_from_log(log_rho, eq_scale)
+        ctx.batch = batch
+        ctx.save_for_backward(rho)
+        ctx.ldtype = log_rho.dtype
+        return rho
+
+    @staticmethod
+    def backward(ctx, grho):
+        (rho,) = ctx.saved_tensors
+        return None, ctx.batch.rho_from_log_backward(rho, grho).to(ctx.ldtype), None
+
+
+class AlphaBroadcast(torch.autograd.Function):
+    """alpha_k[K] -> alpha[K, ninst]."""
+
+    @staticmethod
+    def forward(ctx, batch, alpha_k):
+        ctx.batch = batch
+        ctx.adtype = alpha_k.dtype
+        return batch.alpha_broadcast(alpha_k)
+
+    @staticmethod
+    def backward(ctx, galpha):
+        return None, ctx.batch.alpha_reduce(galpha).to(ctx.adtype)
+
+
+def unrolled_residual_loss(batch, log_rho, alpha_k, sigma=1e-6, eq_scale=1e3, x0=None, s0=None,
+                           y0=None):
+    """Meta-loss of the batched differentiable workload: sum over instances of
+    ||r_p^K||^2 + ||r_d^K||^2, differentiable in the per-step log rho_k and
+    alpha_k (and the warm start)."""
+    K = log_rho.numel()
+    rho = RhoFromLog.apply(batch, log_rho, eq_scale)
+    alpha = AlphaBroadcast.apply(batch, alpha_k)
+    xK, sK, yK, loss = CosmoUnroll.apply(batch, K, sigma, rho, alpha, x0, s0, y0)
+    return loss.sum(), (xK, sK, yK, loss)
+
+
+# ---------------------------------------------------------------------------
+def _psd_layout(ps):
+    ps = np.asarray(ps, np.int32)
+    d = ps.astype(np.int64) * (ps + 1) // 2
+    off = np.concatenate([[0], np.cumsum(d)[:-1]]).astype(np.int64)
+    return ps, off, int(d.sum()), int(ps.sum()), int((ps.astype(np.int64) ** 2).sum())
+
+
+def psd_project(v: torch.Tensor, ps, precision="mixed"):
+    """Batched PSD projection (Eq. psd-proj) of svec blocks stored back to back
+    in v.  Returns (projected svec, eigenvalues, eigenvectors column-major per
+    block)."""
+    ps, off, d, sl, su = _psd_layout(ps)
+    assert v.numel() == d
+    out = torch.empty_like(v)
+    lam = torch.empty(sl, dtype=v.dtype, device=v.device)
+    U = torch.empty(su, dtype=v.dtype, device=v.device)
+    prec = _abi.PREC_FP64 if precision == "fp64" else _abi.PREC_MIXED
+    check(lib().cosmo_psd_project(prec, len(ps), _ptr(ps, c_int32), _ptr(off, c_int64),
+                                  _tp(v.contiguous()), _tp(out), _tp(lam), _tp(U), _stream()))
+    return out, lam, U
+
+
+def psd_dk_backward(lam, U, g, ps, precision="mixed", tau=1e-12):
+    """Daleckii-Krein backward (Eq. psd-cotangent-dk) for blocks laid out as
+    psd_project returns them."""
+    ps, off, d, sl, su = _psd_layout(ps)
+    out = torch.empty_like(g)
+    prec = _abi.PREC_FP64 if precision == "fp64" else _abi.PREC_MIXED
+    check(lib().cosmo_psd_dk_backward(prec, len(ps), _ptr(ps, c_int32), _ptr(off, c_int64),
+                                      _tp(lam.contiguous()), _tp(U.contiguous()),
+                                      _tp(g.contiguous()), _tp(out), float(tau), _stream()))
+    return out

@@ -1,0 +1,303 @@
+"""GPU parity of the unrolled iteration (forward and backward) against the
+CPU oracle, through the C ABI.
+
+Tolerances.  FP64 path: the oracle solves the KKT system directly, the GPU by
+CG to a relative residual of 1e-12 here; the averaged ADMM map adds per-step
+solve errors at most linearly, so iterates and gradients agree to about
+K * kappa(M) * 1e-12 -- the tests use 1e-7.  Mixed path (float iterates,
+double reductions): objective within 1e-4 of the magnitude of the terms it
+sums, the loss ||r||^2 with ||r|| within 1e-4 of the OSQP-style residual
+normaliser, iterates within 1e-4, gradients within 1e-3 (norm-wise per
+output) -- the accuracy gate of the batched differentiable workload, at the
+small K used here.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from _cases import (maxcut_batch, socp_batch, edge_instance, unconstrained_instance,
+                    random_inputs, oracle_batch, rel_inf, rel_l2, default_rho_rows)
+from synth import covsteer_problem, lovasz_problem, erdos_renyi, cycle_graph
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def run_gpu(problems, rho, alpha, x0, s0, y0, precision, sigma=1e-6, gloss=True, **opts):
+    from paper_2606_13825_b300 import CosmoBatch
+    b = CosmoBatch(problems, precision=precision, **opts)
+    dt = b.dtype
+    t = lambda a: None if a is None else torch.tensor(a, dtype=dt, device="cuda")
+    xK, sK, yK, loss = b.forward(rho.shape[0], t(rho), t(alpha), t(x0), t(s0), t(y0), sigma=sigma)
+    gl = torch.ones(b.ninst, dtype=torch.float64, device="cuda") if gloss else None
+    g = b.backward(gloss=gl)
+    rp2, rd2, obj = b.residuals(xK, sK, yK)
+    torch.cuda.synchronize()
+    out = {"xK": xK, "sK": sK, "yK": yK, "loss": loss, "obj": obj, **g}
+    out = {k: (v.double().cpu().numpy() if v is not None else None) for k, v in out.items()}
+    out["flags"] = b.status()
+    out["batch"] = b
+    return out
+
+
+def compare(gpu, ora, precision, check_grad=True):
+    if precision == "fp64":
+        tol_state, tol_grad = 1e-7, 1e-7
+        for k in ("xK", "sK", "yK"):
+            assert rel_inf(gpu[k], ora[k]) < tol_state, k
+        assert rel_inf(gpu["loss"], ora["loss"]) < tol_state
+        if check_grad:
+            for k in ("grho", "galpha", "gx0", "gs0", "gy0"):
+                assert rel_inf(gpu[k], ora[k]) < tol_grad, (k, rel_inf(gpu[k], ora[k]))
+    else:
+        # objective / loss relative to the magnitude of the terms they sum
+        # (|q||x| + |x||P||x| resp. the squared OSQP-style residual scale):
+        # FP32 iterates cannot give 1e-4 relative to a value that is itself
+        # formed by cancellation
+        for i in range(len(ora["loss"])):
+            lo, rs = ora["loss"][i], ora["res_scale"][i]
+            assert abs(gpu["loss"][i] - lo) <= 1e-4 * max(lo, 2 * math.sqrt(lo) * rs + 1e-4 * rs * rs), i
+            assert abs(gpu["obj"][i] - ora["obj"][i]) <= 1e-4 * max(abs(ora["obj"][i]), ora["obj_scale"][i]), i
+        for k in ("xK", "sK", "yK"):
+            assert rel_inf(gpu[k], ora[k]) < 1e-4, (k, rel_inf(gpu[k], ora[k]))
+        if check_grad:
+            for k in ("grho", "galpha", "gx0", "gs0", "gy0"):
+                assert rel_l2(gpu[k], ora[k]) < 1e-3, (k, rel_l2(gpu[k], ora[k]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_maxcut_batch_forward_backward(precision):
+    _need_gpu()
+    probs = maxcut_batch([3, 5, 8, 12, 17, 23], seed=101)
+    K = 6
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=7)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not gpu["flags"].any(), gpu["flags"]
+    compare(gpu, ora, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_maxcut_large_block_tiles(precision):
+    """A 41x41 PSD block exercises the 4x4 register tiles of the DK contractions."""
+    _need_gpu()
+    probs = maxcut_batch([41], seed=102)
+    K = 2
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=8)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    compare(gpu, ora, precision)
+
+
+@pytest.mark.parametrize("precision,value_type", [("fp64", "f32"), ("mixed", "f32")])
+def test_socp_batch(precision, value_type):
+    _need_gpu()
+    probs = socp_batch(3, seed=4100)
+    K = 4
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=9)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, value_type=value_type,
+                  cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not (gpu["flags"] & 3).any(), gpu["flags"]
+    compare(gpu, ora, precision)
+
+
+def test_socp_bf16_values_vs_rounded_oracle():
+    """BF16 storage of P and A: parity against the oracle run on the same
+    bf16-rounded matrices (the rounding is the input, not an error)."""
+    _need_gpu()
+    import scipy.sparse as sp
+    probs = socp_batch(2, seed=4200)
+    rnd = lambda M: sp.csr_matrix((torch.tensor(M.data).to(torch.bfloat16).double().numpy(), M.indices, M.indptr), shape=M.shape)
+    for p in probs:
+        p.A = rnd(p.A)
+        p.P = rnd(p.P)
+    K = 3
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=10)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, "mixed", value_type="bf16")
+    compare(gpu, ora, "mixed")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_covsteer_many_small_blocks(precision):
+    _need_gpu()
+    probs = [covsteer_problem(5100 + j, T=2) for j in range(3)]
+    K = 4
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=11)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    compare(gpu, ora, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_cones_and_empty_instance(precision):
+    """Every cone type, SOC dims 1/2, PSD orders 1/2/3, an all-zero row of A and
+    an instance with no constraints at all, in one ragged batch."""
+    _need_gpu()
+    probs = [edge_instance(1), unconstrained_instance(2), edge_instance(3)]
+    K = 5
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=12)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, cg_tol=1e-13 if precision == "fp64" else 1e-8)
+    compare(gpu, ora, precision)
+
+
+def test_lovasz_repeated_eigenvalues_fp64_and_mixed():
+    """Vertex-transitive graphs (cycle C_7, complete K_6) make the iterate's
+    PSD block have coincident eigenvalues; DK must stay finite and match."""
+    _need_gpu()
+    probs = [lovasz_problem(7, cycle_graph(7)), lovasz_problem(6, [(i, j) for i in range(6) for j in range(i + 1, 6)])]
+    K = 6
+    rho, alpha, _, _, _ = random_inputs(probs, K, seed=13, noise=0.0)
+    alpha[:] = 1.6
+    ora = oracle_batch(probs, rho, alpha, 1e-6, None, None, None)
+    for prec in ("fp64", "mixed"):
+        gpu = run_gpu(probs, rho, alpha, None, None, None, prec, cg_tol=1e-12 if prec == "fp64" else 1e-8)
+        for k in ("grho", "galpha"):
+            assert np.all(np.isfinite(gpu[k]))
+        compare(gpu, ora, prec)
+
+
+def test_checkpointing_is_bitwise_identical():
+    _need_gpu()
+    probs = maxcut_batch([6, 9, 14], seed=103) + socp_batch(1, seed=4300)
+    K = 7
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=14)
+    full = run_gpu(probs, rho, alpha, x0, s0, y0, "mixed")
+    for c in (1, 2, 3):
+        ck = run_gpu(probs, rho, alpha, x0, s0, y0, "mixed", checkpoint_every=c)
+        for k in ("xK", "loss", "grho", "galpha", "gx0", "gs0", "gy0"):
+            assert np.array_equal(full[k], ck[k]), (c, k)
+
+
+def test_graph_direct_and_repeat_are_bitwise_identical():
+    _need_gpu()
+    probs = maxcut_batch([7, 11], seed=104) + [edge_instance(4)]
+    K = 5
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=15)
+    a = run_gpu(probs, rho, alpha, x0, s0, y0, "mixed", use_graph=1)
+    b = run_gpu(probs, rho, alpha, x0, s0, y0, "mixed", use_graph=0)
+    for k in ("xK", "loss", "grho", "galpha", "gy0"):
+        assert np.array_equal(a[k], b[k]), k
+    # same batch object, second call (graph replay), and a second backward
+    bt = a["batch"]
+    t = lambda v: torch.tensor(v, dtype=torch.float32, device="cuda")
+    xK, _, _, loss = bt.forward(K, t(rho), t(alpha), t(x0), t(s0), t(y0))
+    g1 = bt.backward(gloss=torch.ones(bt.ninst, dtype=torch.float64, device="cuda"))
+    g2 = bt.backward(gloss=torch.ones(bt.ninst, dtype=torch.float64, device="cuda"))
+    assert np.array_equal(loss.double().cpu().numpy(), a["loss"])
+    assert torch.equal(g1["grho"], g2["grho"]) and torch.equal(g1["gx0"], g2["gx0"])
+    assert np.array_equal(g1["grho"].double().cpu().numpy(), a["grho"])
+
+
+def test_fd_fp64_gpu_directional():
+    """Central finite differences of the GPU FP64 path (h = 1e-6 as the
+    batched workload prescribes; 1e-4 as a truncation/rounding cross-check)
+    against its own analytic gradient, along random directions in
+    (log rho_k, alpha_k)."""
+    _need_gpu()
+    from paper_2606_13825_b300 import CosmoBatch
+    from paper_2606_13825_b300.solver import unrolled_residual_loss
+    probs = maxcut_batch([6, 9, 13], seed=105)
+    b = CosmoBatch(probs, precision="fp64", cg_tol=1e-13)
+    K = 5
+    rng = np.random.default_rng(16)
+    lr = torch.tensor(np.log(0.1) + 0.2 * rng.standard_normal(K), dtype=torch.float64, device="cuda",
+                      requires_grad=True)
+    ak = torch.tensor(1.6 - 0.3 * rng.random(K), dtype=torch.float64, device="cuda", requires_grad=True)
+    L, _ = unrolled_residual_loss(b, lr, ak)
+    L.backward()
+    for _ in range(3):
+        dl = torch.tensor(rng.standard_normal(K), device="cuda", dtype=torch.float64)
+        da = torch.tensor(rng.standard_normal(K), device="cuda", dtype=torch.float64)
+        an = float((lr.grad * dl).sum() + (ak.grad * da).sum())
+        errs = []
+        for h in (1e-6, 1e-4):
+            with torch.no_grad():
+                Lp, _ = unrolled_residual_loss(b, lr + h * dl, ak + h * da)
+                Lm, _ = unrolled_residual_loss(b, lr - h * dl, ak - h * da)
+            errs.append(abs(float(Lp - Lm) / (2 * h) - an))
+        assert min(errs) <= 1e-5 * (abs(an) + 1e-3 * float(L)), (errs, an)
+
+
+def test_autograd_chain_matches_oracle():
+    """torch.autograd through RhoFromLog -> CosmoUnroll -> AlphaBroadcast gives
+    the oracle's gradient w.r.t. the per-step (log rho_k, alpha_k)."""
+    _need_gpu()
+    from paper_2606_13825_b300 import CosmoBatch
+    from paper_2606_13825_b300.solver import unrolled_residual_loss
+    probs = maxcut_batch([5, 8, 10], seed=106)
+    K = 4
+    rng = np.random.default_rng(17)
+    lr0 = np.log(0.1) + 0.2 * rng.standard_normal(K)
+    ak0 = 1.6 - 0.3 * rng.random(K)
+    rows = np.concatenate([np.where(p.row_types() == 0, 1e3, 1.0) for p in probs])
+    rho = np.exp(lr0)[:, None] * rows[None, :]
+    alpha = np.tile(ak0[:, None], (1, len(probs)))
+    ora = oracle_batch(probs, rho, alpha, 1e-6, None, None, None)
+    g_lr = (ora["grho"] * rho).sum(axis=1)
+    g_ak = ora["galpha"].sum(axis=1)
+    for prec, tol in (("fp64", 1e-7), ("mixed", 1e-3)):
+        b = CosmoBatch(probs, precision=prec, cg_tol=1e-12 if prec == "fp64" else 1e-8)
+        lr = torch.tensor(lr0, dtype=torch.float64, device="cuda", requires_grad=True)
+        ak = torch.tensor(ak0, dtype=torch.float64, device="cuda", requires_grad=True)
+        L, _ = unrolled_residual_loss(b, lr, ak)
+        L.backward()
+        assert abs(float(L) - ora["loss"].sum()) <= (1e-9 if prec == "fp64" else 1e-4) * ora["loss"].sum()
+        assert rel_l2(lr.grad.cpu().numpy(), g_lr) < tol
+        assert rel_l2(ak.grad.cpu().numpy(), g_ak) < tol
+        # the host-buffer end-to-end entry point computes the same step
+        loss_h, glr_h, gak_h = b.step_host(K, lr0, ak0)
+        assert np.allclose(loss_h.sum(), float(L), rtol=1e-12, atol=0)
+        assert np.array_equal(glr_h, lr.grad.cpu().numpy())
+        assert np.array_equal(gak_h, ak.grad.cpu().numpy())
+
+
+def test_parameter_maps_closed_form():
+    _need_gpu()
+    from paper_2606_13825_b300 import CosmoBatch
+    probs = maxcut_batch([4, 6], seed=107)
+    b = CosmoBatch(probs, precision="fp64")
+    lr = torch.tensor([0.3, -1.0, 2.0], dtype=torch.float64, device="cuda")
+    rho = b.rho_from_log(lr, 1e3).cpu().numpy()
+    rows = np.concatenate([np.where(p.row_types() == 0, 1e3, 1.0) for p in probs])
+    assert np.allclose(rho, np.exp(lr.cpu().numpy())[:, None] * rows[None, :], rtol=1e-15)
+    g = torch.randn(3, b.m_total, dtype=torch.float64, device="cuda")
+    gl = b.rho_from_log_backward(torch.tensor(rho, device="cuda"), g).cpu().numpy()
+    assert np.allclose(gl, (g.cpu().numpy() * rho).sum(1), rtol=1e-12)
+    a = b.alpha_broadcast(torch.tensor([1.1, 1.5, 1.9], dtype=torch.float64, device="cuda"))
+    assert a.shape == (3, 2) and float(a[2, 1]) == 1.9
+    ga = torch.randn(3, 2, dtype=torch.float64, device="cuda")
+    assert np.allclose(b.alpha_reduce(ga).cpu().numpy(), ga.sum(1).cpu().numpy(), rtol=1e-14)
+
+
+def test_device_flags_bad_parameters_and_cg_cap():
+    """Conditions found on the device are reported per instance, never trap."""
+    _need_gpu()
+    from paper_2606_13825_b300 import CosmoBatch, _abi
+    probs = socp_batch(2, seed=4400)
+    K = 2
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=18)
+    rho[0, 3] = -1.0            # instance 0
+    alpha[1, 1] = 2.5           # instance 1
+    b = CosmoBatch(probs, precision="mixed")
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    b.forward(K, t(rho), t(alpha))
+    f = b.status()
+    assert f[0] & _abi.FLAG_BAD_PARAM and f[1] & _abi.FLAG_BAD_PARAM
+    assert not b.status().any()        # cleared by the read
+    b2 = CosmoBatch(probs, precision="fp64", cg_max_iter=1, cg_tol=1e-14)
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=19)
+    tt = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    b2.forward(K, tt(rho), tt(alpha), tt(x0), tt(s0), tt(y0))
+    assert (b2.status() & _abi.FLAG_CG_CAP).all()
+    with pytest.raises(_abi.CosmoError) as ei:
+        CosmoBatch(probs, precision="fp64").backward()
+    assert ei.value.status == _abi.COSMO_E_STATE
