@@ -268,6 +268,33 @@ cosmo_status cosmo_status_sync(cosmo_batch* batch, int32_t* flags_host);
 
 /* ---- standalone kernels (each is one step of the path, usable alone) ---- */
 
+/* Matrix-free solve of the reduced system of Sec. 2.3, Eq. (reduced):
+ *     (P + sigma I + A' D(rho) A) x = rhs
+ * for ninst independent blocks of a block-diagonal batch, by Jacobi-
+ * preconditioned CG (App. D) with double inner products, one CTA per block.
+ * Every array is caller-owned DEVICE memory; real = float (MIXED) or double
+ * (FP64):
+ *   col_off, row_off: int64 [ninst+1] (columns / rows of each block)
+ *   A_rowptr int64 [m+1], A_col int32, A_val real: A in CSR (global indices)
+ *   AT_rowptr int64 [n+1], AT_col int32, AT_val real: the CSR of A'
+ *   P_rowptr int64 [n+1], P_col int32, P_val real: P (both triangles), or
+ *     all three NULL for P = 0
+ *   rho real [m] (> 0), rhs real [n]
+ *   x real [n]: in, the warm start when warm_start = 1 (else ignored);
+ *     out, the solution
+ *   iters int32 [ninst] or NULL: CG iterations per block (== max_iter means
+ *     the cap was reached before ||r|| <= tol ||rhs||)
+ * Workspace (4n + m reals, 2 ninst int32) is allocated stream-ordered on
+ * `stream` and released before return.  Errors: E_INVAL, E_NOMEM, E_CUDA. */
+cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_t m,
+                             const int64_t* col_off, const int64_t* row_off,
+                             const int64_t* A_rowptr, const int32_t* A_col, const void* A_val,
+                             const int64_t* AT_rowptr, const int32_t* AT_col, const void* AT_val,
+                             const int64_t* P_rowptr, const int32_t* P_col, const void* P_val,
+                             double sigma, const void* rho, const void* rhs, void* x,
+                             int32_t warm_start, double tol, int32_t max_iter, int32_t* iters,
+                             void* stream);
+
 /* Batched PSD projection, Eq. (psd-proj), on nblk blocks given in svec form.
  * Block j has order p[j] and starts at svec offset off[j] of v and out
  * (dev real, sum of p(p+1)/2 entries).  lam (dev real, sum p, may be NULL)

@@ -86,6 +86,9 @@ _SIGS = {
     "cosmo_profile_enable": (c_int32, [c_void_p, c_char_p]),
     "cosmo_profile_read": (c_int32, [c_void_p, c_char_p, POINTER(c_double), POINTER(c_int64),
                                      c_int32]),
+    "cosmo_pcg_solve": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
+                        [c_double, c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
+                         c_void_p, c_void_p]),
     "cosmo_psd_project": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_psd_dk_backward": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),

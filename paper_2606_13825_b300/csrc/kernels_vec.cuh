@@ -565,6 +565,32 @@ __global__ void k_rect_adjoint(Prob<T, V> P, int32_t K, T* __restrict__ g) {
 }
 
 // ---------------------------------------------------------------------------
+// standalone solve helpers: the Jacobi preconditioner from a caller's CSR
+// (the diagonal of P is looked up in its rows) and an identity schedule
+// ---------------------------------------------------------------------------
+template <class T, class V>
+__global__ void k_precond_csr(Prob<T, V> P, double sigma, const T* __restrict__ rho,
+                              T* __restrict__ dinv) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.n_total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    T acc = (T)sigma;
+    if (P.P_rp) {
+      for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e)
+        if (P.P_ci[e] == j) acc += (T)ldv(P.P_v, e);
+    }
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) {
+      const T a = (T)ldv(P.AT_v, e);
+      acc += a * a * rho[P.AT_ci[e]];
+    }
+    dinv[j] = T(1) / acc;
+  }
+}
+
+__global__ void k_iota(int32_t n, int32_t* __restrict__ out) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
+}
+
+// ---------------------------------------------------------------------------
 // parameter maps for per-iteration learnable scalars
 // ---------------------------------------------------------------------------
 template <class T, class V>

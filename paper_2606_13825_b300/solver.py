@@ -379,3 +379,52 @@ def psd_dk_backward(lam, U, g, ps, precision="mixed", tau=1e-12):
                                       _tp(lam.contiguous()), _tp(U.contiguous()),
                                       _tp(g.contiguous()), _tp(out), float(tau), _stream()))
     return out
+
+
+# ---------------------------------------------------------------------------
+class ReducedSystem:
+    """Device CSR copies of A, A' and P for standalone solves of the reduced
+    system (P + sigma I + A'D(rho)A) x = rhs (Sec. 2.3, Eq. reduced).
+    `blocks` lists (P_i, A_i) of a block-diagonal batch (scipy matrices)."""
+
+    def __init__(self, blocks, precision="mixed", device=0):
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        dev = torch.device("cuda", int(device))
+        Ps = [sp.csr_matrix(P) for P, _ in blocks]
+        As = [sp.csr_matrix(A) for _, A in blocks]
+        ns = [A.shape[1] for A in As]
+        ms = [A.shape[0] for A in As]
+        A = sp.block_diag(As, format="csr")
+        P = sp.block_diag(Ps, format="csr")
+        AT = A.T.tocsr()
+        for M in (A, P, AT):
+            M.sort_indices()
+        self.ninst = len(blocks)
+        self.n = int(sum(ns))
+        self.m = int(sum(ms))
+        i64 = lambda a: torch.tensor(np.asarray(a, np.int64), device=dev)
+        i32 = lambda a: torch.tensor(np.asarray(a, np.int32), device=dev)
+        rv = lambda a: torch.tensor(np.asarray(a, np.float64), dtype=self.dtype, device=dev)
+        self.col_off = i64(np.concatenate([[0], np.cumsum(ns)]))
+        self.row_off = i64(np.concatenate([[0], np.cumsum(ms)]))
+        self.A = (i64(A.indptr), i32(A.indices), rv(A.data))
+        self.AT = (i64(AT.indptr), i32(AT.indices), rv(AT.data))
+        self.P = (i64(P.indptr), i32(P.indices), rv(P.data)) if P.nnz else (None, None, None)
+
+    def args(self):
+        return [_tp(self.col_off), _tp(self.row_off), *map(_tp, self.A), *map(_tp, self.AT),
+                *map(_tp, self.P)]
+
+
+def pcg_solve(system: ReducedSystem, sigma, rho, rhs, x0=None, tol=1e-8, max_iter=500):
+    """x = (P + sigma I + A'D(rho)A)^-1 rhs by the library's Jacobi-PCG;
+    returns (x, iterations per block)."""
+    x = x0.clone().contiguous() if x0 is not None else torch.zeros_like(rhs)
+    iters = torch.zeros(system.ninst, dtype=torch.int32, device=rhs.device)
+    prec = _abi.PREC_FP64 if system.precision == "fp64" else _abi.PREC_MIXED
+    check(lib().cosmo_pcg_solve(prec, system.ninst, system.n, system.m, *system.args(),
+                                float(sigma), _tp(rho.contiguous()), _tp(rhs.contiguous()), _tp(x),
+                                1 if x0 is not None else 0, float(tol), int(max_iter), _tp(iters),
+                                _stream()))
+    return x, iters
