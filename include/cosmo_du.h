@@ -295,6 +295,32 @@ cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_
                              int32_t warm_start, double tol, int32_t max_iter, int32_t* iters,
                              void* stream);
 
+/* The same solve as cosmo_pcg_solve, for callers that must not allocate device
+ * memory while they run (a controller calling the solver at a fixed rate
+ * cannot risk cudaMalloc's latency, implicit synchronisation or failure; a
+ * host that gives the library a fixed device budget may forbid allocation).
+ * The paper has no counterpart: this is an interface for such callers.
+ * Arguments, layouts and results are those of cosmo_pcg_solve.  The CG
+ * workspace (4n + m reals and 2 ninst int32) comes from one file-scope device
+ * array of COSMO_PCG_NOALLOC_MAX_BYTES bytes, which every GPU that loads the
+ * library holds until the process exits; larger problems return E_INVAL.
+ * The call makes no cudaMalloc / cudaFree / allocating library call.
+ * The first call on each device looks up the array's device address with
+ * that device current, so make it before any stream capture.  All calls
+ * share the array (it keeps the previous call's contents; the call clears
+ * what must start at zero): calls that overlap on the GPU race on it and
+ * must be ordered by the caller. */
+#define COSMO_PCG_NOALLOC_MAX_BYTES (16 * 1024 * 1024)
+cosmo_status cosmo_pcg_solve_noalloc(int32_t precision, int32_t ninst, int64_t n, int64_t m,
+                                     const int64_t* col_off, const int64_t* row_off,
+                                     const int64_t* A_rowptr, const int32_t* A_col,
+                                     const void* A_val, const int64_t* AT_rowptr,
+                                     const int32_t* AT_col, const void* AT_val,
+                                     const int64_t* P_rowptr, const int32_t* P_col,
+                                     const void* P_val, double sigma, const void* rho,
+                                     const void* rhs, void* x, int32_t warm_start, double tol,
+                                     int32_t max_iter, int32_t* iters, void* stream);
+
 /* Batched PSD projection, Eq. (psd-proj), on nblk blocks given in svec form.
  * Block j has order p[j] and starts at svec offset off[j] of v and out
  * (dev real, sum of p(p+1)/2 entries).  lam (dev real, sum p, may be NULL)

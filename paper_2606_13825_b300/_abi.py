@@ -89,6 +89,9 @@ _SIGS = {
     "cosmo_pcg_solve": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
                         [c_double, c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int32,
                          c_void_p, c_void_p]),
+    "cosmo_pcg_solve_noalloc": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
+                                [c_double, c_void_p, c_void_p, c_void_p, c_int32, c_double,
+                                 c_int32, c_void_p, c_void_p]),
     "cosmo_psd_project": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_psd_dk_backward": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),

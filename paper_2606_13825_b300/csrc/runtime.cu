@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <type_traits>
@@ -1282,3 +1283,116 @@ cosmo_status cosmo_psd_dk_backward(int32_t precision, int32_t nblk, const int32_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the standalone reduced-system solve.
+//
+// Some callers cannot allocate device memory once they are running: a
+// fixed-rate control loop (an MPC or covariance-steering controller that
+// calls the solver every few milliseconds) cannot afford cudaMalloc's latency,
+// its implicit device synchronisation or the chance that it fails mid-run;
+// hosts that hand the library a fixed device budget up front may forbid any
+// allocation outside it.  For them the CG workspace lives in one file-scope
+// device array, reserved when the library is loaded and held on every GPU that
+// loads it until the process exits.
+//
+// Host code may not pass g_pcg_scratch itself to a kernel: on the host that
+// name is only a stand-in for the device symbol.  The first call on each
+// device looks up the symbol's device address (cudaGetSymbolAddress, with that
+// device current) and caches it; that first call should therefore happen
+// before any stream capture.  Every call shares the one array, so calls that
+// overlap on the GPU (different streams, or different host threads on the
+// same device) race on it; the caller must order them.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_pcg_scratch[COSMO_PCG_NOALLOC_MAX_BYTES];
+
+static std::mutex g_scratch_mu;
+static void* g_scratch_addr[64] = {nullptr};
+
+static cosmo_status scratch_address(void** out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(COSMO_E_INVAL, "device ordinal %d not supported", dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return fail(COSMO_E_CUDA, "cudaGetSymbolAddress of the solve scratch failed on device %d: %s",
+                  dev, cudaGetErrorString(e));
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return COSMO_OK;
+}
+
+template <class T>
+static cosmo_status pcg_solve_noalloc_t(int32_t ninst, int64_t n, int64_t m, const int64_t* col_off,
+                                        const int64_t* row_off, const int64_t* A_rp,
+                                        const int32_t* A_ci, const void* A_v, const int64_t* AT_rp,
+                                        const int32_t* AT_ci, const void* AT_v, const int64_t* P_rp,
+                                        const int32_t* P_ci, const void* P_v, double sigma,
+                                        const void* rho, const void* rhs, void* x, int32_t warm,
+                                        double tol, int32_t maxit, int32_t* iters,
+                                        cudaStream_t st) {
+  const size_t need = sizeof(T) * (size_t)(4 * n + m) + sizeof(int32_t) * 2 * (size_t)ninst;
+  if (need > (size_t)COSMO_PCG_NOALLOC_MAX_BYTES)
+    return fail(COSMO_E_INVAL,
+                "cosmo_pcg_solve_noalloc: n=%lld, m=%lld, ninst=%d need %zu bytes of scratch, "
+                "above the fixed maximum of %d bytes",
+                (long long)n, (long long)m, ninst, need, (int)COSMO_PCG_NOALLOC_MAX_BYTES);
+  void* base = nullptr;
+  TRY(scratch_address(&base));
+  T* dinv = reinterpret_cast<T*>(base);
+  T* r = dinv + n;
+  T* p = r + n;
+  T* u = p + n;
+  T* t = u + n;
+  int32_t* flags = reinterpret_cast<int32_t*>(t + m);
+  int32_t* sched = flags + ninst;
+  Prob<T, T> P{};
+  P.ninst = ninst; P.n_total = n; P.m_total = m; P.col_off = col_off; P.row_off = row_off;
+  P.A_rp = A_rp; P.A_ci = A_ci; P.A_v = (const T*)A_v;
+  P.AT_rp = AT_rp; P.AT_ci = AT_ci; P.AT_v = (const T*)AT_v;
+  P.P_rp = P_rp; P.P_ci = P_ci; P.P_v = (const T*)P_v;
+  P.inst_sched = sched;
+  // the array keeps the previous call's contents: the flag words must start at zero
+  CU(cudaMemsetAsync(flags, 0, sizeof(int32_t) * ninst, st));
+  k_iota<<<grid_for(ninst, 256), 256, 0, st>>>(ninst, sched);
+  k_precond_csr<T, T><<<grid_for(n, 256), 256, 0, st>>>(P, sigma, (const T*)rho, dinv);
+  CgArgs<T> ca{};
+  ca.rhs = (const T*)rhs; ca.x = (T*)x; ca.x0 = nullptr; ca.rho = (const T*)rho; ca.dinv = dinv;
+  ca.sigma = sigma; ca.r = r; ca.p = p; ca.u = u; ca.t = t; ca.tol = tol; ca.maxit = maxit;
+  ca.zero_start = warm ? 0 : 1; ca.flag_bit = F_CG_CAP; ca.flags = flags; ca.iters = iters;
+  k_pcg<T, T, 256><<<ninst, 256, 0, st>>>(P, ca);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(COSMO_E_CUDA, "pcg launch failed: %s", cudaGetErrorString(e));
+  g_launches += 3;
+  return COSMO_OK;
+}
+
+extern "C" cosmo_status cosmo_pcg_solve_noalloc(
+    int32_t precision, int32_t ninst, int64_t n, int64_t m, const int64_t* col_off,
+    const int64_t* row_off, const int64_t* A_rowptr, const int32_t* A_col, const void* A_val,
+    const int64_t* AT_rowptr, const int32_t* AT_col, const void* AT_val, const int64_t* P_rowptr,
+    const int32_t* P_col, const void* P_val, double sigma, const void* rho, const void* rhs,
+    void* x, int32_t warm_start, double tol, int32_t max_iter, int32_t* iters, void* stream) {
+  g_err.clear();
+  if (ninst < 1 || n < 1 || m < 0 || !col_off || !row_off || !AT_rowptr || !A_rowptr || !rho ||
+      !rhs || !x || !(sigma > 0.0) || !(tol > 0.0) || max_iter < 1 ||
+      (m > 0 && (!A_col || !A_val || !AT_col || !AT_val)) ||
+      ((P_rowptr != nullptr) != (P_col != nullptr)) || ((P_rowptr != nullptr) != (P_val != nullptr)))
+    return fail(COSMO_E_INVAL, "bad arguments to cosmo_pcg_solve_noalloc");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == COSMO_PREC_FP64)
+    return pcg_solve_noalloc_t<double>(ninst, n, m, col_off, row_off, A_rowptr, A_col, A_val,
+                                       AT_rowptr, AT_col, AT_val, P_rowptr, P_col, P_val, sigma,
+                                       rho, rhs, x, warm_start, tol, max_iter, iters, st);
+  if (precision == COSMO_PREC_MIXED)
+    return pcg_solve_noalloc_t<float>(ninst, n, m, col_off, row_off, A_rowptr, A_col, A_val,
+                                      AT_rowptr, AT_col, AT_val, P_rowptr, P_col, P_val, sigma,
+                                      rho, rhs, x, warm_start, tol, max_iter, iters, st);
+  return fail(COSMO_E_INVAL, "unknown precision");
+}
