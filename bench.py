@@ -264,6 +264,11 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    inf = b.info()
+    work = {"jacobi_sweeps_per_block": inf["eig_sweeps"] / max(inf["eig_blocks"], 1),
+            "cg_iters_per_solve": inf["cg_iters"] / max(inf["cg_solves"], 1),
+            "adjoint_cg_iters_per_solve": inf["adj_cg_iters"] / max(inf["adj_cg_solves"], 1)}
+
     # ---------------- per-kernel breakdown (one extra step, all classes) ----
     b.profile(None)
     b.profile_read(None, reset=True)
@@ -351,7 +356,7 @@ def main():
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
             "cpu_baseline": cpu, "plain_fp64": plain,
             "ratio_vs_plain_fp64": (value / world) / plain["value"] if plain else None,
-            "kernel_ms_per_step": breakdown, "wall_s_timed": t_wall}
+            "kernel_ms_per_step": breakdown, "work": work, "wall_s_timed": t_wall}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -152,6 +152,10 @@ typedef struct {
   int32_t tape_valid;       /* 1 if a backward can run now */
   int64_t kernels_launched; /* kernels this batch launched so far (graph replays
                                count their kernels) */
+  /* work counters since creation (cosmo_batch_get_info synchronises to read them) */
+  int64_t eig_sweeps, eig_blocks;       /* Jacobi sweeps summed over PSD-block projections */
+  int64_t cg_iters, cg_solves;          /* forward CG iterations / solves (per instance) */
+  int64_t adj_cg_iters, adj_cg_solves;  /* adjoint CG iterations / solves */
 } cosmo_batch_info;
 
 typedef struct cosmo_batch cosmo_batch;

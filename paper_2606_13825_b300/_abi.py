@@ -55,7 +55,9 @@ class BatchInfo(ctypes.Structure):
                 ("m_total", c_int64), ("nnzA", c_int64), ("nnzP", c_int64),
                 ("n_soc", c_int32), ("n_psd", c_int32), ("max_psd_p", c_int32),
                 ("psd_u_entries", c_int64), ("device_bytes", c_int64), ("last_K", c_int32),
-                ("tape_valid", c_int32), ("kernels_launched", c_int64)]
+                ("tape_valid", c_int32), ("kernels_launched", c_int64),
+                ("eig_sweeps", c_int64), ("eig_blocks", c_int64), ("cg_iters", c_int64),
+                ("cg_solves", c_int64), ("adj_cg_iters", c_int64), ("adj_cg_solves", c_int64)]
 
 
 _SIGS = {

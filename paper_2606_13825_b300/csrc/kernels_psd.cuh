@@ -29,15 +29,19 @@ __device__ __forceinline__ void svec_ij(int e, int& i, int& j) {
   i = e - jj * (jj + 1) / 2;
 }
 
-// round-robin pair k of round `rd` for pe (even) indices; index pe-1 is fixed
+// round-robin pair k of round `rd` (0 <= rd < pe-1, 0 <= k < pe/2) for pe
+// (even) indices; index pe-1 is fixed, the others rotate.  The sums stay in
+// [0, 2m), so one conditional subtraction replaces the modulo.
 __device__ __forceinline__ void rr_pair(int rd, int k, int pe, int& a, int& b) {
   const int m = pe - 1;
   if (k == 0) {
     a = m;
-    b = rd % m;
+    b = rd;
   } else {
-    a = (rd + k) % m;
-    b = (rd - k + m) % m;
+    a = rd + k;
+    if (a >= m) a -= m;
+    b = rd - k + m;
+    if (b >= m) b -= m;
   }
 }
 
@@ -50,79 +54,190 @@ template <> __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a)
 
 // Cyclic Jacobi on the symmetric matrix A (pe x ld, zero-padded) in shared
 // memory; V <- accumulated rotations (starts as the identity).  Stops when
-// off(A) <= tol ||A||_F or after max_sweeps (returns false then).
+// off(A) <= tol' ||A||_F with tol' = max(tol, 4 eps sqrt(p)) (below that the
+// rounding of the rotations themselves keeps off(A) from shrinking), or when
+// from the fifth sweep on a sweep fails to halve off(A)^2 (quadratic
+// convergence has ended at the rounding floor); returns the number of sweeps
+// run, negative if max_sweeps was reached first.
+//
+// Rounds are software-pipelined.  Phase X: every thread applies round r's
+// rotations to the 2x2 blocks (k, l), k <= l, of A (mirrored), from a
+// precomputed triangular index table.  Phase Y: the first warps compute round
+// r+1's pairs and rotations from the updated A into the other half of a
+// double buffer while the remaining warps apply round r's rotations to the
+// columns of V (V never feeds a rotation), rows fastest (odd stride ld: no
+// bank conflicts).  Two barriers per round, no idle rotation phase.
+// Shared scratch: cs [2 pe] T, pr [2 pe] u16, tri [np(np+1)/2] u32.
 template <class T>
-__device__ bool jacobi_eig(T* A, T* V, T* cs, double* red, int p, double tol, int max_sweeps) {
+__device__ __forceinline__ void jacobi_rotations(const T* A, T* cs, uint16_t* pr, int rd, int p,
+                                                 int pe, int ld, int first, int stride) {
+  const int np = pe / 2;
+  for (int k = first; k < np; k += stride) {
+    int a, b;
+    rr_pair(rd, k, pe, a, b);
+    T c = T(1), s = T(0);
+    if (a < p && b < p) {
+      // only the upper triangle of A is kept
+      const T apq = a < b ? A[a * ld + b] : A[b * ld + a];
+      if (apq != T(0)) {
+        // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = theta / phi, written
+        // as sign(theta) phi / (|theta| + sqrt(theta^2 + phi^2)): one root, one
+        // division, no overflow of tau when apq is tiny
+        const T theta = A[b * ld + b] - A[a * ld + a];
+        const T phi = T(2) * apq;
+        const T r = sqrt(theta * theta + phi * phi);
+        const T t = copysign(T(1), theta) * phi / (fabs(theta) + r);
+        c = rsqrt_(T(1) + t * t);
+        s = t * c;
+      }
+    }
+    cs[2 * k] = c;
+    cs[2 * k + 1] = s;
+    pr[2 * k] = (uint16_t)a;
+    pr[2 * k + 1] = (uint16_t)b;
+  }
+}
+
+template <class T>
+__device__ int jacobi_eig(T* A, T* V, T* cs2, uint16_t* pr2, uint32_t* tri, double* red, int p,
+                          double tol, int max_sweeps) {
   const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
-  for (int e = threadIdx.x; e < pe * ld; e += blockDim.x) {
+  const int ntri = np * (np + 1) / 2;
+  const int nt = blockDim.x;
+  // warps that compute rotations in phase Y; the rest update V meanwhile
+  const int rot_threads = ((np + 31) / 32) * 32;
+  const bool split = nt >= rot_threads + 64;
+  const int v_first = split ? rot_threads : 0;
+  const int v_stride = nt - v_first;
+  for (int e = threadIdx.x; e < pe * ld; e += nt) {
     const int i = e / ld, j = e % ld;
     V[e] = (i == j) ? T(1) : T(0);
   }
+  for (int e = threadIdx.x; e < ntri; e += nt) {
+    int k, l;
+    svec_ij(e, k, l);           // k <= l
+    tri[e] = (uint32_t)k | ((uint32_t)l << 16);
+  }
   __syncthreads();
-  const double tol2 = tol * tol;
-  bool ok = false;
+  const double tol_eff = fmax(tol, 4.0 * Eps<T>::v * sqrt((double)p));
+  const double tol2 = tol_eff * tol_eff;
+  double prev_off2 = 0.0;
+  const int nV = pe * np;
+  // e / pe by a float reciprocal: exact for e < 2^20 and pe <= 2048, since
+  // (e + 1/2) / pe stays at least 1/(2 pe) away from the integers
+  const float inv_pe = 1.0f / (float)pe;
+  int result = -max_sweeps;
   for (int sweep = 0;; ++sweep) {
-    double acc[2] = {0.0, 0.0};
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-      const int i = e / p, j = e % p;
+    double acc[2] = {0.0, 0.0};   // off-diagonal and diagonal sums of squares (upper triangle)
+    for (int e = threadIdx.x; e < p * (p + 1) / 2; e += nt) {
+      int i, j;
+      svec_ij(e, i, j);
       const double v = (double)A[i * ld + j];
-      acc[1] += v * v;
-      if (i != j) acc[0] += v * v;
+      if (i == j) acc[1] += v * v;
+      else acc[0] += v * v;
     }
     block_sum<2>(acc, red);
-    if (acc[0] <= tol2 * acc[1]) { ok = true; break; }
+    const double off2 = 2.0 * acc[0], tot2 = off2 + acc[1];
+    if (off2 <= tol2 * tot2 || (sweep >= 5 && off2 > 0.5 * prev_off2)) { result = sweep; break; }
     if (sweep >= max_sweeps) break;
+    prev_off2 = off2;
+    jacobi_rotations(A, cs2, pr2, 0, p, pe, ld, threadIdx.x, nt);
+    __syncthreads();
     for (int rd = 0; rd < pe - 1; ++rd) {
-      for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        int a, b;
-        rr_pair(rd, k, pe, a, b);
-        T c = T(1), s = T(0);
-        if (a < p && b < p) {
-          const T apq = A[a * ld + b];
-          if (apq != T(0)) {
-            const T tau = (A[b * ld + b] - A[a * ld + a]) / (T(2) * apq);
-            const T t = copysign(T(1), tau) / (fabs(tau) + hypot_(T(1), tau));
-            c = rsqrt_(T(1) + t * t);
-            s = t * c;
+      const T* cs = cs2 + (rd & 1) * pe;
+      const uint16_t* pr = pr2 + (rd & 1) * pe;
+      // ---- phase X: A <- J'AJ on the 2x2 blocks (k, l), k <= l, on the upper
+      // triangle only (entry (r, c) lives at [min(r,c)][max(r,c)]); two blocks
+      // per thread in flight (all loads before any store: blocks are disjoint)
+      for (int e0 = threadIdx.x; e0 < ntri; e0 += 2 * nt) {
+        T x[2][4], cc[2][2], ss[2][2];
+        int o[2][4];
+        bool v[2], dg[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int e = e0 + u * nt;
+          v[u] = e < ntri;
+          const uint32_t kl = tri[v[u] ? e : 0];
+          const int k = (int)(kl & 0xffffu), l = (int)(kl >> 16);
+          dg[u] = k == l;
+          const int ak = pr[2 * k], bk = pr[2 * k + 1], al = pr[2 * l], bl = pr[2 * l + 1];
+          cc[u][0] = cs[2 * k]; ss[u][0] = cs[2 * k + 1];
+          cc[u][1] = cs[2 * l]; ss[u][1] = cs[2 * l + 1];
+          o[u][0] = ak < al ? ak * ld + al : al * ld + ak;
+          o[u][1] = ak < bl ? ak * ld + bl : bl * ld + ak;
+          o[u][2] = bk < al ? bk * ld + al : al * ld + bk;
+          o[u][3] = bk < bl ? bk * ld + bl : bl * ld + bk;
+          x[u][0] = A[o[u][0]];
+          x[u][1] = A[o[u][1]];
+          x[u][2] = A[o[u][2]];
+          x[u][3] = A[o[u][3]];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (!v[u]) continue;
+          const T ck = cc[u][0], sk = ss[u][0], cl = cc[u][1], sl = ss[u][1];
+          // rows: [r_a; r_b] <- [[c, -s], [s, c]] [r_a; r_b]
+          const T y11 = ck * x[u][0] - sk * x[u][2], y12 = ck * x[u][1] - sk * x[u][3];
+          const T y21 = sk * x[u][0] + ck * x[u][2], y22 = sk * x[u][1] + ck * x[u][3];
+          // columns: [c_a, c_b] <- [c_a, c_b] [[c, s], [-s, c]]
+          const T z11 = cl * y11 - sl * y12, z12 = sl * y11 + cl * y12;
+          const T z21 = cl * y21 - sl * y22, z22 = sl * y21 + cl * y22;
+          if (dg[u]) {
+            // (a,a), (a,b)=(b,a), (b,b): the rotation annihilates the coupling
+            A[o[u][0]] = z11;
+            A[o[u][1]] = T(0);
+            A[o[u][3]] = z22;
+          } else {
+            A[o[u][0]] = z11;
+            A[o[u][1]] = z12;
+            A[o[u][2]] = z21;
+            A[o[u][3]] = z22;
           }
         }
-        cs[2 * k] = c;
-        cs[2 * k + 1] = s;
       }
       __syncthreads();
-      // A <- J'AJ as independent 2x2 blocks (pair k rows, pair l columns)
-      for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
-        const int k = e / np, l = e % np;
-        int ak, bk, al, bl;
-        rr_pair(rd, k, pe, ak, bk);
-        rr_pair(rd, l, pe, al, bl);
-        const T ck = cs[2 * k], sk = cs[2 * k + 1], cl = cs[2 * l], sl = cs[2 * l + 1];
-        const T x11 = A[ak * ld + al], x12 = A[ak * ld + bl];
-        const T x21 = A[bk * ld + al], x22 = A[bk * ld + bl];
-        // rows: [r_a; r_b] <- [[c, -s], [s, c]] [r_a; r_b]
-        const T y11 = ck * x11 - sk * x21, y12 = ck * x12 - sk * x22;
-        const T y21 = sk * x11 + ck * x21, y22 = sk * x12 + ck * x22;
-        // columns: [c_a, c_b] <- [c_a, c_b] [[c, s], [-s, c]]
-        T z11 = cl * y11 - sl * y12, z12 = sl * y11 + cl * y12;
-        T z21 = cl * y21 - sl * y22, z22 = sl * y21 + cl * y22;
-        if (k == l) { z12 = T(0); z21 = T(0); }
-        A[ak * ld + al] = z11; A[ak * ld + bl] = z12;
-        A[bk * ld + al] = z21; A[bk * ld + bl] = z22;
+      // ---- phase Y: rotations of round rd+1 (first warps) || V <- V J_rd
+      const bool more = rd + 1 < pe - 1;
+      if (split) {
+        if (threadIdx.x < rot_threads) {
+          if (more) jacobi_rotations(A, cs2 + ((rd + 1) & 1) * pe, pr2 + ((rd + 1) & 1) * pe,
+                                     rd + 1, p, pe, ld, threadIdx.x, rot_threads);
+        }
+      } else if (more) {
+        jacobi_rotations(A, cs2 + ((rd + 1) & 1) * pe, pr2 + ((rd + 1) & 1) * pe, rd + 1, p, pe,
+                         ld, threadIdx.x, nt);
       }
-      // V <- V J (rows i, pair l)
-      for (int e = threadIdx.x; e < pe * np; e += blockDim.x) {
-        const int i = e / np, l = e % np;
-        int al, bl;
-        rr_pair(rd, l, pe, al, bl);
-        const T cl = cs[2 * l], sl = cs[2 * l + 1];
-        const T va = V[i * ld + al], vb = V[i * ld + bl];
-        V[i * ld + al] = cl * va - sl * vb;
-        V[i * ld + bl] = sl * va + cl * vb;
+      if (threadIdx.x >= v_first) {
+        // four column-pair updates in flight
+        for (int e0 = threadIdx.x - v_first; e0 < nV; e0 += 4 * v_stride) {
+          T va[4], vb[4], cl[4], sl[4];
+          int oa[4], ob[4];
+          bool v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * v_stride;
+            v[u] = e < nV;
+            const int ee = v[u] ? e : 0;
+            const int l = __float2int_rz(((float)ee + 0.5f) * inv_pe), i = ee - l * pe;
+            oa[u] = i * ld + pr[2 * l];
+            ob[u] = i * ld + pr[2 * l + 1];
+            cl[u] = cs[2 * l];
+            sl[u] = cs[2 * l + 1];
+            va[u] = V[oa[u]];
+            vb[u] = V[ob[u]];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!v[u]) continue;
+            V[oa[u]] = cl[u] * va[u] - sl[u] * vb[u];
+            V[ob[u]] = sl[u] * va[u] + cl[u] * vb[u];
+          }
+        }
       }
       __syncthreads();
     }
   }
-  return ok;
+  return result;
 }
 
 // C(i, j) = sum_k A(i, k) B(k, j) for i, j < p, with A(i, k) = A[i*ar + k*ac],
@@ -171,12 +286,30 @@ __device__ __forceinline__ void smem_gemm_auto(int p, const T* A, int ar, int ac
 }
 
 // shared memory the Jacobi projection needs for order p (bytes)
+// layout: A, V [pe x ld] T | cs [2 pe] T | sel [pe + 2] int | pr [2 pe] u16 |
+// tri [np(np+1)/2] u32 | red (8-aligned) [2 nt/32] double
 template <class T>
 __host__ __device__ inline size_t psd_fwd_smem(int p, int nt) {
-  const int pe = psd_pe(p), ld = psd_ld(p);
-  return (size_t)2 * pe * ld * sizeof(T) + (size_t)pe * sizeof(T) + (size_t)pe * sizeof(int) +
-         (size_t)(2 * (nt / 32)) * sizeof(double) + 64;
+  const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
+  return (size_t)2 * pe * ld * sizeof(T) + (size_t)2 * pe * sizeof(T) +
+         (size_t)(pe + 2) * sizeof(int) + (size_t)2 * pe * sizeof(uint16_t) +
+         (size_t)(np * (np + 1) / 2) * sizeof(uint32_t) + (size_t)(2 * (nt / 32)) * sizeof(double) + 64;
 }
+
+template <class T>
+struct JacobiSmem {
+  T* A; T* V; T* cs; int* sel; uint16_t* pr; uint32_t* tri; double* red;
+  __device__ JacobiSmem(unsigned char* raw, int p) {
+    const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
+    A = reinterpret_cast<T*>(raw);
+    V = A + pe * ld;
+    cs = V + pe * ld;
+    sel = reinterpret_cast<int*>(cs + 2 * pe);
+    pr = reinterpret_cast<uint16_t*>(sel + pe + 2);
+    tri = reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(pr + 2 * pe + 1) & ~uintptr_t(3));
+    red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tri + np * (np + 1) / 2) + 7) & ~uintptr_t(7));
+  }
+};
 template <class T>
 __host__ __device__ inline size_t psd_bwd_smem(int p, int nt) {
   const int pe = psd_pe(p), ld = psd_ld(p);
@@ -197,18 +330,17 @@ struct PsdIterIO {   // inside the unrolled iteration
 template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T* lam_slot,
                                                 T* U_slot, double tol, int max_sweeps,
-                                                int32_t* flags) {
+                                                int32_t* flags, int sched_off,
+                                                unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int blk = P.psd_sched[blockIdx.x];
+  const int blk = P.psd_sched[sched_off + blockIdx.x];
   const int p = P.psd_p[blk];
   const int pe = psd_pe(p), ld = psd_ld(p);
   const int64_t row0 = P.psd_row0[blk];
-  T* A = reinterpret_cast<T*>(smraw);
-  T* Vm = A + pe * ld;
-  T* cs = Vm + pe * ld;
-  int* sel = reinterpret_cast<int*>(cs + pe);
-  double* red = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(sel + pe + 2) & ~uintptr_t(7));
-  red = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(red) + 8);
+  JacobiSmem<T> sm(smraw, p);
+  T* A = sm.A;
+  T* Vm = sm.V;
+  int* sel = sm.sel;
   const int inst = io.row_inst[row0];
   const T al = io.alpha[inst], rh = io.rho[row0];
   const int d = p * (p + 1) / 2;
@@ -224,8 +356,14 @@ __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T
     A[j * ld + i] = v;
   }
   __syncthreads();
-  const bool ok = jacobi_eig(A, Vm, cs, red, p, tol, max_sweeps);
-  if (!ok && threadIdx.x == 0) atomicOr(&flags[inst], F_EIG_CAP);
+  const int sweeps = jacobi_eig(A, Vm, sm.cs, sm.pr, sm.tri, sm.red, p, tol, max_sweeps);
+  if (threadIdx.x == 0) {
+    if (sweeps < 0) atomicOr(&flags[inst], F_EIG_CAP);
+    if (stats) {
+      atomicAdd(&stats[0], (unsigned long long)(sweeps < 0 ? -sweeps : sweeps));
+      atomicAdd(&stats[1], 1ull);
+    }
+  }
   // tape: eigenvalues and eigenvectors (column-major per block)
   T* lam = lam_slot + P.psd_loff[blk];
   T* U = U_slot + P.psd_uoff[blk];
@@ -313,9 +451,9 @@ struct PsdBwdIO {
 // b3 (PSD): vbar = svec(U (L o (U' smat(g) U)) U') per block
 template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_psd_bwd(Prob<T, V> P, PsdBwdIO<T> io, const T* lam_slot,
-                                                const T* U_slot, double dk_tau_rel) {
+                                                const T* U_slot, double dk_tau_rel, int sched_off) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int blk = P.psd_sched[blockIdx.x];
+  const int blk = P.psd_sched[sched_off + blockIdx.x];
   const int p = P.psd_p[blk];
   const int pe = psd_pe(p), ld = psd_ld(p);
   const int64_t row0 = P.psd_row0[blk];
@@ -379,12 +517,9 @@ __global__ void __launch_bounds__(NT) k_psd_project_batch(PsdBatch<T> B, const T
   const int blk = blockIdx.x;
   const int p = B.p[blk];
   const int pe = psd_pe(p), ld = psd_ld(p);
-  T* A = reinterpret_cast<T*>(smraw);
-  T* Vm = A + pe * ld;
-  T* cs = Vm + pe * ld;
-  int* sel = reinterpret_cast<int*>(cs + pe);
-  double* red = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(sel + pe + 2) & ~uintptr_t(7));
-  red = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(red) + 8);
+  JacobiSmem<T> sm(smraw, p);
+  T* A = sm.A;
+  T* Vm = sm.V;
   const int64_t o = B.off[blk];
   const int d = p * (p + 1) / 2;
   for (int e = threadIdx.x; e < pe * ld; e += NT) A[e] = T(0);
@@ -398,8 +533,8 @@ __global__ void __launch_bounds__(NT) k_psd_project_batch(PsdBatch<T> B, const T
     A[j * ld + i] = x;
   }
   __syncthreads();
-  const bool ok = jacobi_eig(A, Vm, cs, red, p, tol, max_sweeps);
-  if (!ok && threadIdx.x == 0 && flag) atomicOr(flag, F_EIG_CAP);
+  const int sweeps = jacobi_eig(A, Vm, sm.cs, sm.pr, sm.tri, sm.red, p, tol, max_sweeps);
+  if (sweeps < 0 && threadIdx.x == 0 && flag) atomicOr(flag, F_EIG_CAP);
   if (lam_out)
     for (int k = threadIdx.x; k < p; k += NT) lam_out[B.loff[blk] + k] = A[k * ld + k];
   if (U_out)

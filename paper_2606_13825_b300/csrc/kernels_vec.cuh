@@ -120,6 +120,7 @@ struct CgArgs {
   int32_t flag_bit;
   int32_t* flags;
   int32_t* iters;    // [ninst] CG iterations used (may be null)
+  unsigned long long* stats;  // [2] total iterations, solves (may be null)
 };
 
 // u = M v on the columns [c0, c1) of one instance (rows [r0, r1)); CTA-wide.
@@ -210,6 +211,10 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
     if (rr > thr) atomicOr(&a.flags[inst], a.flag_bit);
     if (!(rr == rr)) atomicOr(&a.flags[inst], F_NONFINITE);
     if (a.iters) a.iters[inst] = it;
+    if (a.stats) {
+      atomicAdd(&a.stats[0], (unsigned long long)it);
+      atomicAdd(&a.stats[1], 1ull);
+    }
   }
 }
 

@@ -354,6 +354,7 @@ struct ImplT : Impl {
   Prob<T, V> P{};
   cudaStream_t cap = nullptr;
   int32_t* flags = nullptr;
+  unsigned long long* stats = nullptr;  // [6]: Jacobi sweeps, blocks; CG iters, solves; adjoint CG iters, solves
   // K-independent workspace
   T *xi = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_u = nullptr, *cg_t = nullptr;
   T *xb[2] = {nullptr, nullptr}, *sb[2] = {nullptr, nullptr}, *yb[2] = {nullptr, nullptr};
@@ -378,7 +379,11 @@ struct ImplT : Impl {
   int64_t gfwd_nk = 0, gbwd_nk = 0;
   int64_t launched = 0;
   int64_t seq_kernels = 0;  // kernels enqueued by the sequence being built
-  int psd_nt = 256;
+  // PSD blocks (sorted by p, largest first) split into size buckets, each
+  // launched with its own CTA size on a forked stream
+  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; };
+  std::vector<Bucket> buckets;
+  cudaEvent_t ev_fork = nullptr;
   // optional CUDA-event timing of launches (direct mode only)
   int prof_mode = 0;            // 0 off, 1 every kernel, 2 kernels whose tag == prof_tag
   std::string prof_tag;
@@ -390,6 +395,8 @@ struct ImplT : Impl {
 
   explicit ImplT(const cosmo_options& o, HostPlan& hp) : opt(o), h(hp) {}
   ~ImplT() override {
+    for (auto& bk : buckets) { if (bk.s) cudaStreamDestroy(bk.s); if (bk.done) cudaEventDestroy(bk.done); }
+    if (ev_fork) cudaEventDestroy(ev_fork);
     for (auto& r : prof_pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ev_pool) cudaEventDestroy(e);
     if (gfwd) cudaGraphExecDestroy(gfwd);
@@ -473,6 +480,8 @@ struct ImplT : Impl {
     const int64_t n = h.n, m = h.m;
     TRY(arena.alloc(&flags, h.ninst));
     CU(cudaMemset(flags, 0, sizeof(int32_t) * h.ninst));
+    TRY(arena.alloc(&stats, 6));
+    CU(cudaMemset(stats, 0, sizeof(unsigned long long) * 6));
     TRY(arena.alloc(&xi, n)); TRY(arena.alloc(&cg_r, n)); TRY(arena.alloc(&cg_p, n));
     TRY(arena.alloc(&cg_u, n)); TRY(arena.alloc(&cg_t, m));
     for (int i = 0; i < 2; ++i) {
@@ -483,15 +492,33 @@ struct ImplT : Impl {
     TRY(arena.alloc(&gx_in, n)); TRY(arena.alloc(&gs_in, m)); TRY(arena.alloc(&gy_in, m));
     TRY(arena.alloc(&loss_buf, h.ninst)); TRY(arena.alloc(&gloss_buf, h.ninst));
     if (P.npsd > 0) {
-      const size_t fs = psd_fwd_smem<T>(h.max_p, psd_nt), bs = psd_bwd_smem<T>(h.max_p, psd_nt);
       int dev = 0, maxs = 0;
       CU(cudaGetDevice(&dev));
       CU(cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      if ((int64_t)fs > maxs || (int64_t)bs > maxs)
-        return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
-                    h.max_p, std::max(fs, bs), maxs);
-      CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
-      CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
+      // size classes: p > 56 -> 512 threads, 33..56 -> 256, <= 32 -> 128
+      auto nt_for = [](int p) { return p > 56 ? 512 : (p > 32 ? 256 : 128); };
+      for (size_t q = 0; q < h.psd_sched.size();) {
+        const int p0 = h.psd_p[h.psd_sched[q]];
+        const int nt = nt_for(p0);
+        size_t e = q;
+        while (e < h.psd_sched.size() && nt_for(h.psd_p[h.psd_sched[e]]) == nt) ++e;
+        Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr};
+        CU(cudaStreamCreateWithFlags(&bk.s, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
+        const size_t fs = psd_fwd_smem<T>(p0, nt), bs = psd_bwd_smem<T>(p0, nt);
+        if ((int64_t)fs > maxs || (int64_t)bs > maxs)
+          return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
+                      p0, std::max(fs, bs), maxs);
+        buckets.push_back(bk);
+        q = e;
+      }
+      CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+      CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
     }
     return COSMO_OK;
   }
@@ -542,6 +569,36 @@ struct ImplT : Impl {
     }
     kern<<<grid, block, smem, st>>>(args...);
     ++seq_kernels;
+    if (rec) {
+      cudaEventRecord(r.e1, st);
+      prof_pending.push_back(r);
+    }
+  }
+
+  // Fork one launch per PSD bucket onto the bucket streams and join them back
+  // into st (captured as parallel graph branches).  Timed as one group.
+  template <class F>
+  void psd_group(const char* tag, cudaStream_t st, F launch_bucket) {
+    const bool rec = prof_mode != 0 && !capturing && (prof_mode == 1 || prof_tag == tag);
+    Rec r{tag, nullptr, nullptr};
+    if (rec) {
+      r.e0 = get_event();
+      r.e1 = get_event();
+      cudaEventRecord(r.e0, st);
+    }
+    if (buckets.size() == 1) {
+      launch_bucket(buckets[0], st);
+      ++seq_kernels;
+    } else {
+      cudaEventRecord(ev_fork, st);
+      for (auto& bk : buckets) {
+        cudaStreamWaitEvent(bk.s, ev_fork, 0);
+        launch_bucket(bk, bk.s);
+        cudaEventRecord(bk.done, bk.s);
+        ++seq_kernels;
+      }
+      for (auto& bk : buckets) cudaStreamWaitEvent(st, bk.done, 0);
+    }
     if (rec) {
       cudaEventRecord(r.e1, st);
       prof_pending.push_back(r);
@@ -605,7 +662,7 @@ struct ImplT : Impl {
     ca.rhs = xi; ca.x = xt; ca.x0 = xt_warm; ca.rho = rho; ca.dinv = dinv + (int64_t)k * h.n;
     ca.sigma = sig; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = opt.cg_tol;
     ca.maxit = opt.cg_max_iter; ca.zero_start = xt_warm ? 0 : 1; ca.flag_bit = F_CG_CAP;
-    ca.flags = flags; ca.iters = nullptr;
+    ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 2;
     launch("pcg", k_pcg<T, V, 256>, h.ninst, 256, 0, st, P, ca);
     StepPtrs<T> sp{};
     sp.x = st_x(slot); sp.s = st_s(slot); sp.y = st_y(slot);
@@ -616,8 +673,15 @@ struct ImplT : Impl {
     if (P.nsoc) launch("soc_fwd", k_soc_fwd<T, V>, grid_for((int64_t)P.nsoc * 32, 256, INT32_MAX), 256, 0, st, P, sp);
     if (P.npsd) {
       PsdIterIO<T> io{stt, st_s(slot), st_y(slot), rho, alpha, st_s(slot + 1), st_y(slot + 1), P.row_inst};
-      launch("psd_fwd", k_psd_fwd<T, V, 256>, P.npsd, 256, psd_fwd_smem<T>(h.max_p, 256), st, P, io,
-             sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags);
+      psd_group("psd_fwd", st, [&](const Bucket& bk, cudaStream_t s) {
+        const size_t sm = psd_fwd_smem<T>(bk.maxp, bk.nt);
+        if (bk.nt == 512)
+          k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats);
+        else if (bk.nt == 256)
+          k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats);
+        else
+          k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats);
+      });
     }
   }
 
@@ -677,15 +741,22 @@ struct ImplT : Impl {
     if (P.nsoc) launch("soc_bwd", k_soc_bwd<T, V>, grid_for((int64_t)P.nsoc * 32, 256, INT32_MAX), 256, 0, st, P, q);
     if (P.npsd) {
       PsdBwdIO<T> io{gproj, vbar, P.row_inst};
-      launch("psd_bwd", k_psd_bwd<T, V, 256>, P.npsd, 256, psd_bwd_smem<T>(h.max_p, 256), st, P, io,
-             (const T*)q.lam, (const T*)q.U, opt.dk_gap_tau);
+      psd_group("psd_bwd", st, [&](const Bucket& bk, cudaStream_t s) {
+        const size_t sm = psd_bwd_smem<T>(bk.maxp, bk.nt);
+        if (bk.nt == 512)
+          k_psd_bwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
+        else if (bk.nt == 256)
+          k_psd_bwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
+        else
+          k_psd_bwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
+      });
     }
     launch("bwd_relax", k_bwd_relax<T, V, 256>, h.ninst, 256, 0, st, P, q);
     CgArgs<T> ca{};
     ca.rhs = adjrhs; ca.x = lamt; ca.x0 = nullptr; ca.rho = q.rho;
     ca.dinv = dinv + (int64_t)k * h.n; ca.sigma = q.sigma; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u;
     ca.t = cg_t; ca.tol = opt.cg_tol; ca.maxit = opt.cg_max_iter; ca.zero_start = 1;
-    ca.flag_bit = F_ADJ_CG_CAP; ca.flags = flags; ca.iters = nullptr;
+    ca.flag_bit = F_ADJ_CG_CAP; ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 4;
     launch("pcg_adj", k_pcg<T, V, 256>, h.ninst, 256, 0, st, P, ca);
     launch("bwd_solve", k_bwd_solve<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, q);
   }
@@ -891,6 +962,18 @@ struct ImplT : Impl {
     o->last_K = K;
     o->tape_valid = tape_valid ? 1 : 0;
     o->kernels_launched = launched;
+    unsigned long long st6[6] = {0, 0, 0, 0, 0, 0};
+    if (cudaDeviceSynchronize() == cudaSuccess &&
+        cudaMemcpy(st6, stats, sizeof(st6), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      o->eig_sweeps = (int64_t)st6[0];
+      o->eig_blocks = (int64_t)st6[1];
+      o->cg_iters = (int64_t)st6[2];
+      o->cg_solves = (int64_t)st6[3];
+      o->adj_cg_iters = (int64_t)st6[4];
+      o->adj_cg_solves = (int64_t)st6[5];
+    } else {
+      cudaGetLastError();
+    }
   }
 };
 
