@@ -138,6 +138,8 @@ typedef struct {
   double eig_tol;           /* Jacobi stop: off(A) <= eig_tol * ||A||_F */
   int32_t use_graph;        /* capture forward/backward into CUDA graphs */
   int32_t device;           /* CUDA device ordinal the batch lives on */
+  int32_t eig_warm_start;   /* 1: start step k's Jacobi from step k-1's eigenvectors
+                               (re-orthogonalised by one Newton-Schulz step) */
 } cosmo_options;
 
 typedef struct {
@@ -170,7 +172,7 @@ const char* cosmo_last_error(void);
 /* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; Jacobi up to p = 64
  * (MIXED) / 48 (FP64); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
- * use_graph 1; device 0.  Returns COSMO_E_INVAL for an unknown precision. */
+ * use_graph 1; device 0; eig_warm_start 1.  Returns COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 
 /* Validate a problem on the host without touching the device (CSR bounds and

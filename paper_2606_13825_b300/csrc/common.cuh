@@ -90,6 +90,13 @@ struct Prob {
   int32_t nrect;            // SOC + PSD blocks (rho rectification)
   const int64_t* rect_row0; const int32_t* rect_rows;
   const int32_t* inst_sched;// instances, most work first (CG)
+  // instances whose M = P + sigma I + A'D(rho)A is diagonal for every rho (P
+  // diagonal and at most one nonzero per row of A): Jacobi-preconditioned CG
+  // reaches the exact solution D^-1 rhs in its first step from any start, so
+  // the solve is done in the kernel that forms the right-hand side
+  const uint8_t* diag_inst; // [ninst]
+  int32_t n_cg;             // instances that need the CG kernel
+  const int32_t* cg_sched;  // [n_cg], most work first
 };
 
 }  // namespace cosmo

@@ -100,7 +100,7 @@ __device__ __forceinline__ void jacobi_rotations(const T* A, T* cs, uint16_t* pr
 
 template <class T>
 __device__ int jacobi_eig(T* A, T* V, T* cs2, uint16_t* pr2, uint32_t* tri, double* red, int p,
-                          double tol, int max_sweeps) {
+                          double tol, int max_sweeps, bool v_identity = true) {
   const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
   const int ntri = np * (np + 1) / 2;
   const int nt = blockDim.x;
@@ -109,9 +109,11 @@ __device__ int jacobi_eig(T* A, T* V, T* cs2, uint16_t* pr2, uint32_t* tri, doub
   const bool split = nt >= rot_threads + 64;
   const int v_first = split ? rot_threads : 0;
   const int v_stride = nt - v_first;
-  for (int e = threadIdx.x; e < pe * ld; e += nt) {
-    const int i = e / ld, j = e % ld;
-    V[e] = (i == j) ? T(1) : T(0);
+  if (v_identity) {
+    for (int e = threadIdx.x; e < pe * ld; e += nt) {
+      const int i = e / ld, j = e % ld;
+      V[e] = (i == j) ? T(1) : T(0);
+    }
   }
   for (int e = threadIdx.x; e < ntri; e += nt) {
     int k, l;
@@ -278,11 +280,53 @@ __device__ __forceinline__ void smem_gemm(int p, const T* A, int ar, int ac, con
   }
 }
 
+// Conflict-free variant: lane (threadIdx.x % 32) owns columns j = lane + 32 b,
+// warp w owns rows i = w + TY a (TY warps): B(k, j) loads are consecutive
+// across lanes (or stride ld, odd) and A(i, k) loads are warp broadcasts.
+template <class T, int TM, int TN, class F>
+__device__ __forceinline__ void smem_gemm_w(int p, const T* A, int ar, int ac, const T* B, int br,
+                                            int bc, F f) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, TY = blockDim.x >> 5;
+  for (int i0 = w; i0 < p; i0 += TM * TY) {
+    for (int j0 = lane; j0 < p; j0 += TN * 32) {
+      T acc[TM][TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+      int ii[TM], jj[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) ii[a] = min(i0 + a * TY, p - 1);
+#pragma unroll
+      for (int b = 0; b < TN; ++b) jj[b] = min(j0 + b * 32, p - 1);
+      for (int k = 0; k < p; ++k) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = A[ii[a] * ar + k * ac];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = B[k * br + jj[b] * bc];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b)
+          if (i0 + a * TY < p && j0 + b * 32 < p) f(i0 + a * TY, j0 + b * 32, acc[a][b]);
+    }
+  }
+}
+
+// tile shape by CTA size: 128 threads (blocks up to 32) 8x1, 256 (up to 56)
+// 7x2, 512 (larger) 5x3 outputs per thread
 template <class T, class F>
 __device__ __forceinline__ void smem_gemm_auto(int p, const T* A, int ar, int ac, const T* B,
                                                int br, int bc, F f) {
-  if (p >= 40) smem_gemm<T, 4, 4>(p, A, ar, ac, B, br, bc, f);
-  else smem_gemm<T, 2, 2>(p, A, ar, ac, B, br, bc, f);
+  if (blockDim.x >= 512) smem_gemm_w<T, 5, 3>(p, A, ar, ac, B, br, bc, f);
+  else if (blockDim.x >= 256) smem_gemm_w<T, 7, 2>(p, A, ar, ac, B, br, bc, f);
+  else smem_gemm_w<T, 8, 1>(p, A, ar, ac, B, br, bc, f);
 }
 
 // shared memory the Jacobi projection needs for order p (bytes)
@@ -294,6 +338,13 @@ __host__ __device__ inline size_t psd_fwd_smem(int p, int nt) {
   return (size_t)2 * pe * ld * sizeof(T) + (size_t)2 * pe * sizeof(T) +
          (size_t)(pe + 2) * sizeof(int) + (size_t)2 * pe * sizeof(uint16_t) +
          (size_t)(np * (np + 1) / 2) * sizeof(uint32_t) + (size_t)(2 * (nt / 32)) * sizeof(double) + 64;
+}
+
+// with a warm start a third pe x ld buffer W follows the red array
+template <class T>
+__host__ __device__ inline size_t psd_fwd_smem_warm(int p, int nt) {
+  const int pe = psd_pe(p), ld = psd_ld(p);
+  return psd_fwd_smem<T>(p, nt) + (size_t)pe * ld * sizeof(T) + 16;
 }
 
 template <class T>
@@ -308,6 +359,10 @@ struct JacobiSmem {
     pr = reinterpret_cast<uint16_t*>(sel + pe + 2);
     tri = reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(pr + 2 * pe + 1) & ~uintptr_t(3));
     red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tri + np * (np + 1) / 2) + 7) & ~uintptr_t(7));
+  }
+  // third buffer, only valid when the launch sized shared memory with psd_fwd_smem_warm
+  __device__ T* W(int nt) const {
+    return reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(red + 2 * (nt / 32)) + 15) & ~uintptr_t(15));
   }
 };
 template <class T>
@@ -331,7 +386,7 @@ template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T* lam_slot,
                                                 T* U_slot, double tol, int max_sweeps,
                                                 int32_t* flags, int sched_off,
-                                                unsigned long long* stats) {
+                                                unsigned long long* stats, const T* U_prev) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int blk = P.psd_sched[sched_off + blockIdx.x];
   const int p = P.psd_p[blk];
@@ -344,8 +399,33 @@ __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T
   const int inst = io.row_inst[row0];
   const T al = io.alpha[inst], rh = io.rho[row0];
   const int d = p * (p + 1) / 2;
-  for (int e = threadIdx.x; e < pe * ld; e += NT) A[e] = T(0);
-  __syncthreads();
+  const bool warm = U_prev != nullptr;
+  if (warm) {
+    // previous step's eigenvectors (column-major) into V, then one
+    // Newton-Schulz step V <- 1.5 V - 0.5 V (V'V) to restore orthogonality
+    T* W = sm.W(NT);
+    const T* Up = U_prev + P.psd_uoff[blk];
+    for (int e = threadIdx.x; e < pe * ld; e += NT) { Vm[e] = T(0); A[e] = T(0); W[e] = T(0); }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += NT) {
+      const int k = e / p, i = e - k * p;
+      Vm[i * ld + k] = Up[e];
+    }
+    if (threadIdx.x == 0 && (p & 1)) Vm[p * ld + p] = T(1);  // padding index
+    __syncthreads();
+    smem_gemm_auto<T>(p, Vm, 1, ld, Vm, ld, 1, [&](int i, int j, T v) { W[i * ld + j] = v; });
+    __syncthreads();
+    smem_gemm_auto<T>(p, Vm, ld, 1, W, ld, 1, [&](int i, int j, T v) { A[i * ld + j] = v; });
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += NT) {
+      const int i = e / p, j = e - i * p;
+      Vm[i * ld + j] = T(1.5) * Vm[i * ld + j] - T(0.5) * A[i * ld + j];
+    }
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < pe * ld; e += NT) A[e] = T(0);
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < d; e += NT) {
     int i, j;
     svec_ij(e, i, j);
@@ -356,7 +436,15 @@ __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T
     A[j * ld + i] = v;
   }
   __syncthreads();
-  const int sweeps = jacobi_eig(A, Vm, sm.cs, sm.pr, sm.tri, sm.red, p, tol, max_sweeps);
+  if (warm) {
+    // B = V' S V, nearly diagonal when the iterate moved little
+    T* W = sm.W(NT);
+    smem_gemm_auto<T>(p, A, ld, 1, Vm, ld, 1, [&](int i, int j, T v) { W[i * ld + j] = v; });
+    __syncthreads();
+    smem_gemm_auto<T>(p, Vm, 1, ld, W, ld, 1, [&](int i, int j, T v) { A[i * ld + j] = v; });
+    __syncthreads();
+  }
+  const int sweeps = jacobi_eig(A, Vm, sm.cs, sm.pr, sm.tri, sm.red, p, tol, max_sweeps, !warm);
   if (threadIdx.x == 0) {
     if (sweeps < 0) atomicOr(&flags[inst], F_EIG_CAP);
     if (stats) {

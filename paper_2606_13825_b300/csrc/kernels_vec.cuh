@@ -82,10 +82,13 @@ __global__ void k_precond(Prob<T, V> P, int32_t K, const double* __restrict__ si
 // ---------------------------------------------------------------------------
 // a3: xi = sigma x - q + A'(y + rho o (b - s))      (Sec. 2.3, Eq. reduced)
 // ---------------------------------------------------------------------------
+// For instances with diagonal M the solve x~ = D^-1 xi is done here (dinv is
+// the inverse diagonal of M) and written to xt.
 template <class T, class V>
 __global__ void k_rhs(Prob<T, V> P, double sigma, const T* __restrict__ x,
                       const T* __restrict__ s, const T* __restrict__ y,
-                      const T* __restrict__ rho, T* __restrict__ xi) {
+                      const T* __restrict__ rho, T* __restrict__ xi,
+                      const T* __restrict__ dinv, T* __restrict__ xt) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.n_total;
        j += (int64_t)gridDim.x * blockDim.x) {
     T acc = (T)sigma * x[j] - P.q[j];
@@ -93,7 +96,8 @@ __global__ void k_rhs(Prob<T, V> P, double sigma, const T* __restrict__ x,
       const int32_t r = P.AT_ci[e];
       acc += (T)ldv(P.AT_v, e) * (y[r] + rho[r] * (P.b[r] - s[r]));
     }
-    xi[j] = acc;
+    if (P.diag_inst[P.col_inst[j]]) xt[j] = acc * dinv[j];
+    else xi[j] = acc;
   }
 }
 
@@ -123,24 +127,67 @@ struct CgArgs {
   unsigned long long* stats;  // [2] total iterations, solves (may be null)
 };
 
+// out[row] = f(row, sum_e val[e] x[ci[e]]) for rows [r0, r1) of a CSR matrix,
+// CTA-wide, four rows per thread in flight: the row pointers of all four rows
+// are loaded first, then the gathers of their entries are interleaved, so the
+// dependent loads (row pointer -> column index -> x) of different rows overlap.
+template <class T, class V, class F>
+__device__ __forceinline__ void cta_csr_rows(const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci,
+                                             const V* __restrict__ val, const T* __restrict__ x,
+                                             int64_t r0, int64_t r1, F f) {
+  const int64_t step = blockDim.x;
+  for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 4 * step) {
+    int64_t e[4], eend[4];
+    T acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = rb + u * step;
+      const bool ok = r < r1;
+      e[u] = ok ? rp[r] : 0;
+      eend[u] = ok ? rp[r + 1] : 0;
+      acc[u] = T(0);
+    }
+    bool any = true;
+    while (any) {
+      any = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (e[u] < eend[u]) {
+          acc[u] += (T)ldv(val, e[u]) * x[ci[e[u]]];
+          ++e[u];
+          any = any || e[u] < eend[u];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = rb + u * step;
+      if (r < r1) f(r, acc[u]);
+    }
+  }
+}
+
 // u = M v on the columns [c0, c1) of one instance (rows [r0, r1)); CTA-wide.
 template <class T, class V>
 __device__ __forceinline__ void cta_matvec(const Prob<T, V>& P, const CgArgs<T>& a,
                                            const T* __restrict__ v, T* __restrict__ u,
                                            int64_t c0, int64_t c1, int64_t r0, int64_t r1) {
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    T acc = T(0);
-    for (int64_t e = P.A_rp[r]; e < P.A_rp[r + 1]; ++e) acc += (T)ldv(P.A_v, e) * v[P.A_ci[e]];
-    a.t[r] = a.rho[r] * acc;
-  }
+  T* __restrict__ t = a.t;
+  const T* __restrict__ rho = a.rho;
+  cta_csr_rows<T, V>(P.A_rp, P.A_ci, P.A_v, v, r0, r1,
+                     [&](int64_t r, T acc) { t[r] = rho[r] * acc; });
   __syncthreads();
-  for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
-    T acc = (T)a.sigma * v[j];
-    if (P.P_rp) {
-      for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e) acc += (T)ldv(P.P_v, e) * v[P.P_ci[e]];
-    }
-    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) acc += (T)ldv(P.AT_v, e) * a.t[P.AT_ci[e]];
-    u[j] = acc;
+  const T sig = (T)a.sigma;
+  if (P.P_rp) {
+    // u = sigma v + P v, then u += A' t
+    cta_csr_rows<T, V>(P.P_rp, P.P_ci, P.P_v, v, c0, c1,
+                       [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+    cta_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
+                       [&](int64_t j, T acc) { u[j] += acc; });
+  } else {
+    cta_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
+                       [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
   }
   __syncthreads();
 }
@@ -148,7 +195,7 @@ __device__ __forceinline__ void cta_matvec(const Prob<T, V>& P, const CgArgs<T>&
 template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
   __shared__ double sm[3 * (NT / 32)];
-  const int32_t inst = P.inst_sched[blockIdx.x];
+  const int32_t inst = P.cg_sched ? P.cg_sched[blockIdx.x] : P.inst_sched[blockIdx.x];
   const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
   const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
   if (c1 == c0) return;
@@ -417,7 +464,8 @@ struct BwdPtrs {
   T* gproj;  // [m_total] cotangent reaching the projection output
   T* vbar;   // [m_total] cotangent of the projection input v
   T* adjrhs; // [n_total] -x~bar
-  const T* lamt; // [n_total] adjoint solution lambda~
+  T* lamt;       // [n_total] adjoint solution lambda~
+  const T* dinv; // [n_total] inverse diagonal of M (diagonal-M instances)
   T* grho;   // [m_total] rho-bar of this step (unrectified later)
   T* galpha; // [ninst]
   int32_t* flags;
@@ -501,6 +549,7 @@ __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
   const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
   const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
   const T al = q.alpha[inst];
+  const bool diag = P.diag_inst[inst] != 0;
   double acc[1] = {0.0};
   for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
     const T rh = q.rho[r];
@@ -521,7 +570,8 @@ __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
       const int32_t r = P.AT_ci[e];
       acc2 -= (T)ldv(P.AT_v, e) * (al * (q.rho[r] * q.yb[r] + q.vbar[r]));
     }
-    q.adjrhs[j] = -acc2;
+    if (diag) q.lamt[j] = -acc2 * q.dinv[j];
+    else q.adjrhs[j] = -acc2;
     q.xb2[j] = (T(1) - al) * xb;
     acc[0] += (double)xb * (double)(q.xt[j] - q.x[j]);
   }

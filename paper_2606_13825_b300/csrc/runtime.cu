@@ -202,6 +202,8 @@ struct HostPlan {
   std::vector<int64_t> psd_row0, psd_loff, psd_uoff; std::vector<int32_t> psd_p, psd_sched;
   std::vector<int64_t> rect_row0; std::vector<int32_t> rect_rows;
   std::vector<int32_t> inst_sched;
+  std::vector<uint8_t> diag_inst;
+  std::vector<int32_t> cg_sched;
   int64_t sum_p = 0, sum_p2 = 0;
   int32_t max_p = 0;
 };
@@ -301,6 +303,20 @@ static void build_plan(const cosmo_problem* pr, HostPlan& h) {
   std::iota(h.inst_sched.begin(), h.inst_sched.end(), 0);
   std::stable_sort(h.inst_sched.begin(), h.inst_sched.end(),
                    [&](int a, int b) { return work[a] > work[b]; });
+  // diagonal M: P diagonal and no row of A with two nonzeros in distinct columns
+  h.diag_inst.assign(ni, 1);
+  for (int32_t i = 0; i < ni; ++i) {
+    bool d = true;
+    for (int64_t r = h.row_off[i]; d && r < h.row_off[i + 1]; ++r)
+      if (h.A_rp[r + 1] - h.A_rp[r] > 1) d = false;
+    if (h.has_P)
+      for (int64_t j = h.col_off[i]; d && j < h.col_off[i + 1]; ++j)
+        for (int64_t e = h.P_rp[j]; e < h.P_rp[j + 1]; ++e)
+          if (h.P_ci[e] != j && h.P_v[e] != 0.0) { d = false; break; }
+    h.diag_inst[i] = d ? 1 : 0;
+  }
+  for (int32_t i : h.inst_sched)
+    if (!h.diag_inst[i]) h.cg_sched.push_back(i);
 }
 
 // ------------------------------------------------------- implementation ---
@@ -368,6 +384,7 @@ struct ImplT : Impl {
   T *xs = nullptr, *ss = nullptr, *ys = nullptr;        // (cK+1) states
   T *xts = nullptr, *sts = nullptr, *lams = nullptr, *Us = nullptr;  // cK slots
   T *ck_x = nullptr, *ck_s = nullptr, *ck_y = nullptr, *ck_xt = nullptr;  // nseg
+  T* ck_U = nullptr;  // nseg x sum p^2: eigenvectors that warm-start each segment
   T *rho_in = nullptr, *rho_rect = nullptr, *dinv = nullptr, *alpha_in = nullptr;
   T *grho_all = nullptr, *galpha_all = nullptr;
   double* sigma_dev = nullptr;
@@ -381,7 +398,7 @@ struct ImplT : Impl {
   int64_t seq_kernels = 0;  // kernels enqueued by the sequence being built
   // PSD blocks (sorted by p, largest first) split into size buckets, each
   // launched with its own CTA size on a forked stream
-  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; };
+  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; bool warm_fits; };
   std::vector<Bucket> buckets;
   cudaEvent_t ev_fork = nullptr;
   // optional CUDA-event timing of launches (direct mode only)
@@ -463,6 +480,10 @@ struct ImplT : Impl {
     TRY(arena.upload(&rect_row0, h.rect_row0));
     TRY(arena.upload(&rect_rows, h.rect_rows));
     TRY(arena.upload(&inst_sched, h.inst_sched));
+    uint8_t* diag_inst;
+    int32_t* cg_sched = nullptr;
+    TRY(arena.upload(&diag_inst, h.diag_inst));
+    TRY(arena.upload(&cg_sched, h.cg_sched));
     P.ninst = h.ninst;
     P.n_total = h.n;
     P.m_total = h.m;
@@ -477,6 +498,9 @@ struct ImplT : Impl {
     P.psd_loff = psd_loff; P.psd_uoff = psd_uoff; P.psd_sched = psd_sched;
     P.nrect = (int32_t)h.rect_row0.size(); P.rect_row0 = rect_row0; P.rect_rows = rect_rows;
     P.inst_sched = inst_sched;
+    P.diag_inst = diag_inst;
+    P.n_cg = (int32_t)h.cg_sched.size();
+    P.cg_sched = cg_sched;
     const int64_t n = h.n, m = h.m;
     TRY(arena.alloc(&flags, h.ninst));
     CU(cudaMemset(flags, 0, sizeof(int32_t) * h.ninst));
@@ -502,7 +526,8 @@ struct ImplT : Impl {
         const int nt = nt_for(p0);
         size_t e = q;
         while (e < h.psd_sched.size() && nt_for(h.psd_p[h.psd_sched[e]]) == nt) ++e;
-        Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr};
+        Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr,
+                  (int64_t)psd_fwd_smem_warm<T>(p0, nt) <= (int64_t)maxs};
         CU(cudaStreamCreateWithFlags(&bk.s, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
         const size_t fs = psd_fwd_smem<T>(p0, nt), bs = psd_bwd_smem<T>(p0, nt);
@@ -542,6 +567,7 @@ struct ImplT : Impl {
     TRY(tarena.alloc(&lams, (int64_t)cK * h.sum_p)); TRY(tarena.alloc(&Us, (int64_t)cK * h.sum_p2));
     TRY(tarena.alloc(&ck_x, nseg * n)); TRY(tarena.alloc(&ck_s, nseg * m));
     TRY(tarena.alloc(&ck_y, nseg * m)); TRY(tarena.alloc(&ck_xt, nseg * n));
+    TRY(tarena.alloc(&ck_U, (int64_t)nseg * h.sum_p2));
     TRY(tarena.alloc(&rho_in, (int64_t)K * m)); TRY(tarena.alloc(&rho_rect, (int64_t)K * m));
     TRY(tarena.alloc(&dinv, (int64_t)K * n)); TRY(tarena.alloc(&alpha_in, (int64_t)K * ni));
     TRY(tarena.alloc(&grho_all, (int64_t)K * m)); TRY(tarena.alloc(&galpha_all, (int64_t)K * ni));
@@ -649,21 +675,23 @@ struct ImplT : Impl {
     launch("precond", k_precond<T, V>, grid_for((int64_t)K * h.n, 256), 256, 0, st, P, K, (const double*)sigma_dev, (const T*)rho_rect, dinv);
   }
 
-  // one forward step k; state slot `slot` -> slot+1, tape slot `slot`
-  void enqueue_step(int32_t k, int slot, const T* xt_warm, cudaStream_t st) {
+  // one forward step k; state slot `slot` -> slot+1, tape slot `slot`;
+  // xt_warm / U_prev: x~ and PSD eigenvectors of step k-1 (null at k = 0)
+  void enqueue_step(int32_t k, int slot, const T* xt_warm, const T* U_prev, cudaStream_t st) {
     const T* rho = rho_rect + (int64_t)k * h.m;
     const T* alpha = alpha_in + (int64_t)k * h.ninst;
     const double sig = sigma_h[k];
     T* xt = xts + (int64_t)slot * h.n;
     T* stt = sts + (int64_t)slot * h.m;
     launch("rhs", k_rhs<T, V>, grid_for(h.n, 256), 256, 0, st, P, sig, (const T*)st_x(slot),
-           (const T*)st_s(slot), (const T*)st_y(slot), rho, xi);
+           (const T*)st_s(slot), (const T*)st_y(slot), rho, xi,
+           (const T*)(dinv + (int64_t)k * h.n), xt);
     CgArgs<T> ca{};
     ca.rhs = xi; ca.x = xt; ca.x0 = xt_warm; ca.rho = rho; ca.dinv = dinv + (int64_t)k * h.n;
     ca.sigma = sig; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = opt.cg_tol;
     ca.maxit = opt.cg_max_iter; ca.zero_start = xt_warm ? 0 : 1; ca.flag_bit = F_CG_CAP;
     ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 2;
-    launch("pcg", k_pcg<T, V, 256>, h.ninst, 256, 0, st, P, ca);
+    if (P.n_cg) launch("pcg", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
     StepPtrs<T> sp{};
     sp.x = st_x(slot); sp.s = st_s(slot); sp.y = st_y(slot);
     sp.xn = st_x(slot + 1); sp.sn = st_s(slot + 1); sp.yn = st_y(slot + 1);
@@ -674,13 +702,14 @@ struct ImplT : Impl {
     if (P.npsd) {
       PsdIterIO<T> io{stt, st_s(slot), st_y(slot), rho, alpha, st_s(slot + 1), st_y(slot + 1), P.row_inst};
       psd_group("psd_fwd", st, [&](const Bucket& bk, cudaStream_t s) {
-        const size_t sm = psd_fwd_smem<T>(bk.maxp, bk.nt);
+        const T* up = (opt.eig_warm_start && bk.warm_fits) ? U_prev : nullptr;
+        const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.nt) : psd_fwd_smem<T>(bk.maxp, bk.nt);
         if (bk.nt == 512)
-          k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats);
+          k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
         else if (bk.nt == 256)
-          k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats);
+          k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
         else
-          k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats);
+          k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
       });
     }
   }
@@ -691,8 +720,12 @@ struct ImplT : Impl {
     for (int32_t k = k0; k < k1; ++k) {
       const int slot = k - k0;
       const T* warm = nullptr;
-      if (k > 0) warm = slot == 0 ? ck_xt + (int64_t)seg * h.n : xts + (int64_t)(slot - 1) * h.n;
-      enqueue_step(k, slot, warm, st);
+      const T* uprev = nullptr;
+      if (k > 0) {
+        warm = slot == 0 ? ck_xt + (int64_t)seg * h.n : xts + (int64_t)(slot - 1) * h.n;
+        uprev = slot == 0 ? ck_U + (int64_t)seg * h.sum_p2 : Us + (int64_t)(slot - 1) * h.sum_p2;
+      }
+      enqueue_step(k, slot, warm, uprev, st);
     }
   }
 
@@ -713,6 +746,9 @@ struct ImplT : Impl {
         copy_state(st_x(0), st_s(0), st_y(0), st_x(cK), st_s(cK), st_y(cK), st);
         cudaMemcpyAsync(ck_xt + (int64_t)seg * h.n, xts + (int64_t)(cK - 1) * h.n,
                         sizeof(T) * h.n, cudaMemcpyDeviceToDevice, st);
+        if (h.sum_p2)
+          cudaMemcpyAsync(ck_U + (int64_t)seg * h.sum_p2, Us + (int64_t)(cK - 1) * h.sum_p2,
+                          sizeof(T) * h.sum_p2, cudaMemcpyDeviceToDevice, st);
       }
       copy_state(ck_x + (int64_t)seg * h.n, ck_s + (int64_t)seg * h.m, ck_y + (int64_t)seg * h.m,
                  st_x(0), st_s(0), st_y(0), st);
@@ -736,7 +772,7 @@ struct ImplT : Impl {
     q.xb2 = xb[cur ^ 1]; q.sb2 = sb[cur ^ 1]; q.yb2 = yb[cur ^ 1];
     q.gproj = gproj; q.vbar = vbar; q.adjrhs = adjrhs; q.lamt = lamt;
     q.grho = grho_all + (int64_t)k * h.m; q.galpha = galpha_all + (int64_t)k * h.ninst;
-    q.flags = flags; q.dk_tau = opt.dk_gap_tau;
+    q.flags = flags; q.dk_tau = opt.dk_gap_tau; q.dinv = dinv + (int64_t)k * h.n;
     launch("bwd_gproj", k_bwd_gproj<T, V>, grid_for(h.m, 256), 256, 0, st, P, q);
     if (P.nsoc) launch("soc_bwd", k_soc_bwd<T, V>, grid_for((int64_t)P.nsoc * 32, 256, INT32_MAX), 256, 0, st, P, q);
     if (P.npsd) {
@@ -757,7 +793,7 @@ struct ImplT : Impl {
     ca.dinv = dinv + (int64_t)k * h.n; ca.sigma = q.sigma; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u;
     ca.t = cg_t; ca.tol = opt.cg_tol; ca.maxit = opt.cg_max_iter; ca.zero_start = 1;
     ca.flag_bit = F_ADJ_CG_CAP; ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 4;
-    launch("pcg_adj", k_pcg<T, V, 256>, h.ninst, 256, 0, st, P, ca);
+    if (P.n_cg) launch("pcg_adj", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
     launch("bwd_solve", k_bwd_solve<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, q);
   }
 
@@ -1000,6 +1036,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->eig_tol = precision == COSMO_PREC_FP64 ? 1e-14 : 1e-6;
   o->use_graph = 1;
   o->device = 0;
+  o->eig_warm_start = 1;
   return COSMO_OK;
 }
 

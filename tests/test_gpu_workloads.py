@@ -98,13 +98,14 @@ def test_full_size_batched_maxcut(config2):
     xs_d, ss_d, ys_d = d["x"], d["s"], d["y"]
     ro, co = bm.packed.row_off, bm.packed.col_off
     # Mixed vs FP64 on every instance.  Objective: the 1e-4 gate, relative to
-    # the value.  Residual norms: within 1e-4 of the OSQP-style normaliser
-    # (App. E) -- asserted with a 2x margin (measured max ~1e-4, median
-    # 4e-6).  Strict value-relative residual/loss errors reach 1e-2 on
-    # instances whose residual is small, because FP32 iterates and an FP32
-    # eigensolver carry an absolute error of eps32 * ||S||_F per step; they
-    # are reported, not asserted.  Gradients: asserted median < 1e-2
-    # (measured ~2.5e-3; the 1e-3 gate is not met by the FP32 eigensolver).
+    # the value (measured max 1.5e-5).  Residual norms: within 1e-4 of the
+    # OSQP-style normaliser (App. E; measured max 1.9e-5).  Strict
+    # value-relative residual/loss errors reach 1e-2 on instances whose
+    # residual is small, because FP32 iterates and an FP32 eigensolver carry
+    # an absolute error of eps32 * ||S||_F per step; they are reported, not
+    # asserted.  Gradients: the 1e-3 gate holds in the median over instances
+    # (measured 8e-4); single instances whose trajectory passes an
+    # eigenvalue through zero (a kink of the projection) differ by more.
     errs = []
     for i in range(len(config2)):
         pr = config2[i]
@@ -113,10 +114,10 @@ def test_full_size_batched_maxcut(config2):
         x, s, y = xs_d[cs], ss_d[rs], ys_d[rs]
         scale_p = max(np.linalg.norm(pr.A @ x), np.linalg.norm(s), np.linalg.norm(pr.b))
         scale_d = max(np.linalg.norm(pr.q), np.linalg.norm(pr.A.T @ y))
-        assert abs(math.sqrt(rp_m[i]) - math.sqrt(rp_d[i])) <= 2e-4 * scale_p, i
-        assert abs(math.sqrt(rd_m[i]) - math.sqrt(rd_d[i])) <= 2e-4 * scale_d, i
+        assert abs(math.sqrt(rp_m[i]) - math.sqrt(rp_d[i])) <= 1e-4 * scale_p, i
+        assert abs(math.sqrt(rd_m[i]) - math.sqrt(rd_d[i])) <= 1e-4 * scale_d, i
         errs.append(rel_l2(grho_m[:, rs], grho_d[:, rs]))
-    assert np.median(errs) < 1e-2, np.median(errs)
+    assert np.median(errs) < 1e-3, np.median(errs)
     # sampled instances against the oracle (the smallest ones finish in seconds)
     order = np.argsort([p.meta["nv"] for p in config2], kind="stable")[:3]
     for i in order:
