@@ -132,8 +132,11 @@ typedef struct {
   double dk_gap_tau;        /* Loewner-matrix gap threshold, relative:
                                tau = dk_gap_tau * max(1, max|lambda|) */
   int32_t eig_jacobi_max_p; /* PSD blocks with p <= this use the cyclic Jacobi
-                               solver, larger ones tridiagonalisation + QL;
-                               <= 0 selects the built-in default */
+                               solver (shared memory), larger ones Householder
+                               tridiagonalisation + implicit QL (global memory)
+                               and a global-memory DK backward; <= 0: every
+                               block whose warm-started Jacobi fits in shared
+                               memory uses Jacobi */
   int32_t eig_max_sweeps;   /* Jacobi sweep cap (flag COSMO_FLAG_EIG_CAP) */
   double eig_tol;           /* Jacobi stop: off(A) <= eig_tol * ||A||_F */
   int32_t use_graph;        /* capture forward/backward into CUDA graphs */
@@ -170,8 +173,8 @@ int64_t cosmo_kernel_launch_count(void);
 const char* cosmo_last_error(void);
 
 /* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
- * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; Jacobi up to p = 64
- * (MIXED) / 48 (FP64); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
+ * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
+ * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
  * use_graph 1; device 0; eig_warm_start 1.  Returns COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 
@@ -327,7 +330,8 @@ cosmo_status cosmo_pcg_solve_noalloc(int32_t precision, int32_t ninst, int64_t n
                                      const void* rhs, void* x, int32_t warm_start, double tol,
                                      int32_t max_iter, int32_t* iters, void* stream);
 
-/* Batched PSD projection, Eq. (psd-proj), on nblk blocks given in svec form.
+/* Batched PSD projection, Eq. (psd-proj), on nblk blocks given in svec form
+ * (cyclic Jacobi for p <= 64, tridiagonalisation + implicit QL above).
  * Block j has order p[j] and starts at svec offset off[j] of v and out
  * (dev real, sum of p(p+1)/2 entries).  lam (dev real, sum p, may be NULL)
  * and U (dev real, sum p^2, column-major per block, may be NULL) receive the

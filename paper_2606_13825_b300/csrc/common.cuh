@@ -27,6 +27,10 @@ template <class T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = 5.9604644775390625e-08; };
 template <> struct Eps<double> { static constexpr double v = 1.1102230246251565e-16; };
 
+template <class T> struct MaxVal;
+template <> struct MaxVal<float> { static constexpr float v = 3.4028234663852886e+38f; };
+template <> struct MaxVal<double> { static constexpr double v = 1.7976931348623157e+308; };
+
 __device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
 

@@ -86,9 +86,13 @@ __device__ __forceinline__ void jacobi_rotations(const T* A, T* cs, uint16_t* pr
         const T theta = A[b * ld + b] - A[a * ld + a];
         const T phi = T(2) * apq;
         const T r = sqrt(theta * theta + phi * phi);
-        const T t = copysign(T(1), theta) * phi / (fabs(theta) + r);
-        c = rsqrt_(T(1) + t * t);
-        s = t * c;
+        // r underflows to 0 only when the coupling itself is negligible (and
+        // overflows only for entries near the range limit): skip the rotation
+        if (r > T(0) && r <= MaxVal<T>::v) {
+          const T t = copysign(T(1), theta) * phi / (fabs(theta) + r);
+          c = rsqrt_(T(1) + t * t);
+          s = t * c;
+        }
       }
     }
     cs[2 * k] = c;

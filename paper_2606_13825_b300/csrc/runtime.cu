@@ -21,6 +21,7 @@
 #include "../../include/cosmo_du.h"
 #include "common.cuh"
 #include "kernels_psd.cuh"
+#include "kernels_tql.cuh"
 #include "kernels_vec.cuh"
 
 using namespace cosmo;
@@ -398,7 +399,10 @@ struct ImplT : Impl {
   int64_t seq_kernels = 0;  // kernels enqueued by the sequence being built
   // PSD blocks (sorted by p, largest first) split into size buckets, each
   // launched with its own CTA size on a forked stream
-  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; bool warm_fits; };
+  // method 0: CTA-resident Jacobi + shared-memory DK; method 1 (large blocks):
+  // tridiagonal + QL in the tape slot + global-memory DK
+  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; bool warm_fits; int method; };
+  T* dk_work = nullptr;  // 2 x sum p^2: DK scratch of large blocks
   std::vector<Bucket> buckets;
   cudaEvent_t ev_fork = nullptr;
   // optional CUDA-event timing of launches (direct mode only)
@@ -519,24 +523,46 @@ struct ImplT : Impl {
       int dev = 0, maxs = 0;
       CU(cudaGetDevice(&dev));
       CU(cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      // size classes: p > 56 -> 512 threads, 33..56 -> 256, <= 32 -> 128
-      auto nt_for = [](int p) { return p > 56 ? 512 : (p > 32 ? 256 : 128); };
+      // Jacobi size classes: p > 56 -> 512 threads, 33..56 -> 256, <= 32 -> 128.
+      // Blocks above the cutoff (option eig_jacobi_max_p; by default the
+      // largest p whose warm-started Jacobi and DK fit in shared memory) take
+      // the large-block path with 256 threads.
+      auto fits_jacobi = [&](int p) {
+        const int nt = p > 56 ? 512 : (p > 32 ? 256 : 128);
+        return (int64_t)psd_fwd_smem_warm<T>(p, nt) <= maxs && (int64_t)psd_bwd_smem<T>(p, nt) <= maxs;
+      };
+      auto class_of = [&](int p) {
+        const bool big = opt.eig_jacobi_max_p > 0 ? (p > opt.eig_jacobi_max_p || !fits_jacobi(p)) : !fits_jacobi(p);
+        if (big) return 1000;                    // large-block path
+        return p > 56 ? 512 : (p > 32 ? 256 : 128);
+      };
+      bool any_big = false;
       for (size_t q = 0; q < h.psd_sched.size();) {
         const int p0 = h.psd_p[h.psd_sched[q]];
-        const int nt = nt_for(p0);
+        const int cls = class_of(p0);
         size_t e = q;
-        while (e < h.psd_sched.size() && nt_for(h.psd_p[h.psd_sched[e]]) == nt) ++e;
+        while (e < h.psd_sched.size() && class_of(h.psd_p[h.psd_sched[e]]) == cls) ++e;
+        const int method = cls == 1000 ? 1 : 0;
+        const int nt = method ? 256 : cls;
         Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr,
-                  (int64_t)psd_fwd_smem_warm<T>(p0, nt) <= (int64_t)maxs};
+                  method == 0 && (int64_t)psd_fwd_smem_warm<T>(p0, nt) <= (int64_t)maxs, method};
         CU(cudaStreamCreateWithFlags(&bk.s, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
-        const size_t fs = psd_fwd_smem<T>(p0, nt), bs = psd_bwd_smem<T>(p0, nt);
-        if ((int64_t)fs > maxs || (int64_t)bs > maxs)
-          return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
-                      p0, std::max(fs, bs), maxs);
+        if (method == 0) {
+          const size_t fs = psd_fwd_smem<T>(p0, nt), bs = psd_bwd_smem<T>(p0, nt);
+          if ((int64_t)fs > maxs || (int64_t)bs > maxs)
+            return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
+                        p0, std::max(fs, bs), maxs);
+        } else {
+          any_big = true;
+          if ((int64_t)tql_smem<T>(p0, nt) > maxs)
+            return fail(COSMO_E_INVAL, "PSD order %d too large", p0);
+        }
         buckets.push_back(bk);
         q = e;
       }
+      if (any_big) TRY(arena.alloc(&dk_work, 2 * h.sum_p2));
+      CU(cudaFuncSetAttribute(k_psd_fwd_tql<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -702,6 +728,11 @@ struct ImplT : Impl {
     if (P.npsd) {
       PsdIterIO<T> io{stt, st_s(slot), st_y(slot), rho, alpha, st_s(slot + 1), st_y(slot + 1), P.row_inst};
       psd_group("psd_fwd", st, [&](const Bucket& bk, cudaStream_t s) {
+        if (bk.method == 1) {
+          k_psd_fwd_tql<T, V, 256><<<bk.count, 256, tql_smem<T>(bk.maxp, 256), s>>>(
+              P, io, sp.lam, sp.U, flags, bk.start, stats, 30 * 4);
+          return;
+        }
         const T* up = (opt.eig_warm_start && bk.warm_fits) ? U_prev : nullptr;
         const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.nt) : psd_fwd_smem<T>(bk.maxp, bk.nt);
         if (bk.nt == 512)
@@ -778,6 +809,11 @@ struct ImplT : Impl {
     if (P.npsd) {
       PsdBwdIO<T> io{gproj, vbar, P.row_inst};
       psd_group("psd_bwd", st, [&](const Bucket& bk, cudaStream_t s) {
+        if (bk.method == 1) {
+          k_psd_bwd_global<T, V, 256><<<bk.count, 256, 0, s>>>(P, io, q.lam, q.U, dk_work,
+                                                               opt.dk_gap_tau, bk.start);
+          return;
+        }
         const size_t sm = psd_bwd_smem<T>(bk.maxp, bk.nt);
         if (bk.nt == 512)
           k_psd_bwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
@@ -1031,7 +1067,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->cg_max_iter = 500;
   o->checkpoint_every = 0;
   o->dk_gap_tau = 1e-12;
-  o->eig_jacobi_max_p = precision == COSMO_PREC_FP64 ? 48 : 64;
+  o->eig_jacobi_max_p = 0;
   o->eig_max_sweeps = 30;
   o->eig_tol = precision == COSMO_PREC_FP64 ? 1e-14 : 1e-6;
   o->use_graph = 1;
@@ -1244,32 +1280,51 @@ cosmo_status cosmo_step_host(cosmo_batch* b, int32_t K, double sigma, double eq_
 template <class T>
 static cosmo_status psd_project_t(int32_t nblk, const int32_t* p_h, const int64_t* off_h,
                                   const void* v, void* out, void* lam, void* U, cudaStream_t st) {
+  // Jacobi for p <= 64, tridiagonal + QL above; two launches when mixed
   std::vector<int32_t> p(p_h, p_h + nblk);
   std::vector<int64_t> off(off_h, off_h + nblk), loff(nblk), uoff(nblk);
   int64_t sl = 0, su = 0;
-  int maxp = 0;
   for (int32_t j = 0; j < nblk; ++j) {
     if (p[j] < 1 || p[j] > 1024) return fail(COSMO_E_INVAL, "PSD order out of range");
     loff[j] = sl; uoff[j] = su; sl += p[j]; su += (int64_t)p[j] * p[j];
-    maxp = std::max(maxp, p[j]);
   }
-  const size_t smem = psd_fwd_smem<T>(maxp, 256);
   int dev = 0, maxs = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if ((int64_t)smem > maxs) return fail(COSMO_E_INVAL, "PSD order %d too large for one CTA", maxp);
-  CU(cudaFuncSetAttribute(k_psd_project_batch<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   DevArena a;
-  int32_t *dp, *dflag;
-  int64_t *doff, *dloff, *duoff;
-  TRY(a.upload(&dp, p)); TRY(a.upload(&doff, off)); TRY(a.upload(&dloff, loff));
-  TRY(a.upload(&duoff, uoff)); TRY(a.alloc(&dflag, 1));
+  T* Uw = (T*)U;
+  if (!Uw) TRY(a.alloc(&Uw, su));
+  int32_t* dflag;
+  TRY(a.alloc(&dflag, 1));
   CU(cudaMemsetAsync(dflag, 0, sizeof(int32_t), st));
-  PsdBatch<T> B{nblk, dp, doff, dloff, duoff};
   const double tol = sizeof(T) == 8 ? 1e-14 : 1e-6;
-  k_psd_project_batch<T, 256><<<nblk, 256, smem, st>>>(B, (const T*)v, (T*)out, (T*)lam, (T*)U, tol, 30, dflag);
-  CU(cudaGetLastError());
-  g_launches += 1;
+  for (int method = 0; method < 2; ++method) {
+    std::vector<int32_t> pp;
+    std::vector<int64_t> oo, lo, uo;
+    int maxp = 0;
+    for (int32_t j = 0; j < nblk; ++j)
+      if ((p[j] > 64) == (method == 1)) {
+        pp.push_back(p[j]); oo.push_back(off[j]); lo.push_back(loff[j]); uo.push_back(uoff[j]);
+        maxp = std::max(maxp, p[j]);
+      }
+    if (pp.empty()) continue;
+    int32_t* dp;
+    int64_t *doff, *dloff, *duoff;
+    TRY(a.upload(&dp, pp)); TRY(a.upload(&doff, oo)); TRY(a.upload(&dloff, lo)); TRY(a.upload(&duoff, uo));
+    PsdBatch<T> B{(int32_t)pp.size(), dp, doff, dloff, duoff};
+    if (method == 0) {
+      const size_t smem = psd_fwd_smem<T>(maxp, 256);
+      if ((int64_t)smem > maxs) return fail(COSMO_E_INVAL, "PSD order %d too large for one CTA", maxp);
+      CU(cudaFuncSetAttribute(k_psd_project_batch<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_psd_project_batch<T, 256><<<B.nblk, 256, smem, st>>>(B, (const T*)v, (T*)out, (T*)lam, Uw, tol, 30, dflag);
+    } else {
+      const size_t smem = tql_smem<T>(maxp, 256);
+      CU(cudaFuncSetAttribute(k_psd_project_tql<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_psd_project_tql<T, 256><<<B.nblk, 256, smem, st>>>(B, (const T*)v, (T*)out, (T*)lam, Uw, 120, dflag);
+    }
+    CU(cudaGetLastError());
+    g_launches += 1;
+  }
   CU(cudaStreamSynchronize(st));
   return COSMO_OK;
 }

@@ -319,3 +319,20 @@ def test_eig_warm_start_matches_cold():
     compare(warm, ora, "fp64")
     info_w, info_c = warm["batch"].info(), cold["batch"].info()
     assert info_w["eig_sweeps"] <= info_c["eig_sweeps"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_block_path_forced_on_small_blocks(precision):
+    """eig_jacobi_max_p = 4 sends every block of order >= 5 through the
+    tridiagonal + QL projection and the global-memory DK backward; forward
+    and every gradient must still match the oracle."""
+    _need_gpu()
+    probs = maxcut_batch([3, 6, 11, 19], seed=109) + \
+        [lovasz_problem(7, cycle_graph(7)), covsteer_problem(5200, T=1)]
+    K = 5
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=20)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, eig_jacobi_max_p=4,
+                  cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not (gpu["flags"] & 4).any(), gpu["flags"]
+    compare(gpu, ora, precision)

@@ -93,3 +93,36 @@ def test_dk_clustered_app_c(delta):
     assert np.all(np.isfinite(dk))
     ref = C.vjp_psd(lg.cpu().numpy(), Ug.cpu().numpy().reshape(p, p).T, g, p)
     assert np.abs(dk - ref).max() <= 1e-11 * np.abs(g).max() * p
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_psd_project_large_blocks_tridiagonal_ql(precision):
+    """Blocks above the Jacobi cutoff use Householder tridiagonalisation and
+    implicit QL; checked against the oracle's eigh / projection."""
+    _need_gpu()
+    from paper_2606_13825_b300 import psd_project
+    rng = np.random.default_rng(22)
+    ps = [65, 100, 150, 200]
+    vs, refs, lams = [], [], []
+    for p in ps:
+        S = rng.standard_normal((p, p)); S = S + S.T
+        if p == 150:                       # repeated eigenvalues
+            Q, _ = np.linalg.qr(rng.standard_normal((p, p)))
+            S = (Q * np.repeat([-1.0, 0.5, 2.0], 50)) @ Q.T
+            S = 0.5 * (S + S.T)
+        v = C.svec(S)
+        ref, lam, _ = C.proj_psd(v, p)
+        vs.append(v); refs.append(ref); lams.append(np.sort(lam))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out, lam, U = psd_project(torch.tensor(np.concatenate(vs), dtype=dt, device="cuda"), ps, precision)
+    out = out.double().cpu().numpy(); lam = lam.double().cpu().numpy(); U = U.double().cpu().numpy()
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    o = lo = uo = 0
+    for p, ref, lref in zip(ps, refs, lams):
+        d = p * (p + 1) // 2
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(out[o:o + d] - ref).max() <= tol * scale * p, p
+        assert np.abs(np.sort(lam[lo:lo + p]) - lref).max() <= tol * max(1.0, np.abs(lref).max()) * p
+        Ub = U[uo:uo + p * p].reshape(p, p).T
+        assert np.abs(Ub.T @ Ub - np.eye(p)).max() <= tol * p * 10
+        o += d; lo += p; uo += p * p
