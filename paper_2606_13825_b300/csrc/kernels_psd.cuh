@@ -52,26 +52,38 @@ template <class T> __device__ __forceinline__ T rsqrt_(T a);
 template <> __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
 template <> __device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
 
-// Cyclic Jacobi on the symmetric matrix A (pe x ld, zero-padded) in shared
-// memory; V <- accumulated rotations (starts as the identity).  Stops when
-// off(A) <= tol' ||A||_F with tol' = max(tol, 4 eps sqrt(p)) (below that the
-// rounding of the rotations themselves keeps off(A) from shrinking), or when
-// from the fifth sweep on a sweep fails to halve off(A)^2 (quadratic
-// convergence has ended at the rounding floor); returns the number of sweeps
-// run, negative if max_sweeps was reached first.
+// One rotation of the round-robin schedule: pair (a, b) packed as a | b << 16
+// and its (c, s), in one 16-byte record (two for double).
+template <class T> struct __align__(16) PairRec { uint32_t ab; uint32_t pad; T c, s; };
+template <> struct __align__(16) PairRec<float> { uint32_t ab; float c, s, pad; };
+
+// Cyclic Jacobi on the symmetric matrix A (pe x ld, zero-padded; only the
+// upper triangle is read and kept) in shared memory; V <- V J_1 J_2 ... (V
+// starts as the identity, or holds a warm start).  Stops when off(A) <=
+// tol' ||A||_F with tol' = max(tol, 4 eps sqrt(p)) (below that the rounding
+// of the rotations themselves keeps off(A) from shrinking), or when from the
+// fifth sweep on a sweep fails to halve off(A)^2 (quadratic convergence has
+// ended at the rounding floor); returns the number of sweeps run, negative if
+// max_sweeps was reached first.
+//
+// Rotations with |a_pq| <= tol' ||A||_F / (4p) are skipped: if every
+// remaining coupling is that small, off(A) <= tol' ||A||_F / 4 already.  A
+// round in which no pair rotates skips its updates.
 //
 // Rounds are software-pipelined.  Phase X: every thread applies round r's
-// rotations to the 2x2 blocks (k, l), k <= l, of A (mirrored), from a
-// precomputed triangular index table.  Phase Y: the first warps compute round
-// r+1's pairs and rotations from the updated A into the other half of a
-// double buffer while the remaining warps apply round r's rotations to the
-// columns of V (V never feeds a rotation), rows fastest (odd stride ld: no
-// bank conflicts).  Two barriers per round, no idle rotation phase.
-// Shared scratch: cs [2 pe] T, pr [2 pe] u16, tri [np(np+1)/2] u32.
+// rotations to the 2x2 blocks (k, l), k <= l, of A's upper triangle (entry
+// (r, c) at [min][max]), from a precomputed triangular index table.  Phase Y:
+// the first warps compute round r+1's pairs and rotations from the updated A
+// into the other half of a double buffer while the remaining warps apply round
+// r's rotations to V, one warp per column pair, lanes over rows (odd stride
+// ld: no bank conflicts).  Two barriers per round.
+// Shared scratch: recs [2 pe/2] PairRec<T>, tri [np(np+1)/2] u32.
 template <class T>
-__device__ __forceinline__ void jacobi_rotations(const T* A, T* cs, uint16_t* pr, int rd, int p,
-                                                 int pe, int ld, int first, int stride) {
+__device__ __forceinline__ bool jacobi_rotations(const T* A, PairRec<T>* rec, int rd, int p,
+                                                 int pe, int ld, int first, int stride,
+                                                 T thresh) {
   const int np = pe / 2;
+  bool any = false;
   for (int k = first; k < np; k += stride) {
     int a, b;
     rr_pair(rd, k, pe, a, b);
@@ -79,40 +91,42 @@ __device__ __forceinline__ void jacobi_rotations(const T* A, T* cs, uint16_t* pr
     if (a < p && b < p) {
       // only the upper triangle of A is kept
       const T apq = a < b ? A[a * ld + b] : A[b * ld + a];
-      if (apq != T(0)) {
+      if (fabs(apq) > thresh) {
         // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = theta / phi, written
-        // as sign(theta) phi / (|theta| + sqrt(theta^2 + phi^2)): one root, one
-        // division, no overflow of tau when apq is tiny
+        // as sign(theta) phi / (|theta| + sqrt(theta^2 + phi^2)): one root and
+        // one division; the rotation is skipped if the root under/overflows
         const T theta = A[b * ld + b] - A[a * ld + a];
         const T phi = T(2) * apq;
         const T r = sqrt(theta * theta + phi * phi);
-        // r underflows to 0 only when the coupling itself is negligible (and
-        // overflows only for entries near the range limit): skip the rotation
         if (r > T(0) && r <= MaxVal<T>::v) {
           const T t = copysign(T(1), theta) * phi / (fabs(theta) + r);
           c = rsqrt_(T(1) + t * t);
           s = t * c;
+          any = true;
         }
       }
     }
-    cs[2 * k] = c;
-    cs[2 * k + 1] = s;
-    pr[2 * k] = (uint16_t)a;
-    pr[2 * k + 1] = (uint16_t)b;
+    PairRec<T> pr;
+    pr.ab = (uint32_t)a | ((uint32_t)b << 16);
+    pr.c = c;
+    pr.s = s;
+    rec[k] = pr;
   }
+  return any;
 }
 
 template <class T>
-__device__ int jacobi_eig(T* A, T* V, T* cs2, uint16_t* pr2, uint32_t* tri, double* red, int p,
+__device__ int jacobi_eig(T* A, T* V, PairRec<T>* rec2, uint32_t* tri, double* red, int p,
                           double tol, int max_sweeps, bool v_identity = true) {
   const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
   const int ntri = np * (np + 1) / 2;
   const int nt = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nt >> 5;
   // warps that compute rotations in phase Y; the rest update V meanwhile
-  const int rot_threads = ((np + 31) / 32) * 32;
-  const bool split = nt >= rot_threads + 64;
-  const int v_first = split ? rot_threads : 0;
-  const int v_stride = nt - v_first;
+  const int rot_warps = (np + 31) / 32;
+  const bool split = nwarps >= rot_warps + 2;
+  const int v_first_warp = split ? rot_warps : 0;
+  const int v_warps = nwarps - v_first_warp;
   if (v_identity) {
     for (int e = threadIdx.x; e < pe * ld; e += nt) {
       const int i = e / ld, j = e % ld;
@@ -128,10 +142,6 @@ __device__ int jacobi_eig(T* A, T* V, T* cs2, uint16_t* pr2, uint32_t* tri, doub
   const double tol_eff = fmax(tol, 4.0 * Eps<T>::v * sqrt((double)p));
   const double tol2 = tol_eff * tol_eff;
   double prev_off2 = 0.0;
-  const int nV = pe * np;
-  // e / pe by a float reciprocal: exact for e < 2^20 and pe <= 2048, since
-  // (e + 1/2) / pe stays at least 1/(2 pe) away from the integers
-  const float inv_pe = 1.0f / (float)pe;
   int result = -max_sweeps;
   for (int sweep = 0;; ++sweep) {
     double acc[2] = {0.0, 0.0};   // off-diagonal and diagonal sums of squares (upper triangle)
@@ -147,100 +157,97 @@ __device__ int jacobi_eig(T* A, T* V, T* cs2, uint16_t* pr2, uint32_t* tri, doub
     if (off2 <= tol2 * tot2 || (sweep >= 5 && off2 > 0.5 * prev_off2)) { result = sweep; break; }
     if (sweep >= max_sweeps) break;
     prev_off2 = off2;
-    jacobi_rotations(A, cs2, pr2, 0, p, pe, ld, threadIdx.x, nt);
-    __syncthreads();
+    const T thresh = (T)(tol_eff * sqrt(tot2) / (4.0 * p));
+    // __syncthreads_or hands every thread the OR: whether the round rotates
+    bool active = __syncthreads_or(jacobi_rotations(A, rec2, 0, p, pe, ld, threadIdx.x, nt, thresh));
     for (int rd = 0; rd < pe - 1; ++rd) {
-      const T* cs = cs2 + (rd & 1) * pe;
-      const uint16_t* pr = pr2 + (rd & 1) * pe;
+      const PairRec<T>* rec = rec2 + (rd & 1) * np;
       // ---- phase X: A <- J'AJ on the 2x2 blocks (k, l), k <= l, on the upper
-      // triangle only (entry (r, c) lives at [min(r,c)][max(r,c)]); two blocks
-      // per thread in flight (all loads before any store: blocks are disjoint)
-      for (int e0 = threadIdx.x; e0 < ntri; e0 += 2 * nt) {
-        T x[2][4], cc[2][2], ss[2][2];
-        int o[2][4];
-        bool v[2], dg[2];
+      // triangle only; two blocks per thread in flight (all loads before any
+      // store: blocks are disjoint)
+      if (active) {
+        for (int e0 = threadIdx.x; e0 < ntri; e0 += 2 * nt) {
+          T x[2][4], cc[2][2], ss[2][2];
+          int o[2][4];
+          bool v[2], dg[2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int e = e0 + u * nt;
-          v[u] = e < ntri;
-          const uint32_t kl = tri[v[u] ? e : 0];
-          const int k = (int)(kl & 0xffffu), l = (int)(kl >> 16);
-          dg[u] = k == l;
-          const int ak = pr[2 * k], bk = pr[2 * k + 1], al = pr[2 * l], bl = pr[2 * l + 1];
-          cc[u][0] = cs[2 * k]; ss[u][0] = cs[2 * k + 1];
-          cc[u][1] = cs[2 * l]; ss[u][1] = cs[2 * l + 1];
-          o[u][0] = ak < al ? ak * ld + al : al * ld + ak;
-          o[u][1] = ak < bl ? ak * ld + bl : bl * ld + ak;
-          o[u][2] = bk < al ? bk * ld + al : al * ld + bk;
-          o[u][3] = bk < bl ? bk * ld + bl : bl * ld + bk;
-          x[u][0] = A[o[u][0]];
-          x[u][1] = A[o[u][1]];
-          x[u][2] = A[o[u][2]];
-          x[u][3] = A[o[u][3]];
-        }
+          for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * nt;
+            v[u] = e < ntri;
+            const uint32_t kl = tri[v[u] ? e : 0];
+            const int k = (int)(kl & 0xffffu), l = (int)(kl >> 16);
+            dg[u] = k == l;
+            const PairRec<T> rk = rec[k], rl = rec[l];
+            const int ak = (int)(rk.ab & 0xffffu), bk = (int)(rk.ab >> 16);
+            const int al = (int)(rl.ab & 0xffffu), bl = (int)(rl.ab >> 16);
+            cc[u][0] = rk.c; ss[u][0] = rk.s;
+            cc[u][1] = rl.c; ss[u][1] = rl.s;
+            o[u][0] = ak < al ? ak * ld + al : al * ld + ak;
+            o[u][1] = ak < bl ? ak * ld + bl : bl * ld + ak;
+            o[u][2] = bk < al ? bk * ld + al : al * ld + bk;
+            o[u][3] = bk < bl ? bk * ld + bl : bl * ld + bk;
+            x[u][0] = A[o[u][0]];
+            x[u][1] = A[o[u][1]];
+            x[u][2] = A[o[u][2]];
+            x[u][3] = A[o[u][3]];
+          }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (!v[u]) continue;
-          const T ck = cc[u][0], sk = ss[u][0], cl = cc[u][1], sl = ss[u][1];
-          // rows: [r_a; r_b] <- [[c, -s], [s, c]] [r_a; r_b]
-          const T y11 = ck * x[u][0] - sk * x[u][2], y12 = ck * x[u][1] - sk * x[u][3];
-          const T y21 = sk * x[u][0] + ck * x[u][2], y22 = sk * x[u][1] + ck * x[u][3];
-          // columns: [c_a, c_b] <- [c_a, c_b] [[c, s], [-s, c]]
-          const T z11 = cl * y11 - sl * y12, z12 = sl * y11 + cl * y12;
-          const T z21 = cl * y21 - sl * y22, z22 = sl * y21 + cl * y22;
-          if (dg[u]) {
-            // (a,a), (a,b)=(b,a), (b,b): the rotation annihilates the coupling
-            A[o[u][0]] = z11;
-            A[o[u][1]] = T(0);
-            A[o[u][3]] = z22;
-          } else {
-            A[o[u][0]] = z11;
-            A[o[u][1]] = z12;
-            A[o[u][2]] = z21;
-            A[o[u][3]] = z22;
+          for (int u = 0; u < 2; ++u) {
+            if (!v[u]) continue;
+            const T ck = cc[u][0], sk = ss[u][0], cl = cc[u][1], sl = ss[u][1];
+            // rows: [r_a; r_b] <- [[c, -s], [s, c]] [r_a; r_b]
+            const T y11 = ck * x[u][0] - sk * x[u][2], y12 = ck * x[u][1] - sk * x[u][3];
+            const T y21 = sk * x[u][0] + ck * x[u][2], y22 = sk * x[u][1] + ck * x[u][3];
+            // columns: [c_a, c_b] <- [c_a, c_b] [[c, s], [-s, c]]
+            const T z11 = cl * y11 - sl * y12, z12 = sl * y11 + cl * y12;
+            const T z21 = cl * y21 - sl * y22, z22 = sl * y21 + cl * y22;
+            if (dg[u]) {
+              // (a,a), (a,b)=(b,a), (b,b): the rotation annihilates the coupling
+              A[o[u][0]] = z11;
+              if (ck != T(1) || sk != T(0)) A[o[u][1]] = T(0);
+              A[o[u][3]] = z22;
+            } else {
+              A[o[u][0]] = z11;
+              A[o[u][1]] = z12;
+              A[o[u][2]] = z21;
+              A[o[u][3]] = z22;
+            }
           }
         }
       }
       __syncthreads();
       // ---- phase Y: rotations of round rd+1 (first warps) || V <- V J_rd
       const bool more = rd + 1 < pe - 1;
+      bool any_next = false;
+      PairRec<T>* rec_next = rec2 + ((rd + 1) & 1) * np;
       if (split) {
-        if (threadIdx.x < rot_threads) {
-          if (more) jacobi_rotations(A, cs2 + ((rd + 1) & 1) * pe, pr2 + ((rd + 1) & 1) * pe,
-                                     rd + 1, p, pe, ld, threadIdx.x, rot_threads);
-        }
+        if (warp < rot_warps && more)
+          any_next = jacobi_rotations(A, rec_next, rd + 1, p, pe, ld, threadIdx.x, rot_warps * 32, thresh);
       } else if (more) {
-        jacobi_rotations(A, cs2 + ((rd + 1) & 1) * pe, pr2 + ((rd + 1) & 1) * pe, rd + 1, p, pe,
-                         ld, threadIdx.x, nt);
+        any_next = jacobi_rotations(A, rec_next, rd + 1, p, pe, ld, threadIdx.x, nt, thresh);
       }
-      if (threadIdx.x >= v_first) {
-        // four column-pair updates in flight
-        for (int e0 = threadIdx.x - v_first; e0 < nV; e0 += 4 * v_stride) {
-          T va[4], vb[4], cl[4], sl[4];
-          int oa[4], ob[4];
-          bool v[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * v_stride;
-            v[u] = e < nV;
-            const int ee = v[u] ? e : 0;
-            const int l = __float2int_rz(((float)ee + 0.5f) * inv_pe), i = ee - l * pe;
-            oa[u] = i * ld + pr[2 * l];
-            ob[u] = i * ld + pr[2 * l + 1];
-            cl[u] = cs[2 * l];
-            sl[u] = cs[2 * l + 1];
-            va[u] = V[oa[u]];
-            vb[u] = V[ob[u]];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (!v[u]) continue;
-            V[oa[u]] = cl[u] * va[u] - sl[u] * vb[u];
-            V[ob[u]] = sl[u] * va[u] + cl[u] * vb[u];
+      if (active && warp >= v_first_warp) {
+        // one warp per column pair l; lanes over rows (conflict-free)
+        for (int l = warp - v_first_warp; l < np; l += v_warps) {
+          const PairRec<T> rl = rec[l];
+          if (rl.c == T(1) && rl.s == T(0)) continue;
+          const int al = (int)(rl.ab & 0xffffu), bl = (int)(rl.ab >> 16);
+          for (int i0 = lane; i0 < pe; i0 += 64) {
+            T va[2], vb[2];
+            const int i1 = i0 + 32;
+            va[0] = V[i0 * ld + al];
+            vb[0] = V[i0 * ld + bl];
+            if (i1 < pe) { va[1] = V[i1 * ld + al]; vb[1] = V[i1 * ld + bl]; }
+            V[i0 * ld + al] = rl.c * va[0] - rl.s * vb[0];
+            V[i0 * ld + bl] = rl.s * va[0] + rl.c * vb[0];
+            if (i1 < pe) {
+              V[i1 * ld + al] = rl.c * va[1] - rl.s * vb[1];
+              V[i1 * ld + bl] = rl.s * va[1] + rl.c * vb[1];
+            }
           }
         }
       }
-      __syncthreads();
+      active = __syncthreads_or(any_next);
     }
   }
   return result;
@@ -334,14 +341,14 @@ __device__ __forceinline__ void smem_gemm_auto(int p, const T* A, int ar, int ac
 }
 
 // shared memory the Jacobi projection needs for order p (bytes)
-// layout: A, V [pe x ld] T | cs [2 pe] T | sel [pe + 2] int | pr [2 pe] u16 |
-// tri [np(np+1)/2] u32 | red (8-aligned) [2 nt/32] double
+// layout: A, V [pe x ld] T | recs [pe] PairRec<T> (16-aligned) | sel [pe + 2]
+// int | flags [4] int | tri [np(np+1)/2] u32 | red (8-aligned) [2 nt/32] double
 template <class T>
 __host__ __device__ inline size_t psd_fwd_smem(int p, int nt) {
   const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
-  return (size_t)2 * pe * ld * sizeof(T) + (size_t)2 * pe * sizeof(T) +
-         (size_t)(pe + 2) * sizeof(int) + (size_t)2 * pe * sizeof(uint16_t) +
-         (size_t)(np * (np + 1) / 2) * sizeof(uint32_t) + (size_t)(2 * (nt / 32)) * sizeof(double) + 64;
+  return (size_t)2 * pe * ld * sizeof(T) + 16 + (size_t)pe * sizeof(PairRec<T>) +
+         (size_t)(pe + 6) * sizeof(int) + (size_t)(np * (np + 1) / 2) * sizeof(uint32_t) +
+         (size_t)(2 * (nt / 32)) * sizeof(double) + 64;
 }
 
 // with a warm start a third pe x ld buffer W follows the red array
@@ -353,15 +360,15 @@ __host__ __device__ inline size_t psd_fwd_smem_warm(int p, int nt) {
 
 template <class T>
 struct JacobiSmem {
-  T* A; T* V; T* cs; int* sel; uint16_t* pr; uint32_t* tri; double* red;
+  T* A; T* V; PairRec<T>* rec; int* sel; int* flag2; uint32_t* tri; double* red;
   __device__ JacobiSmem(unsigned char* raw, int p) {
     const int pe = psd_pe(p), ld = psd_ld(p), np = pe / 2;
     A = reinterpret_cast<T*>(raw);
     V = A + pe * ld;
-    cs = V + pe * ld;
-    sel = reinterpret_cast<int*>(cs + 2 * pe);
-    pr = reinterpret_cast<uint16_t*>(sel + pe + 2);
-    tri = reinterpret_cast<uint32_t*>(reinterpret_cast<uintptr_t>(pr + 2 * pe + 1) & ~uintptr_t(3));
+    rec = reinterpret_cast<PairRec<T>*>((reinterpret_cast<uintptr_t>(V + pe * ld) + 15) & ~uintptr_t(15));
+    sel = reinterpret_cast<int*>(rec + 2 * np);
+    flag2 = sel + pe + 2;
+    tri = reinterpret_cast<uint32_t*>(flag2 + 4);
     red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tri + np * (np + 1) / 2) + 7) & ~uintptr_t(7));
   }
   // third buffer, only valid when the launch sized shared memory with psd_fwd_smem_warm
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T
     smem_gemm_auto<T>(p, Vm, 1, ld, W, ld, 1, [&](int i, int j, T v) { A[i * ld + j] = v; });
     __syncthreads();
   }
-  const int sweeps = jacobi_eig(A, Vm, sm.cs, sm.pr, sm.tri, sm.red, p, tol, max_sweeps, !warm);
+  const int sweeps = jacobi_eig(A, Vm, sm.rec, sm.tri, sm.red, p, tol, max_sweeps, !warm);
   if (threadIdx.x == 0) {
     if (sweeps < 0) atomicOr(&flags[inst], F_EIG_CAP);
     if (stats) {
@@ -625,7 +632,7 @@ __global__ void __launch_bounds__(NT) k_psd_project_batch(PsdBatch<T> B, const T
     A[j * ld + i] = x;
   }
   __syncthreads();
-  const int sweeps = jacobi_eig(A, Vm, sm.cs, sm.pr, sm.tri, sm.red, p, tol, max_sweeps);
+  const int sweeps = jacobi_eig(A, Vm, sm.rec, sm.tri, sm.red, p, tol, max_sweeps);
   if (sweeps < 0 && threadIdx.x == 0 && flag) atomicOr(flag, F_EIG_CAP);
   if (lam_out)
     for (int k = threadIdx.x; k < p; k += NT) lam_out[B.loff[blk] + k] = A[k * ld + k];
