@@ -59,7 +59,7 @@ typedef enum {
   COSMO_E_CUDA = 3,       /* a CUDA runtime call failed */
   COSMO_E_NOTCONV = 4,    /* (flag) CG reached its iteration cap */
   COSMO_E_NONFINITE = 5,  /* (flag) a non-finite iterate was produced */
-  COSMO_E_TIMEOUT = 6,    /* reserved: bounded device wait gave up */
+  COSMO_E_TIMEOUT = 6,    /* a bounded device wait gave up (grid-wide CG barrier) */
   COSMO_E_STATE = 7,      /* call out of order (e.g. backward without tape) */
   COSMO_E_NODEVICE = 8    /* no CUDA device */
 } cosmo_status;
@@ -294,7 +294,20 @@ cosmo_status cosmo_status_sync(cosmo_batch* batch, int32_t* flags_host);
  *   iters int32 [ninst] or NULL: CG iterations per block (== max_iter means
  *     the cap was reached before ||r|| <= tol ||rhs||)
  * Workspace (4n + m reals, 2 ninst int32) is allocated stream-ordered on
- * `stream` and released before return.  Errors: E_INVAL, E_NOMEM, E_CUDA. */
+ * `stream` and released before return.
+ * Large instances: zero-start solves of fewer than 148 instances with more
+ * than 1e5 nonzeros of A each on average run a grid-wide CG instead (row and
+ * column tiles spread over all SMs).  When each instance's t (m_i reals) and
+ * a column segment of z fit in shared memory, the arrays are 16-byte aligned
+ * and the column indices increase along every row of A, the whole solve is
+ * one cooperative launch (the Chronopoulos-Gear form of Jacobi-PCG: the same
+ * iterates in exact arithmetic, one reduction point per iteration, grid
+ * barriers between phases); otherwise three kernels per iteration gather
+ * from global memory.  Both synchronise the stream before returning.  The
+ * rows of instance i must only reference its own columns (other columns
+ * read as zero in the cooperative path).  A grid barrier wait that does not
+ * end within about one second returns E_TIMEOUT (x is then undefined).
+ * Errors: E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT. */
 cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_t m,
                              const int64_t* col_off, const int64_t* row_off,
                              const int64_t* A_rowptr, const int32_t* A_col, const void* A_val,

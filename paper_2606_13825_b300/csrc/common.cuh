@@ -41,9 +41,22 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Same butterfly in the value's own type.  On this GPU an FP64 warp
+// instruction costs about 16 SM cycles (two FP64 lanes per clock per SM), so
+// per-row sums of float data stay in float.
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_allsum(double v) { return warp_sum(v); }
+
 // Block sum of NV doubles, broadcast to every thread; fixed summation order
-// (warp butterflies, then warps in index order), so results are bitwise
-// reproducible run to run.  `sm` needs NV * (blockDim.x / 32) doubles.
+// (warp butterflies, then a butterfly over the warps' values in warp 0), so
+// results are bitwise reproducible run to run.  Only warp 0 combines the
+// warps: with every thread re-adding all warp values, the FP64 adds of a
+// 1024-thread block cost microseconds on this GPU's narrow FP64 pipe.
+// `sm` needs NV * (blockDim.x / 32) doubles; blockDim.x <= 1024.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -55,12 +68,46 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
     for (int q = 0; q < NV; ++q) sm[q * nw + warp] = v[q];
   }
   __syncthreads();
+  if (warp == 0) {
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += sm[q * nw + w];
-    v[q] = t;
+    for (int q = 0; q < NV; ++q) {
+      const double t = warp_sum(lane < nw ? sm[q * nw + lane] : 0.0);
+      __syncwarp();
+      if (lane == 0) sm[q * nw] = t;
+    }
   }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = sm[q * nw];
+  __syncthreads();
+}
+
+// The same for per-thread partials held in the value type T: the warp
+// butterflies run in T (float adds on the full-rate pipe), only the
+// combination of the warps' values is in double.
+template <int NV, class T>
+__device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV], double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  T w[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) w[q] = warp_allsum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sm[q * nw + warp] = (double)w[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const double t = warp_sum(lane < nw ? sm[q * nw + lane] : 0.0);
+      __syncwarp();
+      if (lane == 0) sm[q * nw] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = sm[q * nw];
   __syncthreads();
 }
 

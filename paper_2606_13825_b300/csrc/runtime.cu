@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "kernels_psd.cuh"
 #include "kernels_tql.cuh"
+#include "kernels_gcg.cuh"
 #include "kernels_vec.cuh"
 
 using namespace cosmo;
@@ -1401,6 +1402,261 @@ static cosmo_status pcg_solve_t(int32_t ninst, int64_t n, int64_t m, const int64
   return COSMO_OK;
 }
 
+// Grid-wide CG (zero start) for large instances: column / row tiles of 64,
+// three kernels per iteration, convergence read back every 8 iterations (the
+// call synchronises the stream on this path).
+// k_gcg_persist<T, va, vat> for batch widths va, vat in {1, 2, 4} (null when
+// not instantiated)
+template <class T>
+static const void* persist_kernel(int va, int vat) {
+  auto pick = [&](auto a_tag) -> const void* {
+    constexpr int VA = decltype(a_tag)::value;
+    if (vat == 1) return (const void*)k_gcg_persist<T, VA, 1>;
+    if (vat == 2) return (const void*)k_gcg_persist<T, VA, 2>;
+    if constexpr (sizeof(T) == 4) {
+      if (vat == 4) return (const void*)k_gcg_persist<T, VA, 4>;
+    }
+    return nullptr;
+  };
+  if (va == 1) return pick(std::integral_constant<int, 1>{});
+  if (va == 2) return pick(std::integral_constant<int, 2>{});
+  if constexpr (sizeof(T) == 4) {
+    if (va == 4) return pick(std::integral_constant<int, 4>{});
+  }
+  return nullptr;
+}
+
+template <class T>
+static cosmo_status pcg_solve_grid_t(int32_t ninst, int64_t n, int64_t m, const int64_t* col_off_d,
+                                     const int64_t* row_off_d, const Prob<T, T>& P0, double sigma,
+                                     const void* rho, const void* rhs, void* x, double tol,
+                                     int32_t maxit, int32_t* iters, cudaStream_t st) {
+  std::vector<int64_t> co(ninst + 1), ro(ninst + 1), prp;
+  int64_t nnz_a = 0;
+  CU(cudaMemcpyAsync(co.data(), col_off_d, sizeof(int64_t) * (ninst + 1), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(ro.data(), row_off_d, sizeof(int64_t) * (ninst + 1), cudaMemcpyDeviceToHost, st));
+  if (P0.P_rp) {
+    prp.resize(n + 1);
+    CU(cudaMemcpyAsync(prp.data(), P0.P_rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+  }
+  if (m > 0) CU(cudaMemcpyAsync(&nnz_a, P0.A_rp + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  // P rows of at most 16 entries take one thread per row in the cols phase
+  int short_p = 1;
+  for (int64_t j = 0; j + 1 < (int64_t)prp.size() && short_p; ++j) short_p = prp[j + 1] - prp[j] <= 16;
+  const int64_t nnz_p = prp.empty() ? 0 : prp[n];
+  // batch width of the row routine from the mean row length; scalar loads
+  // when an array is not 16-byte aligned
+  auto aligned = [](const void* p, const void* q) {
+    return ((uintptr_t)p % 16 == 0) && ((uintptr_t)q % 16 == 0);
+  };
+  auto vq_for = [](int64_t nnz, int64_t rows) {
+    const int64_t mean = rows > 0 ? nnz / rows : 0;
+    return mean >= 384 ? 4 : mean >= 128 ? 2 : 1;
+  };
+  int64_t max_n = 0, max_m = 0;
+  for (int32_t i = 0; i < ninst; ++i) {
+    max_n = std::max(max_n, co[i + 1] - co[i]);
+    max_m = std::max(max_m, ro[i + 1] - ro[i]);
+  }
+  int dev = 0, nsm = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+  // Tiles of `mult`-aligned rows (columns) that never cross an instance;
+  // `count` tiles of an instance with `len` rows at tile size t.
+  auto tiles_at = [&](const std::vector<int64_t>& off, int64_t t) {
+    int64_t c = 0;
+    for (int32_t i = 0; i < ninst; ++i) c += (off[i + 1] - off[i] + t - 1) / t;
+    return c;
+  };
+  // Persistent path: one CTA per SM, at most nsm row tiles and nsm column
+  // tiles, the staged vectors in shared memory.
+  const size_t SMEM_CAP = 220 * 1024;
+  // (ends: with at most nsm instances, tiles as long as the longest instance
+  // give at most nsm tiles)
+  int64_t RT = std::max<int64_t>(32, ((m + nsm - 1) / nsm + 31) / 32 * 32);
+  int64_t CT = std::max<int64_t>(32, ((n + nsm - 1) / nsm + 31) / 32 * 32);
+  if (ninst <= nsm) {
+    while (tiles_at(ro, RT) > nsm) RT += 32;
+    while (tiles_at(co, CT) > nsm) CT += 32;
+  }
+  // Staging layout (T entries): R phase: a column segment of z (at most
+  // SEG_BYTES, so that about 124 KB of L1 stays free for the loads in flight)
+  // plus 2 x 16 bytes of alignment slack, then the row partial sums [RT];
+  // C phase: t over the instance's rows (+ slack), then the tile's P z [CT].
+  const int64_t E = 16 / (int64_t)sizeof(T);
+  const int64_t SEG_BYTES = 100 * 1024;
+  const int nseg = (int)std::max<int64_t>(1, (max_n * (int64_t)sizeof(T) + SEG_BYTES - 1) / SEG_BYTES);
+  const int64_t seg_stage = (max_n + nseg - 1) / nseg + 2 * E;
+  const int64_t sp_off = max_m + 2 * E;
+  const int64_t stage_len = std::max(seg_stage + RT, sp_off + CT);
+  const size_t persist_smem = ((size_t)stage_len * sizeof(T) + 7) / 8 * 8 + sizeof(GcgScal) * ninst;
+  // the persistent kernel is instantiated for batch widths (A, A') in
+  // {1, 2, 4}^2 (at most 2 for double values) and 16-byte aligned arrays
+  const bool all_aligned = aligned(P0.A_ci, P0.A_v) && aligned(P0.AT_ci, P0.AT_v) &&
+                           (!P0.P_rp || aligned(P0.P_ci, P0.P_v));
+  const int vmax = sizeof(T) == 4 ? 4 : 2;
+  // (the R phase streams each row one column segment at a time)
+  const int pva = std::min(vq_for(nnz_a / nseg, m), vmax), pvat = std::min(vq_for(nnz_a, n), vmax);
+  const void* pkern = persist_kernel<T>(pva, pvat);
+  bool persist = all_aligned && pkern && ninst <= nsm && persist_smem <= SMEM_CAP;
+  if (persist) {
+    CU(cudaFuncSetAttribute(pkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pkern, GCG_NT_SMEM, persist_smem));
+    persist = per_sm >= 1;
+  }
+  DevArena a;
+  int32_t* seg_off = nullptr;
+  if (persist && nseg > 1) {
+    // entries of each row before each segment boundary; needs sorted rows
+    int32_t* unsorted;
+    TRY(a.alloc(&seg_off, (int64_t)(nseg - 1) * std::max<int64_t>(m, 1)));
+    TRY(a.alloc(&unsorted, 1));
+    CU(cudaMemsetAsync(unsorted, 0, sizeof(int32_t), st));
+    if (m > 0) {
+      k_gcg_split<T><<<(int)((m * 32 + 255) / 256), 256, 0, st>>>(P0, nseg, seg_off, unsorted);
+      ++g_launches;
+    }
+    int32_t h_unsorted = 0;
+    CU(cudaMemcpyAsync(&h_unsorted, unsorted, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h_unsorted) persist = false;   // global gathers need no sorted rows
+  }
+  // Fallback: 256-thread CTAs gathering from global memory, tiles sized for
+  // about four resident CTAs per SM (a multiple of 8, at most 256).
+  auto tile_global = [&](int64_t total) {
+    int64_t t = (total + 4 * nsm - 1) / (4 * nsm);
+    t = (t + 7) / 8 * 8;
+    return std::min<int64_t>(std::max<int64_t>(t, 8), 256);
+  };
+  const int64_t RTILE = persist ? RT : tile_global(m), CTILE = persist ? CT : tile_global(n);
+
+  std::vector<int32_t> ct_inst, rt_inst, it_lo(ninst), it_hi(ninst), rt_first;
+  std::vector<int64_t> ct_lo, ct_hi, rt_lo, rt_hi;
+  for (int32_t i = 0; i < ninst; ++i) {
+    it_lo[i] = (int32_t)ct_inst.size();
+    for (int64_t c = co[i]; c < co[i + 1]; c += CTILE) {
+      ct_inst.push_back(i); ct_lo.push_back(c); ct_hi.push_back(std::min(co[i + 1], c + CTILE));
+    }
+    it_hi[i] = (int32_t)ct_inst.size();
+    // the global path needs a row tile per instance (possibly empty): it records the iteration count
+    bool first = true;
+    for (int64_t q = ro[i]; q < ro[i + 1] || (first && !persist); q += RTILE) {
+      rt_inst.push_back(i); rt_lo.push_back(q); rt_hi.push_back(std::min(ro[i + 1], q + RTILE));
+      rt_first.push_back(first ? 1 : 0);
+      first = false;
+      if (ro[i + 1] <= q) break;
+    }
+  }
+  if (ct_inst.empty()) return COSMO_OK;
+  GcgTiles G{};
+  int32_t *d_ct_inst, *d_it_lo, *d_it_hi, *d_rt_inst = nullptr, *d_rt_first = nullptr;
+  int64_t *d_ct_lo, *d_ct_hi, *d_rt_lo = nullptr, *d_rt_hi = nullptr;
+  TRY(a.upload(&d_ct_inst, ct_inst)); TRY(a.upload(&d_ct_lo, ct_lo)); TRY(a.upload(&d_ct_hi, ct_hi));
+  TRY(a.upload(&d_it_lo, it_lo)); TRY(a.upload(&d_it_hi, it_hi));
+  if (!rt_inst.empty()) {
+    TRY(a.upload(&d_rt_inst, rt_inst)); TRY(a.upload(&d_rt_lo, rt_lo)); TRY(a.upload(&d_rt_hi, rt_hi));
+    TRY(a.upload(&d_rt_first, rt_first));
+  }
+  G.nct = (int32_t)ct_inst.size(); G.ct_inst = d_ct_inst; G.ct_lo = d_ct_lo; G.ct_hi = d_ct_hi;
+  G.it_lo = d_it_lo; G.it_hi = d_it_hi;
+  G.nrt = (int32_t)rt_inst.size(); G.rt_inst = d_rt_inst; G.rt_lo = d_rt_lo; G.rt_hi = d_rt_hi;
+  G.rt_first = d_rt_first;
+  G.nnz_a = nnz_a; G.nnz_p = nnz_p;
+  G.vq_a = aligned(P0.A_ci, P0.A_v) ? vq_for(nnz_a, m) : 0;
+  G.vq_at = aligned(P0.AT_ci, P0.AT_v) ? vq_for(nnz_a, n) : 0;
+  G.vq_p = P0.P_rp && aligned(P0.P_ci, P0.P_v) ? vq_for(nnz_p, n) : 0;
+  Prob<T, T> P = P0;
+  T* dinv;
+  TRY(a.alloc(&dinv, n));
+  k_precond_csr<T, T><<<grid_for(n, 256), 256, 0, st>>>(P, sigma, (const T*)rho, dinv);
+  ++g_launches;
+
+  if (persist) {
+    GcgPersist<T> S{};
+    T *rr, *zz, *pp, *ss, *ww, *tt;
+    // z and t are staged in 16-byte groups: padded to whole groups past the end
+    TRY(a.alloc(&rr, n)); TRY(a.alloc(&zz, n + 2 * E)); TRY(a.alloc(&pp, n)); TRY(a.alloc(&ss, n));
+    TRY(a.alloc(&ww, n)); TRY(a.alloc(&tt, std::max<int64_t>(m, 1) + 2 * E));
+    CU(cudaMemsetAsync(zz, 0, sizeof(T) * (n + 2 * E), st));
+    CU(cudaMemsetAsync(tt, 0, sizeof(T) * (std::max<int64_t>(m, 1) + 2 * E), st));
+    double *pg, *prr, *pd, *pbb;
+    TRY(a.alloc(&pg, G.nct)); TRY(a.alloc(&prr, G.nct)); TRY(a.alloc(&pd, G.nct)); TRY(a.alloc(&pbb, G.nct));
+    unsigned* bar;
+    TRY(a.alloc(&bar, 4));   // arrive, generation, error word
+    CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
+    S.rhs = (const T*)rhs; S.x = (T*)x; S.rho = (const T*)rho; S.dinv = dinv; S.sigma = sigma;
+    S.r = rr; S.z = zz; S.p = pp; S.s = ss; S.w = ww; S.t = tt;
+    S.part_g = pg; S.part_rr = prr; S.part_d = pd; S.part_bb = pbb;
+    S.iters = iters; S.tol = tol; S.maxit = maxit; S.short_p = short_p; S.stage_len = stage_len;
+    S.nseg = nseg; S.seg_off = seg_off; S.sp_off = sp_off; S.ps_off = seg_stage;
+    GridBar B{bar, bar + 1, reinterpret_cast<int32_t*>(bar + 2), 2000000000LL};   // about 1 s at 2 GHz
+    const int grid = std::max(G.nct, G.nrt);
+    void* args[] = {(void*)&P, (void*)&G, (void*)&S, (void*)&B};
+    CU(cudaLaunchCooperativeKernel(pkern, dim3(grid), dim3(GCG_NT_SMEM), args, persist_smem, st));
+    ++g_launches;
+    int32_t herr = 0;
+    CU(cudaMemcpyAsync(&herr, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (herr) return fail(COSMO_E_TIMEOUT, "grid CG: a grid barrier wait gave up");
+    return COSMO_OK;
+  }
+
+  using T2 = typename Vec2<T>::type;
+  GcgState<T> S{};
+  T *rr, *uu, *tt;
+  T2* zp;
+  TRY(a.alloc(&rr, n)); TRY(a.alloc(&uu, n)); TRY(a.alloc(&zp, n));
+  TRY(a.alloc(&tt, std::max<int64_t>(m, 1)));
+  double *pa, *pb, *sc_rz, *sc_beta, *sc_alpha, *sc_bb;
+  int32_t *cnt_grp, *cnt_inst, *sc_state, *running;
+  TRY(a.alloc(&pa, G.nct)); TRY(a.alloc(&pb, G.nct));
+  TRY(a.alloc(&sc_rz, 2 * ninst)); TRY(a.alloc(&sc_beta, 2 * ninst)); TRY(a.alloc(&sc_state, 2 * ninst));
+  TRY(a.alloc(&sc_alpha, ninst)); TRY(a.alloc(&sc_bb, ninst));
+  TRY(a.alloc(&cnt_grp, G.nct)); TRY(a.alloc(&cnt_inst, ninst));
+  TRY(a.alloc(&running, maxit + 1));
+  CU(cudaMemsetAsync(cnt_grp, 0, sizeof(int32_t) * G.nct, st));
+  CU(cudaMemsetAsync(cnt_inst, 0, sizeof(int32_t) * ninst, st));
+  CU(cudaMemsetAsync(running, 0, sizeof(int32_t) * (maxit + 1), st));
+  S.rhs = (const T*)rhs; S.x = (T*)x; S.rho = (const T*)rho; S.dinv = dinv; S.sigma = sigma;
+  S.r = rr; S.zp = zp; S.u = uu; S.t = tt; S.part_a = pa; S.part_b = pb; S.cnt_grp = cnt_grp; S.cnt_inst = cnt_inst;
+  S.sc_rz = sc_rz; S.sc_beta = sc_beta; S.sc_state = sc_state; S.sc_alpha = sc_alpha; S.sc_bb = sc_bb;
+  S.iters = iters; S.running = running; S.tol = tol; S.maxit = maxit;
+  const size_t cols_smem_bytes = (size_t)CTILE * sizeof(T);
+  k_gcg_init<T><<<G.nct, GCG_NT, 0, st>>>(G, S);
+  ++g_launches;
+  int32_t* h_run = nullptr;
+  CU(cudaMallocHost(&h_run, sizeof(int32_t)));
+  cosmo_status status = COSMO_OK;
+  for (int it = 0; it <= maxit; ++it) {
+    k_gcg_rows<T><<<G.nrt, GCG_NT, 0, st>>>(P, G, S, it);
+    ++g_launches;
+    if (it == maxit) break;   // the rows kernel at maxit records the capped counts
+    k_gcg_cols<T><<<G.nct, GCG_NT, cols_smem_bytes, st>>>(P, G, S, it, short_p);
+    k_gcg_update<T><<<G.nct, GCG_NT, 0, st>>>(P, G, S, it);
+    g_launches += 2;
+    if ((it & 7) == 7) {
+      // instances still running at this iteration (counted by its rows kernel)
+      cudaMemcpyAsync(h_run, running + it, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { status = fail(COSMO_E_CUDA, "grid CG failed: %s", cudaGetErrorString(e)); break; }
+      if (*h_run == 0) {
+        k_gcg_rows<T><<<G.nrt, GCG_NT, 0, st>>>(P, G, S, it + 1);   // records iteration counts
+        ++g_launches;
+        break;
+      }
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess && status == COSMO_OK) status = fail(COSMO_E_CUDA, "grid CG launch failed: %s", cudaGetErrorString(e));
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess && status == COSMO_OK) status = fail(COSMO_E_CUDA, "grid CG failed: %s", cudaGetErrorString(e));
+  cudaFreeHost(h_run);
+  return status;
+}
+
 extern "C" {
 
 cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_t m,
@@ -1418,6 +1674,30 @@ cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_
       ((P_rowptr != nullptr) != (P_col != nullptr)) || ((P_rowptr != nullptr) != (P_val != nullptr)))
     return fail(COSMO_E_INVAL, "bad arguments to cosmo_pcg_solve");
   cudaStream_t st = (cudaStream_t)stream;
+  // large zero-start solves (few instances, more than 1e5 nonzeros of A per
+  // instance on average) take the grid-wide CG; the rest one CTA per instance
+  int64_t nnzA = 0;
+  if (m > 0) {
+    CU(cudaMemcpyAsync(&nnzA, A_rowptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  const bool grid = !warm_start && ninst < 148 && nnzA / ninst > 100000;
+  if (grid) {
+    if (precision == COSMO_PREC_FP64 || precision == COSMO_PREC_MIXED) {
+      auto make = [&](auto tag) {
+        using T = decltype(tag);
+        Prob<T, T> P{};
+        P.ninst = ninst; P.n_total = n; P.m_total = m; P.col_off = col_off; P.row_off = row_off;
+        P.A_rp = A_rowptr; P.A_ci = A_col; P.A_v = (const T*)A_val;
+        P.AT_rp = AT_rowptr; P.AT_ci = AT_col; P.AT_v = (const T*)AT_val;
+        P.P_rp = P_rowptr; P.P_ci = P_col; P.P_v = (const T*)P_val;
+        return pcg_solve_grid_t<T>(ninst, n, m, col_off, row_off, P, sigma, rho, rhs, x, tol,
+                                   max_iter, iters, st);
+      };
+      return precision == COSMO_PREC_FP64 ? make(double(0)) : make(float(0));
+    }
+    return fail(COSMO_E_INVAL, "unknown precision");
+  }
   if (precision == COSMO_PREC_FP64)
     return pcg_solve_t<double>(ninst, n, m, col_off, row_off, A_rowptr, A_col, A_val, AT_rowptr,
                                AT_col, AT_val, P_rowptr, P_col, P_val, sigma, rho, rhs, x,

@@ -306,13 +306,29 @@ def covsteer_problem(seed: int, nx=4, nu=2, T=20, w_var=0.01,
 
 
 # ------------------------------------------- App. B linear-system instances --
-def linsys_instance(n: int, seed: int, density=0.01):
+def _sprandn_rows(rows, cols, density, rng):
+    """Large sparse N(0,1) matrix: round(cols*density) column draws per row
+    (with replacement, duplicates dropped), for sizes where sampling cell
+    indices without replacement is too slow."""
+    k = max(1, int(round(cols * density)))
+    ci = np.sort(rng.integers(0, cols, size=(rows, k)), axis=1)
+    keep = np.ones_like(ci, dtype=bool)
+    keep[:, 1:] = ci[:, 1:] != ci[:, :-1]
+    counts = keep.sum(axis=1)
+    indptr = np.concatenate([[0], np.cumsum(counts)])
+    indices = ci[keep].astype(np.int32)
+    data = rng.standard_normal(indices.size)
+    return sp.csr_matrix((data, indices, indptr), shape=(rows, cols))
+
+
+def linsys_instance(n: int, seed: int, density=0.01, row_sampler=False):
     """App. B: P diagonal with U(0,10) entries; A (n/2 x n) with 1% N(0,1)
-    nonzeros; rho ~ U(0,1); b ~ N(0,1); target x* ~ N(0,1)."""
+    nonzeros; rho ~ U(0,1); b ~ N(0,1); target x* ~ N(0,1).  row_sampler
+    draws A row by row (large n)."""
     rng = np.random.default_rng(seed)
     m = n // 2
     Pd = rng.uniform(0.0, 10.0, size=n)
-    A = _sprandn(m, n, density, rng)
+    A = _sprandn_rows(m, n, density, rng) if row_sampler else _sprandn(m, n, density, rng)
     rho = rng.uniform(0.0, 1.0, size=m)
     b = rng.standard_normal(m)
     xstar = rng.standard_normal(n)

@@ -49,3 +49,85 @@ def test_pcg_solve_batched_vs_dense(precision):
     # warm start at the solution: converges immediately
     x2, it2 = pcg_solve(sysm, 1e-6, t(rho), t(rhs), x0=t(x), tol=max(tol, 1e-6), max_iter=2000)
     assert int(it2.max()) <= 3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_cg_large_instance(precision):
+    """A 1%-dense App. B instance large enough (n = 6000, ~1.8e5 nonzeros) to
+    take the grid-wide CG; against a dense FP64 solve."""
+    _need_gpu()
+    from paper_2606_13825_b300.solver import ReducedSystem, pcg_solve
+    d = linsys_instance(6000, seed=6006, density=0.01, row_sampler=True)
+    assert d["A"].nnz > 100000
+    sysm = ReducedSystem([(d["P"], d["A"])], precision)
+    dt = sysm.dtype
+    rho = d["rho"] + 0.05
+    rhs = np.random.default_rng(4).standard_normal(6000)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    x, iters = pcg_solve(sysm, 1e-6, t(rho), t(rhs), tol=tol, max_iter=3000)
+    x = x.double().cpu().numpy()
+    ref = _dense_solve(d["P"], d["A"], 1e-6, rho, rhs)
+    err = np.abs(x - ref).max() / np.abs(ref).max()
+    assert err < (1e-8 if precision == "fp64" else 2e-3), err
+    assert 0 < int(iters[0]) < 3000
+
+
+def _true_residual(blocks, sigma, rho, rhs, x):
+    """Per instance ||M x - rhs|| / ||rhs|| in FP64 (scipy), M = P + sigma I + A'D(rho)A."""
+    out, c, r = [], 0, 0
+    for P, A in blocks:
+        m, n = A.shape
+        xi = x[c:c + n]
+        Mx = P @ xi + sigma * xi + A.T @ (rho[r:r + m] * (A @ xi))
+        out.append(np.linalg.norm(Mx - rhs[c:c + n]) / np.linalg.norm(rhs[c:c + n]))
+        c, r = c + n, r + m
+    return np.array(out)
+
+
+def test_grid_cg_global_gather_fp64():
+    """n = 60000 in FP64: p^ (480 KB) and t (240 KB) exceed shared memory, so
+    both SpMV halves gather from global memory; checked by the true residual."""
+    _need_gpu()
+    from paper_2606_13825_b300.solver import ReducedSystem, pcg_solve
+    d = linsys_instance(60000, seed=6060, density=0.01, row_sampler=True)
+    blocks = [(d["P"], d["A"])]
+    sysm = ReducedSystem(blocks, "fp64")
+    rho = d["rho"] + 0.05
+    rhs = np.random.default_rng(6).standard_normal(60000)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    x, iters = pcg_solve(sysm, 1e-6, t(rho), t(rhs), tol=1e-10, max_iter=3000)
+    res = _true_residual(blocks, 1e-6, rho, rhs, x.cpu().numpy())
+    assert res.max() < 1e-9, res
+    assert 0 < int(iters[0]) < 3000
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_cg_several_instances(precision):
+    """Three App. B instances of different sizes in one grid solve (tiles of
+    several instances, per-instance scalars and stopping); true residual and
+    iteration count of each against a solve of that instance alone."""
+    _need_gpu()
+    from paper_2606_13825_b300.solver import ReducedSystem, pcg_solve
+    ds = [linsys_instance(n, seed=6200 + n, density=0.01, row_sampler=True) for n in (12000, 20000, 9000)]
+    blocks = [(d["P"], d["A"]) for d in ds]
+    sysm = ReducedSystem(blocks, precision)
+    dt = sysm.dtype
+    rng = np.random.default_rng(7)
+    rho = np.concatenate([d["rho"] + 0.05 for d in ds])
+    rhs = rng.standard_normal(sysm.n)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    x, iters = pcg_solve(sysm, 1e-6, t(rho), t(rhs), tol=tol, max_iter=3000)
+    res = _true_residual(blocks, 1e-6, rho, rhs, x.double().cpu().numpy())
+    assert res.max() < (1e-9 if precision == "fp64" else 5e-4), res
+    c = r = 0
+    for k, (P, A) in enumerate(blocks):
+        m, n = A.shape
+        one = ReducedSystem([(P, A)], precision)
+        x1, it1 = pcg_solve(one, 1e-6, t(rho[r:r + m]), t(rhs[c:c + n]), tol=tol, max_iter=3000)
+        if precision == "fp64":
+            assert abs(int(it1[0]) - int(iters[k])) <= 1, (k, it1, iters)
+        err = float((x1.double() - x[c:c + n].double()).abs().max() / x1.double().abs().max())
+        assert err < (1e-8 if precision == "fp64" else 1e-3), (k, err)
+        c, r = c + n, r + m
