@@ -44,6 +44,47 @@ def problems(rank=0):
     return [maxcut_problem(nv, e) for nv, e in graphs]
 
 
+# -------------------------------------------------------------- workloads --
+# Each workload: problems, unroll depth, batch options, whether the warm start
+# is learned, and a description.  "maxcut" is the headline metric; the others
+# are the paper's other problem classes at their stated sizes.
+def workload_spec(name, rank=0):
+    from synth import (lovasz_problem, random_graph_batch, cycle_graph, complete_graph,
+                       socp_problem, covsteer_problem)
+    if name == "maxcut":
+        return dict(probs=problems(rank), K=K_UNROLL, opts={}, value_type="f32", learn_start=False,
+                    metric=METRIC, desc=WORKLOAD)
+    if name == "lovasz":
+        graphs = random_graph_batch(64, 3000 + rank * 64, 100, 200, 0.5, 0.5)
+        probs = [lovasz_problem(nv, e) for nv, e in graphs]
+        # vertex-transitive graphs (coincident eigenvalues at the optimum)
+        for j in range(16):
+            nv = 100 + (j * 100) // 15
+            probs.append(lovasz_problem(nv, cycle_graph(nv) if j % 2 == 0 else complete_graph(nv)))
+        return dict(probs=probs, K=30, opts={"checkpoint_every": 5}, value_type="f32", learn_start=False,
+                    metric="unrolled fwd+bwd instance-iters/sec (Lovasz theta, batched mixed precision)",
+                    desc="Lovasz theta SDPs: 64 G(n,1/2) graphs n ~ U{100..200} (seeds 3000+j) + 16 "
+                         "vertex-transitive cycles/complete graphs n in [100,200]; K=30, checkpoint every 5; "
+                         "learnable log rho_k / alpha_k; loss ||r_p^K||^2+||r_d^K||^2")
+    if name == "socp":
+        probs = [socp_problem(4000 + rank * 64 + j) for j in range(64)]
+        # FP32 iterates reach a relative CG residual of about eps32 * kappa(M)
+        return dict(probs=probs, K=100, opts={"cg_tol": 1e-6}, value_type="bf16", learn_start=False,
+                    metric="unrolled fwd+bwd instance-iters/sec (sparse SOCP, batched mixed precision)",
+                    desc="random sparse SOCPs: 64 instances (seeds 4000+j), n=5000, A 8000x5000 density 1e-3, "
+                         "P=M'M+1e-3 I (M 500x5000 density 1e-3), 200 SOCs d ~ U{3..50} + orthant, planted "
+                         "solution; K=100; BF16 A values (P FP32), FP32 iterates, CG tol 1e-6; "
+                         "loss ||r_p^K||^2+||r_d^K||^2")
+    if name == "covsteer":
+        probs = [covsteer_problem(5000 + rank * 512 + j) for j in range(512)]
+        return dict(probs=probs, K=40, opts={"use_graph": 1}, value_type="f32", learn_start=True,
+                    metric="unrolled fwd+bwd instance-iters/sec (covariance steering, batched mixed precision)",
+                    desc="covariance-steering stand-in SDPs: 512 instances (seeds 5000+j), nx=4, nu=2, T=20, "
+                         "PSD blocks 20x p8 + 20x p6 + p4; K=40; learned warm start and log rho_k / alpha_k; "
+                         "one CUDA graph per forward / backward")
+    raise ValueError(name)
+
+
 # ----------------------------------------------------------------- clocks --
 class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -217,7 +258,8 @@ def psd_flops(probs):
     """Algorithmic flops of one PSD-projection launch: symmetric eigen-
     decomposition with vectors 9 p^3 (Golub & Van Loan's count for symmetric
     QR) plus the reconstruction U max(L,0) U' 2 p^3, summed over blocks."""
-    return float(sum(11.0 * p.meta["nv"] ** 3 for p in probs))
+    from synth.problem import PSD
+    return float(sum(11.0 * d ** 3 for p in probs for (ct, d) in p.cones if ct == PSD))
 
 
 def main():
@@ -230,8 +272,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--profile", action="store_true",
                     help="run only W steps of the workload (the command profiled under ncu)")
-    ap.add_argument("--workload", default="maxcut", choices=["maxcut", "linsys"],
-                    help="maxcut: the batched differentiable max-cut step (the metric); "
+    ap.add_argument("--workload", default="maxcut",
+                    choices=["maxcut", "lovasz", "socp", "covsteer", "linsys"],
+                    help="maxcut: the batched differentiable max-cut step (the headline metric); "
+                         "lovasz / socp / covsteer: the paper's other classes at their stated sizes; "
                          "linsys: the App. B reduced-system CG at n=5e4 (HBM roofline of SpMV/CG)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -253,17 +297,30 @@ def main():
     from paper_2606_13825_b300 import CosmoBatch, lib
     from paper_2606_13825_b300.solver import unrolled_residual_loss
 
-    probs = problems(rank)
-    K = K_UNROLL
-    b = CosmoBatch(probs, precision="mixed", device=local, use_graph=0)
+    spec = workload_spec(args.workload, rank)
+    probs, K = spec["probs"], spec["K"]
+    n_inst = len(probs)
+    opts = dict(spec["opts"])
+    use_graph = int(opts.pop("use_graph", 0))
+    b = CosmoBatch(probs, precision="mixed", value_type=spec["value_type"], device=local,
+                   use_graph=use_graph, **opts)
     lr = torch.full((K,), math.log(0.1), dtype=torch.float64, device=dev, requires_grad=True)
     ak = torch.full((K,), 1.6, dtype=torch.float64, device=dev, requires_grad=True)
+    starts = None
+    if spec["learn_start"]:
+        starts = [torch.zeros(nn, dtype=torch.float32, device=dev, requires_grad=True)
+                  for nn in (b.n_total, b.m_total, b.m_total)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    def step(batch=b):
         lr.grad = None
         ak.grad = None
-        L, _ = unrolled_residual_loss(b, lr, ak)
+        kw = {}
+        if starts:
+            for t_ in starts:
+                t_.grad = None
+            kw = dict(x0=starts[0], s0=starts[1], y0=starts[2])
+        L, _ = unrolled_residual_loss(batch, lr, ak, **kw)
         L.backward()
         return L
 
@@ -276,8 +333,11 @@ def main():
         return 0
 
     # ---------------- timed region: K steps, L2 flushed between steps -------
-    b.profile("psd_fwd")
-    b.profile_read("psd_fwd", reset=True)
+    has_psd = any(ct == 4 for p in probs for (ct, _) in p.cones)
+    dom = "psd_fwd" if has_psd else "pcg"          # dominant kernel class
+    if not use_graph:
+        b.profile(dom)
+        b.profile_read(dom, reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -303,14 +363,18 @@ def main():
     t_wall = time.perf_counter() - t_wall
     launches = lib().cosmo_kernel_launch_count() - n0
     clk = clocks.stop()
-    psd_ms, psd_n = b.profile_read("psd_fwd", reset=True)
-    b.profile(enable=False)
+    # the roofline kernel is timed live in the timed region (direct launches);
+    # graph-launched workloads time it in a separate direct-launch batch below
+    dom_ms, dom_n = (0.0, 0)
+    if not use_graph:
+        dom_ms, dom_n = b.profile_read(dom, reset=True)
+        b.profile(enable=False)
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t)
     ms_per_step = total_ms / args.steps
-    value = world * N_INST * K * args.steps / (total_ms / 1e3)
+    value = world * n_inst * K * args.steps / (total_ms / 1e3)
 
     if rank != 0:
         if dist:
@@ -323,29 +387,60 @@ def main():
             "adjoint_cg_iters_per_solve": inf["adj_cg_iters"] / max(inf["adj_cg_solves"], 1)}
 
     # ---------------- per-kernel breakdown (one extra step, all classes) ----
-    b.profile(None)
-    b.profile_read(None, reset=True)
-    step()
+    bb = b
+    if use_graph:
+        bb = CosmoBatch(probs, precision="mixed", value_type=spec["value_type"], device=local,
+                        use_graph=0, **opts)
+        step(bb)
+        torch.cuda.synchronize()
+    bb.profile(None)
+    bb.profile_read(None, reset=True)
+    step(bb)
     torch.cuda.synchronize()
     breakdown = {}
-    for kname in b.KERNEL_CLASSES:
-        ms, n = b.profile_read(kname, reset=False)
+    for kname in bb.KERNEL_CLASSES:
+        ms, n = bb.profile_read(kname, reset=False)
         if n:
             breakdown[kname] = round(ms, 4)
-    b.profile(enable=False)
+    if use_graph:
+        dom_ms, dom_n = bb.profile_read(dom, reset=False)
+    bb.profile(enable=False)
 
     # ---------------- roofline of the dominant kernel ------------------------
-    flops = psd_flops(probs)
-    avg_s = psd_ms / max(psd_n, 1) / 1e3
-    achieved = flops / avg_s / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = None
-    roof = {"kernel": "psd_fwd (cyclic Jacobi eigensolver + reconstruction, CTA per block)",
-            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop/FMA x 2032 MHz",
-            "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches_timed": psd_n,
-            "algorithmic_count": "sum over blocks of 9p^3 (eigh) + 2p^3 (reconstruction)"}
+    avg_s = dom_ms / max(dom_n, 1) / 1e3
+    if has_psd:
+        flops = psd_flops(probs)
+        achieved = flops / avg_s / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"kernel": "psd_fwd (cyclic Jacobi eigensolver + reconstruction, CTA per block)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop/FMA x 2032 MHz",
+                "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches_timed": dom_n,
+                "algorithmic_count": "sum over blocks of 9p^3 (eigh) + 2p^3 (reconstruction)"}
+    else:
+        # CG: every iteration streams A, A' and P once (value + column index)
+        # plus ~8 n-vectors of 4 bytes; iterations counted on the device
+        vb = 2 if spec["value_type"] == "bf16" else 4
+        nnzA = sum(p.A.nnz for p in probs)
+        nnzP = sum(p.P.nnz for p in probs)
+        inf0 = bb.info()
+        it_per_solve = inf0["cg_iters"] / max(inf0["cg_solves"], 1)
+        bytes_per_it = (2 * nnzA + nnzP) * (vb + 4) + 8 * 4 * sum(p.A.shape[1] for p in probs)
+        bytes_launch = bytes_per_it * it_per_solve
+        peak = 6478.6
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peak = float(json.load(f).get("hbm_gbs", peak))
+        except Exception:
+            pass
+        achieved = bytes_launch / avg_s / 1e9
+        roof = {"kernel": "pcg (Jacobi-PCG, CTA per instance, matrix-free SpMV with A, A', P)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3, "launches_timed": dom_n,
+                "algorithmic_count": "per CG iteration (2 nnz(A) + nnz(P)) x (value + int32 index) "
+                                     "+ 8 n x 4 bytes, times the mean CG iterations per solve"}
 
     # ---------------- end to end through host buffers ------------------------
     lr_h = torch.full((K,), math.log(0.1), dtype=torch.float64).pin_memory().numpy()
@@ -360,19 +455,19 @@ def main():
         t1 = time.perf_counter()
         b.step_host(K, lr_h, ak_h)        # synchronises before returning
         total_e2e += time.perf_counter() - t1
-    e2e_value = N_INST * K * args.steps / total_e2e
+    e2e_value = n_inst * K * args.steps / total_e2e
     e2e = {"value": e2e_value, "unit": "instance-iters/s", "h2d_bytes_per_step": 2 * K * 8,
-           "d2h_bytes_per_step": (N_INST + 2 * K) * 8,
+           "d2h_bytes_per_step": (n_inst + 2 * K) * 8,
            "api": "cosmo_step_host (host log_rho_k, alpha_k in; loss and gradients out; pinned)"}
 
     # ---------------- plain FP64 one-instance-per-launch GPU form ------------
     plain = None
     if not args.no_plain:
         rng = np.random.default_rng(1)
-        sample = rng.choice(N_INST, size=8, replace=False)
+        sample = rng.choice(n_inst, size=min(8, n_inst) if args.workload == "maxcut" else 2, replace=False)
         tot, iters = 0.0, 0
         for i in sample:
-            b1 = CosmoBatch([probs[i]], precision="fp64", device=local, use_graph=0)
+            b1 = CosmoBatch([probs[i]], precision="fp64", device=local, use_graph=0, **opts)
             l1 = torch.full((K,), math.log(0.1), dtype=torch.float64, device=dev, requires_grad=True)
             a1 = torch.full((K,), 1.6, dtype=torch.float64, device=dev, requires_grad=True)
             L, _ = unrolled_residual_loss(b1, l1, a1)
@@ -389,22 +484,23 @@ def main():
             iters += K
             del b1
         plain = {"value": iters / tot, "unit": "instance-iters/s",
-                 "sample": f"8 instances (seeded choice, n={sorted(int(probs[i].meta['nv']) for i in sample)}), "
-                           "each its own FP64 batch, direct launches, K=50 fwd+bwd"}
+                 "sample": f"{len(sample)} instances (seeded choice, n={sorted(int(probs[i].A.shape[1]) for i in sample)}), "
+                           f"each its own FP64 batch, direct launches, K={K} fwd+bwd"}
 
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and args.workload == "maxcut":
         cpu = cpu_oracle_sample(4, K, min(4, os.cpu_count() or 1))
 
-    line = {"metric": METRIC, "value": value, "unit": "instance-iters/s", "n_gpus": world,
+    line = {"metric": spec["metric"], "value": value, "unit": "instance-iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "instances_per_gpu": N_INST, "K": K,
+            "config": {"workload": spec["desc"], "instances_per_gpu": n_inst, "K": K,
                        "precision": "float iterates, double CG/residual/eigen-gap reductions",
                        "l2": "flushed between steps (256 MB write, outside the events)",
-                       "launch": "direct launches on the current stream (CUDA graphs are the library "
-                                 "default; off here so per-kernel CUDA events can be recorded)",
+                       "launch": ("one CUDA graph per forward / backward" if use_graph else
+                                  "direct launches on the current stream (CUDA graphs are the library "
+                                  "default; off here so per-kernel CUDA events can be recorded)"),
                        "parallelism": f"dp{world} (independent instances per GPU, no collective)"},
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
             "cpu_baseline": cpu, "plain_fp64": plain,

@@ -124,7 +124,10 @@ typedef struct {
 
 typedef struct {
   int32_t precision;        /* COSMO_PREC_MIXED or COSMO_PREC_FP64 */
-  int32_t value_type;       /* COSMO_VAL_F32 / COSMO_VAL_BF16 (MIXED only) */
+  int32_t value_type;       /* COSMO_VAL_F32 / COSMO_VAL_BF16 (MIXED only): storage of A
+                               and A'.  P is stored in the iterate type: entrywise BF16
+                               rounding of P = M'M + reg I perturbs it by more than its
+                               smallest eigenvalue and can make the QP nonconvex. */
   double cg_tol;            /* stop when ||r|| <= cg_tol * ||rhs|| (App. D: 1e-8) */
   int32_t cg_max_iter;      /* CG cap per solve; flag COSMO_FLAG_*CG_CAP */
   int32_t checkpoint_every; /* 0: keep the whole tape; c > 0: keep states every

@@ -124,7 +124,9 @@ struct Prob {
   const uint8_t* row_kind;  // [m_total] cone type of each row
   const int64_t* A_rp; const int32_t* A_ci; const V* A_v;     // m_total rows
   const int64_t* AT_rp; const int32_t* AT_ci; const V* AT_v;  // n_total rows
-  const int64_t* P_rp; const int32_t* P_ci; const V* P_v;     // n_total rows or null
+  // P keeps the iterate type: a BF16-rounded P = M'M + reg I can lose
+  // positive semidefiniteness (rounding error above its smallest eigenvalue)
+  const int64_t* P_rp; const int32_t* P_ci; const T* P_v;     // n_total rows or null
   const T* Pdiag;   // [n_total]
   const T* q;       // [n_total]
   const T* b;       // [m_total]

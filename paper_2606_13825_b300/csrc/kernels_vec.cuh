@@ -128,40 +128,51 @@ struct CgArgs {
 };
 
 // out[row] = f(row, sum_e val[e] x[ci[e]]) for rows [r0, r1) of a CSR matrix,
-// CTA-wide, four rows per thread in flight: the row pointers of all four rows
-// are loaded first, then the gathers of their entries are interleaved, so the
-// dependent loads (row pointer -> column index -> x) of different rows overlap.
+// CTA-wide, one thread per row, two rows per thread in flight.  Each row is
+// read in chunks of 8 entries: the column indices and values of a chunk of
+// both rows are loaded first, then all their gathers, so a short row costs
+// two dependent round trips instead of two per entry.  The sum runs along the
+// row in entry order.
 template <class T, class V, class F>
 __device__ __forceinline__ void cta_csr_rows(const int64_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci,
                                              const V* __restrict__ val, const T* __restrict__ x,
                                              int64_t r0, int64_t r1, F f) {
+  constexpr int U = 8;
   const int64_t step = blockDim.x;
-  for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 4 * step) {
-    int64_t e[4], eend[4];
-    T acc[4];
+  for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 2 * step) {
+    int64_t e[2], eend[2];
+    T acc[2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const int64_t r = rb + u * step;
       const bool ok = r < r1;
       e[u] = ok ? rp[r] : 0;
       eend[u] = ok ? rp[r + 1] : 0;
       acc[u] = T(0);
     }
-    bool any = true;
-    while (any) {
-      any = false;
+    while (e[0] < eend[0] || e[1] < eend[1]) {
+      int32_t c[2][U];
+      T v[2][U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (e[u] < eend[u]) {
-          acc[u] += (T)ldv(val, e[u]) * x[ci[e[u]]];
-          ++e[u];
-          any = any || e[u] < eend[u];
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t idx = e[u] + k;
+          const bool ok = idx < eend[u];
+          c[u][k] = ok ? ci[idx] : -1;
+          v[u][k] = ok ? (T)ldv(val, idx) : T(0);
         }
-      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+          if (c[u][k] >= 0) acc[u] += v[u][k] * x[c[u][k]];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) e[u] = min(e[u] + U, eend[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const int64_t r = rb + u * step;
       if (r < r1) f(r, acc[u]);
     }
@@ -181,7 +192,7 @@ __device__ __forceinline__ void cta_matvec(const Prob<T, V>& P, const CgArgs<T>&
   const T sig = (T)a.sigma;
   if (P.P_rp) {
     // u = sigma v + P v, then u += A' t
-    cta_csr_rows<T, V>(P.P_rp, P.P_ci, P.P_v, v, c0, c1,
+    cta_csr_rows<T, T>(P.P_rp, P.P_ci, P.P_v, v, c0, c1,
                        [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
     cta_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
                        [&](int64_t j, T acc) { u[j] += acc; });

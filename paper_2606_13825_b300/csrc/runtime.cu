@@ -206,6 +206,7 @@ struct HostPlan {
   std::vector<int32_t> inst_sched;
   std::vector<uint8_t> diag_inst;
   std::vector<int32_t> cg_sched;
+  int32_t cg_nt = 256;      // threads of a CG CTA (one CTA per instance)
   int64_t sum_p = 0, sum_p2 = 0;
   int32_t max_p = 0;
 };
@@ -317,8 +318,15 @@ static void build_plan(const cosmo_problem* pr, HostPlan& h) {
           if (h.P_ci[e] != j && h.P_v[e] != 0.0) { d = false; break; }
     h.diag_inst[i] = d ? 1 : 0;
   }
+  int64_t cg_max = 0;
   for (int32_t i : h.inst_sched)
-    if (!h.diag_inst[i]) h.cg_sched.push_back(i);
+    if (!h.diag_inst[i]) {
+      h.cg_sched.push_back(i);
+      cg_max = std::max(cg_max, (h.row_off[i + 1] - h.row_off[i]) + (h.col_off[i + 1] - h.col_off[i]));
+    }
+  // large instances take 512-thread CG CTAs (more rows in flight per SpMV);
+  // many small ones 256 (two CTAs resident per SM)
+  h.cg_nt = cg_max >= 8192 ? 512 : 256;
 }
 
 // ------------------------------------------------------- implementation ---
@@ -450,8 +458,8 @@ struct ImplT : Impl {
     int32_t *row_inst, *col_inst, *A_ci, *AT_ci, *P_ci = nullptr, *soc_dim, *psd_p, *psd_sched,
         *rect_rows, *inst_sched;
     uint8_t* row_kind;
-    V *A_v, *AT_v, *P_v = nullptr;
-    T *Pdiag, *q, *b, *bl = nullptr, *bu = nullptr;
+    V *A_v, *AT_v;
+    T *P_v = nullptr, *Pdiag, *q, *b, *bl = nullptr, *bu = nullptr;
     TRY(arena.upload(&col_off, h.col_off));
     TRY(arena.upload(&row_off, h.row_off));
     TRY(arena.upload(&row_inst, h.row_inst));
@@ -466,7 +474,7 @@ struct ImplT : Impl {
     if (h.has_P) {
       TRY(arena.upload(&P_rp, h.P_rp));
       TRY(arena.upload(&P_ci, h.P_ci));
-      TRY(arena.upload(&P_v, convV(h.P_v)));
+      TRY(arena.upload(&P_v, conv<T>(h.P_v)));
     }
     TRY(arena.upload(&Pdiag, conv<T>(h.Pdiag)));
     TRY(arena.upload(&q, conv<T>(h.q)));
@@ -718,7 +726,10 @@ struct ImplT : Impl {
     ca.sigma = sig; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = opt.cg_tol;
     ca.maxit = opt.cg_max_iter; ca.zero_start = xt_warm ? 0 : 1; ca.flag_bit = F_CG_CAP;
     ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 2;
-    if (P.n_cg) launch("pcg", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+    if (P.n_cg) {
+      if (h.cg_nt == 512) launch("pcg", k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
+      else launch("pcg", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+    }
     StepPtrs<T> sp{};
     sp.x = st_x(slot); sp.s = st_s(slot); sp.y = st_y(slot);
     sp.xn = st_x(slot + 1); sp.sn = st_s(slot + 1); sp.yn = st_y(slot + 1);
@@ -830,7 +841,10 @@ struct ImplT : Impl {
     ca.dinv = dinv + (int64_t)k * h.n; ca.sigma = q.sigma; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u;
     ca.t = cg_t; ca.tol = opt.cg_tol; ca.maxit = opt.cg_max_iter; ca.zero_start = 1;
     ca.flag_bit = F_ADJ_CG_CAP; ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 4;
-    if (P.n_cg) launch("pcg_adj", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+    if (P.n_cg) {
+      if (h.cg_nt == 512) launch("pcg_adj", k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
+      else launch("pcg_adj", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+    }
     launch("bwd_solve", k_bwd_solve<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, q);
   }
 

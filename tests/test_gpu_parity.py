@@ -109,15 +109,15 @@ def test_socp_batch(precision, value_type):
 
 
 def test_socp_bf16_values_vs_rounded_oracle():
-    """BF16 storage of P and A: parity against the oracle run on the same
-    bf16-rounded matrices (the rounding is the input, not an error)."""
+    """BF16 storage of A: parity against the oracle run on the same
+    bf16-rounded A (the rounding is the input, not an error).  P stays in the
+    iterate type (its BF16 rounding can be indefinite)."""
     _need_gpu()
     import scipy.sparse as sp
     probs = socp_batch(2, seed=4200)
     rnd = lambda M: sp.csr_matrix((torch.tensor(M.data).to(torch.bfloat16).double().numpy(), M.indices, M.indptr), shape=M.shape)
     for p in probs:
         p.A = rnd(p.A)
-        p.P = rnd(p.P)
     K = 3
     rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=10)
     ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
