@@ -88,7 +88,8 @@ enum {
   COSMO_FLAG_ADJ_CG_CAP = 2,    /* adjoint CG hit cg_max_iter */
   COSMO_FLAG_EIG_CAP = 4,       /* eigensolver hit its sweep/iteration cap */
   COSMO_FLAG_NONFINITE = 8,     /* non-finite iterate or cotangent */
-  COSMO_FLAG_BAD_PARAM = 16     /* rho <= 0, non-finite, or alpha outside (0, 2) */
+  COSMO_FLAG_BAD_PARAM = 16,    /* rho <= 0, non-finite, or alpha outside (0, 2) */
+  COSMO_FLAG_TIMEOUT = 32       /* a bounded device wait gave up (tensor-core DK backward) */
 };
 
 /* One cone: type and dimension.  For PSD, dim = p and the cone occupies
@@ -146,6 +147,8 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal the batch lives on */
   int32_t eig_warm_start;   /* 1: start step k's Jacobi from step k-1's eigenvectors
                                (re-orthogonalised by one Newton-Schulz step) */
+  int32_t dk_tensor_cores;  /* 1: MIXED-precision DK backward of blocks of order <= 80 on
+                               the tensor cores (tcgen05, split-TF32 products); 0: CUDA cores */
 } cosmo_options;
 
 typedef struct {
@@ -178,7 +181,8 @@ const char* cosmo_last_error(void);
 /* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
  * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
- * use_graph 1; device 0; eig_warm_start 1.  Returns COSMO_E_INVAL for an unknown precision. */
+ * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1.  Returns COSMO_E_INVAL for an
+ * unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 
 /* Validate a problem on the host without touching the device (CSR bounds and

@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NOTCONV"
                 5: "E_NONFINITE", 6: "E_TIMEOUT", 7: "E_STATE", 8: "E_NODEVICE"}
 PREC_MIXED, PREC_FP64 = 0, 1
 VAL_F32, VAL_BF16 = 0, 1
-FLAG_CG_CAP, FLAG_ADJ_CG_CAP, FLAG_EIG_CAP, FLAG_NONFINITE, FLAG_BAD_PARAM = 1, 2, 4, 8, 16
+FLAG_CG_CAP, FLAG_ADJ_CG_CAP, FLAG_EIG_CAP, FLAG_NONFINITE, FLAG_BAD_PARAM, FLAG_TIMEOUT = 1, 2, 4, 8, 16, 32
 
 
 class CosmoError(RuntimeError):
@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("cg_max_iter", c_int32), ("checkpoint_every", c_int32),
                 ("dk_gap_tau", c_double), ("eig_jacobi_max_p", c_int32),
                 ("eig_max_sweeps", c_int32), ("eig_tol", c_double), ("use_graph", c_int32),
-                ("device", c_int32), ("eig_warm_start", c_int32)]
+                ("device", c_int32), ("eig_warm_start", c_int32), ("dk_tensor_cores", c_int32)]
 
 
 class BatchInfo(ctypes.Structure):

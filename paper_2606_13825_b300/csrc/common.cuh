@@ -14,7 +14,7 @@ enum : uint8_t { K_ZERO = 0, K_NONNEG = 1, K_BOX = 2, K_SOC = 3, K_PSD = 4 };
 
 // per-instance flag bits, identical to the C ABI
 enum : int32_t {
-  F_CG_CAP = 1, F_ADJ_CG_CAP = 2, F_EIG_CAP = 4, F_NONFINITE = 8, F_BAD_PARAM = 16
+  F_CG_CAP = 1, F_ADJ_CG_CAP = 2, F_EIG_CAP = 4, F_NONFINITE = 8, F_BAD_PARAM = 16, F_TIMEOUT = 32
 };
 
 __device__ __forceinline__ float ldv(const float* p, int64_t i) { return __ldg(p + i); }

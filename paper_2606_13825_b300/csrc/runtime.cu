@@ -23,6 +23,7 @@
 #include "kernels_psd.cuh"
 #include "kernels_tql.cuh"
 #include "kernels_gcg.cuh"
+#include "kernels_tc.cuh"
 #include "kernels_vec.cuh"
 
 using namespace cosmo;
@@ -579,6 +580,9 @@ struct ImplT : Impl {
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      if constexpr (std::is_same<T, float>::value)
+        CU(cudaFuncSetAttribute(k_psd_bwd_tc<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dk_tc_smem(DK_TC_MAXP)));
     }
     return COSMO_OK;
   }
@@ -825,6 +829,13 @@ struct ImplT : Impl {
           k_psd_bwd_global<T, V, 256><<<bk.count, 256, 0, s>>>(P, io, q.lam, q.U, dk_work,
                                                                opt.dk_gap_tau, bk.start);
           return;
+        }
+        if constexpr (std::is_same<T, float>::value) {
+          if (opt.dk_tensor_cores && bk.maxp <= DK_TC_MAXP) {
+            k_psd_bwd_tc<V><<<bk.count, DK_TC_NT, dk_tc_smem(bk.maxp), s>>>(P, io, q.lam, q.U, opt.dk_gap_tau,
+                                                                            bk.start, flags);
+            return;
+          }
         }
         const size_t sm = psd_bwd_smem<T>(bk.maxp, bk.nt);
         if (bk.nt == 512)
@@ -1088,6 +1099,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->use_graph = 1;
   o->device = 0;
   o->eig_warm_start = 1;
+  o->dk_tensor_cores = 1;
   return COSMO_OK;
 }
 
@@ -1368,6 +1380,25 @@ static cosmo_status psd_dk_t(int32_t nblk, const int32_t* p_h, const int64_t* of
   int64_t *doff, *dloff, *duoff;
   TRY(a.upload(&dp, p)); TRY(a.upload(&doff, off)); TRY(a.upload(&dloff, loff)); TRY(a.upload(&duoff, uoff));
   PsdBatch<T> B{nblk, dp, doff, dloff, duoff};
+  if constexpr (std::is_same<T, float>::value) {
+    if (maxp <= DK_TC_MAXP) {
+      // tensor-core path (the default of the batched backward for these orders)
+      int32_t* err;
+      TRY(a.alloc(&err, 1));
+      CU(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+      const size_t tsm = dk_tc_smem(maxp);
+      CU(cudaFuncSetAttribute(k_psd_dk_batch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+      k_psd_dk_batch_tc<<<nblk, DK_TC_NT, tsm, st>>>(B, (const float*)lam, (const float*)U, (const float*)g,
+                                                     (float*)out, tau, err);
+      CU(cudaGetLastError());
+      g_launches += 1;
+      int32_t herr = 0;
+      CU(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      if (herr) return fail(COSMO_E_TIMEOUT, "tensor-core DK backward: a bounded wait gave up");
+      return COSMO_OK;
+    }
+  }
   k_psd_dk_batch<T, 256><<<nblk, 256, smem, st>>>(B, (const T*)lam, (const T*)U, (const T*)g, (T*)out, tau);
   CU(cudaGetLastError());
   g_launches += 1;
