@@ -7,7 +7,7 @@
 // (pn = p rounded up to 16):
 //   1  W  = U' G
 //   2  G' = (W U) o Gamma        (Gamma applied while reading the accumulator)
-//   3  Y  = U G'
+//   3  Y  = U G''                 (G' is symmetric up to rounding)
 //   4  S_bar = Y U'               (upper triangle written as svec)
 // Every product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi with each FP32
 // operand split into two TF32 parts (x = hi + lo, hi = tf32(x),
@@ -134,12 +134,6 @@ __device__ __forceinline__ int dk_tc_at(int r, int c, int sbo) {
   return (r >> 3) * sbo + (c >> 2) * 32 + (r & 7) * 4 + (c & 3);
 }
 
-__device__ __forceinline__ void dk_tc_put(float* hi, float* lo, int idx, float x) {
-  const float h = tc::tf32(x);
-  hi[idx] = h;
-  lo[idx] = tc::tf32(x - h);
-}
-
 // Loewner weight of max(x, 0) for FP32 eigenvalues: same-sign pairs need no
 // division (1 for two positive, 0 for two non-positive, 1/2 for two exact
 // zeros); mixed-sign pairs take the FP64 gap test and divided difference.
@@ -179,8 +173,8 @@ __device__ __forceinline__ bool dk_tc_gemm(uint32_t taddr, const float* Ah, cons
   return ok;
 }
 
-// f(row, col, value) over the accumulator rows < pn and columns < pn: warp w
-// reads lanes 32 (w % 4) .. + 31 and the column half w / 4
+// f(row, col0, v[8]) for 8 consecutive accumulator columns col0.. of a row
+// < pn: warp w reads lanes 32 (w % 4) .. + 31 and the column half w / 4
 template <class F>
 __device__ __forceinline__ void dk_tc_epilogue(uint32_t taddr, int pn, F f) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -189,10 +183,22 @@ __device__ __forceinline__ void dk_tc_epilogue(uint32_t taddr, int pn, F f) {
   for (int c = c0; c < c0 + pn / 2; c += 8) {
     float v[8];
     tc::ld8(taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)c, v);
-    if (row < pn) {
+    if (row < pn) f(row, c, v);
+  }
+}
+
+// 8 consecutive values of row r from column c (a multiple of 8) as two
+// 16-byte stores per part (each 4 columns are one core-matrix row)
+__device__ __forceinline__ void dk_tc_put8(float* hi, float* lo, int r, int c, int sbo, const float (&v)[8]) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) f(row, c + j, v[j]);
-    }
+  for (int h = 0; h < 2; ++h) {
+    float4 a, b;
+    a.x = tc::tf32(v[4 * h]); a.y = tc::tf32(v[4 * h + 1]); a.z = tc::tf32(v[4 * h + 2]); a.w = tc::tf32(v[4 * h + 3]);
+    b.x = tc::tf32(v[4 * h] - a.x); b.y = tc::tf32(v[4 * h + 1] - a.y);
+    b.z = tc::tf32(v[4 * h + 2] - a.z); b.w = tc::tf32(v[4 * h + 3] - a.w);
+    const int idx = dk_tc_at(r, c + 4 * h, sbo);
+    *reinterpret_cast<float4*>(hi + idx) = a;
+    *reinterpret_cast<float4*>(lo + idx) = b;
   }
 }
 
@@ -216,19 +222,41 @@ __device__ bool dk_tc_block(int p, const float* __restrict__ U, const float* __r
   const uint32_t ncols = pn <= 32 ? 32u : (pn <= 64 ? 64u : 128u);
   if (warp == 0) tc::alloc(tslot, ncols);
   if (tid == 0) tc::mbar_init(mbar, 1);
-  for (int e = tid; e < pn * pn; e += DK_TC_NT) {
-    const int r = e / pn, c = e % pn;
-    const bool in = r < p && c < p;
-    const int idx = dk_tc_at(r, c, sbo);
-    dk_tc_put(Uth, Utl, idx, in ? U[r * p + c] : 0.f);          // U'(r, c) = U(c, r)
-    dk_tc_put(Urh, Url, idx, in ? U[c * p + r] : 0.f);          // U(r, c)
-    float gv = 0.f;
-    if (in) {
-      const int i = min(r, c), j = max(r, c);
-      gv = g[j * (j + 1) / 2 + i];
-      if (i != j) gv *= (float)kInvSqrt2;
+  // staging in destination order: thread f writes the 16-byte core-matrix
+  // row (r, c..c+3), consecutive threads consecutive rows of a core matrix
+  // (no bank conflicts); U is read from L2 with strided scalar loads
+  const int q4 = pn / 4;
+  for (int f = tid; f < pn * q4; f += DK_TC_NT) {
+    const int r = ((f >> 3) / q4) * 8 + (f & 7), c = ((f >> 3) % q4) * 4;
+    float ut[4], ur[4], gv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = c + j;
+      const bool in = r < p && cc < p;
+      ut[j] = in ? U[r * p + cc] : 0.f;          // U'(r, cc) = U(cc, r)
+      ur[j] = in ? U[cc * p + r] : 0.f;          // U(r, cc)
+      float g0 = 0.f;
+      if (in) {
+        const int i = min(r, cc), jj = max(r, cc);
+        g0 = g[jj * (jj + 1) / 2 + i];
+        if (i != jj) g0 *= (float)kInvSqrt2;
+      }
+      gv[j] = g0;                                // G (symmetric)
     }
-    dk_tc_put(Xh, Xl, idx, gv);                                // G (symmetric)
+    const int idx = dk_tc_at(r, c, sbo);
+    float4 h, l;
+    h = make_float4(tc::tf32(ut[0]), tc::tf32(ut[1]), tc::tf32(ut[2]), tc::tf32(ut[3]));
+    l = make_float4(tc::tf32(ut[0] - h.x), tc::tf32(ut[1] - h.y), tc::tf32(ut[2] - h.z), tc::tf32(ut[3] - h.w));
+    *reinterpret_cast<float4*>(Uth + idx) = h;
+    *reinterpret_cast<float4*>(Utl + idx) = l;
+    h = make_float4(tc::tf32(ur[0]), tc::tf32(ur[1]), tc::tf32(ur[2]), tc::tf32(ur[3]));
+    l = make_float4(tc::tf32(ur[0] - h.x), tc::tf32(ur[1] - h.y), tc::tf32(ur[2] - h.z), tc::tf32(ur[3] - h.w));
+    *reinterpret_cast<float4*>(Urh + idx) = h;
+    *reinterpret_cast<float4*>(Url + idx) = l;
+    h = make_float4(tc::tf32(gv[0]), tc::tf32(gv[1]), tc::tf32(gv[2]), tc::tf32(gv[3]));
+    l = make_float4(tc::tf32(gv[0] - h.x), tc::tf32(gv[1] - h.y), tc::tf32(gv[2] - h.z), tc::tf32(gv[3] - h.w));
+    *reinterpret_cast<float4*>(Xh + idx) = h;
+    *reinterpret_cast<float4*>(Xl + idx) = l;
   }
   for (int k = tid; k < p; k += DK_TC_NT) lamf[k] = lam[k];
   __syncthreads();
@@ -245,22 +273,31 @@ __device__ bool dk_tc_block(int p, const float* __restrict__ U, const float* __r
 
   // 1: W = U' G  (A = U', B rows j = G(., j))
   bool ok = dk_tc_gemm(taddr, Uth, Utl, Xh, Xl, pn, mbar, 0);
-  if (ok) dk_tc_epilogue(taddr, pn, [&](int k, int j, float v) { dk_tc_put(Xh, Xl, dk_tc_at(k, j, sbo), v); });
-  // 2: G' = (W U) o Gamma  (A = W, B rows l = U(., l)); stored as B of step 3 (row l, K k)
+  if (ok) dk_tc_epilogue(taddr, pn, [&](int k, int c, float (&v)[8]) { dk_tc_put8(Xh, Xl, k, c, sbo, v); });
+  // 2: G' = (W U) o Gamma  (A = W, B rows l = U(., l)).  G' is symmetric up to
+  // rounding; it is stored as it comes (row k, K l), so step 3 forms U G''.
   ok = ok && dk_tc_gemm(taddr, Xh, Xl, Uth, Utl, pn, mbar, 1);
   if (ok)
-    dk_tc_epilogue(taddr, pn, [&](int k, int l, float v) {
-      const float gv = (k < p && l < p) ? v * dk_tc_gamma(lamf[k], lamf[l], tau) : 0.f;
-      dk_tc_put(Xh, Xl, dk_tc_at(l, k, sbo), gv);
+    dk_tc_epilogue(taddr, pn, [&](int k, int c, float (&v)[8]) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int l = c + j;
+        v[j] = (k < p && l < p) ? v[j] * dk_tc_gamma(lamf[k], lamf[l], tau) : 0.f;
+      }
+      dk_tc_put8(Xh, Xl, k, c, sbo, v);
     });
-  // 3: Y = U G'  (A = U, B rows l = G'(., l))
+  // 3: Y = U G''  (A = U, B rows k = G'(k, .))
   ok = ok && dk_tc_gemm(taddr, Urh, Url, Xh, Xl, pn, mbar, 0);
-  if (ok) dk_tc_epilogue(taddr, pn, [&](int i, int l, float v) { dk_tc_put(Xh, Xl, dk_tc_at(i, l, sbo), v); });
+  if (ok) dk_tc_epilogue(taddr, pn, [&](int i, int c, float (&v)[8]) { dk_tc_put8(Xh, Xl, i, c, sbo, v); });
   // 4: S_bar = Y U'  (A = Y, B rows j = U(j, .)); upper triangle to svec
   ok = ok && dk_tc_gemm(taddr, Xh, Xl, Urh, Url, pn, mbar, 1);
   if (ok)
-    dk_tc_epilogue(taddr, pn, [&](int i, int j, float v) {
-      if (i <= j && j < p) out[j * (j + 1) / 2 + i] = i == j ? v : v * (float)kSqrt2;
+    dk_tc_epilogue(taddr, pn, [&](int i, int c, float (&v)[8]) {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = c + jj;
+        if (i <= j && j < p) out[j * (j + 1) / 2 + i] = i == j ? v[jj] : v[jj] * (float)kSqrt2;
+      }
     });
   tc::fence_before();
   __syncthreads();

@@ -662,14 +662,14 @@ __global__ void k_iota(int32_t n, int32_t* __restrict__ out) {
 template <class T, class V>
 __global__ void k_rho_from_log(Prob<T, V> P, int32_t K, const double* __restrict__ logr,
                                double eq_scale, T* __restrict__ rho) {
-  const int64_t tot = (int64_t)K * P.m_total;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t k = (int32_t)(e / P.m_total);
-    const int64_t r = e % P.m_total;
-    const double base = exp(logr[k]);
-    rho[e] = (T)(P.row_kind[r] == K_ZERO ? eq_scale * base : base);
-  }
+  // blockIdx.y = step k: exp(log rho_k) once per thread, not per entry
+  const int32_t k = blockIdx.y;
+  const double base = exp(logr[k]);
+  const T b1 = (T)base, beq = (T)(eq_scale * base);
+  T* __restrict__ out = rho + (int64_t)k * P.m_total;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.m_total;
+       r += (int64_t)gridDim.x * blockDim.x)
+    out[r] = P.row_kind[r] == K_ZERO ? beq : b1;
 }
 
 // glog[k] = sum_r grho[k][r] rho[k][r]; one CTA per step, fixed order.

@@ -1012,8 +1012,9 @@ struct ImplT : Impl {
   }
 
   cosmo_status rho_from_log(int32_t K_, const double* lr, double eq, void* rho, cudaStream_t st) override {
-    if (K_ < 1 || !lr || !rho) return fail(COSMO_E_INVAL, "bad arguments to rho_from_log");
-    k_rho_from_log<T, V><<<grid_for((int64_t)K_ * h.m, 256), 256, 0, st>>>(P, K_, lr, eq, (T*)rho);
+    if (K_ < 1 || K_ > 65535 || !lr || !rho) return fail(COSMO_E_INVAL, "bad arguments to rho_from_log");
+    const dim3 grid(grid_for(h.m, 256, 148 * 4), K_);   // y: step
+    k_rho_from_log<T, V><<<grid, 256, 0, st>>>(P, K_, lr, eq, (T*)rho);
     CU(cudaGetLastError());
     launched += 1; g_launches += 1;
     return COSMO_OK;
