@@ -8,6 +8,8 @@
 // the rows of the paper's problem classes hold few nonzeros.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace cosmo {
@@ -133,11 +135,11 @@ struct CgArgs {
 // both rows are loaded first, then all their gathers, so a short row costs
 // two dependent round trips instead of two per entry.  The sum runs along the
 // row in entry order.
-template <class T, class V, class F>
-__device__ __forceinline__ void cta_csr_rows(const int64_t* __restrict__ rp,
-                                             const int32_t* __restrict__ ci,
-                                             const V* __restrict__ val, const T* __restrict__ x,
-                                             int64_t r0, int64_t r1, F f) {
+template <bool COH, class T, class V, class F>
+__device__ __forceinline__ void cta_csr_rows_c(const int64_t* __restrict__ rp,
+                                               const int32_t* __restrict__ ci,
+                                               const V* __restrict__ val, const T* __restrict__ x,
+                                               int64_t r0, int64_t r1, F f) {
   constexpr int U = 8;
   const int64_t step = blockDim.x;
   for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 2 * step) {
@@ -167,7 +169,7 @@ __device__ __forceinline__ void cta_csr_rows(const int64_t* __restrict__ rp,
       for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int k = 0; k < U; ++k)
-          if (c[u][k] >= 0) acc[u] += v[u][k] * x[c[u][k]];
+          if (c[u][k] >= 0) acc[u] += v[u][k] * (COH ? __ldcg(x + c[u][k]) : x[c[u][k]]);
 #pragma unroll
       for (int u = 0; u < 2; ++u) e[u] = min(e[u] + U, eend[u]);
     }
@@ -179,37 +181,103 @@ __device__ __forceinline__ void cta_csr_rows(const int64_t* __restrict__ rp,
   }
 }
 
-// u = M v on the columns [c0, c1) of one instance (rows [r0, r1)); CTA-wide.
-template <class T, class V>
-__device__ __forceinline__ void cta_matvec(const Prob<T, V>& P, const CgArgs<T>& a,
-                                           const T* __restrict__ v, T* __restrict__ u,
-                                           int64_t c0, int64_t c1, int64_t r0, int64_t r1) {
+template <class T, class V, class F>
+__device__ __forceinline__ void cta_csr_rows(const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci,
+                                             const V* __restrict__ val, const T* __restrict__ x,
+                                             int64_t r0, int64_t r1, F f) {
+  cta_csr_rows_c<false>(rp, ci, val, x, r0, r1, f);
+}
+
+// CTA barrier (CS = 1) or cluster barrier over the CS CTAs of an instance
+template <int CS>
+__device__ __forceinline__ void cg_sync() {
+  if constexpr (CS == 1) __syncthreads();
+  else cooperative_groups::this_cluster().sync();
+}
+
+// Sum of NV doubles over the CTAs of a cluster (every thread holds its CTA's
+// total on entry): each CTA publishes its totals in shared memory, then every
+// CTA reads all of them through distributed shared memory in rank order, so
+// all CTAs hold the same bitwise result.  Two slot sets alternate, so one
+// cluster barrier per reduction suffices (a slot set is rewritten only after
+// the next reduction's barrier, which every reader of it has passed).
+template <int CS, int NV>
+__device__ __forceinline__ void cg_cluster_sum(double (&v)[NV], double* slots, int& par) {
+  if constexpr (CS > 1) {
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    double* my = slots + par * NV;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) my[q] = v[q];
+    }
+    cl.sync();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int rk = 0; rk < CS; ++rk) {
+      const double* ps = cl.map_shared_rank(my, rk);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[q] += ps[q];
+    }
+    par ^= 1;
+  }
+}
+
+// u = M v on this CTA's columns [c0, c1) of one instance (its rows [r0, r1)
+// produce t); with CS > 1 the CTAs of a cluster split the instance's rows and
+// columns and v, t are gathered through L2.
+template <int CS, class T, class V>
+__device__ __forceinline__ void cta_matvec_cl(const Prob<T, V>& P, const CgArgs<T>& a,
+                                              const T* __restrict__ v, T* __restrict__ u,
+                                              int64_t c0, int64_t c1, int64_t r0, int64_t r1) {
+  constexpr bool COH = CS > 1;
   T* __restrict__ t = a.t;
   const T* __restrict__ rho = a.rho;
-  cta_csr_rows<T, V>(P.A_rp, P.A_ci, P.A_v, v, r0, r1,
-                     [&](int64_t r, T acc) { t[r] = rho[r] * acc; });
-  __syncthreads();
+  cta_csr_rows_c<COH, T, V>(P.A_rp, P.A_ci, P.A_v, v, r0, r1,
+                            [&](int64_t r, T acc) { t[r] = rho[r] * acc; });
+  cg_sync<CS>();
   const T sig = (T)a.sigma;
   if (P.P_rp) {
     // u = sigma v + P v, then u += A' t
-    cta_csr_rows<T, T>(P.P_rp, P.P_ci, P.P_v, v, c0, c1,
-                       [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
-    cta_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
-                       [&](int64_t j, T acc) { u[j] += acc; });
+    cta_csr_rows_c<COH, T, T>(P.P_rp, P.P_ci, P.P_v, v, c0, c1,
+                              [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+    cta_csr_rows_c<COH, T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
+                              [&](int64_t j, T acc) { u[j] += acc; });
   } else {
-    cta_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
-                       [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+    cta_csr_rows_c<COH, T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1,
+                              [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
   }
   __syncthreads();
 }
 
-template <class T, class V, int NT>
+template <class T, class V>
+__device__ __forceinline__ void cta_matvec(const Prob<T, V>& P, const CgArgs<T>& a,
+                                           const T* __restrict__ v, T* __restrict__ u,
+                                           int64_t c0, int64_t c1, int64_t r0, int64_t r1) {
+  cta_matvec_cl<1>(P, a, v, u, c0, c1, r0, r1);
+}
+
+// a4 / b5: Jacobi-PCG on one instance per CTA (CS = 1) or per cluster of CS
+// CTAs (launched with that cluster size), each CTA owning a contiguous slice
+// of the instance's rows and columns.  Stop when ||r||^2 <= tol^2 ||rhs||^2
+// (recursively updated r) or at the cap; dots in double.
+template <class T, class V, int NT, int CS = 1>
 __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
   __shared__ double sm[3 * (NT / 32)];
-  const int32_t inst = P.cg_sched ? P.cg_sched[blockIdx.x] : P.inst_sched[blockIdx.x];
-  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
-  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
-  if (c1 == c0) return;
+  __shared__ double slots[2 * 3];
+  int par = 0;
+  int cid = blockIdx.x, rank = 0;
+  if constexpr (CS > 1) {
+    cid = blockIdx.x / CS;
+    rank = (int)cooperative_groups::this_cluster().block_rank();
+  }
+  const int32_t inst = P.cg_sched ? P.cg_sched[cid] : P.inst_sched[cid];
+  const int64_t ic0 = P.col_off[inst], ic1 = P.col_off[inst + 1];
+  const int64_t ir0 = P.row_off[inst], ir1 = P.row_off[inst + 1];
+  if (ic1 == ic0) return;   // the whole cluster (same instance)
+  const int64_t cw = (ic1 - ic0 + CS - 1) / CS, rw = (ir1 - ir0 + CS - 1) / CS;
+  const int64_t c0 = ic0 + min(ic1 - ic0, rank * cw), c1 = ic0 + min(ic1 - ic0, (rank + 1) * cw);
+  const int64_t r0 = ir0 + min(ir1 - ir0, rank * rw), r1 = ir0 + min(ir1 - ir0, (rank + 1) * rw);
   T* __restrict__ x = a.x;
   T* __restrict__ r = a.r;
   T* __restrict__ p = a.p;
@@ -219,8 +287,8 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
   } else {
     if (a.x0 && a.x0 != a.x)
       for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) x[j] = a.x0[j];
-    __syncthreads();
-    cta_matvec(P, a, x, u, c0, c1, r0, r1);
+    cg_sync<CS>();
+    cta_matvec_cl<CS>(P, a, x, u, c0, c1, r0, r1);
   }
   double s3[3] = {0.0, 0.0, 0.0};   // rz, rr, bb
   for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
@@ -234,6 +302,7 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
     s3[2] += (double)bj * (double)bj;
   }
   block_sum<3>(s3, sm);
+  cg_cluster_sum<CS, 3>(s3, slots, par);   // (its barrier, or block_sum's, publishes p)
   double rz = s3[0], rr = s3[1];
   const double thr = a.tol * a.tol * s3[2];
   int32_t it = 0;
@@ -242,10 +311,11 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
     rr = 0.0;
   }
   while (rr > thr && it < a.maxit) {
-    cta_matvec(P, a, p, u, c0, c1, r0, r1);
+    cta_matvec_cl<CS>(P, a, p, u, c0, c1, r0, r1);
     double s1[1] = {0.0};
     for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) s1[0] += (double)p[j] * (double)u[j];
     block_sum<1>(s1, sm);
+    cg_cluster_sum<CS, 1>(s1, slots, par);
     if (!(s1[0] > 0.0)) break;  // breakdown (p = 0 or non-finite): stop, flagged below
     const T al = (T)(rz / s1[0]);
     double s2[2] = {0.0, 0.0};
@@ -258,14 +328,18 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
       s2[1] += (double)rj * (double)rj;
     }
     block_sum<2>(s2, sm);
+    cg_cluster_sum<CS, 2>(s2, slots, par);
     const T be = (T)(s2[0] / rz);
     rz = s2[0];
     rr = s2[1];
     for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) p[j] = a.dinv[j] * r[j] + be * p[j];
-    __syncthreads();
+    cg_sync<CS>();
     ++it;
   }
-  if (threadIdx.x == 0) {
+  // no CTA leaves while a peer may still read its slots (after a break, or
+  // when the loop did not run)
+  if constexpr (CS > 1) cooperative_groups::this_cluster().sync();
+  if (rank == 0 && threadIdx.x == 0) {
     if (rr > thr) atomicOr(&a.flags[inst], a.flag_bit);
     if (!(rr == rr)) atomicOr(&a.flags[inst], F_NONFINITE);
     if (a.iters) a.iters[inst] = it;

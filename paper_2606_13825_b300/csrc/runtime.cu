@@ -207,7 +207,8 @@ struct HostPlan {
   std::vector<int32_t> inst_sched;
   std::vector<uint8_t> diag_inst;
   std::vector<int32_t> cg_sched;
-  int32_t cg_nt = 256;      // threads of a CG CTA (one CTA per instance)
+  int32_t cg_nt = 256;      // threads of a CG CTA
+  int32_t cg_cs = 1;        // CTAs per instance (thread-block cluster) in the CG
   int64_t sum_p = 0, sum_p2 = 0;
   int32_t max_p = 0;
 };
@@ -328,6 +329,14 @@ static void build_plan(const cosmo_problem* pr, HostPlan& h) {
   // large instances take 512-thread CG CTAs (more rows in flight per SpMV);
   // many small ones 256 (two CTAs resident per SM)
   h.cg_nt = cg_max >= 8192 ? 512 : 256;
+  // few large instances: a cluster of 2 or 4 CTAs per instance, so that the
+  // CG of e.g. 64 SOCP instances spreads over more than 64 SMs
+  const int64_t ncg = (int64_t)h.cg_sched.size();
+  h.cg_cs = 1;
+  if (cg_max >= 8192 && ncg > 0) {
+    if (4 * ncg <= 148) h.cg_cs = 4;
+    else if (2 * ncg <= 148) h.cg_cs = 2;
+  }
 }
 
 // ------------------------------------------------------- implementation ---
@@ -640,6 +649,49 @@ struct ImplT : Impl {
     }
   }
 
+  // the same with a thread-block cluster of cs CTAs along x
+  template <class Kern, class... Args>
+  void launch_cluster(const char* tag, Kern kern, int grid, int block, size_t smem, cudaStream_t st, int cs,
+                      Args... args) {
+    const bool rec = prof_mode != 0 && !capturing && (prof_mode == 1 || prof_tag == tag);
+    Rec r{tag, nullptr, nullptr};
+    if (rec) {
+      r.e0 = get_event();
+      r.e1 = get_event();
+      cudaEventRecord(r.e0, st);
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+    ++seq_kernels;
+    if (rec) {
+      cudaEventRecord(r.e1, st);
+      prof_pending.push_back(r);
+    }
+  }
+
+  // CG launch: one CTA or one cluster of cg_cs CTAs per instance
+  void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
+    if (h.cg_cs == 4)
+      launch_cluster(tag, k_pcg<T, V, 512, 4>, P.n_cg * 4, 512, 0, st, 4, P, ca);
+    else if (h.cg_cs == 2)
+      launch_cluster(tag, k_pcg<T, V, 512, 2>, P.n_cg * 2, 512, 0, st, 2, P, ca);
+    else if (h.cg_nt == 512)
+      launch(tag, k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
+    else
+      launch(tag, k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+  }
+
   // Fork one launch per PSD bucket onto the bucket streams and join them back
   // into st (captured as parallel graph branches).  Timed as one group.
   template <class F>
@@ -730,10 +782,7 @@ struct ImplT : Impl {
     ca.sigma = sig; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = opt.cg_tol;
     ca.maxit = opt.cg_max_iter; ca.zero_start = xt_warm ? 0 : 1; ca.flag_bit = F_CG_CAP;
     ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 2;
-    if (P.n_cg) {
-      if (h.cg_nt == 512) launch("pcg", k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
-      else launch("pcg", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
-    }
+    if (P.n_cg) launch_pcg("pcg", st, ca);
     StepPtrs<T> sp{};
     sp.x = st_x(slot); sp.s = st_s(slot); sp.y = st_y(slot);
     sp.xn = st_x(slot + 1); sp.sn = st_s(slot + 1); sp.yn = st_y(slot + 1);
@@ -852,10 +901,7 @@ struct ImplT : Impl {
     ca.dinv = dinv + (int64_t)k * h.n; ca.sigma = q.sigma; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u;
     ca.t = cg_t; ca.tol = opt.cg_tol; ca.maxit = opt.cg_max_iter; ca.zero_start = 1;
     ca.flag_bit = F_ADJ_CG_CAP; ca.flags = flags; ca.iters = nullptr; ca.stats = stats + 4;
-    if (P.n_cg) {
-      if (h.cg_nt == 512) launch("pcg_adj", k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
-      else launch("pcg_adj", k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
-    }
+    if (P.n_cg) launch_pcg("pcg_adj", st, ca);
     launch("bwd_solve", k_bwd_solve<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, q);
   }
 
