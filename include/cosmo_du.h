@@ -149,6 +149,9 @@ typedef struct {
                                (re-orthogonalised by one Newton-Schulz step) */
   int32_t dk_tensor_cores;  /* 1: MIXED-precision DK backward of blocks of order <= 80 on
                                the tensor cores (tcgen05, split-TF32 products); 0: CUDA cores */
+  int32_t cg_cluster;       /* CTAs per instance in the CG: 0 automatic (2 or 4 for fewer
+                               than 74 / 37 instances with >= 8192 rows + columns, else 1);
+                               1, 2 or 4 forced */
 } cosmo_options;
 
 typedef struct {
@@ -181,8 +184,8 @@ const char* cosmo_last_error(void);
 /* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
  * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
- * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1.  Returns COSMO_E_INVAL for an
- * unknown precision. */
+ * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0.  Returns
+ * COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 
 /* Validate a problem on the host without touching the device (CSR bounds and

@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("cg_max_iter", c_int32), ("checkpoint_every", c_int32),
                 ("dk_gap_tau", c_double), ("eig_jacobi_max_p", c_int32),
                 ("eig_max_sweeps", c_int32), ("eig_tol", c_double), ("use_graph", c_int32),
-                ("device", c_int32), ("eig_warm_start", c_int32), ("dk_tensor_cores", c_int32)]
+                ("device", c_int32), ("eig_warm_start", c_int32), ("dk_tensor_cores", c_int32),
+                ("cg_cluster", c_int32)]
 
 
 class BatchInfo(ctypes.Structure):

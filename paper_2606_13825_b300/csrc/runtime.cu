@@ -682,9 +682,10 @@ struct ImplT : Impl {
 
   // CG launch: one CTA or one cluster of cg_cs CTAs per instance
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
-    if (h.cg_cs == 4)
+    const int cs = opt.cg_cluster > 0 ? opt.cg_cluster : h.cg_cs;
+    if (cs == 4)
       launch_cluster(tag, k_pcg<T, V, 512, 4>, P.n_cg * 4, 512, 0, st, 4, P, ca);
-    else if (h.cg_cs == 2)
+    else if (cs == 2)
       launch_cluster(tag, k_pcg<T, V, 512, 2>, P.n_cg * 2, 512, 0, st, 2, P, ca);
     else if (h.cg_nt == 512)
       launch(tag, k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
@@ -1147,6 +1148,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->device = 0;
   o->eig_warm_start = 1;
   o->dk_tensor_cores = 1;
+  o->cg_cluster = 0;
   return COSMO_OK;
 }
 
@@ -1168,7 +1170,8 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
   if (o.value_type != COSMO_VAL_F32 && o.value_type != COSMO_VAL_BF16)
     return fail(COSMO_E_INVAL, "unknown value type %d", o.value_type);
   if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
-      o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0))
+      o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
+      !(o.cg_cluster == 0 || o.cg_cluster == 1 || o.cg_cluster == 2 || o.cg_cluster == 4))
     return fail(COSMO_E_INVAL, "invalid options");
   TRY(validate(prob));
   int ndev = 0;

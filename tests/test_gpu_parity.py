@@ -108,6 +108,25 @@ def test_socp_batch(precision, value_type):
     compare(gpu, ora, precision)
 
 
+@pytest.mark.parametrize("cs", [2, 4])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_socp_cg_on_clusters(precision, cs):
+    """The CG on thread-block clusters (forced on small instances; the
+    automatic choice uses them for few large ones): each CTA of a cluster
+    owns a slice of the instance's rows and columns, dots combine through
+    distributed shared memory.  Same parity against the oracle as one CTA
+    per instance."""
+    _need_gpu()
+    probs = socp_batch(3, seed=4150)
+    K = 4
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=19)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, cg_cluster=cs,
+                  cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not (gpu["flags"] & 3).any(), gpu["flags"]
+    compare(gpu, ora, precision)
+
+
 def test_socp_bf16_values_vs_rounded_oracle():
     """BF16 storage of A: parity against the oracle run on the same
     bf16-rounded A (the rounding is the input, not an error).  P stays in the
