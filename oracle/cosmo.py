@@ -130,6 +130,42 @@ def loss_sq(problem, x, s, y):
     return rp @ rp + rd @ rd
 
 
+def loss_logratio(problem, xs, ss, ys, den=None):
+    """Self-supervised meta-loss of Sec. 4 (Experiments, the log-residual
+    loss): sum over k = 1..K of
+        log( ||r_d^k||^2 / ||r_d^0||^2 + ||r_p^k||^2 / ||r_p^0||^2 )
+    with the k = 0 norms held constant (detached) and r_d with the sign of
+    the dual-residual reading (Px + q - A'y).  A term whose k = 0 norm is
+    zero is dropped, and a step whose sum is zero contributes nothing (the
+    paper leaves both cases open).  den = (a0, b0) overrides the k = 0
+    squared norms (used to differentiate with them held fixed)."""
+    if den is None:
+        rp0, rd0 = residuals(problem, xs[0], ss[0], ys[0])
+        a0, b0 = rd0 @ rd0, rp0 @ rp0
+    else:
+        a0, b0 = den
+    L = 0.0
+    for k in range(1, len(xs)):
+        rp, rd = residuals(problem, xs[k], ss[k], ys[k])
+        S = (rd @ rd / a0 if a0 > 0 else 0.0) + (rp @ rp / b0 if b0 > 0 else 0.0)
+        if S > 0:
+            L += np.log(S)
+    return L
+
+
+def _logratio_cot(problem, x, s, y, a0, b0, g):
+    """Cotangents (x, s, y) of g * log(S) at one state, S as in loss_logratio."""
+    rp, rd = residuals(problem, x, s, y)
+    S = (rd @ rd / a0 if a0 > 0 else 0.0) + (rp @ rp / b0 if b0 > 0 else 0.0)
+    if S <= 0:
+        return None
+    wa = g / (S * a0) if a0 > 0 else 0.0
+    wb = g / (S * b0) if b0 > 0 else 0.0
+    # d||r_d||^2/dx = 2 P r_d, d/dy = -2 A r_d; d||r_p||^2/dx = 2 A'r_p, d/ds = 2 r_p
+    return (2.0 * wa * (problem.P @ rd) + 2.0 * wb * (problem.A.T @ rp), 2.0 * wb * rp,
+            -2.0 * wa * (problem.A @ rd))
+
+
 # ---------------------------------------------------------------- forward --
 @dataclass
 class Step:
@@ -197,11 +233,13 @@ def forward(problem, rho, alpha, sigma, x0=None, s0=None, y0=None, keep=True):
 
 
 # --------------------------------------------------------------- backward --
-def backward(problem, tr, gx=None, gs=None, gy=None, gloss=0.0, tau=None):
+def backward(problem, tr, gx=None, gs=None, gy=None, gloss=0.0, tau=None, glogratio=0.0):
     """Reverse pass through ``forward``.
 
     gx, gs, gy: cotangents of x^K, s^K, y^K (None = 0)
     gloss:      cotangent of loss_sq(x^K, s^K, y^K)
+    glogratio:  cotangent of loss_logratio over the trajectory (its k = 0
+                norms held constant), injected at every state k = 1..K
     Returns dict with grho (K, m) w.r.t. the unrectified rho, galpha (K,),
     gx0, gs0, gy0."""
     n, m = problem.n, problem.m
@@ -214,9 +252,18 @@ def backward(problem, tr, gx=None, gs=None, gy=None, gloss=0.0, tau=None):
         xb = xb + gloss * (2.0 * (problem.A.T @ rp) + 2.0 * (problem.P @ rd))
         sb = sb + gloss * 2.0 * rp
         yb = yb - gloss * 2.0 * (problem.A @ rd)
+    a0 = b0 = 0.0
+    if glogratio != 0.0:
+        rp0, rd0 = residuals(problem, tr.xs[0], tr.ss[0], tr.ys[0])
+        a0, b0 = rd0 @ rd0, rp0 @ rp0
     grho = np.zeros((K, m))
     galpha = np.zeros(K)
     for k in range(K - 1, -1, -1):
+        if glogratio != 0.0:
+            # the loss term of state k + 1 (the output of step k)
+            c = _logratio_cot(problem, tr.xs[k + 1], tr.ss[k + 1], tr.ys[k + 1], a0, b0, glogratio)
+            if c is not None:
+                xb, sb, yb = xb + c[0], sb + c[1], yb + c[2]
         st_ = tr.steps[k]
         r, a = st_.rho, st_.alpha
         sn = tr.ss[k + 1]

@@ -228,3 +228,68 @@ def test_rectify_and_adjoint(rng):
     for t, d, r0, r1 in pr.cone_offsets():
         rr = cosmo.rectify(pr, r)[r0:r1]
         assert np.ptp(rr) < 1e-15
+
+
+def _fd_check_logratio(pr, K, seed, steps=(1e-3, 1e-4), tol=1e-5):
+    """Directional central differences of the log-residual meta-loss (Sec. 4)
+    over (rho, alpha, x0, s0, y0).  Its k = 0 norms are detached, so the
+    finite differences hold them at their unperturbed values (den=)."""
+    rng = np.random.default_rng(seed)
+    m, n = pr.m, pr.n
+    rho = np.tile(default_rho(pr), (K, 1)) * np.exp(0.3 * rng.standard_normal((K, m)))
+    alpha = 1.6 - 0.3 * rng.random(K)
+    x0 = rng.standard_normal(n); s0 = rng.standard_normal(m); y0 = rng.standard_normal(m)
+    args = [rho, alpha, x0, s0, y0]
+    rp0, rd0 = cosmo.residuals(pr, x0, s0, y0)
+    den = (rd0 @ rd0, rp0 @ rp0)
+
+    def L(a):
+        tr = cosmo.forward(pr, a[0], a[1], 1e-6, a[2], a[3], a[4])
+        return cosmo.loss_logratio(pr, tr.xs, tr.ss, tr.ys, den=den), tr
+
+    l0, tr = L(args)
+    assert abs(l0 - cosmo.loss_logratio(pr, tr.xs, tr.ss, tr.ys)) < 1e-12 * max(1.0, abs(l0))
+    assert _kink_margin(pr, tr) > 1e-3
+    g = cosmo.backward(pr, tr, glogratio=1.0)
+    grads = [g["grho"], g["galpha"], g["gx0"], g["gs0"], g["gy0"]]
+    for i in range(5):
+        d = rng.standard_normal(args[i].shape)
+        an = float(np.sum(grads[i] * d))
+        errs = []
+        for h in steps:
+            ap = list(args); ap[i] = args[i] + h * d
+            am = list(args); am[i] = args[i] - h * d
+            fd = (L(ap)[0] - L(am)[0]) / (2 * h)
+            errs.append(abs(fd - an))
+        assert min(errs) <= tol * (abs(an) + 1e-3 * max(1.0, abs(l0))), (i, errs, an)
+
+
+def test_logratio_loss_gradients_fd_maxcut():
+    rng = np.random.default_rng(31)
+    pr = maxcut_problem(6, erdos_renyi(6, 0.5, rng))
+    _fd_check_logratio(pr, K=4, seed=32)
+
+
+def test_logratio_loss_gradients_fd_socp():
+    pr = socp_problem(4170, n=12, m=20, density=0.3, m_M=4, n_soc=2, soc_lo=3, soc_hi=5)
+    _fd_check_logratio(pr, K=3, seed=33)
+
+
+def test_logratio_loss_definition():
+    """Closed form: a trajectory that stays at z^0 has loss K log 2 (every
+    normalised sum is 1 + 1); and the loss sums one term per state 1..K."""
+    rng = np.random.default_rng(34)
+    pr = maxcut_problem(5, erdos_renyi(5, 0.6, rng))
+    x0 = rng.standard_normal(pr.n); s0 = rng.standard_normal(pr.m); y0 = rng.standard_normal(pr.m)
+    K = 3
+    L = cosmo.loss_logratio(pr, [x0] * (K + 1), [s0] * (K + 1), [y0] * (K + 1))
+    assert abs(L - K * np.log(2.0)) < 1e-12
+    K = 2
+    rho = np.tile(default_rho(pr), (K, 1))
+    tr = cosmo.forward(pr, rho, np.full(K, 1.6), 1e-6, x0, s0, y0)
+    rp0, rd0 = cosmo.residuals(pr, x0, s0, y0)
+    terms = []
+    for k in (1, 2):
+        rp, rd = cosmo.residuals(pr, tr.xs[k], tr.ss[k], tr.ys[k])
+        terms.append(np.log(rd @ rd / (rd0 @ rd0) + rp @ rp / (rp0 @ rp0)))
+    assert abs(cosmo.loss_logratio(pr, tr.xs, tr.ss, tr.ys) - sum(terms)) < 1e-12 * abs(sum(terms))
