@@ -152,6 +152,11 @@ typedef struct {
   int32_t cg_cluster;       /* CTAs per instance in the CG: 0 automatic (2 or 4 for fewer
                                than 74 / 37 instances with >= 8192 rows + columns, else 1);
                                1, 2 or 4 forced */
+  int32_t loss_kind;        /* per-instance loss of cosmo_forward / cotangent of
+                               cosmo_backward: 0 ||r_p^K||^2 + ||r_d^K||^2; 1 the log-residual
+                               loss of Sec. 4, sum_{k=1..K} log(||r_d^k||^2/||r_d^0||^2 +
+                               ||r_p^k||^2/||r_p^0||^2), k = 0 norms held constant, a term with
+                               a zero k = 0 norm dropped */
 } cosmo_options;
 
 typedef struct {
@@ -184,8 +189,8 @@ const char* cosmo_last_error(void);
 /* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
  * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
- * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0.  Returns
- * COSMO_E_INVAL for an unknown precision. */
+ * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0; loss_kind 0.
+ * Returns COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 
 /* Validate a problem on the host without touching the device (CSR bounds and

@@ -487,6 +487,74 @@ __global__ void __launch_bounds__(NT) k_residuals(Prob<T, V> P, ResArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Log-residual meta-loss of Sec. 4: per instance
+//   L = sum_{k=1..K} log(S_k),  S_k = ||r_d^k||^2 / ||r_d^0||^2 + ||r_p^k||^2 / ||r_p^0||^2
+// with the k = 0 norms held constant; rd2 / rp2 hold ||r_d^k||^2, ||r_p^k||^2
+// as [K + 1][ninst].  A term with a zero k = 0 norm is dropped and a step with
+// S_k = 0 contributes nothing.  FP64 (one thread per instance).
+__device__ __forceinline__ double logratio_sum(double a0, double b0, double ak, double bk) {
+  return (a0 > 0.0 ? ak / a0 : 0.0) + (b0 > 0.0 ? bk / b0 : 0.0);
+}
+
+__global__ void k_logratio_loss(int32_t ninst, int32_t K, const double* __restrict__ rd2,
+                                const double* __restrict__ rp2, double* __restrict__ loss) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  const double a0 = rd2[i], b0 = rp2[i];
+  double L = 0.0;
+  for (int32_t k = 1; k <= K; ++k) {
+    const double S = logratio_sum(a0, b0, rd2[(int64_t)k * ninst + i], rp2[(int64_t)k * ninst + i]);
+    if (S > 0.0) L += log(S);
+  }
+  loss[i] = L;
+}
+
+// weights of state k's cotangent: d(g log S_k)/d||r_d^k||^2 = g / (S_k a0),
+// d/d||r_p^k||^2 = g / (S_k b0)
+template <class T>
+__global__ void k_logratio_w(int32_t ninst, int32_t k, const double* __restrict__ rd2,
+                             const double* __restrict__ rp2, const double* __restrict__ gloss, T* wa, T* wb) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  const double a0 = rd2[i], b0 = rp2[i];
+  const double S = logratio_sum(a0, b0, rd2[(int64_t)k * ninst + i], rp2[(int64_t)k * ninst + i]);
+  const double g = gloss ? gloss[i] : 0.0;
+  wa[i] = (T)((S > 0.0 && a0 > 0.0) ? g / (S * a0) : 0.0);
+  wb[i] = (T)((S > 0.0 && b0 > 0.0) ? g / (S * b0) : 0.0);
+}
+
+// add state k's cotangent: x_bar += 2 wa P r_d + 2 wb A'r_p, s_bar += 2 wb r_p,
+// y_bar -= 2 wa A r_d (r_p, r_d the state's residual vectors)
+template <class T, class V>
+__global__ void k_logratio_seed(Prob<T, V> P, const T* __restrict__ rp, const T* __restrict__ rd,
+                                const T* __restrict__ wa, const T* __restrict__ wb, T* xb, T* sb, T* yb) {
+  const int64_t tot = P.m_total + P.n_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < P.m_total) {
+      const int64_t r = e;
+      const int32_t i = P.row_inst[r];
+      const T a = wa[i], b = wb[i];
+      T ard = T(0);
+      if (a != T(0))
+        for (int64_t q = P.A_rp[r]; q < P.A_rp[r + 1]; ++q) ard += (T)ldv(P.A_v, q) * rd[P.A_ci[q]];
+      yb[r] -= T(2) * a * ard;
+      sb[r] += T(2) * b * rp[r];
+    } else {
+      const int64_t j = e - P.m_total;
+      const int32_t i = P.col_inst[j];
+      const T a = wa[i], b = wb[i];
+      T acc = T(0);
+      if (b != T(0))
+        for (int64_t q = P.AT_rp[j]; q < P.AT_rp[j + 1]; ++q) acc += b * (T)ldv(P.AT_v, q) * rp[P.AT_ci[q]];
+      if (P.P_rp && a != T(0))
+        for (int64_t q = P.P_rp[j]; q < P.P_rp[j + 1]; ++q) acc += a * P.P_v[q] * rd[P.P_ci[q]];
+      xb[j] += T(2) * acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // b1: loss backward.  d/dx = 2 (A'r_p + P r_d), d/ds = 2 r_p, d/dy = -2 A r_d,
 // each times the per-instance loss cotangent, plus the caller's cotangents.
 // ---------------------------------------------------------------------------

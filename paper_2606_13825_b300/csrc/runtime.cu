@@ -397,6 +397,11 @@ struct ImplT : Impl {
   T *gproj = nullptr, *vbar = nullptr, *adjrhs = nullptr, *lamt = nullptr, *rp = nullptr,
     *rd = nullptr;
   double *loss_buf = nullptr, *gloss_buf = nullptr;
+  // log-residual meta-loss (loss_kind 1): ||r_d^k||^2, ||r_p^k||^2 for k = 0..K
+  // ([K + 1][ninst], tape arena), per-instance weights of one state's cotangent
+  double *lr_rd2 = nullptr, *lr_rp2 = nullptr;
+  T *lr_wa = nullptr, *lr_wb = nullptr;
+  bool lr_track = false;   // forward: store each new state's residual norms
   T *gx_in = nullptr, *gs_in = nullptr, *gy_in = nullptr;
   // tape (segment buffers) and per-step parameters
   int32_t K = 0, cK = 0, nseg = 0, seg_in_buffer = -1;
@@ -538,6 +543,7 @@ struct ImplT : Impl {
     TRY(arena.alloc(&lamt, n)); TRY(arena.alloc(&rp, m)); TRY(arena.alloc(&rd, n));
     TRY(arena.alloc(&gx_in, n)); TRY(arena.alloc(&gs_in, m)); TRY(arena.alloc(&gy_in, m));
     TRY(arena.alloc(&loss_buf, h.ninst)); TRY(arena.alloc(&gloss_buf, h.ninst));
+    TRY(arena.alloc(&lr_wa, h.ninst)); TRY(arena.alloc(&lr_wb, h.ninst));
     if (P.npsd > 0) {
       int dev = 0, maxs = 0;
       CU(cudaGetDevice(&dev));
@@ -609,6 +615,7 @@ struct ImplT : Impl {
     cK = c;
     nseg = (K + cK - 1) / cK;
     const int64_t n = h.n, m = h.m, ni = h.ninst;
+    TRY(tarena.alloc(&lr_rd2, (int64_t)(K + 1) * ni)); TRY(tarena.alloc(&lr_rp2, (int64_t)(K + 1) * ni));
     TRY(tarena.alloc(&xs, (cK + 1) * n)); TRY(tarena.alloc(&ss, (cK + 1) * m));
     TRY(tarena.alloc(&ys, (cK + 1) * m));
     TRY(tarena.alloc(&xts, (int64_t)cK * n)); TRY(tarena.alloc(&sts, (int64_t)cK * m));
@@ -823,7 +830,15 @@ struct ImplT : Impl {
         uprev = slot == 0 ? ck_U + (int64_t)seg * h.sum_p2 : Us + (int64_t)(slot - 1) * h.sum_p2;
       }
       enqueue_step(k, slot, warm, uprev, st);
+      if (lr_track) enqueue_norms(slot + 1, k + 1, st);
     }
+  }
+
+  // ||r_p||^2, ||r_d||^2 of the state in `slot` into the log-ratio buffers at step index k
+  void enqueue_norms(int slot, int32_t k, cudaStream_t st) {
+    ResArgs<T> ra{st_x(slot), st_s(slot), st_y(slot), nullptr, nullptr,
+                  lr_rp2 + (int64_t)k * h.ninst, lr_rd2 + (int64_t)k * h.ninst, nullptr, nullptr};
+    launch("residuals", k_residuals<T, V, 256>, h.ninst, 256, 0, st, P, ra);
   }
 
   void copy_state(T* dx, T* ds, T* dy, const T* sx, const T* s_, const T* sy, cudaStream_t st) {
@@ -837,6 +852,8 @@ struct ImplT : Impl {
   // whole forward: prep, all segments with checkpoints, optional loss
   void enqueue_forward(bool want_loss, cudaStream_t st) {
     enqueue_prep(st);
+    lr_track = want_loss && opt.loss_kind == 1;
+    if (lr_track) enqueue_norms(0, 0, st);
     for (int32_t seg = 0; seg < nseg; ++seg) {
       if (seg > 0) {
         // slot cK of the previous segment is z^{seg*cK}; x~ of its last step warms CG
@@ -851,7 +868,11 @@ struct ImplT : Impl {
                  st_x(0), st_s(0), st_y(0), st);
       enqueue_segment(seg, st);
     }
-    if (want_loss) {
+    lr_track = false;
+    if (want_loss && opt.loss_kind == 1) {
+      launch("residuals", k_logratio_loss, (h.ninst + 127) / 128, 128, 0, st, h.ninst, K, (const double*)lr_rd2,
+             (const double*)lr_rp2, loss_buf);
+    } else if (want_loss) {
       const int fs = last_len();
       ResArgs<T> ra{st_x(fs), st_s(fs), st_y(fs), rp, rd, nullptr, nullptr, nullptr, loss_buf};
       launch("residuals", k_residuals<T, V, 256>, h.ninst, 256, 0, st, P, ra);
@@ -909,7 +930,11 @@ struct ImplT : Impl {
   // whole backward (cotangents staged in gx_in/gs_in/gy_in/gloss_buf)
   void enqueue_backward(bool use_gloss, cudaStream_t st) {
     const int fs = last_len();
-    SeedArgs<T> sa{rp, rd, use_gloss ? gloss_buf : nullptr, gx_in, gs_in, gy_in, xb[0], sb[0], yb[0]};
+    const bool logratio = opt.loss_kind == 1;
+    // log-ratio loss: the seed carries only the caller's cotangents; every
+    // state's loss term is injected on the way back
+    SeedArgs<T> sa{rp, rd, (use_gloss && !logratio) ? gloss_buf : nullptr, gx_in, gs_in, gy_in,
+                   xb[0], sb[0], yb[0]};
     (void)fs;
     launch("loss_seed", k_loss_seed<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, sa);
     int cur = 0;
@@ -921,6 +946,16 @@ struct ImplT : Impl {
       }
       const int32_t k0 = seg * cK, k1 = std::min(K, k0 + cK);
       for (int32_t k = k1 - 1; k >= k0; --k) {
+        if (logratio && use_gloss) {
+          // cotangent of state k + 1's term, added to the one step k receives
+          const int sl = k + 1 - k0;
+          ResArgs<T> ra{st_x(sl), st_s(sl), st_y(sl), rp, rd, nullptr, nullptr, nullptr, nullptr};
+          launch("residuals", k_residuals<T, V, 256>, h.ninst, 256, 0, st, P, ra);
+          launch("loss_seed", k_logratio_w<T>, (h.ninst + 127) / 128, 128, 0, st, h.ninst, k + 1,
+                 (const double*)lr_rd2, (const double*)lr_rp2, (const double*)gloss_buf, lr_wa, lr_wb);
+          launch("loss_seed", k_logratio_seed<T, V>, grid_for(h.m + h.n, 256), 256, 0, st, P, (const T*)rp,
+                 (const T*)rd, (const T*)lr_wa, (const T*)lr_wb, xb[cur], sb[cur], yb[cur]);
+        }
         enqueue_bwd_step(k, k - k0, cur, st);
         cur ^= 1;
       }
@@ -1149,6 +1184,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->eig_warm_start = 1;
   o->dk_tensor_cores = 1;
   o->cg_cluster = 0;
+  o->loss_kind = 0;
   return COSMO_OK;
 }
 
@@ -1171,7 +1207,8 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
     return fail(COSMO_E_INVAL, "unknown value type %d", o.value_type);
   if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
-      !(o.cg_cluster == 0 || o.cg_cluster == 1 || o.cg_cluster == 2 || o.cg_cluster == 4))
+      !(o.cg_cluster == 0 || o.cg_cluster == 1 || o.cg_cluster == 2 || o.cg_cluster == 4) ||
+      !(o.loss_kind == 0 || o.loss_kind == 1))
     return fail(COSMO_E_INVAL, "invalid options");
   TRY(validate(prob));
   int ndev = 0;

@@ -337,8 +337,9 @@ class AlphaBroadcast(torch.autograd.Function):
 def unrolled_residual_loss(batch, log_rho, alpha_k, sigma=1e-6, eq_scale=1e3, x0=None, s0=None,
                            y0=None):
     """Meta-loss of the batched differentiable workload: sum over instances of
-    ||r_p^K||^2 + ||r_d^K||^2, differentiable in the per-step log rho_k and
-    alpha_k (and the warm start)."""
+    the batch's per-instance loss -- ||r_p^K||^2 + ||r_d^K||^2 by default, the
+    log-residual loss of Sec. 4 for a batch created with loss_kind=1 --
+    differentiable in the per-step log rho_k and alpha_k (and the warm start)."""
     K = log_rho.numel()
     rho = RhoFromLog.apply(batch, log_rho, eq_scale)
     alpha = AlphaBroadcast.apply(batch, alpha_k)

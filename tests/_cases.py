@@ -70,8 +70,10 @@ def random_inputs(problems, K, seed, noise=0.3, warm=True):
     return rho, alpha, x0, s0, y0
 
 
-def oracle_batch(problems, rho, alpha, sigma, x0, s0, y0, gloss=1.0, backward=True):
-    """Run the oracle per instance; results concatenated in batch order."""
+def oracle_batch(problems, rho, alpha, sigma, x0, s0, y0, gloss=1.0, backward=True, loss="sq"):
+    """Run the oracle per instance; results concatenated in batch order.
+    loss: "sq" (||r_p^K||^2 + ||r_d^K||^2) or "logratio" (the log-residual
+    loss of Sec. 4 over the whole trajectory)."""
     K = rho.shape[0]
     out = {k: [] for k in ("xK", "sK", "yK", "loss", "obj", "grho", "galpha", "gx0", "gs0", "gy0",
                            "res_scale", "obj_scale")}
@@ -84,7 +86,10 @@ def oracle_batch(problems, rho, alpha, sigma, x0, s0, y0, gloss=1.0, backward=Tr
                             None if s0 is None else s0[sl_r],
                             None if y0 is None else y0[sl_r], keep=backward)
         out["xK"].append(tr.xs[-1]); out["sK"].append(tr.ss[-1]); out["yK"].append(tr.ys[-1])
-        out["loss"].append(ocosmo.loss_sq(pr, tr.xs[-1], tr.ss[-1], tr.ys[-1]))
+        if loss == "logratio":
+            out["loss"].append(ocosmo.loss_logratio(pr, tr.xs, tr.ss, tr.ys))
+        else:
+            out["loss"].append(ocosmo.loss_sq(pr, tr.xs[-1], tr.ss[-1], tr.ys[-1]))
         out["obj"].append(ocosmo.objective(pr, tr.xs[-1]))
         x, s, y = tr.xs[-1], tr.ss[-1], tr.ys[-1]
         out["obj_scale"].append(float(np.abs(pr.q * x).sum() + 0.5 * abs(x) @ (abs(pr.P) @ abs(x))))
@@ -92,7 +97,8 @@ def oracle_batch(problems, rho, alpha, sigma, x0, s0, y0, gloss=1.0, backward=Tr
         sd_ = max(np.linalg.norm(pr.P @ x), np.linalg.norm(pr.q), np.linalg.norm(pr.A.T @ y))
         out["res_scale"].append(float(np.hypot(sp_, sd_)))
         if backward:
-            g = ocosmo.backward(pr, tr, gloss=gloss)
+            g = (ocosmo.backward(pr, tr, glogratio=gloss) if loss == "logratio"
+                 else ocosmo.backward(pr, tr, gloss=gloss))
             out["grho"].append(g["grho"]); out["galpha"].append(g["galpha"][:, None])
             out["gx0"].append(g["gx0"]); out["gs0"].append(g["gs0"]); out["gy0"].append(g["gy0"])
         c0 += n

@@ -32,7 +32,7 @@ def test_version_and_defaults(L):
     from paper_2606_13825_b300.solver import default_options
     o = default_options("mixed")
     assert o.precision == _abi.PREC_MIXED and o.cg_tol == 1e-8 and o.eig_tol == 1e-6
-    assert o.eig_warm_start == 1 and o.dk_tensor_cores == 1 and o.cg_cluster == 0
+    assert o.eig_warm_start == 1 and o.dk_tensor_cores == 1 and o.cg_cluster == 0 and o.loss_kind == 0
     # the ctypes struct and the C struct agree in size (every field marshalled)
     assert ctypes.sizeof(_abi.Options) == 72
     o = default_options("fp64")

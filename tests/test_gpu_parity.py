@@ -83,6 +83,59 @@ def test_maxcut_batch_forward_backward(precision):
     compare(gpu, ora, precision)
 
 
+def _compare_logratio(gpu, ora, precision, K):
+    """Log-residual loss: L sums K logs, each off by the relative error of
+    its ratio sum, so the mixed bound is K * 1e-4 absolute; gradients as for
+    the squared loss."""
+    tol_l = 1e-7 if precision == "fp64" else K * 1e-4
+    assert np.abs(gpu["loss"] - ora["loss"]).max() <= tol_l * max(1.0, np.abs(ora["loss"]).max()), \
+        (gpu["loss"], ora["loss"])
+    for k in ("grho", "galpha", "gx0", "gs0", "gy0"):
+        err = rel_inf(gpu[k], ora[k]) if precision == "fp64" else rel_l2(gpu[k], ora[k])
+        assert err < (1e-7 if precision == "fp64" else 1e-3), (k, err)
+
+
+@pytest.mark.parametrize("precision,ckpt", [("fp64", 0), ("fp64", 2), ("mixed", 0), ("mixed", 4)])
+def test_maxcut_logratio_loss(precision, ckpt):
+    """Log-residual meta-loss (loss_kind 1): the loss and every gradient,
+    with and without checkpointed recomputation of the trajectory."""
+    _need_gpu()
+    probs = maxcut_batch([3, 5, 8, 12, 17, 23], seed=111)
+    K = 6
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=17)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0, loss="logratio")
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, loss_kind=1, checkpoint_every=ckpt,
+                  cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not gpu["flags"].any(), gpu["flags"]
+    _compare_logratio(gpu, ora, precision, K)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_socp_logratio_loss(precision):
+    _need_gpu()
+    probs = socp_batch(3, seed=4200)
+    K = 5
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=19)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0, loss="logratio")
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, loss_kind=1,
+                  cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not (gpu["flags"] & 3).any(), gpu["flags"]
+    _compare_logratio(gpu, ora, precision, K)
+
+
+def test_logratio_edge_cones_zero_start():
+    """Every cone type, and a zero warm start (r_p^0 = -b, r_d^0 = q), plus an
+    instance without constraints (||r_p^0|| = 0, its term dropped): the same
+    loss and gradients as the oracle in FP64."""
+    _need_gpu()
+    probs = [edge_instance(5), unconstrained_instance(7), edge_instance(6)]
+    K = 3
+    rho, alpha, _, _, _ = random_inputs(probs, K, seed=23)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, None, None, None, loss="logratio")
+    gpu = run_gpu(probs, rho, alpha, None, None, None, "fp64", loss_kind=1, cg_tol=1e-12)
+    _compare_logratio(gpu, ora, "fp64", K)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_maxcut_large_block_tiles(precision):
     """A 41x41 PSD block exercises the 4x4 register tiles of the DK contractions."""
