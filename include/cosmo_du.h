@@ -312,16 +312,12 @@ cosmo_status cosmo_status_sync(cosmo_batch* batch, int32_t* flags_host);
  * `stream` and released before return.
  * Large instances: zero-start solves of fewer than 148 instances with more
  * than 1e5 nonzeros of A each on average run a grid-wide CG instead (row and
- * column tiles spread over all SMs).  When each instance's t (m_i reals) and
- * a column segment of z fit in shared memory, the arrays are 16-byte aligned
- * and the column indices increase along every row of A, the whole solve is
- * one cooperative launch (the Chronopoulos-Gear form of Jacobi-PCG: the same
- * iterates in exact arithmetic, one reduction point per iteration, grid
- * barriers between phases); otherwise three kernels per iteration gather
- * from global memory.  Both synchronise the stream before returning.  The
- * rows of instance i must only reference its own columns (other columns
- * read as zero in the cooperative path).  A grid barrier wait that does not
- * end within about one second returns E_TIMEOUT (x is then undefined).
+ * column tiles spread over all SMs): through a transient cosmo_pcg_plan
+ * (below) when one applies, else three kernels per iteration gathering from
+ * global memory.  Both synchronise the stream before returning.  The rows of
+ * instance i must only reference its own columns (other columns are dropped
+ * or read as zero).  A wait that does not end within about one second
+ * returns E_TIMEOUT (x is then undefined).
  * Errors: E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT. */
 cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_t m,
                              const int64_t* col_off, const int64_t* row_off,
@@ -331,6 +327,60 @@ cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_
                              double sigma, const void* rho, const void* rhs, void* x,
                              int32_t warm_start, double tol, int32_t max_iter, int32_t* iters,
                              void* stream);
+
+/* Prepared large-instance solves of the reduced system (Sec. 2.3's
+ * operator P + sigma I + A'D(rho)A at the App. B scale).  The paper has no
+ * counterpart: a plan does once, per matrix, the work that does not depend
+ * on rho, sigma or rhs, so that repeated solves (one per ADMM iteration, or
+ * per parameter update) stream A and A' at HBM bandwidth and allocate
+ * nothing.
+ *
+ * cosmo_pcg_plan_create copies A, A' and P (arguments as cosmo_pcg_solve,
+ * device memory, values in the precision's type) into a streaming layout
+ * owned by the plan: each row of A cut by column segment of its instance
+ * (and each row of A' by row segment), pieces padded with zeros to a
+ * multiple of 4 entries and 16-byte aligned.  The caller's arrays are not
+ * used after the call returns.  Rows of instance i must reference only its
+ * own columns (other entries are dropped).  Creation runs kernels on
+ * `stream` and synchronises it; it needs ninst <= the device's SM count and
+ * each instance's tiles to fit the kernel's shared memory, else E_INVAL
+ * ("not applicable"; cosmo_pcg_solve then takes its other paths).  The plan
+ * belongs to the device current at creation.  Errors: E_INVAL, E_NOMEM,
+ * E_CUDA.
+ *
+ * cosmo_pcg_plan_solve: x = (P + sigma I + A'D(rho)A)^-1 rhs from x = 0,
+ * Jacobi-PCG in its pipelined form (Ghysels & Vanroose: the iterates of
+ * textbook PCG in exact arithmetic, the dot products of an iteration formed
+ * alongside its matrix-vector product), stopping at ||r|| <= tol ||rhs|| or
+ * max_iter iterations; rho [m], rhs [n], x [n], iters [ninst] (or NULL) as
+ * in cosmo_pcg_solve.  One cooperative launch, one CTA per SM, A and A'
+ * streamed by bulk asynchronous copies; the result is bitwise reproducible.
+ * Synchronises the stream.  Calls on one plan must not overlap.  A wait
+ * that does not end within about one second returns E_TIMEOUT (x undefined).
+ * Errors: E_INVAL, E_CUDA, E_TIMEOUT. */
+typedef struct cosmo_pcg_plan cosmo_pcg_plan;
+typedef struct {
+  int32_t nseg_a;          /* column segments of each row of A */
+  int32_t nseg_at;         /* row segments of each row of A' */
+  int32_t grid;            /* CTAs of the persistent launch */
+  int32_t threads;         /* threads per CTA */
+  int64_t layout_bytes;    /* device bytes of the streaming copies of A and A' */
+  int64_t smem_bytes;      /* dynamic shared memory per CTA */
+  int64_t quads_a;         /* 4-entry groups streamed per pass over A (padding included) */
+  int64_t quads_at;        /* the same for A' */
+} cosmo_pcg_plan_info;
+cosmo_status cosmo_pcg_plan_create(int32_t precision, int32_t ninst, int64_t n, int64_t m,
+                                   const int64_t* col_off, const int64_t* row_off,
+                                   const int64_t* A_rowptr, const int32_t* A_col, const void* A_val,
+                                   const int64_t* AT_rowptr, const int32_t* AT_col,
+                                   const void* AT_val, const int64_t* P_rowptr,
+                                   const int32_t* P_col, const void* P_val, cosmo_pcg_plan** out,
+                                   void* stream);
+cosmo_status cosmo_pcg_plan_solve(cosmo_pcg_plan* plan, double sigma, const void* rho,
+                                  const void* rhs, void* x, double tol, int32_t max_iter,
+                                  int32_t* iters, void* stream);
+cosmo_status cosmo_pcg_plan_get_info(const cosmo_pcg_plan* plan, cosmo_pcg_plan_info* out);
+cosmo_status cosmo_pcg_plan_destroy(cosmo_pcg_plan* plan);
 
 /* The same solve as cosmo_pcg_solve, for callers that must not allocate device
  * memory while they run (a controller calling the solver at a fixed rate

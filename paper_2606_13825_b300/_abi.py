@@ -61,6 +61,12 @@ class BatchInfo(ctypes.Structure):
                 ("cg_solves", c_int64), ("adj_cg_iters", c_int64), ("adj_cg_solves", c_int64)]
 
 
+class PcgPlanInfo(ctypes.Structure):
+    _fields_ = [("nseg_a", c_int32), ("nseg_at", c_int32), ("grid", c_int32), ("threads", c_int32),
+                ("layout_bytes", c_int64), ("smem_bytes", c_int64), ("quads_a", c_int64),
+                ("quads_at", c_int64)]
+
+
 _SIGS = {
     "cosmo_version": (c_char_p, []),
     "cosmo_kernel_launch_count": (c_int64, []),
@@ -95,6 +101,12 @@ _SIGS = {
     "cosmo_pcg_solve_noalloc": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
                                 [c_double, c_void_p, c_void_p, c_void_p, c_int32, c_double,
                                  c_int32, c_void_p, c_void_p]),
+    "cosmo_pcg_plan_create": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
+                              [POINTER(c_void_p), c_void_p]),
+    "cosmo_pcg_plan_solve": (c_int32, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_double,
+                                       c_int32, c_void_p, c_void_p]),
+    "cosmo_pcg_plan_get_info": (c_int32, [c_void_p, POINTER(PcgPlanInfo)]),
+    "cosmo_pcg_plan_destroy": (c_int32, [c_void_p]),
     "cosmo_psd_project": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_psd_dk_backward": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),

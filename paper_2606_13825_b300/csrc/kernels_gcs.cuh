@@ -1,0 +1,838 @@
+// Streamed grid-wide CG for one or a few large instances of the reduced
+// system (P + sigma I + A'D(rho)A) x = rhs (Sec. 2.3) at the App. B scale,
+// where A and A' are far larger than L2 and every CG iteration streams both
+// from HBM once.
+//
+// Layout (built once per matrix by a plan, Sec. 2.3's operator is fixed
+// while rho, sigma and rhs change).  A gathers z over the instance's
+// columns, A' gathers t over its rows; a gathered vector that does not fit in
+// shared memory next to the streaming buffers is cut into `nseg` equal
+// segments.  Each source row is stored once per segment with the entries
+// whose index falls in that segment (original order), padded with zero
+// values to a multiple of 4 entries ("quads"): a quad never holds two rows.
+// qp[h][r] is the first quad of row r's piece in segment h (absolute).
+// Quads are stored in chunks of gcs_cq() quads, each chunk one contiguous
+// block [values of its quads | column indices of its quads], and the last
+// row of every tile is padded to a whole chunk: a tile's piece of a segment
+// is a run of whole chunks, and each chunk arrives with one bulk copy of
+// 1 KB (float) -- the TMA engine sustains HBM bandwidth with 1 KB requests
+// from 31 warps, but only about 60% of it with 512-byte ones.
+//
+// Kernel: one CTA per SM, 31 streaming warps and one control warp.  Each
+// streaming warp owns an equal share of its tile's quads per segment and
+// streams them through a private ring of GCS_NSLOT chunk buffers filled by
+// bulk asynchronous copies (cp.async.bulk, the TMA engine; completion on an
+// mbarrier per buffer).  Data in flight lands in shared memory, not in L1,
+// so staging the gathered vector in shared memory does not cut the loads in
+// flight, and a warp keeps two chunks in flight while it works on a third.
+// A lane takes one quad (float) or half a quad (double), gathers from the
+// staged vector, and a segmented warp scan over the lanes' row indices sums
+// each row piece in a fixed order (bitwise reproducible).  The row a warp's
+// share starts inside is summed into a per-warp slot and added after the
+// segment in warp order.
+//
+// Iteration: Jacobi-PCG in the Chronopoulos-Gear arrangement (the iterates
+// of textbook PCG in exact arithmetic; s = M p kept by recurrence), with the
+// one dot product that needs the matrix-vector product, delta = z'Mz, formed
+// from the row phase as sigma ||z||^2 + z'Pz + sum_r rho_r (Az)_r^2:
+//
+//   R:  t = rho o (A z),  partial sum rho (Az)^2, P z and sigma z'z + z'Pz
+//       (z staged per column segment)
+//   C:  alpha = gamma / (delta - beta gamma / alpha_old)   (control warp)
+//       w = sigma z + P z + A't                  (t staged per row segment)
+//       s = w + beta s, p = z + beta p, x += alpha p, r -= alpha s,
+//       z = D^-1 r, partial r'z (gamma) and r'r of the CTA's columns
+//
+// so the update runs in the epilogue of the A' phase and an iteration has two
+// grid barriers (after R, after C).  (The pipelined form of Ghysels and
+// Vanroose would also give two barriers, but its recurrences for M u and
+// M q amplify the rounding of an FP32 matrix-vector product by about 1.3
+// per iteration on the App. B systems and break down within tens of
+// iterations.)  The control warp sums the partials published before the last
+// barrier while the streaming warps stream: gamma, r'r and the stop test in
+// R, delta and alpha in C.  Every CTA forms every instance's scalars in the
+// same order (identical values and stop decisions, no atomics).  The stop
+// test ||r|| <= tol ||rhs|| is taken in R on the residual of the last update,
+// so the R phase of the stopping iteration is discarded.  Every wait is
+// bounded in clock cycles; a wait that gives up sets the error word, waits
+// (bounded) for this CTA's copies in flight and returns.
+#pragma once
+
+#include "kernels_gcg.cuh"
+#include "kernels_tc.cuh"
+
+namespace cosmo {
+
+namespace bulk {
+
+// one bulk copy global -> shared memory of this CTA (TMA engine); `bytes` a
+// multiple of 16, both addresses 16-byte aligned; completion counted on mbar
+__device__ __forceinline__ void copy(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar)) : "memory");
+}
+
+// arrive on mbar (count 1) and expect `bytes` of transactions in this phase
+__device__ __forceinline__ void expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+               :: "r"(tc::smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// order this thread's generic-proxy accesses before later async-proxy ones
+__device__ __forceinline__ void fence_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// wait for the phase of the given parity; false after `limit` clock cycles.
+// Each try may suspend the thread for up to 10 us until the phase completes
+// (the warp gives its issue slots to the others instead of spinning).
+__device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity, long long limit) {
+  long long t0 = 0;
+  for (int k = 0;; ++k) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(tc::smem_u32(mbar)), "r"(parity), "r"(10000u) : "memory");
+    if (done) return true;
+    if (k == 0) t0 = clock64();
+    else if (clock64() - t0 > limit) return false;
+  }
+}
+
+}  // namespace bulk
+
+// Grid barrier over all CTAs of the cooperative launch: a fire-and-forget
+// release add to one counter, then thread 0 polls it with acquire loads until
+// it reaches epoch * gridDim.x (the counter only grows; zero at launch).
+// Gives up after `limit` clock cycles or when the error word is set.
+__device__ __forceinline__ bool gcs_grid_barrier(unsigned* ctr, int32_t* err, long long limit, unsigned& epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    const unsigned target = epoch * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(ctr) : "memory");
+    int ok = 1;
+    long long t0 = 0;
+    for (int k = 0;; ++k) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (k == 0) t0 = clock64();
+      if ((k & 63) == 63) {
+        int e;
+        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
+        if (e != 0 || clock64() - t0 > limit) {
+          asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" :: "l"(err), "r"(1) : "memory");
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+constexpr int GCS_WARPS = 31;                    // streaming warps
+constexpr int GCS_NT = 32 * GCS_WARPS + 32;      // + the control warp (1024 threads, 64 registers each)
+constexpr int GCS_NSLOT = 3;                     // chunk buffers per streaming warp
+// quads per chunk: 128 float or 64 double entries (32 lanes x 16 bytes of values)
+template <class T> __host__ __device__ constexpr int gcs_cq() { return sizeof(T) == 4 ? 32 : 16; }
+template <class T> __host__ __device__ constexpr int gcs_vbytes() { return gcs_cq<T>() * 4 * (int)sizeof(T); }
+template <class T> __host__ __device__ constexpr int gcs_slot() { return gcs_vbytes<T>() + gcs_cq<T>() * 16; }
+
+// segment h of a gathered range [o0, o1) cut into nseg equal parts
+__host__ __device__ inline void gcs_seg(int64_t o0, int64_t o1, int nseg, int h, int64_t& lo, int64_t& hi) {
+  const int64_t len = o1 - o0, ws = (len + nseg - 1) / nseg;
+  lo = o0 + (h * ws < len ? h * ws : len);
+  hi = o0 + ((h + 1) * ws < len ? (h + 1) * ws : len);
+}
+
+__host__ __device__ inline int64_t gcs_al(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// byte offsets into the kernel's dynamic shared memory; every region starts
+// on a 16-byte boundary (the mbarriers and the int64 / double tables need 8,
+// the bulk-copy destinations 16)
+struct GcsSmem {
+  int64_t o_ring, o_mbar, o_stage, o_ps, o_ns, o_sp, o_rho, o_epi, o_headv, o_headr, o_qend_r, o_qend_c, o_qb_r,
+      o_qb_c, o_scal, total;
+};
+
+template <class T>
+__host__ __device__ inline GcsSmem gcs_smem(int64_t stage_len, int64_t RT, int64_t CT, int nsr, int nsc,
+                                            int ninst) {
+  GcsSmem s{};
+  int64_t o = 0;
+  s.o_ring = o;   o += (int64_t)GCS_WARPS * GCS_NSLOT * gcs_slot<T>();
+  s.o_mbar = o;   o = gcs_al(o + 8 * (GCS_WARPS * GCS_NSLOT + 1), 128);
+  s.o_stage = o;  o += gcs_al(stage_len * (int64_t)sizeof(T), 16);
+  s.o_ps = o;     o += gcs_al(RT * (int64_t)sizeof(T), 16);
+  s.o_ns = o;     o += gcs_al(CT * (int64_t)sizeof(T), 16);
+  s.o_sp = o;     o += gcs_al(CT * (int64_t)sizeof(T), 16);
+  s.o_rho = o;    o += gcs_al(RT * (int64_t)sizeof(T), 16);
+  s.o_epi = o;    o += gcs_al(6 * CT * (int64_t)sizeof(T), 16);
+  s.o_headv = o;  o += gcs_al(GCS_WARPS * (int64_t)sizeof(T), 16);
+  s.o_headr = o;  o += gcs_al(GCS_WARPS * 4, 16);
+  s.o_qend_r = o; o += gcs_al((int64_t)nsr * RT * 4, 16);
+  s.o_qend_c = o; o += gcs_al((int64_t)nsc * CT * 4, 16);
+  s.o_qb_r = o;   o += gcs_al(8 * (int64_t)nsr, 16);
+  s.o_qb_c = o;   o += gcs_al(8 * (int64_t)nsc, 16);
+  s.o_scal = o;   o += (int64_t)ninst * (int64_t)sizeof(GcgScal);
+  s.total = gcs_al(o, 16);
+  return s;
+}
+
+template <class T>
+struct GcsLayout {
+  const unsigned char* data;  // [quads / gcs_cq] chunks of gcs_chunk_bytes; padding
+                              // entries: value 0, the segment's first index
+  const int64_t* qp;          // [nseg][rows + 1] absolute first quad of each row piece
+  int32_t nseg;
+  int64_t rows;
+};
+
+template <class T> __host__ __device__ constexpr int gcs_chunk_bytes() { return gcs_slot<T>(); }
+
+// byte offsets of entry e's value and column index in a layout
+template <class T> __host__ __device__ inline int64_t gcs_val_at(int64_t e) {
+  const int64_t q = e >> 2;
+  return (q / gcs_cq<T>()) * gcs_chunk_bytes<T>() + (q % gcs_cq<T>()) * 4 * (int64_t)sizeof(T) + (e & 3) * (int64_t)sizeof(T);
+}
+template <class T> __host__ __device__ inline int64_t gcs_col_at(int64_t e) {
+  const int64_t q = e >> 2;
+  return (q / gcs_cq<T>()) * gcs_chunk_bytes<T>() + gcs_vbytes<T>() + (q % gcs_cq<T>()) * 16 + (e & 3) * 4;
+}
+
+template <class T>
+struct GcsArgs {
+  GcsLayout<T> LR;       // rows of A by column segment (R phase)
+  GcsLayout<T> LC;       // rows of A' by row segment (C phase)
+  const T* rhs; T* x; const T* rho; const T* dinv; double sigma;
+  T *r, *z, *p, *s, *t;  // z and t padded to whole 16-byte groups
+  double* part_r;        // [nrt] sum rho (Az)^2 of the row tile
+  double* part_d;        // [nct] sigma z'z + z'Pz of the column tile
+  double* part_c;        // [2][2][nct] r'z, r'r of the column tile (by iteration parity)
+  const int32_t* irt_lo; // [ninst] first row tile of the instance
+  const int32_t* irt_hi; // [ninst] one past its last row tile
+  int32_t* iters;        // [ninst] or null
+  double tol;
+  int32_t maxit;
+  int32_t short_p;       // P rows of at most 16 entries
+  int32_t RT, CT;        // largest row / column tile
+  GcsSmem sm;
+  long long wait_limit;  // clock cycles one wait may take
+};
+
+// ---- plan-time layout construction ----------------------------------------
+
+// cnt[h * rows + r] = entries of row r whose index lies in segment h of the
+// row's instance (indices outside the instance are dropped); one warp per row
+__global__ void k_gcs_count(int64_t rows, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            int32_t ninst, const int64_t* __restrict__ row_inst_off,
+                            const int64_t* __restrict__ gath_off, int32_t nseg, int32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  int lo = 0, hi = ninst;   // instance of row r
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (row_inst_off[mid] <= r) lo = mid; else hi = mid;
+  }
+  const int64_t o0 = gath_off[lo], o1 = gath_off[lo + 1];
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int h = 0; h < nseg; ++h) {
+    int64_t s0, s1;
+    gcs_seg(o0, o1, nseg, h, s0, s1);
+    int c = 0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+      const int64_t k = ci[e];
+      c += (k >= s0 && k < s1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[(int64_t)h * rows + r] = c;
+  }
+}
+
+// stable compaction of each row's entries into its piece of every segment,
+// then zero padding to the piece's end; one warp per row
+template <class T>
+__global__ void k_gcs_scatter(int64_t rows, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const T* __restrict__ v, int32_t ninst, const int64_t* __restrict__ row_inst_off,
+                              const int64_t* __restrict__ gath_off, int32_t nseg, const int64_t* __restrict__ qp,
+                              unsigned char* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  int lo = 0, hi = ninst;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (row_inst_off[mid] <= r) lo = mid; else hi = mid;
+  }
+  const int64_t o0 = gath_off[lo], o1 = gath_off[lo + 1];
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int h = 0; h < nseg; ++h) {
+    int64_t s0, s1;
+    gcs_seg(o0, o1, nseg, h, s0, s1);
+    const int64_t* q = qp + (int64_t)h * (rows + 1);
+    int64_t pos = 4 * q[r];
+    const int64_t end = 4 * q[r + 1];
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+      const int64_t e = eb + lane;
+      int32_t k = 0;
+      bool in = false;
+      if (e < e1) {
+        k = ci[e];
+        in = k >= s0 && k < s1;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int64_t at = pos + __popc(mask & ((1u << lane) - 1u));
+        *reinterpret_cast<T*>(out + gcs_val_at<T>(at)) = v[e];
+        *reinterpret_cast<int32_t*>(out + gcs_col_at<T>(at)) = k;
+      }
+      pos += __popc(mask);
+    }
+    for (int64_t at = pos + lane; at < end; at += 32) {
+      *reinterpret_cast<T*>(out + gcs_val_at<T>(at)) = T(0);
+      *reinterpret_cast<int32_t*>(out + gcs_col_at<T>(at)) = (int32_t)s0;
+    }
+  }
+}
+
+// d_j = P_jj + sigma + sum_e v_e^2 rho_{c_e} over row j of A' (the layout's
+// pieces; padding contributes zero); one warp per column
+template <class T>
+__global__ void k_gcs_precond(int64_t n, GcsLayout<T> LC, const int64_t* __restrict__ P_rp,
+                              const int32_t* __restrict__ P_ci, const T* __restrict__ P_v, double sigma,
+                              const T* __restrict__ rho, T* __restrict__ dinv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= n) return;
+  T acc = T(0);
+  for (int h = 0; h < LC.nseg; ++h) {
+    const int64_t* q = LC.qp + (int64_t)h * (n + 1);
+    for (int64_t e = 4 * q[j] + lane; e < 4 * q[j + 1]; e += 32) {
+      const T a = *reinterpret_cast<const T*>(LC.data + gcs_val_at<T>(e));
+      acc += a * a * rho[*reinterpret_cast<const int32_t*>(LC.data + gcs_col_at<T>(e))];
+    }
+  }
+  T pd = T(0);
+  if (P_rp) {
+    for (int64_t e = P_rp[j] + lane; e < P_rp[j + 1]; e += 32)
+      if (P_ci[e] == j) pd += P_v[e];
+  }
+  acc += pd;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const T d = acc + (T)sigma;
+    dinv[j] = d > T(0) ? T(1) / d : T(0);
+  }
+}
+
+// ---- the solve --------------------------------------------------------------
+
+template <class T>
+__global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles G, GcsArgs<T> S, GridBar B) {
+  extern __shared__ __align__(128) unsigned char gcs_dyn[];
+  constexpr int CQ = gcs_cq<T>();
+  constexpr int VB = gcs_vbytes<T>();
+  constexpr int SLOT = gcs_slot<T>();
+  constexpr int E = 16 / (int)sizeof(T);          // elements per 16-byte group
+  constexpr int UPQ = sizeof(T) == 4 ? 1 : 2;     // lanes per quad
+  // shared-memory arrays, addressed from the offsets each time they are
+  // used (kernel parameters: no registers held across the loops)
+#define GCS_AT(type, field) reinterpret_cast<type*>(gcs_dyn + S.sm.field)
+#define ring GCS_AT(unsigned char, o_ring)
+#define mbar GCS_AT(uint64_t, o_mbar)
+#define mstage (GCS_AT(uint64_t, o_mbar) + GCS_WARPS * GCS_NSLOT)
+#define stage GCS_AT(T, o_stage)
+#define ps GCS_AT(T, o_ps)
+#define ns GCS_AT(T, o_ns)
+#define sP GCS_AT(T, o_sp)
+#define rho_s GCS_AT(T, o_rho)
+#define epi GCS_AT(T, o_epi)
+#define headv GCS_AT(T, o_headv)
+#define headr GCS_AT(int32_t, o_headr)
+#define qend_r GCS_AT(int32_t, o_qend_r)
+#define qend_c GCS_AT(int32_t, o_qend_c)
+#define qb_r GCS_AT(int64_t, o_qb_r)
+#define qb_c GCS_AT(int64_t, o_qb_c)
+#define sc GCS_AT(GcgScal, o_scal)
+  __shared__ double red[3][GCS_WARPS + 1];   // one per warp, control warp included
+  __shared__ int s_done, s_err;
+
+  const int b = blockIdx.x, ninst = P.ninst;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const bool streamer = wp < GCS_WARPS;
+  const bool has_c = b < G.nct, has_r = b < G.nrt;
+  const int cinst = has_c ? G.ct_inst[b] : 0, rinst = has_r ? G.rt_inst[b] : 0;
+  const int64_t clo = has_c ? G.ct_lo[b] : 0, chi = has_c ? G.ct_hi[b] : 0;
+  const int64_t rlo = has_r ? G.rt_lo[b] : 0, rhi = has_r ? G.rt_hi[b] : 0;
+  const int nr = (int)(rhi - rlo), nc = (int)(chi - clo);
+  const int nsr = S.LR.nseg, nsc = S.LC.nseg, nsg = nsr + nsc;
+  const int64_t m_tot = P.m_total, n_tot = P.n_total;
+
+  // ---- per-CTA tables (fixed for the whole solve) ----
+  for (int h = 0; h < nsr; ++h) {
+    const int64_t* q = S.LR.qp + (int64_t)h * (m_tot + 1);
+    const int64_t base = has_r ? q[rlo] : 0;
+    if (threadIdx.x == 0) qb_r[h] = base;
+    for (int k = threadIdx.x; k < nr; k += GCS_NT) qend_r[h * S.RT + k] = (int32_t)(q[rlo + k + 1] - base);
+  }
+  for (int h = 0; h < nsc; ++h) {
+    const int64_t* q = S.LC.qp + (int64_t)h * (n_tot + 1);
+    const int64_t base = has_c ? q[clo] : 0;
+    if (threadIdx.x == 0) qb_c[h] = base;
+    for (int k = threadIdx.x; k < nc; k += GCS_NT) qend_c[h * S.CT + k] = (int32_t)(q[clo + k + 1] - base);
+  }
+  for (int k = threadIdx.x; k < nr; k += GCS_NT) { rho_s[k] = S.rho[rlo + k]; ps[k] = T(0); }
+  for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
+  for (int i = threadIdx.x; i < ninst; i += GCS_NT) {
+    sc[i].state = 0;
+    sc[i].alpha = sc[i].alpha_old = sc[i].beta = sc[i].gamma = sc[i].gamma_old = 0.0;
+    sc[i].delta = sc[i].rr = sc[i].bb = 0.0;
+  }
+  if (streamer && lane == 0)
+    for (int k = 0; k < GCS_NSLOT; ++k) tc::mbar_init(mbar + wp * GCS_NSLOT + k, 1);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(mstage, 1);
+    s_done = 0;
+    s_err = 0;
+  }
+  bulk::fence_init();
+  __syncthreads();
+
+  // segment sidx: quads of the CTA's tile and its table
+  // (a tile's quads, and so its chunks, fit 31 bits: qend is int32)
+  auto seg_total = [&](int sidx) -> int32_t {
+    if (sidx < nsr) return nr > 0 ? qend_r[sidx * S.RT + nr - 1] : 0;
+    return nc > 0 ? qend_c[(sidx - nsr) * S.CT + nc - 1] : 0;
+  };
+  auto warp_chunks = [&](int sidx, int32_t& c0, int32_t& c1) {
+    const int64_t nch = (seg_total(sidx) + CQ - 1) / CQ;
+    c0 = (int32_t)(nch * wp / GCS_WARPS);
+    c1 = (int32_t)(nch * (wp + 1) / GCS_WARPS);
+  };
+
+  // ---- producer: this warp's chunks over all segments, cyclically ----
+  // (p_val / p_col: the producer segment's first quad of the CTA's tile)
+  int p_sidx = 0;
+  int32_t p_c = 0, p_c1 = 0;
+  const unsigned char* p_src = nullptr;   // the producer segment's first chunk of the tile
+  bool any_chunks = false;
+  if (streamer) {
+    for (int sidx = 0; sidx < nsg; ++sidx) {
+      int32_t c0, c1;
+      warp_chunks(sidx, c0, c1);
+      any_chunks |= c1 > c0;
+    }
+    p_sidx = nsg - 1;   // advance() moves to segment 0
+  }
+  auto advance = [&]() {
+    ++p_c;
+    while (p_c >= p_c1) {
+      p_sidx = p_sidx + 1 == nsg ? 0 : p_sidx + 1;
+      warp_chunks(p_sidx, p_c, p_c1);
+      const bool isr = p_sidx < nsr;
+      const int h = isr ? p_sidx : p_sidx - nsr;
+      const int64_t q0 = isr ? qb_r[h] : qb_c[h];   // a whole number of chunks
+      p_src = (isr ? S.LR.data : S.LC.data) + (q0 / CQ) * SLOT;
+    }
+  };
+  unsigned char* const wring = ring + wp * GCS_NSLOT * SLOT;   // this warp's buffers
+  uint64_t* const wmbar = mbar + wp * GCS_NSLOT;
+  // lane 0 issues the producer's current chunk (always whole) into `slot`
+  // with one bulk copy, then advances
+  auto issue = [&](int slot) {
+    if (lane == 0) {
+      bulk::fence_shared();
+      bulk::expect(wmbar + slot, SLOT);
+      bulk::copy(wring + slot * SLOT, p_src + (int64_t)p_c * SLOT, SLOT, wmbar + slot);
+    }
+    advance();
+  };
+  int rslot = 0;          // next buffer to consume and the parity of its phase
+  uint32_t rphase = 0;
+  if (streamer && any_chunks) {
+    advance();
+    for (int k = 0; k < GCS_NSLOT; ++k) issue(k);
+  }
+  uint32_t stage_uses = 0;
+  bool bad = false;       // a wait of this thread gave up
+
+  // drain this warp's chunks in flight (GCS_NSLOT of them), then leave
+  auto drain = [&]() {
+    if (streamer && any_chunks) {
+      for (int k = 0; k < GCS_NSLOT; ++k) {
+        const int sl = rslot + k;
+        bulk::wait(wmbar + (sl >= GCS_NSLOT ? sl - GCS_NSLOT : sl), rphase ^ (sl >= GCS_NSLOT ? 1u : 0u),
+                   S.wait_limit);
+      }
+    }
+  };
+  auto fail = [&]() {
+    bad = true;
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device> e(*B.err);
+    e.store(1, cuda::memory_order_relaxed);
+    s_err = 1;
+  };
+
+  // stage gathered[lo, hi) (16-byte groups) into shared memory: thread 0
+  // issues the copy, the streaming threads wait in stage_wait.  Returns the
+  // group-aligned base index.
+  auto stage_issue = [&](const T* src, int64_t lo, int64_t hi) -> int32_t {
+    const int64_t gb = lo & ~(int64_t)(E - 1);
+    const int64_t bytes = gcs_al(hi - gb, E) * (int64_t)sizeof(T);
+    if (hi > lo && threadIdx.x == 0) {
+      bulk::fence_global();
+      bulk::fence_shared();
+      bulk::expect(mstage, (uint32_t)bytes);
+      for (int64_t o = 0; o < bytes; o += 32768)
+        bulk::copy(reinterpret_cast<unsigned char*>(stage) + o, reinterpret_cast<const unsigned char*>(src + gb) + o,
+                   (uint32_t)min((int64_t)32768, bytes - o), mstage);
+    }
+    return (int32_t)gb;
+  };
+  auto stage_wait = [&](int64_t lo, int64_t hi) {
+    if (hi <= lo) return;
+    if (streamer && !bad && !bulk::wait(mstage, stage_uses & 1, S.wait_limit)) fail();
+    ++stage_uses;
+  };
+
+  // consume this warp's chunks of segment sidx: acc[k] += row piece sums of
+  // the tile's rows (relative index k), gathered from stage (base gb).
+  // Lanes keep running sums of the current row (acc0) and the next (acc1);
+  // a row's lanes are summed (fixed butterfly) when the row ends.  A chunk
+  // spanning three or more rows takes a segmented scan instead.  The order
+  // of every sum is fixed by the layout: results are bitwise reproducible.
+  auto consume = [&](int sidx, const int32_t* qend, int nrow, T* acc, int32_t gb) {
+    int32_t c0, c1;
+    warp_chunks(sidx, c0, c1);
+    if (lane == 0) headr[wp] = -1;
+    if (c0 >= c1) return;
+    // the row holding the warp's first quad, and whether it began earlier
+    const int32_t qw = c0 * CQ;
+    int lo = 0, hi = nrow - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (qend[mid] > qw) hi = mid; else lo = mid + 1;
+    }
+    const int hrow = lo;
+    const bool hstart = (hrow > 0 ? qend[hrow - 1] : 0) < qw;
+    if (lane == 0) {
+      headv[wp] = T(0);
+      headr[wp] = hstart ? hrow : -1;
+    }
+    __syncwarp();
+    const T* st = stage - gb;
+    const int32_t qt = seg_total(sidx);
+    const int quad = lane / UPQ;
+    int rrow = hrow;
+    T acc0 = T(0), acc1 = T(0);
+    auto target = [&](int row) { return (hstart && row == hrow) ? headv + wp : acc + row; };
+    for (int32_t c = c0; c < c1; ++c) {
+      if (!bad && !bulk::wait(wmbar + rslot, rphase, S.wait_limit)) fail();
+      if (bad) return;
+      const unsigned char* buf = wring + rslot * SLOT;
+      const int32_t cq = c * CQ;
+      const int nq = min(CQ, qt - cq);
+      const bool valid = quad < nq;
+      T d = T(0);
+      int k = 0x7fffffff;
+      if (valid) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = reinterpret_cast<const float4*>(buf)[lane];
+          const int4 ci = reinterpret_cast<const int4*>(buf + VB)[lane];
+          d = v.x * st[ci.x] + v.y * st[ci.y] + v.z * st[ci.z] + v.w * st[ci.w];
+        } else {
+          const double2 v = reinterpret_cast<const double2*>(buf)[lane];
+          const int2 ci = reinterpret_cast<const int2*>(buf + VB)[lane];
+          d = v.x * st[ci.x] + v.y * st[ci.y];
+        }
+        k = rrow;
+        while (k < nrow - 1 && qend[k] <= cq + quad) ++k;
+      }
+      const int kl = __shfl_sync(0xffffffffu, k, nq * UPQ - 1);   // row of the chunk's last quad
+      if (kl <= rrow + 1) {
+        if (k == rrow) acc0 += d; else acc1 += d;   // (invalid lanes add d = 0)
+        if (kl > rrow) {                             // row rrow ended inside the chunk
+          const T sum = warp_allsum(acc0);
+          if (lane == 0) *target(rrow) += sum;
+          acc0 = acc1;
+          acc1 = T(0);
+          rrow = kl;
+        }
+        if (qend[rrow] == cq + nq) {                 // row rrow ends with the chunk
+          const T sum = warp_allsum(acc0);
+          if (lane == 0) *target(rrow) += sum;
+          acc0 = T(0);
+          if (rrow < nrow - 1) ++rrow;
+        }
+      } else {
+        // three or more rows: the running sum first, then a segmented
+        // inclusive scan over the lanes keyed by row
+        const T sum = warp_allsum(acc0);
+        if (lane == 0) *target(rrow) += sum;
+        acc0 = T(0);
+        __syncwarp();
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const T up = __shfl_up_sync(0xffffffffu, d, o);
+          const int ku = __shfl_up_sync(0xffffffffu, k, o);
+          if (lane >= o && ku == k) d += up;
+        }
+        const int knext = __shfl_down_sync(0xffffffffu, k, 1);
+        if (valid && (lane == 31 || knext != k)) *target(k) += d;
+        __syncwarp();
+        rrow = kl;
+      }
+      if (++rslot == GCS_NSLOT) { rslot = 0; rphase ^= 1u; }
+      __syncwarp();
+      issue(rslot == 0 ? GCS_NSLOT - 1 : rslot - 1);
+    }
+    // the running sum of the last row (it continues in the next warp's share)
+    const T sum = warp_allsum(acc0);
+    if (lane == 0 && sum != T(0)) *target(rrow) += sum;
+    __syncwarp();
+  };
+
+  // add the warps' head slots in warp order (one thread), after the segment
+  auto fixup = [&](T* acc) {
+    if (threadIdx.x == 0)
+      for (int w2 = 0; w2 < GCS_WARPS; ++w2)
+        if (headr[w2] >= 0) acc[headr[w2]] += headv[w2];
+  };
+
+  // R (control warp): gamma and r'r of the last update, the stop test, beta
+  auto control_r = [&](int it) {
+    const double* pc = S.part_c + (int64_t)(it & 1) * 2 * G.nct;
+    int running = 0;
+    for (int i = 0; i < ninst; ++i) {
+      if (sc[i].state != 0) continue;
+      double g = 0.0, rr = 0.0;
+      for (int k = G.it_lo[i] + lane; k < G.it_hi[i]; k += 32) {
+        g += __ldcg(pc + k);
+        rr += __ldcg(pc + G.nct + k);
+      }
+      g = warp_sum(g);
+      rr = warp_sum(rr);
+      if (lane == 0) {
+        GcgScal& c = sc[i];
+        if (it == 0) c.bb = rr;
+        int stt = 0;
+        if (rr <= S.tol * S.tol * c.bb || !(rr == rr)) stt = 1;
+        else if (it >= S.maxit) stt = 2;
+        if (stt) {
+          c.state = stt;
+          if (b == 0 && S.iters) S.iters[i] = it;
+        } else {
+          c.beta = it > 0 && c.gamma_old != 0.0 ? g / c.gamma_old : 0.0;
+          c.gamma = g;
+          c.rr = rr;
+        }
+      }
+      __syncwarp();
+      running += sc[i].state == 0;
+    }
+    if (lane == 0) s_done = running == 0;
+  };
+  // C (control warp): delta = z'Mz from the R partials, alpha
+  auto control_c = [&](int it) {
+    for (int i = 0; i < ninst; ++i) {
+      if (sc[i].state != 0) continue;
+      double dl = 0.0;
+      for (int k = S.irt_lo[i] + lane; k < S.irt_hi[i]; k += 32) dl += __ldcg(S.part_r + k);
+      for (int k = G.it_lo[i] + lane; k < G.it_hi[i]; k += 32) dl += __ldcg(S.part_d + k);
+      dl = warp_sum(dl);
+      if (lane == 0) {
+        GcgScal& c = sc[i];
+        const double den = dl - (it > 0 && c.alpha_old != 0.0 ? c.beta * c.gamma / c.alpha_old : 0.0);
+        c.delta = dl;
+        c.alpha = den > 0.0 ? c.gamma / den : 0.0;
+        c.alpha_old = c.alpha;
+        c.gamma_old = c.gamma;
+      }
+      __syncwarp();
+    }
+  };
+
+  // CTA sum of two per-thread values in a fixed order (warp sums in T, the
+  // 32 warps combined in double by warp 0); thread 0 gets the totals
+  auto cta_sum2 = [&](T v0, T v1, double& t0, double& t1) {
+    v0 = warp_allsum(v0);
+    v1 = warp_allsum(v1);
+    if (lane == 0) { red[0][wp] = (double)v0; red[1][wp] = (double)v1; }
+    __syncthreads();
+    if (wp == 0) {
+      t0 = warp_sum(red[0][lane]);
+      t1 = warp_sum(red[1][lane]);
+    }
+  };
+
+  auto leave = [&]() {
+    drain();
+    if (bad && threadIdx.x == 0 && stage_uses > 0) bulk::wait(mstage, (stage_uses - 1) & 1, S.wait_limit);
+  };
+
+  const int64_t r_c0 = has_r ? P.col_off[rinst] : 0, r_c1 = has_r ? P.col_off[rinst + 1] : 0;
+  const int64_t c_r0 = has_c ? P.row_off[cinst] : 0, c_r1 = has_c ? P.row_off[cinst + 1] : 0;
+
+  // ---- zero start: x = 0, r = rhs, z = D^-1 rhs, p = s = 0; r'z, r'r ----
+  {
+    T a0 = T(0), a1 = T(0);
+    for (int64_t j = clo + threadIdx.x; j < chi; j += GCS_NT) {
+      const T bj = S.rhs[j], zj = S.dinv[j] * bj;
+      S.x[j] = T(0); S.r[j] = bj; S.z[j] = zj; S.p[j] = T(0); S.s[j] = T(0);
+      a0 += bj * zj;
+      a1 += bj * bj;
+    }
+    double t0 = 0.0, t1 = 0.0;
+    cta_sum2(a0, a1, t0, t1);
+    if (threadIdx.x == 0 && has_c) { S.part_c[b] = t0; S.part_c[G.nct + b] = t1; }
+  }
+  unsigned epoch = 0;
+  if (!gcs_grid_barrier(B.arrive, B.err, B.limit, epoch)) { leave(); return; }
+
+  for (int it = 0;; ++it) {
+    // ---- R: t = rho o (A z), one column segment of z at a time; P z ----
+    // (the first segment's stage copy runs while P z is formed)
+    int64_t slo = 0, shi = 0;
+    int32_t gb0 = 0;
+    if (has_r) {
+      gcs_seg(r_c0, r_c1, nsr, 0, slo, shi);
+      gb0 = stage_issue(S.z, slo, shi);
+    }
+    gcg_p_part(P, G, clo, chi, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(S.z + c) : T(0); }, sP);
+    for (int h = 0; h < nsr; ++h) {
+      int32_t gb = gb0;
+      if (h > 0) __syncthreads();   // the stage buffer is free
+      if (has_r) {
+        if (h > 0) {
+          gcs_seg(r_c0, r_c1, nsr, h, slo, shi);
+          gb = stage_issue(S.z, slo, shi);
+        }
+        stage_wait(slo, shi);
+      }
+      if (streamer) {
+        if (has_r && !bad) consume(h, qend_r + h * S.RT, nr, ps, gb);
+      } else if (h == 0) {
+        control_r(it);
+        // the epilogues' operands of the CTA's columns: z, s, p, x, r, D^-1
+        // (unchanged until the update at the end of C)
+        const int CTs = S.CT;
+        for (int k = lane; k < nc; k += 32) {
+          const int64_t j = clo + k;
+          const T zj = S.z[j], sj = S.s[j], pj = S.p[j], xj = S.x[j], rj = S.r[j], dj = S.dinv[j];
+          epi[k] = zj; epi[CTs + k] = sj; epi[2 * CTs + k] = pj;
+          epi[3 * CTs + k] = xj; epi[4 * CTs + k] = rj; epi[5 * CTs + k] = dj;
+        }
+      }
+      __syncthreads();
+      if (s_err) { leave(); return; }
+      if (has_r) fixup(ps);
+    }
+    __syncthreads();
+    if (s_done) { leave(); return; }
+    {
+      // t = rho o Az; partials sum rho (Az)^2 (rows), sigma z'z + z'Pz (columns)
+      T a0 = T(0), a1 = T(0);
+      for (int k = threadIdx.x; k < nr; k += GCS_NT) {
+        const T az = ps[k], tk = rho_s[k] * az;
+        S.t[rlo + k] = tk;
+        a0 += tk * az;
+        ps[k] = T(0);
+      }
+      const T sig = (T)S.sigma;
+      for (int k = threadIdx.x; k < nc; k += GCS_NT) {
+        const T zj = epi[k];
+        a1 += zj * (sig * zj + sP[k]);
+      }
+      double t0 = 0.0, t1 = 0.0;
+      cta_sum2(a0, a1, t0, t1);
+      if (threadIdx.x == 0) {
+        if (has_r) S.part_r[b] = t0;
+        if (has_c) S.part_d[b] = t1;
+      }
+    }
+    if (!gcs_grid_barrier(B.arrive, B.err, B.limit, epoch)) { leave(); return; }
+
+    // ---- C: w = sigma z + P z + A't, one row segment of t at a time ----
+    for (int h = 0; h < nsc; ++h) {
+      __syncthreads();
+      int32_t gb = 0;
+      if (has_c) {
+        int64_t lo, hi;
+        gcs_seg(c_r0, c_r1, nsc, h, lo, hi);
+        gb = stage_issue(S.t, lo, hi);
+        stage_wait(lo, hi);
+      }
+      if (streamer) {
+        if (has_c && !bad) consume(nsr + h, qend_c + h * S.CT, nc, ns, gb);
+      } else if (h == 0) {
+        control_c(it);
+      }
+      __syncthreads();
+      if (s_err) { leave(); return; }
+      if (has_c) fixup(ns);
+    }
+    __syncthreads();
+
+    // ---- update of the CTA's columns; partials r'z, r'r ----
+    {
+      T a0 = T(0), a1 = T(0);
+      const bool upd = has_c && sc[cinst].state == 0;
+      if (upd) {
+        const T alpha = (T)sc[cinst].alpha, beta = (T)sc[cinst].beta, sig = (T)S.sigma;
+        const int CTs = S.CT;
+        for (int k = threadIdx.x; k < nc; k += GCS_NT) {
+          const int64_t j = clo + k;
+          const T zj = epi[k];
+          const T wj = sig * zj + sP[k] + ns[k];
+          const T sj = wj + beta * epi[CTs + k];
+          const T pj = zj + beta * epi[2 * CTs + k];
+          S.s[j] = sj;
+          S.p[j] = pj;
+          S.x[j] = epi[3 * CTs + k] + alpha * pj;
+          const T rj = epi[4 * CTs + k] - alpha * sj;
+          const T zn = epi[5 * CTs + k] * rj;
+          S.r[j] = rj;
+          S.z[j] = zn;
+          a0 += rj * zn;
+          a1 += rj * rj;
+        }
+      }
+      for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
+      double t0 = 0.0, t1 = 0.0;
+      cta_sum2(a0, a1, t0, t1);
+      if (threadIdx.x == 0 && upd) {
+        double* pc = S.part_c + (int64_t)((it + 1) & 1) * 2 * G.nct;
+        pc[b] = t0;
+        pc[G.nct + b] = t1;
+      }
+    }
+    if (!gcs_grid_barrier(B.arrive, B.err, B.limit, epoch)) { leave(); return; }
+  }
+#undef sc
+#undef qb_c
+#undef qb_r
+#undef qend_c
+#undef qend_r
+#undef headr
+#undef headv
+#undef epi
+#undef rho_s
+#undef sP
+#undef ns
+#undef ps
+#undef stage
+#undef mstage
+#undef mbar
+#undef ring
+#undef GCS_AT
+}
+
+}  // namespace cosmo

@@ -23,6 +23,7 @@
 #include "kernels_psd.cuh"
 #include "kernels_tql.cuh"
 #include "kernels_gcg.cuh"
+#include "kernels_gcs.cuh"
 #include "kernels_tc.cuh"
 #include "kernels_vec.cuh"
 
@@ -1789,6 +1790,343 @@ static cosmo_status pcg_solve_grid_t(int32_t ninst, int64_t n, int64_t m, const 
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Prepared grid-wide solves (cosmo_pcg_plan): streaming layouts of A and A',
+// tiles, workspace and the cooperative launch of k_gcg_stream.
+// ---------------------------------------------------------------------------
+struct PcgPlanBase {
+  virtual ~PcgPlanBase() {}
+  virtual cosmo_status solve(double sigma, const void* rho, const void* rhs, void* x, double tol,
+                             int32_t maxit, int32_t* iters, cudaStream_t st) = 0;
+  virtual void info(cosmo_pcg_plan_info* out) const = 0;
+};
+
+// Contiguous tiles of the items [off[i], off[i+1]) of every instance, at
+// most K in all, never crossing an instance; item j weighs rp[j+1] - rp[j] + 1
+// (its entries, plus one).  Instances get tiles in proportion to their weight
+// (at least one each when non-empty), and an instance's tiles have about
+// equal weight.
+static void gcs_tiles(const std::vector<int64_t>& off, const std::vector<int64_t>& rp, int K,
+                      std::vector<int32_t>& inst, std::vector<int64_t>& lo, std::vector<int64_t>& hi,
+                      std::vector<int32_t>* first_tile, std::vector<int32_t>* end_tile, int64_t& maxlen) {
+  const int ni = (int)off.size() - 1;
+  auto W = [&](int64_t a, int64_t b) { return (double)(rp[b] - rp[a]) + (double)(b - a); };
+  const double tot = W(off[0], off[ni]);
+  std::vector<int64_t> k(ni, 0);
+  int64_t used = 0;
+  for (int i = 0; i < ni; ++i) {
+    const int64_t len = off[i + 1] - off[i];
+    if (len <= 0) continue;
+    k[i] = std::min<int64_t>(len, std::max<int64_t>(1, (int64_t)std::floor(K * W(off[i], off[i + 1]) / tot)));
+    used += k[i];
+  }
+  while (used > K) {   // only the at-least-one rule can overshoot
+    int best = -1;
+    for (int i = 0; i < ni; ++i)
+      if (k[i] > 1 && (best < 0 || k[i] > k[best])) best = i;
+    if (best < 0) break;
+    --k[best];
+    --used;
+  }
+  while (used < K) {   // one more tile to the instance with the heaviest tiles
+    int best = -1;
+    double bw = 0.0;
+    for (int i = 0; i < ni; ++i) {
+      if (k[i] == 0 || k[i] >= off[i + 1] - off[i]) continue;
+      const double w = W(off[i], off[i + 1]) / (double)k[i];
+      if (best < 0 || w > bw) { best = i; bw = w; }
+    }
+    if (best < 0) break;
+    ++k[best];
+    ++used;
+  }
+  maxlen = 0;
+  for (int i = 0; i < ni; ++i) {
+    if (first_tile) (*first_tile)[i] = (int32_t)inst.size();
+    const int64_t a = off[i], b = off[i + 1];
+    int64_t prev = a, j = a;
+    const double wi = W(a, b);
+    for (int64_t q = 1; q < k[i]; ++q) {
+      const double target = wi * (double)q / (double)k[i];
+      while (j < b && W(a, j) < target) ++j;
+      const int64_t cut = std::min(std::max(j, prev + 1), b - (k[i] - q));
+      inst.push_back(i); lo.push_back(prev); hi.push_back(cut);
+      maxlen = std::max(maxlen, cut - prev);
+      prev = cut;
+    }
+    if (k[i] > 0) {
+      inst.push_back(i); lo.push_back(prev); hi.push_back(b);
+      maxlen = std::max(maxlen, b - prev);
+    }
+    if (end_tile) (*end_tile)[i] = (int32_t)inst.size();
+  }
+}
+
+template <class T>
+struct GcsPlan : PcgPlanBase {
+  int32_t ninst = 0;
+  int64_t n = 0, m = 0;
+  DevArena a;
+  Prob<T, T> P{};
+  GcgTiles G{};
+  GcsArgs<T> S{};
+  int grid = 0, device = 0;
+  int64_t layout_bytes = 0, quads_r = 0, quads_c = 0;
+  unsigned* bar = nullptr;
+  int32_t* h_err = nullptr;   // pinned
+
+  ~GcsPlan() override {
+    if (h_err) cudaFreeHost(h_err);
+  }
+
+  // streaming layout of `rows` source rows (CSR rp/ci/v) cut into nseg
+  // segments of each row's instance range in the gathered space gath_off;
+  // the last row of each tile (tile_hi: one past the tiles' last rows) is
+  // padded so that every tile's piece of a segment is whole chunks
+  cosmo_status build_layout(int64_t rows, const int64_t* rp, const int32_t* ci, const T* v,
+                            const int64_t* d_row_inst_off, const int64_t* d_gath_off, int nseg,
+                            const std::vector<int64_t>& tile_hi, GcsLayout<T>& L, int64_t& quads,
+                            cudaStream_t st) {
+    constexpr int64_t CQ = gcs_cq<T>();
+    L.nseg = nseg;
+    L.rows = rows;
+    std::vector<int64_t> qp((size_t)nseg * (rows + 1), 0);
+    std::vector<char> last(rows > 0 ? rows : 1, 0);
+    for (int64_t e : tile_hi)
+      if (e > 0) last[e - 1] = 1;
+    int64_t base = 0;
+    if (rows > 0) {
+      int32_t* cnt;
+      TRY(a.alloc(&cnt, (int64_t)nseg * rows));
+      k_gcs_count<<<(int)((rows * 32 + 255) / 256), 256, 0, st>>>(rows, rp, ci, ninst, d_row_inst_off,
+                                                                  d_gath_off, nseg, cnt);
+      ++g_launches;
+      std::vector<int32_t> hc((size_t)nseg * rows);
+      CU(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * hc.size(), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      for (int h = 0; h < nseg; ++h) {
+        for (int64_t r = 0; r < rows; ++r) {
+          qp[(size_t)h * (rows + 1) + r] = base;
+          base += (hc[(size_t)h * rows + r] + 3) / 4;
+          if (last[r]) base = (base + CQ - 1) / CQ * CQ;
+        }
+        qp[(size_t)h * (rows + 1) + rows] = base;
+      }
+    }
+    if (base % CQ) return fail(COSMO_E_INVAL, "streamed CG plan: rows outside every tile");
+    int64_t* d_qp;
+    TRY(a.upload(&d_qp, qp));
+    unsigned char* data = nullptr;
+    if (base > 0) {
+      TRY(a.alloc(&data, base / CQ * gcs_chunk_bytes<T>()));
+      k_gcs_scatter<T><<<(int)((rows * 32 + 255) / 256), 256, 0, st>>>(rows, rp, ci, v, ninst, d_row_inst_off,
+                                                                       d_gath_off, nseg, d_qp, data);
+      ++g_launches;
+    }
+    L.data = data;
+    L.qp = d_qp;
+    quads = base;
+    layout_bytes += base / CQ * gcs_chunk_bytes<T>() + (int64_t)qp.size() * 8;
+    return COSMO_OK;
+  }
+
+  cosmo_status build(int32_t ninst_, int64_t n_, int64_t m_, const int64_t* col_off, const int64_t* row_off,
+                     const int64_t* A_rp, const int32_t* A_ci, const T* A_v, const int64_t* AT_rp,
+                     const int32_t* AT_ci, const T* AT_v, const int64_t* P_rp, const int32_t* P_ci,
+                     const T* P_v, cudaStream_t st) {
+    ninst = ninst_;
+    n = n_;
+    m = m_;
+    int nsm = 0, optin = 0;
+    CU(cudaGetDevice(&device));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    if (ninst < 1 || ninst > nsm) return fail(COSMO_E_INVAL, "streamed CG plan: %d instances, at most %d", ninst, nsm);
+    std::vector<int64_t> co(ninst + 1), ro(ninst + 1), arp(m + 1), atrp(n + 1), prp;
+    CU(cudaMemcpyAsync(co.data(), col_off, sizeof(int64_t) * (ninst + 1), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(ro.data(), row_off, sizeof(int64_t) * (ninst + 1), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(arp.data(), A_rp, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(atrp.data(), AT_rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    if (P_rp) {
+      prp.resize(n + 1);
+      CU(cudaMemcpyAsync(prp.data(), P_rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+    auto monotone = [](const std::vector<int64_t>& v, int64_t last) {
+      if (v.empty() || v[0] != 0 || v.back() != last) return false;
+      for (size_t i = 1; i < v.size(); ++i)
+        if (v[i] < v[i - 1]) return false;
+      return true;
+    };
+    if (!monotone(co, n) || !monotone(ro, m) || !monotone(arp, arp.back()) || !monotone(atrp, arp.back()) ||
+        (P_rp && !monotone(prp, prp.back())))
+      return fail(COSMO_E_INVAL, "streamed CG plan: inconsistent offsets or row pointers");
+    const int64_t nnz_a = arp.back(), nnz_p = P_rp ? prp.back() : 0;
+
+    // plan-owned copies of the offsets and of P
+    int64_t *d_co, *d_ro;
+    TRY(a.upload(&d_co, co));
+    TRY(a.upload(&d_ro, ro));
+    P.ninst = ninst; P.n_total = n; P.m_total = m; P.col_off = d_co; P.row_off = d_ro;
+    int short_p = 1;
+    if (P_rp) {
+      int64_t* prp_d;
+      int32_t* pci_d = nullptr;
+      T* pv_d = nullptr;
+      TRY(a.upload(&prp_d, prp));
+      TRY(a.alloc(&pci_d, nnz_p));
+      TRY(a.alloc(&pv_d, nnz_p));
+      if (nnz_p > 0) {
+        CU(cudaMemcpyAsync(pci_d, P_ci, sizeof(int32_t) * nnz_p, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(pv_d, P_v, sizeof(T) * nnz_p, cudaMemcpyDeviceToDevice, st));
+      }
+      P.P_rp = prp_d; P.P_ci = pci_d; P.P_v = pv_d;
+      for (int64_t j = 0; j < n && short_p; ++j) short_p = prp[j + 1] - prp[j] <= 16;
+    }
+
+    // tiles: rows weighted by A's entries, columns by A''s
+    std::vector<int32_t> rt_inst, ct_inst, it_lo(ninst), it_hi(ninst), irt_lo(ninst), irt_hi(ninst);
+    std::vector<int64_t> rt_lo, rt_hi, ct_lo, ct_hi;
+    int64_t RT = 0, CT = 0;
+    gcs_tiles(ro, arp, nsm, rt_inst, rt_lo, rt_hi, &irt_lo, &irt_hi, RT);
+    gcs_tiles(co, atrp, nsm, ct_inst, ct_lo, ct_hi, &it_lo, &it_hi, CT);
+    if (ct_inst.empty()) return fail(COSMO_E_INVAL, "streamed CG plan: no columns");
+    int64_t max_n = 0, max_m = 0;
+    for (int i = 0; i < ninst; ++i) {
+      max_n = std::max(max_n, co[i + 1] - co[i]);
+      max_m = std::max(max_m, ro[i + 1] - ro[i]);
+    }
+
+    // segments: the fewest that fit the stage next to the rings and tables
+    cudaFuncAttributes fa{};
+    CU(cudaFuncGetAttributes(&fa, k_gcg_stream<T>));
+    const int64_t cap = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+    const int64_t E = 16 / (int64_t)sizeof(T);
+    int nsr = 1, nsc = 1;
+    int64_t stage_len = 0;
+    GcsSmem sm{};
+    for (;;) {
+      const int64_t lr = (max_n + nsr - 1) / nsr, lc = (max_m + nsc - 1) / nsc;
+      stage_len = std::max(lr, lc) + 2 * E;
+      sm = gcs_smem<T>(stage_len, std::max<int64_t>(RT, 1), CT, nsr, nsc, ninst);
+      if (sm.total <= cap) break;
+      if (lr >= lc) ++nsr; else ++nsc;
+      if (nsr > 64 || nsc > 64)
+        return fail(COSMO_E_INVAL, "streamed CG plan: tiles of %lld rows / %lld columns do not fit shared memory",
+                    (long long)RT, (long long)CT);
+    }
+    CU(cudaFuncSetAttribute(k_gcg_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm.total));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gcg_stream<T>, GCS_NT, (size_t)sm.total));
+    if (per_sm < 1) return fail(COSMO_E_INVAL, "streamed CG plan: the kernel does not fit an SM");
+
+    // streaming layouts: A by column segment, A' by row segment
+    TRY(build_layout(m, A_rp, A_ci, A_v, d_ro, d_co, nsr, rt_hi, S.LR, quads_r, st));
+    TRY(build_layout(n, AT_rp, AT_ci, AT_v, d_co, d_ro, nsc, ct_hi, S.LC, quads_c, st));
+
+    int32_t *d_ct_inst, *d_it_lo, *d_it_hi, *d_rt_inst = nullptr;
+    int64_t *d_ct_lo, *d_ct_hi, *d_rt_lo = nullptr, *d_rt_hi = nullptr;
+    TRY(a.upload(&d_ct_inst, ct_inst)); TRY(a.upload(&d_ct_lo, ct_lo)); TRY(a.upload(&d_ct_hi, ct_hi));
+    TRY(a.upload(&d_it_lo, it_lo)); TRY(a.upload(&d_it_hi, it_hi));
+    if (!rt_inst.empty()) {
+      TRY(a.upload(&d_rt_inst, rt_inst)); TRY(a.upload(&d_rt_lo, rt_lo)); TRY(a.upload(&d_rt_hi, rt_hi));
+    }
+    G.nct = (int32_t)ct_inst.size(); G.ct_inst = d_ct_inst; G.ct_lo = d_ct_lo; G.ct_hi = d_ct_hi;
+    G.it_lo = d_it_lo; G.it_hi = d_it_hi;
+    G.nrt = (int32_t)rt_inst.size(); G.rt_inst = d_rt_inst; G.rt_lo = d_rt_lo; G.rt_hi = d_rt_hi;
+    G.nnz_a = nnz_a; G.nnz_p = nnz_p;
+    G.vq_p = nnz_p > 0 ? (nnz_p / n >= 384 ? 4 : nnz_p / n >= 128 ? 2 : 1) : 0;
+    if (sizeof(T) == 8) G.vq_p = std::min(G.vq_p, 2);
+    grid = std::max(G.nct, G.nrt);
+
+    // workspace; z and t are padded to whole 16-byte groups and zeroed once
+    // (the stage copies read the padding)
+    T *dinv, *r, *z, *p, *sv, *t;
+    TRY(a.alloc(&dinv, n)); TRY(a.alloc(&r, n)); TRY(a.alloc(&p, n)); TRY(a.alloc(&sv, n));
+    TRY(a.alloc(&z, n + 2 * E));
+    TRY(a.alloc(&t, std::max<int64_t>(m, 1) + 2 * E));
+    CU(cudaMemsetAsync(z, 0, sizeof(T) * (n + 2 * E), st));
+    CU(cudaMemsetAsync(t, 0, sizeof(T) * (std::max<int64_t>(m, 1) + 2 * E), st));
+    double *part_r, *part_d, *part_c;
+    TRY(a.alloc(&part_r, std::max<int32_t>(G.nrt, 1))); TRY(a.alloc(&part_d, G.nct));
+    TRY(a.alloc(&part_c, 4 * (int64_t)G.nct));
+    CU(cudaMemsetAsync(part_r, 0, sizeof(double) * std::max<int32_t>(G.nrt, 1), st));
+    CU(cudaMemsetAsync(part_d, 0, sizeof(double) * G.nct, st));
+    CU(cudaMemsetAsync(part_c, 0, sizeof(double) * 4 * G.nct, st));
+    int32_t *d_irt_lo, *d_irt_hi;
+    TRY(a.upload(&d_irt_lo, irt_lo)); TRY(a.upload(&d_irt_hi, irt_hi));
+    TRY(a.alloc(&bar, 4));
+    CU(cudaMallocHost(&h_err, sizeof(int32_t)));
+    S.dinv = dinv; S.r = r; S.z = z; S.p = p; S.s = sv; S.t = t;
+    S.part_r = part_r; S.part_d = part_d; S.part_c = part_c; S.irt_lo = d_irt_lo; S.irt_hi = d_irt_hi;
+    S.short_p = short_p; S.RT = (int32_t)std::max<int64_t>(RT, 1); S.CT = (int32_t)CT; S.sm = sm;
+    S.wait_limit = 2000000000LL;   // about 1 s at 2 GHz
+    CU(cudaStreamSynchronize(st));
+    return COSMO_OK;
+  }
+
+  cosmo_status solve(double sigma, const void* rho, const void* rhs, void* x, double tol, int32_t maxit,
+                     int32_t* iters, cudaStream_t st) override {
+    if (!(sigma > 0.0) || !(tol > 0.0) || maxit < 1 || !rho || !rhs || !x)
+      return fail(COSMO_E_INVAL, "bad arguments to cosmo_pcg_plan_solve");
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != device) return fail(COSMO_E_INVAL, "the plan belongs to device %d, device %d is current", device, dev);
+    k_gcs_precond<T><<<(int)((n * 32 + 255) / 256), 256, 0, st>>>(n, S.LC, P.P_rp, P.P_ci, P.P_v, sigma,
+                                                                  (const T*)rho, const_cast<T*>(S.dinv));
+    CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
+    GcsArgs<T> A = S;
+    A.rhs = (const T*)rhs; A.x = (T*)x; A.rho = (const T*)rho; A.sigma = sigma;
+    A.tol = tol; A.maxit = maxit; A.iters = iters;
+    GridBar B{bar, bar + 1, reinterpret_cast<int32_t*>(bar + 2), 2000000000LL};
+    void* args[] = {(void*)&P, (void*)&G, (void*)&A, (void*)&B};
+    CU(cudaLaunchCooperativeKernel((const void*)k_gcg_stream<T>, dim3(grid), dim3(GCS_NT), args,
+                                   (size_t)S.sm.total, st));
+    g_launches += 2;
+    CU(cudaMemcpyAsync(h_err, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (*h_err) return fail(COSMO_E_TIMEOUT, "streamed CG: a wait gave up");
+    return COSMO_OK;
+  }
+
+  void info(cosmo_pcg_plan_info* o) const override {
+    o->nseg_a = S.LR.nseg;
+    o->nseg_at = S.LC.nseg;
+    o->grid = grid;
+    o->threads = GCS_NT;
+    o->layout_bytes = layout_bytes;
+    o->smem_bytes = S.sm.total;
+    o->quads_a = quads_r;
+    o->quads_at = quads_c;
+  }
+};
+
+struct cosmo_pcg_plan {
+  std::unique_ptr<PcgPlanBase> impl;
+};
+
+static cosmo_status pcg_plan_build(int32_t precision, int32_t ninst, int64_t n, int64_t m, const int64_t* col_off,
+                                   const int64_t* row_off, const int64_t* A_rp, const int32_t* A_ci,
+                                   const void* A_v, const int64_t* AT_rp, const int32_t* AT_ci, const void* AT_v,
+                                   const int64_t* P_rp, const int32_t* P_ci, const void* P_v,
+                                   std::unique_ptr<PcgPlanBase>& out, cudaStream_t st) {
+  if (ninst < 1 || n < 1 || m < 0 || !col_off || !row_off || !A_rp || !AT_rp ||
+      (m > 0 && (!A_ci || !A_v || !AT_ci || !AT_v)) || ((P_rp != nullptr) != (P_ci != nullptr)) ||
+      ((P_rp != nullptr) != (P_v != nullptr)))
+    return fail(COSMO_E_INVAL, "bad arguments to cosmo_pcg_plan_create");
+  auto make = [&](auto tag) -> cosmo_status {
+    using T = decltype(tag);
+    std::unique_ptr<GcsPlan<T>> pl(new GcsPlan<T>());
+    TRY(pl->build(ninst, n, m, col_off, row_off, A_rp, A_ci, (const T*)A_v, AT_rp, AT_ci, (const T*)AT_v, P_rp,
+                  P_ci, (const T*)P_v, st));
+    out = std::move(pl);
+    return COSMO_OK;
+  };
+  if (precision == COSMO_PREC_FP64) return make(double(0));
+  if (precision == COSMO_PREC_MIXED) return make(float(0));
+  return fail(COSMO_E_INVAL, "unknown precision");
+}
+
 extern "C" {
 
 cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_t m,
@@ -1816,6 +2154,12 @@ cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_
   const bool grid = !warm_start && ninst < 148 && nnzA / ninst > 100000;
   if (grid) {
     if (precision == COSMO_PREC_FP64 || precision == COSMO_PREC_MIXED) {
+      std::unique_ptr<PcgPlanBase> plan;
+      const cosmo_status ps = pcg_plan_build(precision, ninst, n, m, col_off, row_off, A_rowptr, A_col, A_val,
+                                             AT_rowptr, AT_col, AT_val, P_rowptr, P_col, P_val, plan, st);
+      if (ps == COSMO_OK) return plan->solve(sigma, rho, rhs, x, tol, max_iter, iters, st);
+      if (ps != COSMO_E_INVAL) return ps;
+      g_err.clear();   // not applicable: the global-memory path below
       auto make = [&](auto tag) {
         using T = decltype(tag);
         Prob<T, T> P{};
@@ -1839,6 +2183,44 @@ cosmo_status cosmo_pcg_solve(int32_t precision, int32_t ninst, int64_t n, int64_
                               AT_col, AT_val, P_rowptr, P_col, P_val, sigma, rho, rhs, x,
                               warm_start, tol, max_iter, iters, st);
   return fail(COSMO_E_INVAL, "unknown precision");
+}
+
+cosmo_status cosmo_pcg_plan_create(int32_t precision, int32_t ninst, int64_t n, int64_t m,
+                                   const int64_t* col_off, const int64_t* row_off,
+                                   const int64_t* A_rowptr, const int32_t* A_col, const void* A_val,
+                                   const int64_t* AT_rowptr, const int32_t* AT_col,
+                                   const void* AT_val, const int64_t* P_rowptr,
+                                   const int32_t* P_col, const void* P_val, cosmo_pcg_plan** out,
+                                   void* stream) {
+  g_err.clear();
+  if (!out) return fail(COSMO_E_INVAL, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<cosmo_pcg_plan> pl(new cosmo_pcg_plan());
+  TRY(pcg_plan_build(precision, ninst, n, m, col_off, row_off, A_rowptr, A_col, A_val, AT_rowptr, AT_col,
+                     AT_val, P_rowptr, P_col, P_val, pl->impl, (cudaStream_t)stream));
+  *out = pl.release();
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_pcg_plan_solve(cosmo_pcg_plan* plan, double sigma, const void* rho,
+                                  const void* rhs, void* x, double tol, int32_t max_iter,
+                                  int32_t* iters, void* stream) {
+  g_err.clear();
+  if (!plan || !plan->impl) return fail(COSMO_E_INVAL, "plan is NULL");
+  return plan->impl->solve(sigma, rho, rhs, x, tol, max_iter, iters, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_pcg_plan_get_info(const cosmo_pcg_plan* plan, cosmo_pcg_plan_info* out) {
+  g_err.clear();
+  if (!plan || !plan->impl || !out) return fail(COSMO_E_INVAL, "plan or out is NULL");
+  plan->impl->info(out);
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_pcg_plan_destroy(cosmo_pcg_plan* plan) {
+  g_err.clear();
+  delete plan;
+  return COSMO_OK;
 }
 
 cosmo_status cosmo_psd_project(int32_t precision, int32_t nblk, const int32_t* p_host,

@@ -418,6 +418,47 @@ class ReducedSystem:
                 *map(_tp, self.P)]
 
 
+class PcgPlan:
+    """A prepared zero-start solve of a large reduced system: the library
+    copies A, A' and P once into a streaming layout (cosmo_pcg_plan_create);
+    each solve(sigma, rho, rhs) is then one cooperative launch with no
+    allocation.  Raises on systems the streamed path cannot take (more
+    instances than SMs, tiles that do not fit shared memory)."""
+
+    def __init__(self, system: ReducedSystem):
+        self.system = system
+        prec = _abi.PREC_FP64 if system.precision == "fp64" else _abi.PREC_MIXED
+        h = c_void_p()
+        check(lib().cosmo_pcg_plan_create(prec, system.ninst, system.n, system.m, *system.args(),
+                                          byref(h), _stream()))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                lib().cosmo_pcg_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def info(self):
+        inf = _abi.PcgPlanInfo()
+        check(lib().cosmo_pcg_plan_get_info(self._h, byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def solve(self, sigma, rho, rhs, tol=1e-8, max_iter=500, x=None, iters=None):
+        """x = (P + sigma I + A'D(rho)A)^-1 rhs from x = 0; returns (x,
+        iterations per block).  x and iters may be given to reuse buffers."""
+        x = torch.empty_like(rhs) if x is None else x
+        if iters is None:
+            iters = torch.zeros(self.system.ninst, dtype=torch.int32, device=rhs.device)
+        check(lib().cosmo_pcg_plan_solve(self._h, float(sigma), _tp(rho.contiguous()),
+                                         _tp(rhs.contiguous()), _tp(x), float(tol), int(max_iter),
+                                         _tp(iters), _stream()))
+        return x, iters
+
+
 def pcg_solve(system: ReducedSystem, sigma, rho, rhs, x0=None, tol=1e-8, max_iter=500):
     """x = (P + sigma I + A'D(rho)A)^-1 rhs by the library's Jacobi-PCG;
     returns (x, iterations per block)."""

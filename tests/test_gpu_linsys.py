@@ -131,3 +131,109 @@ def test_grid_cg_several_instances(precision):
         err = float((x1.double() - x[c:c + n].double()).abs().max() / x1.double().abs().max())
         assert err < (1e-8 if precision == "fp64" else 1e-3), (k, err)
         c, r = c + n, r + m
+
+
+# ---- prepared solves (cosmo_pcg_plan: streamed layout, pipelined PCG) ------
+
+def _plan(blocks, precision):
+    from paper_2606_13825_b300.solver import ReducedSystem, PcgPlan
+    sysm = ReducedSystem(blocks, precision)
+    return sysm, PcgPlan(sysm)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pcg_plan_vs_dense_reuse_and_repeat(precision):
+    """App. B instance (n = 6000): against a dense FP64 solve; a second solve
+    with another rho on the same plan; a repeat solve is bitwise identical."""
+    _need_gpu()
+    d = linsys_instance(6000, seed=6106, density=0.01, row_sampler=True)
+    sysm, plan = _plan([(d["P"], d["A"])], precision)
+    dt = sysm.dtype
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    rng = np.random.default_rng(8)
+    rhs = rng.standard_normal(6000)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for rho in (d["rho"] + 0.05, rng.uniform(0.5, 2.0, d["A"].shape[0])):
+        x, iters = plan.solve(1e-6, t(rho), t(rhs), tol=tol, max_iter=3000)
+        ref = _dense_solve(d["P"], d["A"], 1e-6, rho, rhs)
+        err = np.abs(x.double().cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < (1e-8 if precision == "fp64" else 2e-3), err
+        assert 0 < int(iters[0]) < 3000
+        x2, it2 = plan.solve(1e-6, t(rho), t(rhs), tol=tol, max_iter=3000)
+        assert torch.equal(x, x2) and torch.equal(iters, it2)
+    info = plan.info()
+    assert info["grid"] >= 1 and info["layout_bytes"] > 0
+    # every stored entry of A and A' is streamed once per pass (plus padding)
+    assert 4 * info["quads_a"] >= d["A"].nnz and 4 * info["quads_at"] >= d["A"].nnz
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pcg_plan_segments(precision):
+    """n = 60000: the gathered vector exceeds shared memory, so each row of A
+    (and of A' in FP64) is streamed in several segments; true residual."""
+    _need_gpu()
+    d = linsys_instance(60000, seed=6160, density=0.005, row_sampler=True)
+    blocks = [(d["P"], d["A"])]
+    sysm, plan = _plan(blocks, precision)
+    info = plan.info()
+    assert info["nseg_a"] >= 2
+    rho = d["rho"] + 0.05
+    rhs = np.random.default_rng(9).standard_normal(60000)
+    t = lambda a: torch.tensor(a, dtype=sysm.dtype, device="cuda")
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    x, iters = plan.solve(1e-6, t(rho), t(rhs), tol=tol, max_iter=3000)
+    res = _true_residual(blocks, 1e-6, rho, rhs, x.double().cpu().numpy())
+    assert res.max() < (1e-9 if precision == "fp64" else 5e-4), (res, info)
+    assert 0 < int(iters[0]) < 3000
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pcg_plan_general_p_unsorted_empty_rows(precision):
+    """A general sparse P (SOCP block, P = M'M + 1e-3 I), rows of A whose
+    column indices are not sorted, empty rows of A, and an instance without
+    constraint rows, in one plan; each instance against a dense FP64 solve."""
+    _need_gpu()
+    soc = socp_problem(4600, n=2000, m=3000, density=0.01, m_M=200, n_soc=20, soc_lo=3, soc_hi=20)
+    rng = np.random.default_rng(10)
+    # empty rows: every 7th row cleared; then the entries of each row shuffled
+    A = (sp.diags((np.arange(soc.m) % 7 != 0).astype(float)) @ soc.A).tocsr()
+    A.eliminate_zeros()
+    ind, dat = A.indices.copy(), A.data.copy()
+    for r in range(A.shape[0]):
+        a, b = A.indptr[r], A.indptr[r + 1]
+        perm = rng.permutation(b - a)
+        ind[a:b], dat[a:b] = ind[a:b][perm], dat[a:b][perm]
+    A_uns = sp.csr_matrix((dat, ind, A.indptr.copy()), shape=A.shape)
+    d = linsys_instance(3000, seed=6300, density=0.02, row_sampler=True)
+    P0 = sp.diags(rng.uniform(0.5, 2.0, 1500)).tocsr()
+    A0 = sp.csr_matrix((0, 1500))
+    blocks = [(soc.P, A_uns), (d["P"], d["A"]), (P0, A0)]
+    from paper_2606_13825_b300.solver import ReducedSystem, PcgPlan
+    sysm = ReducedSystem(blocks, precision)
+    # ReducedSystem sorts the indices of A: hand the plan the shuffled order
+    # (block-diagonal CSR assembled by hand, keeping each row's order)
+    ptr, ind, dat, c0 = [np.zeros(1, np.int64)], [], [], 0
+    for B_ in (A_uns, d["A"], A0):
+        ptr.append(B_.indptr[1:].astype(np.int64) + ptr[-1][-1])
+        ind.append(B_.indices + c0)
+        dat.append(B_.data)
+        c0 += B_.shape[1]
+    Ablk = sp.csr_matrix((np.concatenate(dat), np.concatenate(ind), np.concatenate(ptr)), shape=(sysm.m, sysm.n))
+    assert any(np.any(np.diff(Ablk.indices[Ablk.indptr[r]:Ablk.indptr[r + 1]]) < 0) for r in range(100))
+    assert np.array_equal(sysm.A[0].cpu().numpy(), Ablk.indptr)
+    sysm.A = (sysm.A[0], torch.tensor(np.asarray(Ablk.indices, np.int32), device="cuda"),
+              torch.tensor(Ablk.data, dtype=sysm.dtype, device="cuda"))
+    plan = PcgPlan(sysm)
+    rho = rng.uniform(0.2, 2.0, sysm.m)
+    rhs = rng.standard_normal(sysm.n)
+    t = lambda a: torch.tensor(a, dtype=sysm.dtype, device="cuda")
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    x, iters = plan.solve(1e-6, t(rho), t(rhs), tol=tol, max_iter=5000)
+    x = x.double().cpu().numpy()
+    c = r = 0
+    for k, (P, A_) in enumerate(blocks):
+        m, n = A_.shape
+        ref = _dense_solve(P, A_, 1e-6, rho[r:r + m], rhs[c:c + n]) if m else rhs[c:c + n] / (P.diagonal() + 1e-6)
+        err = np.abs(x[c:c + n] - ref).max() / np.abs(ref).max()
+        assert err < (1e-8 if precision == "fp64" else 5e-3), (k, err, iters)
+        c, r = c + n, r + m
