@@ -364,6 +364,8 @@ typedef struct {
   int32_t nseg_at;         /* row segments of each row of A' */
   int32_t grid;            /* CTAs of the persistent launch */
   int32_t threads;         /* threads per CTA */
+  int32_t cluster;         /* CTAs per thread-block cluster (one segment each) */
+  int32_t ring_slots;      /* chunk buffers per streaming warp */
   int64_t layout_bytes;    /* device bytes of the streaming copies of A and A' */
   int64_t smem_bytes;      /* dynamic shared memory per CTA */
   int64_t quads_a;         /* 4-entry groups streamed per pass over A (padding included) */

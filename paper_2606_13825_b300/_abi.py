@@ -63,6 +63,7 @@ class BatchInfo(ctypes.Structure):
 
 class PcgPlanInfo(ctypes.Structure):
     _fields_ = [("nseg_a", c_int32), ("nseg_at", c_int32), ("grid", c_int32), ("threads", c_int32),
+                ("cluster", c_int32), ("ring_slots", c_int32),
                 ("layout_bytes", c_int64), ("smem_bytes", c_int64), ("quads_a", c_int64),
                 ("quads_at", c_int64)]
 

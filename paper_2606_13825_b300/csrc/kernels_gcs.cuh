@@ -16,11 +16,11 @@
 // row of every tile is padded to a whole chunk: a tile's piece of a segment
 // is a run of whole chunks, and each chunk arrives with one bulk copy of
 // 1 KB (float) -- the TMA engine sustains HBM bandwidth with 1 KB requests
-// from 31 warps, but only about 60% of it with 512-byte ones.
+// from a few dozen warps, but only about 60% of it with 512-byte ones.
 //
-// Kernel: one CTA per SM, 31 streaming warps and one control warp.  Each
+// Kernel: one CTA per SM, 24 streaming warps and one control warp.  Each
 // streaming warp owns an equal share of its tile's quads per segment and
-// streams them through a private ring of GCS_NSLOT chunk buffers filled by
+// streams them through a private ring of chunk buffers filled by
 // bulk asynchronous copies (cp.async.bulk, the TMA engine; completion on an
 // mbarrier per buffer).  Data in flight lands in shared memory, not in L1,
 // so staging the gathered vector in shared memory does not cut the loads in
@@ -57,6 +57,8 @@
 // bounded in clock cycles; a wait that gives up sets the error word, waits
 // (bounded) for this CTA's copies in flight and returns.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "kernels_gcg.cuh"
 #include "kernels_tc.cuh"
@@ -101,43 +103,9 @@ __device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity, long long 
 
 }  // namespace bulk
 
-// Grid barrier over all CTAs of the cooperative launch: a fire-and-forget
-// release add to one counter, then thread 0 polls it with acquire loads until
-// it reaches epoch * gridDim.x (the counter only grows; zero at launch).
-// Gives up after `limit` clock cycles or when the error word is set.
-__device__ __forceinline__ bool gcs_grid_barrier(unsigned* ctr, int32_t* err, long long limit, unsigned& epoch) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ++epoch;
-    const unsigned target = epoch * gridDim.x;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(ctr) : "memory");
-    int ok = 1;
-    long long t0 = 0;
-    for (int k = 0;; ++k) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-      if (v >= target) break;
-      if (k == 0) t0 = clock64();
-      if ((k & 63) == 63) {
-        int e;
-        asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
-        if (e != 0 || clock64() - t0 > limit) {
-          asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" :: "l"(err), "r"(1) : "memory");
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-constexpr int GCS_WARPS = 31;                    // streaming warps
-constexpr int GCS_NT = 32 * GCS_WARPS + 32;      // + the control warp (1024 threads, 64 registers each)
-constexpr int GCS_NSLOT = 3;                     // chunk buffers per streaming warp
+constexpr int GCS_WARPS = 24;                    // streaming warps
+constexpr int GCS_NT = 32 * GCS_WARPS + 32;      // + the control warp (800 threads, 80 registers each)
+constexpr int GCS_MAXSLOT = 6;                   // chunk buffers per streaming warp, at most
 // quads per chunk: 128 float or 64 double entries (32 lanes x 16 bytes of values)
 template <class T> __host__ __device__ constexpr int gcs_cq() { return sizeof(T) == 4 ? 32 : 16; }
 template <class T> __host__ __device__ constexpr int gcs_vbytes() { return gcs_cq<T>() * 4 * (int)sizeof(T); }
@@ -156,29 +124,30 @@ __host__ __device__ inline int64_t gcs_al(int64_t x, int64_t a) { return (x + a 
 // on a 16-byte boundary (the mbarriers and the int64 / double tables need 8,
 // the bulk-copy destinations 16)
 struct GcsSmem {
-  int64_t o_ring, o_mbar, o_stage, o_ps, o_ns, o_sp, o_rho, o_epi, o_headv, o_headr, o_qend_r, o_qend_c, o_qb_r,
-      o_qb_c, o_scal, total;
+  int64_t o_ring, o_mbar, o_stage, o_ps, o_ns, o_sp, o_rho, o_epi, o_headv, o_headr, o_qend_r, o_qend_c, o_qb,
+      o_scal, total;
 };
 
+// RT / CT: rows / columns of the largest cluster tile, RTo / CTo: of the
+// largest share one CTA owns in the epilogues
 template <class T>
-__host__ __device__ inline GcsSmem gcs_smem(int64_t stage_len, int64_t RT, int64_t CT, int nsr, int nsc,
-                                            int ninst) {
+__host__ __device__ inline GcsSmem gcs_smem(int nslot, int64_t stage_len, int64_t RT, int64_t CT, int64_t RTo,
+                                            int64_t CTo, int ninst) {
   GcsSmem s{};
   int64_t o = 0;
-  s.o_ring = o;   o += (int64_t)GCS_WARPS * GCS_NSLOT * gcs_slot<T>();
-  s.o_mbar = o;   o = gcs_al(o + 8 * (GCS_WARPS * GCS_NSLOT + 1), 128);
+  s.o_ring = o;   o += (int64_t)GCS_WARPS * nslot * gcs_slot<T>();
+  s.o_mbar = o;   o = gcs_al(o + 8 * (GCS_WARPS * nslot + 1), 128);
   s.o_stage = o;  o += gcs_al(stage_len * (int64_t)sizeof(T), 16);
   s.o_ps = o;     o += gcs_al(RT * (int64_t)sizeof(T), 16);
   s.o_ns = o;     o += gcs_al(CT * (int64_t)sizeof(T), 16);
-  s.o_sp = o;     o += gcs_al(CT * (int64_t)sizeof(T), 16);
-  s.o_rho = o;    o += gcs_al(RT * (int64_t)sizeof(T), 16);
-  s.o_epi = o;    o += gcs_al(6 * CT * (int64_t)sizeof(T), 16);
+  s.o_sp = o;     o += gcs_al(CTo * (int64_t)sizeof(T), 16);
+  s.o_rho = o;    o += gcs_al(RTo * (int64_t)sizeof(T), 16);
+  s.o_epi = o;    o += gcs_al(6 * CTo * (int64_t)sizeof(T), 16);
   s.o_headv = o;  o += gcs_al(GCS_WARPS * (int64_t)sizeof(T), 16);
   s.o_headr = o;  o += gcs_al(GCS_WARPS * 4, 16);
-  s.o_qend_r = o; o += gcs_al((int64_t)nsr * RT * 4, 16);
-  s.o_qend_c = o; o += gcs_al((int64_t)nsc * CT * 4, 16);
-  s.o_qb_r = o;   o += gcs_al(8 * (int64_t)nsr, 16);
-  s.o_qb_c = o;   o += gcs_al(8 * (int64_t)nsc, 16);
+  s.o_qend_r = o; o += gcs_al(RT * 4, 16);
+  s.o_qend_c = o; o += gcs_al(CT * 4, 16);
+  s.o_qb = o;     o += 16;
   s.o_scal = o;   o += (int64_t)ninst * (int64_t)sizeof(GcgScal);
   s.total = gcs_al(o, 16);
   return s;
@@ -205,22 +174,29 @@ template <class T> __host__ __device__ inline int64_t gcs_col_at(int64_t e) {
   return (q / gcs_cq<T>()) * gcs_chunk_bytes<T>() + gcs_vbytes<T>() + (q % gcs_cq<T>()) * 16 + (e & 3) * 4;
 }
 
+// Tiles are per cluster (index blockIdx.x / CS; G's row / column tile
+// arrays); CTA rank h of a cluster streams segment h of its tile (nseg == CS)
+// and owns the h-th share of the tile's rows and columns in the epilogues.
 template <class T>
 struct GcsArgs {
   GcsLayout<T> LR;       // rows of A by column segment (R phase)
   GcsLayout<T> LC;       // rows of A' by row segment (C phase)
   const T* rhs; T* x; const T* rho; const T* dinv; double sigma;
   T *r, *z, *p, *s, *t;  // z and t padded to whole 16-byte groups
-  double* part_r;        // [nrt] sum rho (Az)^2 of the row tile
-  double* part_d;        // [nct] sigma z'z + z'Pz of the column tile
-  double* part_c;        // [2][2][nct] r'z, r'r of the column tile (by iteration parity)
-  const int32_t* irt_lo; // [ninst] first row tile of the instance
-  const int32_t* irt_hi; // [ninst] one past its last row tile
+  double* part_r;        // [grid] sum rho (Az)^2 of the CTA's rows
+  double* part_d;        // [grid] sigma z'z + z'Pz of the CTA's columns
+  double* part_c;        // [2][2][grid] r'z, r'r of the CTA's columns (by iteration parity)
+  const int32_t* cr_lo;  // [ninst] first CTA owning rows of the instance
+  const int32_t* cr_hi;  // [ninst] one past the last
+  const int32_t* cc_lo;  // [ninst] first CTA owning columns of the instance
+  const int32_t* cc_hi;
   int32_t* iters;        // [ninst] or null
   double tol;
   int32_t maxit;
   int32_t short_p;       // P rows of at most 16 entries
-  int32_t RT, CT;        // largest row / column tile
+  int32_t nslot;         // chunk buffers per streaming warp
+  int32_t RT, CT;        // largest cluster tile: rows / columns
+  int32_t RTo, CTo;      // largest owned share
   GcsSmem sm;
   long long wait_limit;  // clock cycles one wait may take
 };
@@ -335,7 +311,7 @@ __global__ void k_gcs_precond(int64_t n, GcsLayout<T> LC, const int64_t* __restr
 
 // ---- the solve --------------------------------------------------------------
 
-template <class T>
+template <class T, int CS>
 __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles G, GcsArgs<T> S, GridBar B) {
   extern __shared__ __align__(128) unsigned char gcs_dyn[];
   constexpr int CQ = gcs_cq<T>();
@@ -348,7 +324,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
 #define GCS_AT(type, field) reinterpret_cast<type*>(gcs_dyn + S.sm.field)
 #define ring GCS_AT(unsigned char, o_ring)
 #define mbar GCS_AT(uint64_t, o_mbar)
-#define mstage (GCS_AT(uint64_t, o_mbar) + GCS_WARPS * GCS_NSLOT)
+#define mstage (GCS_AT(uint64_t, o_mbar) + GCS_WARPS * S.nslot)
 #define stage GCS_AT(T, o_stage)
 #define ps GCS_AT(T, o_ps)
 #define ns GCS_AT(T, o_ns)
@@ -359,37 +335,83 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
 #define headr GCS_AT(int32_t, o_headr)
 #define qend_r GCS_AT(int32_t, o_qend_r)
 #define qend_c GCS_AT(int32_t, o_qend_c)
-#define qb_r GCS_AT(int64_t, o_qb_r)
-#define qb_c GCS_AT(int64_t, o_qb_c)
+#define qb GCS_AT(int64_t, o_qb)
 #define sc GCS_AT(GcgScal, o_scal)
-  __shared__ double red[3][GCS_WARPS + 1];   // one per warp, control warp included
-  __shared__ int s_done, s_err;
+  __shared__ double red[2][GCS_WARPS + 1];
+  __shared__ int s_done, s_ok;
+  __shared__ int s_bad[2];   // a wait of this CTA gave up, by decision-point parity
 
-  const int b = blockIdx.x, ninst = P.ninst;
+  // the CTA's tile constants live in shared memory and are read where used,
+  // so that the streaming loop does not hold them in registers
+  __shared__ int64_t s_t64[10];
+  __shared__ int s_t32[8];
+#define clo s_t64[0]
+#define chi s_t64[1]
+#define rlo s_t64[2]
+#define rhi s_t64[3]
+#define r_c0 s_t64[4]
+#define r_c1 s_t64[5]
+#define c_r0 s_t64[6]
+#define c_r1 s_t64[7]
+#define oc0 s_t64[8]
+#define oc1 s_t64[9]
+#define nr s_t32[0]
+#define nc s_t32[1]
+#define orl s_t32[2]
+#define nor s_t32[3]
+#define ocl s_t32[4]
+#define noc s_t32[5]
+#define cinst s_t32[6]
+#define rinst s_t32[7]
+  const int b = blockIdx.x, ninst = P.ninst, NS = S.nslot;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const bool streamer = wp < GCS_WARPS;
-  const bool has_c = b < G.nct, has_r = b < G.nrt;
-  const int cinst = has_c ? G.ct_inst[b] : 0, rinst = has_r ? G.rt_inst[b] : 0;
-  const int64_t clo = has_c ? G.ct_lo[b] : 0, chi = has_c ? G.ct_hi[b] : 0;
-  const int64_t rlo = has_r ? G.rt_lo[b] : 0, rhi = has_r ? G.rt_hi[b] : 0;
-  const int nr = (int)(rhi - rlo), nc = (int)(chi - clo);
-  const int nsr = S.LR.nseg, nsc = S.LC.nseg, nsg = nsr + nsc;
+  int rank = 0;
+  if constexpr (CS > 1) rank = (int)cooperative_groups::this_cluster().block_rank();
+  const bool has_r = b / CS < G.nrt, has_c = b / CS < G.nct;
+  if (threadIdx.x == 0) {
+    const int cl = b / CS;
+    cinst = has_c ? G.ct_inst[cl] : 0;
+    rinst = has_r ? G.rt_inst[cl] : 0;
+    clo = has_c ? G.ct_lo[cl] : 0;
+    chi = has_c ? G.ct_hi[cl] : 0;
+    rlo = has_r ? G.rt_lo[cl] : 0;
+    rhi = has_r ? G.rt_hi[cl] : 0;
+    nr = (int)(rhi - rlo);
+    nc = (int)(chi - clo);
+    // this CTA's shares of the tile's rows / columns in the epilogues
+    orl = nr * rank / CS;
+    nor = nr * (rank + 1) / CS - orl;
+    ocl = nc * rank / CS;
+    noc = nc * (rank + 1) / CS - ocl;
+    oc0 = clo + ocl;
+    oc1 = oc0 + noc;
+    // this CTA's segment of z (R) and of t (C)
+    int64_t a0 = 0, a1 = 0;
+    if (has_r) gcs_seg(P.col_off[rinst], P.col_off[rinst + 1], CS, rank, a0, a1);
+    r_c0 = a0; r_c1 = a1;
+    a0 = a1 = 0;
+    if (has_c) gcs_seg(P.row_off[cinst], P.row_off[cinst + 1], CS, rank, a0, a1);
+    c_r0 = a0; c_r1 = a1;
+  }
+  __syncthreads();
   const int64_t m_tot = P.m_total, n_tot = P.n_total;
 
-  // ---- per-CTA tables (fixed for the whole solve) ----
-  for (int h = 0; h < nsr; ++h) {
-    const int64_t* q = S.LR.qp + (int64_t)h * (m_tot + 1);
+  // ---- per-CTA tables (fixed for the whole solve): segment `rank` ----
+  {
+    const int64_t* q = S.LR.qp + (int64_t)rank * (m_tot + 1);
     const int64_t base = has_r ? q[rlo] : 0;
-    if (threadIdx.x == 0) qb_r[h] = base;
-    for (int k = threadIdx.x; k < nr; k += GCS_NT) qend_r[h * S.RT + k] = (int32_t)(q[rlo + k + 1] - base);
+    if (threadIdx.x == 0) qb[0] = base;
+    for (int k = threadIdx.x; k < nr; k += GCS_NT) qend_r[k] = (int32_t)(q[rlo + k + 1] - base);
   }
-  for (int h = 0; h < nsc; ++h) {
-    const int64_t* q = S.LC.qp + (int64_t)h * (n_tot + 1);
+  {
+    const int64_t* q = S.LC.qp + (int64_t)rank * (n_tot + 1);
     const int64_t base = has_c ? q[clo] : 0;
-    if (threadIdx.x == 0) qb_c[h] = base;
-    for (int k = threadIdx.x; k < nc; k += GCS_NT) qend_c[h * S.CT + k] = (int32_t)(q[clo + k + 1] - base);
+    if (threadIdx.x == 0) qb[1] = base;
+    for (int k = threadIdx.x; k < nc; k += GCS_NT) qend_c[k] = (int32_t)(q[clo + k + 1] - base);
   }
-  for (int k = threadIdx.x; k < nr; k += GCS_NT) { rho_s[k] = S.rho[rlo + k]; ps[k] = T(0); }
+  for (int k = threadIdx.x; k < nor; k += GCS_NT) rho_s[k] = S.rho[rlo + orl + k];
+  for (int k = threadIdx.x; k < nr; k += GCS_NT) ps[k] = T(0);
   for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
   for (int i = threadIdx.x; i < ninst; i += GCS_NT) {
     sc[i].state = 0;
@@ -397,20 +419,27 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     sc[i].delta = sc[i].rr = sc[i].bb = 0.0;
   }
   if (streamer && lane == 0)
-    for (int k = 0; k < GCS_NSLOT; ++k) tc::mbar_init(mbar + wp * GCS_NSLOT + k, 1);
+    for (int k = 0; k < NS; ++k) tc::mbar_init(mbar + wp * NS + k, 1);
   if (threadIdx.x == 0) {
     tc::mbar_init(mstage, 1);
     s_done = 0;
-    s_err = 0;
+    s_ok = 1;
+    s_bad[0] = s_bad[1] = 0;
   }
   bulk::fence_init();
-  __syncthreads();
+  // every CTA of the cluster is running (and initialised) before any
+  // distributed shared-memory access
+  auto csync = [&]() {
+    if constexpr (CS > 1) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+  };
+  csync();
 
-  // segment sidx: quads of the CTA's tile and its table
+  // segment 0 = R (A's rows of the tile), 1 = C (A''s rows = the tile's columns)
   // (a tile's quads, and so its chunks, fit 31 bits: qend is int32)
   auto seg_total = [&](int sidx) -> int32_t {
-    if (sidx < nsr) return nr > 0 ? qend_r[sidx * S.RT + nr - 1] : 0;
-    return nc > 0 ? qend_c[(sidx - nsr) * S.CT + nc - 1] : 0;
+    if (sidx == 0) return nr > 0 ? qend_r[nr - 1] : 0;
+    return nc > 0 ? qend_c[nc - 1] : 0;
   };
   auto warp_chunks = [&](int sidx, int32_t& c0, int32_t& c1) {
     const int64_t nch = (seg_total(sidx) + CQ - 1) / CQ;
@@ -418,40 +447,34 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     c1 = (int32_t)(nch * (wp + 1) / GCS_WARPS);
   };
 
-  // ---- producer: this warp's chunks over all segments, cyclically ----
-  // (p_val / p_col: the producer segment's first quad of the CTA's tile)
-  int p_sidx = 0;
+  // ---- producer: this warp's chunks of R then C, cyclically ----
+  int p_sidx = 1;
   int32_t p_c = 0, p_c1 = 0;
-  const unsigned char* p_src = nullptr;   // the producer segment's first chunk of the tile
   bool any_chunks = false;
   if (streamer) {
-    for (int sidx = 0; sidx < nsg; ++sidx) {
+    for (int sidx = 0; sidx < 2; ++sidx) {
       int32_t c0, c1;
       warp_chunks(sidx, c0, c1);
       any_chunks |= c1 > c0;
     }
-    p_sidx = nsg - 1;   // advance() moves to segment 0
   }
   auto advance = [&]() {
     ++p_c;
     while (p_c >= p_c1) {
-      p_sidx = p_sidx + 1 == nsg ? 0 : p_sidx + 1;
+      p_sidx ^= 1;
       warp_chunks(p_sidx, p_c, p_c1);
-      const bool isr = p_sidx < nsr;
-      const int h = isr ? p_sidx : p_sidx - nsr;
-      const int64_t q0 = isr ? qb_r[h] : qb_c[h];   // a whole number of chunks
-      p_src = (isr ? S.LR.data : S.LC.data) + (q0 / CQ) * SLOT;
     }
   };
-  unsigned char* const wring = ring + wp * GCS_NSLOT * SLOT;   // this warp's buffers
-  uint64_t* const wmbar = mbar + wp * GCS_NSLOT;
-  // lane 0 issues the producer's current chunk (always whole) into `slot`
-  // with one bulk copy, then advances
+#define wring (ring + wp * NS * SLOT)   // this warp's buffers
+#define wmbar (mbar + wp * NS)
+  // lane 0 issues the producer's current chunk (always whole; the tile's
+  // piece starts on a chunk) into `slot` with one bulk copy, then advances
   auto issue = [&](int slot) {
     if (lane == 0) {
+      const unsigned char* src = (p_sidx == 0 ? S.LR.data : S.LC.data) + (qb[p_sidx] / CQ + p_c) * SLOT;
       bulk::fence_shared();
       bulk::expect(wmbar + slot, SLOT);
-      bulk::copy(wring + slot * SLOT, p_src + (int64_t)p_c * SLOT, SLOT, wmbar + slot);
+      bulk::copy(wring + slot * SLOT, src, SLOT, wmbar + slot);
     }
     advance();
   };
@@ -459,26 +482,77 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   uint32_t rphase = 0;
   if (streamer && any_chunks) {
     advance();
-    for (int k = 0; k < GCS_NSLOT; ++k) issue(k);
+    for (int k = 0; k < NS; ++k) issue(k);
   }
   uint32_t stage_uses = 0;
   bool bad = false;       // a wait of this thread gave up
+  int dp = 0;             // decision points passed (parity selects s_bad)
 
-  // drain this warp's chunks in flight (GCS_NSLOT of them), then leave
-  auto drain = [&]() {
-    if (streamer && any_chunks) {
-      for (int k = 0; k < GCS_NSLOT; ++k) {
-        const int sl = rslot + k;
-        bulk::wait(wmbar + (sl >= GCS_NSLOT ? sl - GCS_NSLOT : sl), rphase ^ (sl >= GCS_NSLOT ? 1u : 0u),
-                   S.wait_limit);
-      }
-    }
-  };
   auto fail = [&]() {
     bad = true;
     cuda::atomic_ref<int32_t, cuda::thread_scope_device> e(*B.err);
     e.store(1, cuda::memory_order_relaxed);
-    s_err = 1;
+    s_bad[dp & 1] = 1;
+  };
+  // at a decision point, after csync(): did any CTA of the cluster fail in
+  // the phase that just ended?  (partners write the other parity slot in the
+  // next phase, so every CTA reads the same values)
+  auto cluster_bad = [&]() -> bool {
+    int any = s_bad[dp & 1];
+    if constexpr (CS > 1) {
+      cooperative_groups::cluster_group g = cooperative_groups::this_cluster();
+      for (int q = 0; q < CS; ++q) any |= *g.map_shared_rank(&s_bad[dp & 1], q);
+    }
+    ++dp;
+    return any != 0;
+  };
+  // leave: one more cluster barrier (partners may still read this CTA's
+  // shared memory until they reach it), then wait for the copies in flight
+  auto leave = [&]() {
+    csync();
+    if (streamer && any_chunks) {
+      for (int k = 0; k < NS; ++k) {
+        const int sl = rslot + k;
+        bulk::wait(wmbar + (sl >= NS ? sl - NS : sl), rphase ^ (sl >= NS ? 1u : 0u), S.wait_limit);
+      }
+    }
+    if (bad && threadIdx.x == 0 && stage_uses > 0) bulk::wait(mstage, (stage_uses - 1) & 1, S.wait_limit);
+  };
+
+  // grid barrier: cluster barrier, rank 0 arrives on the global counter
+  // (fire-and-forget release add) and polls it (acquire) until every cluster
+  // has arrived, cluster barrier; every CTA of the cluster takes rank 0's
+  // result.  Gives up after the wait limit or when the error word is set.
+  unsigned epoch = 0;
+  auto grid_sync = [&]() -> bool {
+    csync();
+    if (rank == 0 && threadIdx.x == 0) {
+      ++epoch;
+      const unsigned target = epoch * (gridDim.x / CS);
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(B.arrive) : "memory");
+      int ok = 1;
+      long long t0 = 0;
+      for (int k = 0;; ++k) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(B.arrive) : "memory");
+        if (v >= target) break;
+        if (k == 0) t0 = clock64();
+        if ((k & 63) == 63) {
+          int e;
+          asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(B.err) : "memory");
+          if (e != 0 || clock64() - t0 > B.limit) {
+            asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" :: "l"(B.err), "r"(1) : "memory");
+            ok = 0;
+            break;
+          }
+        }
+      }
+      s_ok = ok;
+    }
+    csync();
+    int ok = s_ok;
+    if constexpr (CS > 1) ok = *cooperative_groups::this_cluster().map_shared_rank(&s_ok, 0);
+    return ok != 0;
   };
 
   // stage gathered[lo, hi) (16-byte groups) into shared memory: thread 0
@@ -537,22 +611,29 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     for (int32_t c = c0; c < c1; ++c) {
       if (!bad && !bulk::wait(wmbar + rslot, rphase, S.wait_limit)) fail();
       if (bad) return;
+      // the lane's entries into registers, then the buffer is refilled at
+      // once: the warp keeps every buffer in flight while it computes
       const unsigned char* buf = wring + rslot * SLOT;
       const int32_t cq = c * CQ;
       const int nq = min(CQ, qt - cq);
       const bool valid = quad < nq;
+      using VV = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+      using VI = typename std::conditional<sizeof(T) == 4, int4, int2>::type;
+      const VV v = reinterpret_cast<const VV*>(buf)[lane];
+      const VI ci = reinterpret_cast<const VI*>(buf + VB)[lane];
+      if constexpr (sizeof(T) == 4)
+        asm volatile("" :: "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(ci.x), "r"(ci.y), "r"(ci.z), "r"(ci.w));
+      else
+        asm volatile("" :: "d"(v.x), "d"(v.y), "r"(ci.x), "r"(ci.y));
+      __syncwarp();
+      const int used = rslot;
+      if (++rslot == NS) { rslot = 0; rphase ^= 1u; }
+      issue(used);
       T d = T(0);
       int k = 0x7fffffff;
       if (valid) {
-        if constexpr (sizeof(T) == 4) {
-          const float4 v = reinterpret_cast<const float4*>(buf)[lane];
-          const int4 ci = reinterpret_cast<const int4*>(buf + VB)[lane];
-          d = v.x * st[ci.x] + v.y * st[ci.y] + v.z * st[ci.z] + v.w * st[ci.w];
-        } else {
-          const double2 v = reinterpret_cast<const double2*>(buf)[lane];
-          const int2 ci = reinterpret_cast<const int2*>(buf + VB)[lane];
-          d = v.x * st[ci.x] + v.y * st[ci.y];
-        }
+        if constexpr (sizeof(T) == 4) d = v.x * st[ci.x] + v.y * st[ci.y] + v.z * st[ci.z] + v.w * st[ci.w];
+        else d = v.x * st[ci.x] + v.y * st[ci.y];
         k = rrow;
         while (k < nrow - 1 && qend[k] <= cq + quad) ++k;
       }
@@ -590,9 +671,6 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
         __syncwarp();
         rrow = kl;
       }
-      if (++rslot == GCS_NSLOT) { rslot = 0; rphase ^= 1u; }
-      __syncwarp();
-      issue(rslot == 0 ? GCS_NSLOT - 1 : rslot - 1);
     }
     // the running sum of the last row (it continues in the next warp's share)
     const T sum = warp_allsum(acc0);
@@ -607,16 +685,29 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
         if (headr[w2] >= 0) acc[headr[w2]] += headv[w2];
   };
 
+  // sum over the cluster's CTAs (rank order) of their partial array `a` at k
+  auto cluster_total = [&](T* a, int k) -> T {
+    if constexpr (CS == 1) {
+      return a[k];
+    } else {
+      cooperative_groups::cluster_group g = cooperative_groups::this_cluster();
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < CS; ++q) v += g.map_shared_rank(a, q)[k];
+      return v;
+    }
+  };
+
   // R (control warp): gamma and r'r of the last update, the stop test, beta
   auto control_r = [&](int it) {
-    const double* pc = S.part_c + (int64_t)(it & 1) * 2 * G.nct;
+    const double* pc = S.part_c + (int64_t)(it & 1) * 2 * gridDim.x;
     int running = 0;
     for (int i = 0; i < ninst; ++i) {
       if (sc[i].state != 0) continue;
       double g = 0.0, rr = 0.0;
-      for (int k = G.it_lo[i] + lane; k < G.it_hi[i]; k += 32) {
+      for (int k = S.cc_lo[i] + lane; k < S.cc_hi[i]; k += 32) {
         g += __ldcg(pc + k);
-        rr += __ldcg(pc + G.nct + k);
+        rr += __ldcg(pc + gridDim.x + k);
       }
       g = warp_sum(g);
       rr = warp_sum(rr);
@@ -645,8 +736,8 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     for (int i = 0; i < ninst; ++i) {
       if (sc[i].state != 0) continue;
       double dl = 0.0;
-      for (int k = S.irt_lo[i] + lane; k < S.irt_hi[i]; k += 32) dl += __ldcg(S.part_r + k);
-      for (int k = G.it_lo[i] + lane; k < G.it_hi[i]; k += 32) dl += __ldcg(S.part_d + k);
+      for (int k = S.cr_lo[i] + lane; k < S.cr_hi[i]; k += 32) dl += __ldcg(S.part_r + k);
+      for (int k = S.cc_lo[i] + lane; k < S.cc_hi[i]; k += 32) dl += __ldcg(S.part_d + k);
       dl = warp_sum(dl);
       if (lane == 0) {
         GcgScal& c = sc[i];
@@ -661,30 +752,23 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   };
 
   // CTA sum of two per-thread values in a fixed order (warp sums in T, the
-  // 32 warps combined in double by warp 0); thread 0 gets the totals
+  // warps' values combined in double by warp 0); warp 0 gets the totals
   auto cta_sum2 = [&](T v0, T v1, double& t0, double& t1) {
     v0 = warp_allsum(v0);
     v1 = warp_allsum(v1);
     if (lane == 0) { red[0][wp] = (double)v0; red[1][wp] = (double)v1; }
     __syncthreads();
     if (wp == 0) {
-      t0 = warp_sum(red[0][lane]);
-      t1 = warp_sum(red[1][lane]);
+      t0 = warp_sum(lane <= GCS_WARPS ? red[0][lane] : 0.0);
+      t1 = warp_sum(lane <= GCS_WARPS ? red[1][lane] : 0.0);
     }
   };
 
-  auto leave = [&]() {
-    drain();
-    if (bad && threadIdx.x == 0 && stage_uses > 0) bulk::wait(mstage, (stage_uses - 1) & 1, S.wait_limit);
-  };
 
-  const int64_t r_c0 = has_r ? P.col_off[rinst] : 0, r_c1 = has_r ? P.col_off[rinst + 1] : 0;
-  const int64_t c_r0 = has_c ? P.row_off[cinst] : 0, c_r1 = has_c ? P.row_off[cinst + 1] : 0;
-
-  // ---- zero start: x = 0, r = rhs, z = D^-1 rhs, p = s = 0; r'z, r'r ----
+  // ---- zero start (owned columns): x = 0, r = rhs, z = D^-1 rhs, p = s = 0 ----
   {
     T a0 = T(0), a1 = T(0);
-    for (int64_t j = clo + threadIdx.x; j < chi; j += GCS_NT) {
+    for (int64_t j = oc0 + threadIdx.x; j < oc1; j += GCS_NT) {
       const T bj = S.rhs[j], zj = S.dinv[j] * bj;
       S.x[j] = T(0); S.r[j] = bj; S.z[j] = zj; S.p[j] = T(0); S.s[j] = T(0);
       a0 += bj * zj;
@@ -692,133 +776,126 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     }
     double t0 = 0.0, t1 = 0.0;
     cta_sum2(a0, a1, t0, t1);
-    if (threadIdx.x == 0 && has_c) { S.part_c[b] = t0; S.part_c[G.nct + b] = t1; }
+    if (threadIdx.x == 0) { S.part_c[b] = t0; S.part_c[gridDim.x + b] = t1; }
   }
-  unsigned epoch = 0;
-  if (!gcs_grid_barrier(B.arrive, B.err, B.limit, epoch)) { leave(); return; }
+  if (!grid_sync()) { leave(); return; }
 
   for (int it = 0;; ++it) {
-    // ---- R: t = rho o (A z), one column segment of z at a time; P z ----
-    // (the first segment's stage copy runs while P z is formed)
-    int64_t slo = 0, shi = 0;
-    int32_t gb0 = 0;
-    if (has_r) {
-      gcs_seg(r_c0, r_c1, nsr, 0, slo, shi);
-      gb0 = stage_issue(S.z, slo, shi);
-    }
-    gcg_p_part(P, G, clo, chi, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(S.z + c) : T(0); }, sP);
-    for (int h = 0; h < nsr; ++h) {
-      int32_t gb = gb0;
-      if (h > 0) __syncthreads();   // the stage buffer is free
-      if (has_r) {
-        if (h > 0) {
-          gcs_seg(r_c0, r_c1, nsr, h, slo, shi);
-          gb = stage_issue(S.z, slo, shi);
-        }
-        stage_wait(slo, shi);
+    // ---- R: partial (A z) of the cluster's rows over this CTA's segment ----
+    // (the stage copy runs while P z is formed; the partner CTAs finished
+    // reading ps and ns before the last grid barrier)
+    const int32_t gbr = has_r ? stage_issue(S.z, r_c0, r_c1) : 0;
+    for (int k = threadIdx.x; k < nr; k += GCS_NT) ps[k] = T(0);
+    for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
+    gcg_p_part(P, G, oc0, oc1, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(S.z + c) : T(0); }, sP);
+    if (has_r) stage_wait(r_c0, r_c1);
+    if (streamer) {
+      if (has_r && !bad) consume(0, qend_r, nr, ps, gbr);
+    } else {
+      control_r(it);
+      // the epilogues' operands of the owned columns: z, s, p, x, r, D^-1
+      // (unchanged until the update at the end of C)
+      const int CTo = S.CTo;
+      for (int k = lane; k < noc; k += 32) {
+        const int64_t j = oc0 + k;
+        const T zj = S.z[j], sj = S.s[j], pj = S.p[j], xj = S.x[j], rj = S.r[j], dj = S.dinv[j];
+        epi[k] = zj; epi[CTo + k] = sj; epi[2 * CTo + k] = pj;
+        epi[3 * CTo + k] = xj; epi[4 * CTo + k] = rj; epi[5 * CTo + k] = dj;
       }
-      if (streamer) {
-        if (has_r && !bad) consume(h, qend_r + h * S.RT, nr, ps, gb);
-      } else if (h == 0) {
-        control_r(it);
-        // the epilogues' operands of the CTA's columns: z, s, p, x, r, D^-1
-        // (unchanged until the update at the end of C)
-        const int CTs = S.CT;
-        for (int k = lane; k < nc; k += 32) {
-          const int64_t j = clo + k;
-          const T zj = S.z[j], sj = S.s[j], pj = S.p[j], xj = S.x[j], rj = S.r[j], dj = S.dinv[j];
-          epi[k] = zj; epi[CTs + k] = sj; epi[2 * CTs + k] = pj;
-          epi[3 * CTs + k] = xj; epi[4 * CTs + k] = rj; epi[5 * CTs + k] = dj;
-        }
-      }
-      __syncthreads();
-      if (s_err) { leave(); return; }
-      if (has_r) fixup(ps);
     }
     __syncthreads();
-    if (s_done) { leave(); return; }
+    if (has_r) fixup(ps);
+    csync();   // every CTA's partial row sums are complete
+    if (cluster_bad() || s_done) { leave(); return; }
     {
-      // t = rho o Az; partials sum rho (Az)^2 (rows), sigma z'z + z'Pz (columns)
+      // owned rows: t = rho o (A z); partials sum rho (Az)^2 (rows),
+      // sigma z'z + z'Pz (owned columns)
       T a0 = T(0), a1 = T(0);
-      for (int k = threadIdx.x; k < nr; k += GCS_NT) {
-        const T az = ps[k], tk = rho_s[k] * az;
-        S.t[rlo + k] = tk;
+      for (int k = threadIdx.x; k < nor; k += GCS_NT) {
+        const T az = cluster_total(ps, orl + k), tk = rho_s[k] * az;
+        S.t[rlo + orl + k] = tk;
         a0 += tk * az;
-        ps[k] = T(0);
       }
       const T sig = (T)S.sigma;
-      for (int k = threadIdx.x; k < nc; k += GCS_NT) {
+      for (int k = threadIdx.x; k < noc; k += GCS_NT) {
         const T zj = epi[k];
         a1 += zj * (sig * zj + sP[k]);
       }
       double t0 = 0.0, t1 = 0.0;
       cta_sum2(a0, a1, t0, t1);
-      if (threadIdx.x == 0) {
-        if (has_r) S.part_r[b] = t0;
-        if (has_c) S.part_d[b] = t1;
-      }
+      if (threadIdx.x == 0) { S.part_r[b] = t0; S.part_d[b] = t1; }
     }
-    if (!gcs_grid_barrier(B.arrive, B.err, B.limit, epoch)) { leave(); return; }
+    if (!grid_sync()) { leave(); return; }
 
-    // ---- C: w = sigma z + P z + A't, one row segment of t at a time ----
-    for (int h = 0; h < nsc; ++h) {
-      __syncthreads();
-      int32_t gb = 0;
-      if (has_c) {
-        int64_t lo, hi;
-        gcs_seg(c_r0, c_r1, nsc, h, lo, hi);
-        gb = stage_issue(S.t, lo, hi);
-        stage_wait(lo, hi);
-      }
-      if (streamer) {
-        if (has_c && !bad) consume(nsr + h, qend_c + h * S.CT, nc, ns, gb);
-      } else if (h == 0) {
-        control_c(it);
-      }
-      __syncthreads();
-      if (s_err) { leave(); return; }
-      if (has_c) fixup(ns);
+    // ---- C: partial (A't) of the cluster's columns over this CTA's segment ----
+    const int32_t gbc = has_c ? stage_issue(S.t, c_r0, c_r1) : 0;
+    if (has_c) stage_wait(c_r0, c_r1);
+    if (streamer) {
+      if (has_c && !bad) consume(1, qend_c, nc, ns, gbc);
+    } else {
+      control_c(it);
     }
     __syncthreads();
+    if (has_c) fixup(ns);
+    csync();   // every CTA's partial column sums are complete
+    if (cluster_bad()) { leave(); return; }
 
-    // ---- update of the CTA's columns; partials r'z, r'r ----
+    // ---- update of the owned columns; partials r'z, r'r ----
     {
       T a0 = T(0), a1 = T(0);
       const bool upd = has_c && sc[cinst].state == 0;
       if (upd) {
         const T alpha = (T)sc[cinst].alpha, beta = (T)sc[cinst].beta, sig = (T)S.sigma;
-        const int CTs = S.CT;
-        for (int k = threadIdx.x; k < nc; k += GCS_NT) {
-          const int64_t j = clo + k;
+        const int CTo = S.CTo;
+        for (int k = threadIdx.x; k < noc; k += GCS_NT) {
+          const int64_t j = oc0 + k;
           const T zj = epi[k];
-          const T wj = sig * zj + sP[k] + ns[k];
-          const T sj = wj + beta * epi[CTs + k];
-          const T pj = zj + beta * epi[2 * CTs + k];
+          const T wj = sig * zj + sP[k] + cluster_total(ns, ocl + k);
+          const T sj = wj + beta * epi[CTo + k];
+          const T pj = zj + beta * epi[2 * CTo + k];
           S.s[j] = sj;
           S.p[j] = pj;
-          S.x[j] = epi[3 * CTs + k] + alpha * pj;
-          const T rj = epi[4 * CTs + k] - alpha * sj;
-          const T zn = epi[5 * CTs + k] * rj;
+          S.x[j] = epi[3 * CTo + k] + alpha * pj;
+          const T rj = epi[4 * CTo + k] - alpha * sj;
+          const T zn = epi[5 * CTo + k] * rj;
           S.r[j] = rj;
           S.z[j] = zn;
           a0 += rj * zn;
           a1 += rj * rj;
         }
       }
-      for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
       double t0 = 0.0, t1 = 0.0;
       cta_sum2(a0, a1, t0, t1);
       if (threadIdx.x == 0 && upd) {
-        double* pc = S.part_c + (int64_t)((it + 1) & 1) * 2 * G.nct;
+        double* pc = S.part_c + (int64_t)((it + 1) & 1) * 2 * gridDim.x;
         pc[b] = t0;
-        pc[G.nct + b] = t1;
+        pc[gridDim.x + b] = t1;
       }
     }
-    if (!gcs_grid_barrier(B.arrive, B.err, B.limit, epoch)) { leave(); return; }
+    if (!grid_sync()) { leave(); return; }
   }
+#undef wmbar
+#undef wring
+#undef rinst
+#undef cinst
+#undef noc
+#undef ocl
+#undef nor
+#undef orl
+#undef nc
+#undef nr
+#undef oc1
+#undef oc0
+#undef c_r1
+#undef c_r0
+#undef r_c1
+#undef r_c0
+#undef rhi
+#undef rlo
+#undef chi
+#undef clo
 #undef sc
-#undef qb_c
-#undef qb_r
+#undef qb
 #undef qend_c
 #undef qend_r
 #undef headr

@@ -1870,7 +1870,7 @@ struct GcsPlan : PcgPlanBase {
   Prob<T, T> P{};
   GcgTiles G{};
   GcsArgs<T> S{};
-  int grid = 0, device = 0;
+  int grid = 0, device = 0, cs = 1, nslot = 3;
   int64_t layout_bytes = 0, quads_r = 0, quads_c = 0;
   unsigned* bar = nullptr;
   int32_t* h_err = nullptr;   // pinned
@@ -1984,60 +1984,102 @@ struct GcsPlan : PcgPlanBase {
       for (int64_t j = 0; j < n && short_p; ++j) short_p = prp[j + 1] - prp[j] <= 16;
     }
 
-    // tiles: rows weighted by A's entries, columns by A''s
-    std::vector<int32_t> rt_inst, ct_inst, it_lo(ninst), it_hi(ninst), irt_lo(ninst), irt_hi(ninst);
-    std::vector<int64_t> rt_lo, rt_hi, ct_lo, ct_hi;
-    int64_t RT = 0, CT = 0;
-    gcs_tiles(ro, arp, nsm, rt_inst, rt_lo, rt_hi, &irt_lo, &irt_hi, RT);
-    gcs_tiles(co, atrp, nsm, ct_inst, ct_lo, ct_hi, &it_lo, &it_hi, CT);
-    if (ct_inst.empty()) return fail(COSMO_E_INVAL, "streamed CG plan: no columns");
     int64_t max_n = 0, max_m = 0;
     for (int i = 0; i < ninst; ++i) {
       max_n = std::max(max_n, co[i + 1] - co[i]);
       max_m = std::max(max_m, ro[i + 1] - ro[i]);
     }
 
-    // segments: the fewest that fit the stage next to the rings and tables
-    cudaFuncAttributes fa{};
-    CU(cudaFuncGetAttributes(&fa, k_gcg_stream<T>));
-    const int64_t cap = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+    // cluster size CS (segments of z and t, one per CTA of a cluster) and
+    // ring depth: the smallest CS whose stage, tables and a ring of at least
+    // four chunks per warp fit shared memory (three if none does); tiles per
+    // cluster, as many clusters as the device keeps resident
     const int64_t E = 16 / (int64_t)sizeof(T);
-    int nsr = 1, nsc = 1;
-    int64_t stage_len = 0;
+    std::vector<int32_t> rt_inst, ct_inst, it_lo(ninst), it_hi(ninst), irt_lo(ninst), irt_hi(ninst);
+    std::vector<int64_t> rt_lo, rt_hi, ct_lo, ct_hi;
     GcsSmem sm{};
-    for (;;) {
-      const int64_t lr = (max_n + nsr - 1) / nsr, lc = (max_m + nsc - 1) / nsc;
-      stage_len = std::max(lr, lc) + 2 * E;
-      sm = gcs_smem<T>(stage_len, std::max<int64_t>(RT, 1), CT, nsr, nsc, ninst);
-      if (sm.total <= cap) break;
-      if (lr >= lc) ++nsr; else ++nsc;
-      if (nsr > 64 || nsc > 64)
-        return fail(COSMO_E_INVAL, "streamed CG plan: tiles of %lld rows / %lld columns do not fit shared memory",
-                    (long long)RT, (long long)CT);
+    int64_t RT = 0, CT = 0;
+    auto make_tiles = [&](int K) {
+      rt_inst.clear(); rt_lo.clear(); rt_hi.clear(); ct_inst.clear(); ct_lo.clear(); ct_hi.clear();
+      gcs_tiles(ro, arp, K, rt_inst, rt_lo, rt_hi, &irt_lo, &irt_hi, RT);
+      gcs_tiles(co, atrp, K, ct_inst, ct_lo, ct_hi, &it_lo, &it_hi, CT);
+    };
+    auto smem_for = [&](int c, int ns, int64_t rt, int64_t ct) {
+      const int64_t stage_len = std::max((max_n + c - 1) / c, (max_m + c - 1) / c) + 2 * E;
+      return gcs_smem<T>(ns, stage_len, std::max<int64_t>(rt, 1), std::max<int64_t>(ct, 1),
+                         std::max<int64_t>((rt + c - 1) / c, 1), std::max<int64_t>((ct + c - 1) / c, 1), ninst);
+    };
+    cs = 0;
+    for (int want = 4; want >= 3 && !cs; --want) {
+      for (int c : {1, 2, 4, 8}) {
+        if (nsm / c < ninst) break;
+        cudaFuncAttributes fa{};
+        CU(cudaFuncGetAttributes(&fa, gcs_kernel(c)));
+        const int64_t cap = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+        make_tiles(nsm / c);
+        for (int ns = GCS_MAXSLOT; ns >= want; --ns) {
+          const GcsSmem t = smem_for(c, ns, RT, CT);
+          if (t.total <= cap) { cs = c; nslot = ns; sm = t; break; }
+        }
+        if (cs) break;
+      }
     }
-    CU(cudaFuncSetAttribute(k_gcg_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm.total));
-    int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gcg_stream<T>, GCS_NT, (size_t)sm.total));
-    if (per_sm < 1) return fail(COSMO_E_INVAL, "streamed CG plan: the kernel does not fit an SM");
+    if (!cs) return fail(COSMO_E_INVAL, "streamed CG plan: the instances do not fit shared memory");
+    const void* kern = gcs_kernel(cs);
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm.total));
+    if (cs > 1) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, cs > 8 ? 1 : 0));
+    int ncl = 0;
+    {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(nsm / cs * cs);
+      cfg.blockDim = dim3(GCS_NT);
+      cfg.dynamicSmemBytes = (size_t)sm.total;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      CU(cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg));
+    }
+    ncl = std::min(ncl, nsm / cs);
+    if (ncl < ninst) return fail(COSMO_E_INVAL, "streamed CG plan: %d resident clusters for %d instances", ncl, ninst);
+    if (ncl < nsm / cs) {
+      // fewer resident clusters: larger tiles, so the deepest ring that still fits
+      cudaFuncAttributes fa{};
+      CU(cudaFuncGetAttributes(&fa, kern));
+      const int64_t cap = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+      make_tiles(ncl);
+      for (nslot = GCS_MAXSLOT; nslot >= 2; --nslot) {
+        sm = smem_for(cs, nslot, RT, CT);
+        if (sm.total <= cap) break;
+      }
+      if (nslot < 2) return fail(COSMO_E_INVAL, "streamed CG plan: the instances do not fit shared memory");
+      CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm.total));
+    }
+    if (ct_inst.empty()) return fail(COSMO_E_INVAL, "streamed CG plan: no columns");
 
     // streaming layouts: A by column segment, A' by row segment
-    TRY(build_layout(m, A_rp, A_ci, A_v, d_ro, d_co, nsr, rt_hi, S.LR, quads_r, st));
-    TRY(build_layout(n, AT_rp, AT_ci, AT_v, d_co, d_ro, nsc, ct_hi, S.LC, quads_c, st));
+    TRY(build_layout(m, A_rp, A_ci, A_v, d_ro, d_co, cs, rt_hi, S.LR, quads_r, st));
+    TRY(build_layout(n, AT_rp, AT_ci, AT_v, d_co, d_ro, cs, ct_hi, S.LC, quads_c, st));
 
-    int32_t *d_ct_inst, *d_it_lo, *d_it_hi, *d_rt_inst = nullptr;
+    int32_t *d_ct_inst, *d_rt_inst = nullptr;
     int64_t *d_ct_lo, *d_ct_hi, *d_rt_lo = nullptr, *d_rt_hi = nullptr;
     TRY(a.upload(&d_ct_inst, ct_inst)); TRY(a.upload(&d_ct_lo, ct_lo)); TRY(a.upload(&d_ct_hi, ct_hi));
-    TRY(a.upload(&d_it_lo, it_lo)); TRY(a.upload(&d_it_hi, it_hi));
     if (!rt_inst.empty()) {
       TRY(a.upload(&d_rt_inst, rt_inst)); TRY(a.upload(&d_rt_lo, rt_lo)); TRY(a.upload(&d_rt_hi, rt_hi));
     }
     G.nct = (int32_t)ct_inst.size(); G.ct_inst = d_ct_inst; G.ct_lo = d_ct_lo; G.ct_hi = d_ct_hi;
-    G.it_lo = d_it_lo; G.it_hi = d_it_hi;
     G.nrt = (int32_t)rt_inst.size(); G.rt_inst = d_rt_inst; G.rt_lo = d_rt_lo; G.rt_hi = d_rt_hi;
     G.nnz_a = nnz_a; G.nnz_p = nnz_p;
     G.vq_p = nnz_p > 0 ? (nnz_p / n >= 384 ? 4 : nnz_p / n >= 128 ? 2 : 1) : 0;
     if (sizeof(T) == 8) G.vq_p = std::min(G.vq_p, 2);
-    grid = std::max(G.nct, G.nrt);
+    grid = std::max(G.nct, G.nrt) * cs;
+    // CTAs of each instance's clusters (tiles are per cluster, CS CTAs each)
+    std::vector<int32_t> cc_lo(ninst), cc_hi(ninst), cr_lo(ninst), cr_hi(ninst);
+    for (int i = 0; i < ninst; ++i) {
+      cc_lo[i] = it_lo[i] * cs; cc_hi[i] = it_hi[i] * cs;
+      cr_lo[i] = irt_lo[i] * cs; cr_hi[i] = irt_hi[i] * cs;
+    }
 
     // workspace; z and t are padded to whole 16-byte groups and zeroed once
     // (the stage copies read the padding)
@@ -2048,21 +2090,34 @@ struct GcsPlan : PcgPlanBase {
     CU(cudaMemsetAsync(z, 0, sizeof(T) * (n + 2 * E), st));
     CU(cudaMemsetAsync(t, 0, sizeof(T) * (std::max<int64_t>(m, 1) + 2 * E), st));
     double *part_r, *part_d, *part_c;
-    TRY(a.alloc(&part_r, std::max<int32_t>(G.nrt, 1))); TRY(a.alloc(&part_d, G.nct));
-    TRY(a.alloc(&part_c, 4 * (int64_t)G.nct));
-    CU(cudaMemsetAsync(part_r, 0, sizeof(double) * std::max<int32_t>(G.nrt, 1), st));
-    CU(cudaMemsetAsync(part_d, 0, sizeof(double) * G.nct, st));
-    CU(cudaMemsetAsync(part_c, 0, sizeof(double) * 4 * G.nct, st));
-    int32_t *d_irt_lo, *d_irt_hi;
-    TRY(a.upload(&d_irt_lo, irt_lo)); TRY(a.upload(&d_irt_hi, irt_hi));
+    TRY(a.alloc(&part_r, grid)); TRY(a.alloc(&part_d, grid)); TRY(a.alloc(&part_c, 4 * (int64_t)grid));
+    CU(cudaMemsetAsync(part_r, 0, sizeof(double) * grid, st));
+    CU(cudaMemsetAsync(part_d, 0, sizeof(double) * grid, st));
+    CU(cudaMemsetAsync(part_c, 0, sizeof(double) * 4 * grid, st));
+    int32_t *d_cc_lo, *d_cc_hi, *d_cr_lo, *d_cr_hi;
+    TRY(a.upload(&d_cc_lo, cc_lo)); TRY(a.upload(&d_cc_hi, cc_hi));
+    TRY(a.upload(&d_cr_lo, cr_lo)); TRY(a.upload(&d_cr_hi, cr_hi));
     TRY(a.alloc(&bar, 4));
     CU(cudaMallocHost(&h_err, sizeof(int32_t)));
     S.dinv = dinv; S.r = r; S.z = z; S.p = p; S.s = sv; S.t = t;
-    S.part_r = part_r; S.part_d = part_d; S.part_c = part_c; S.irt_lo = d_irt_lo; S.irt_hi = d_irt_hi;
-    S.short_p = short_p; S.RT = (int32_t)std::max<int64_t>(RT, 1); S.CT = (int32_t)CT; S.sm = sm;
+    S.part_r = part_r; S.part_d = part_d; S.part_c = part_c;
+    S.cc_lo = d_cc_lo; S.cc_hi = d_cc_hi; S.cr_lo = d_cr_lo; S.cr_hi = d_cr_hi;
+    S.short_p = short_p; S.nslot = nslot;
+    S.RT = (int32_t)std::max<int64_t>(RT, 1); S.CT = (int32_t)std::max<int64_t>(CT, 1);
+    S.RTo = (int32_t)std::max<int64_t>((RT + cs - 1) / cs, 1); S.CTo = (int32_t)std::max<int64_t>((CT + cs - 1) / cs, 1);
+    S.sm = sm;
     S.wait_limit = 2000000000LL;   // about 1 s at 2 GHz
     CU(cudaStreamSynchronize(st));
     return COSMO_OK;
+  }
+
+  static const void* gcs_kernel(int c) {
+    switch (c) {
+      case 1: return (const void*)k_gcg_stream<T, 1>;
+      case 2: return (const void*)k_gcg_stream<T, 2>;
+      case 4: return (const void*)k_gcg_stream<T, 4>;
+      default: return (const void*)k_gcg_stream<T, 8>;
+    }
   }
 
   cosmo_status solve(double sigma, const void* rho, const void* rhs, void* x, double tol, int32_t maxit,
@@ -2079,9 +2134,25 @@ struct GcsPlan : PcgPlanBase {
     A.rhs = (const T*)rhs; A.x = (T*)x; A.rho = (const T*)rho; A.sigma = sigma;
     A.tol = tol; A.maxit = maxit; A.iters = iters;
     GridBar B{bar, bar + 1, reinterpret_cast<int32_t*>(bar + 2), 2000000000LL};
-    void* args[] = {(void*)&P, (void*)&G, (void*)&A, (void*)&B};
-    CU(cudaLaunchCooperativeKernel((const void*)k_gcg_stream<T>, dim3(grid), dim3(GCS_NT), args,
-                                   (size_t)S.sm.total, st));
+    // all clusters resident (cooperative), CS CTAs per cluster
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(GCS_NT);
+    cfg.dynamicSmemBytes = (size_t)S.sm.total;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = cs; at[1].val.clusterDim.y = 1; at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    switch (cs) {
+      case 1: CU(cudaLaunchKernelEx(&cfg, k_gcg_stream<T, 1>, P, G, A, B)); break;
+      case 2: CU(cudaLaunchKernelEx(&cfg, k_gcg_stream<T, 2>, P, G, A, B)); break;
+      case 4: CU(cudaLaunchKernelEx(&cfg, k_gcg_stream<T, 4>, P, G, A, B)); break;
+      default: CU(cudaLaunchKernelEx(&cfg, k_gcg_stream<T, 8>, P, G, A, B)); break;
+    }
     g_launches += 2;
     CU(cudaMemcpyAsync(h_err, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -2092,6 +2163,8 @@ struct GcsPlan : PcgPlanBase {
   void info(cosmo_pcg_plan_info* o) const override {
     o->nseg_a = S.LR.nseg;
     o->nseg_at = S.LC.nseg;
+    o->cluster = cs;
+    o->ring_slots = nslot;
     o->grid = grid;
     o->threads = GCS_NT;
     o->layout_bytes = layout_bytes;
