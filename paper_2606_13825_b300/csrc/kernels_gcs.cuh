@@ -128,10 +128,10 @@ struct GcsSmem {
       o_scal, total;
 };
 
-// RT / CT: rows / columns of the largest cluster tile, RTo / CTo: of the
-// largest share one CTA owns in the epilogues
+// RT: rows of the largest cluster tile, RTo / CTo: of the largest share one
+// CTA owns in the epilogues, CTc: rows of A' one CTA streams at most
 template <class T>
-__host__ __device__ inline GcsSmem gcs_smem(int nslot, int64_t stage_len, int64_t RT, int64_t CT, int64_t RTo,
+__host__ __device__ inline GcsSmem gcs_smem(int nslot, int64_t stage_len, int64_t RT, int64_t CTc, int64_t RTo,
                                             int64_t CTo, int ninst) {
   GcsSmem s{};
   int64_t o = 0;
@@ -139,14 +139,14 @@ __host__ __device__ inline GcsSmem gcs_smem(int nslot, int64_t stage_len, int64_
   s.o_mbar = o;   o = gcs_al(o + 8 * (GCS_WARPS * nslot + 1), 128);
   s.o_stage = o;  o += gcs_al(stage_len * (int64_t)sizeof(T), 16);
   s.o_ps = o;     o += gcs_al(RT * (int64_t)sizeof(T), 16);
-  s.o_ns = o;     o += gcs_al(CT * (int64_t)sizeof(T), 16);
+  s.o_ns = o;     o += gcs_al(CTc * (int64_t)sizeof(T), 16);
   s.o_sp = o;     o += gcs_al(CTo * (int64_t)sizeof(T), 16);
   s.o_rho = o;    o += gcs_al(RTo * (int64_t)sizeof(T), 16);
   s.o_epi = o;    o += gcs_al(6 * CTo * (int64_t)sizeof(T), 16);
   s.o_headv = o;  o += gcs_al(GCS_WARPS * (int64_t)sizeof(T), 16);
   s.o_headr = o;  o += gcs_al(GCS_WARPS * 4, 16);
   s.o_qend_r = o; o += gcs_al(RT * 4, 16);
-  s.o_qend_c = o; o += gcs_al(CT * 4, 16);
+  s.o_qend_c = o; o += gcs_al(CTc * 4, 16);
   s.o_qb = o;     o += 16;
   s.o_scal = o;   o += (int64_t)ninst * (int64_t)sizeof(GcgScal);
   s.total = gcs_al(o, 16);
@@ -175,8 +175,15 @@ template <class T> __host__ __device__ inline int64_t gcs_col_at(int64_t e) {
 }
 
 // Tiles are per cluster (index blockIdx.x / CS; G's row / column tile
-// arrays); CTA rank h of a cluster streams segment h of its tile (nseg == CS)
-// and owns the h-th share of the tile's rows and columns in the epilogues.
+// arrays).  R: CTA rank h of a cluster streams segment h of the rows of its
+// tile (A's layout has nseg == CS; the row sums are combined over the
+// cluster).  C, when the instance's whole t fits shared memory (c_split 0):
+// every CTA stages all of t and rank h streams the rows of A' of the h-th
+// share of the tile's columns (A''s layout has one segment, tiles = the
+// CTAs' shares), so no combination is needed; otherwise (c_split 1) like R,
+// segment h of t and of the rows of A' of the whole tile, combined over the
+// cluster.  Rank h owns the h-th share of the tile's rows and columns in the
+// epilogues.
 template <class T>
 struct GcsArgs {
   GcsLayout<T> LR;       // rows of A by column segment (R phase)
@@ -195,6 +202,7 @@ struct GcsArgs {
   int32_t maxit;
   int32_t short_p;       // P rows of at most 16 entries
   int32_t nslot;         // chunk buffers per streaming warp
+  int32_t c_split;       // C by segment of t (1) or over the whole t (0)
   int32_t RT, CT;        // largest cluster tile: rows / columns
   int32_t RTo, CTo;      // largest owned share
   GcsSmem sm;
@@ -343,8 +351,8 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
 
   // the CTA's tile constants live in shared memory and are read where used,
   // so that the streaming loop does not hold them in registers
-  __shared__ int64_t s_t64[10];
-  __shared__ int s_t32[8];
+  __shared__ int64_t s_t64[11];
+  __shared__ int s_t32[9];
 #define clo s_t64[0]
 #define chi s_t64[1]
 #define rlo s_t64[2]
@@ -363,6 +371,8 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
 #define noc s_t32[5]
 #define cinst s_t32[6]
 #define rinst s_t32[7]
+#define ncs s_t32[8]    // rows of A' this CTA streams in C
+#define cb0 s_t64[10]   // the first of them
   const int b = blockIdx.x, ninst = P.ninst, NS = S.nslot;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const bool streamer = wp < GCS_WARPS;
@@ -390,9 +400,18 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     int64_t a0 = 0, a1 = 0;
     if (has_r) gcs_seg(P.col_off[rinst], P.col_off[rinst + 1], CS, rank, a0, a1);
     r_c0 = a0; r_c1 = a1;
-    a0 = a1 = 0;
-    if (has_c) gcs_seg(P.row_off[cinst], P.row_off[cinst + 1], CS, rank, a0, a1);
-    c_r0 = a0; c_r1 = a1;
+    if (S.c_split) {
+      a0 = a1 = 0;
+      if (has_c) gcs_seg(P.row_off[cinst], P.row_off[cinst + 1], CS, rank, a0, a1);
+      c_r0 = a0; c_r1 = a1;
+      ncs = nc;
+      cb0 = clo;
+    } else {
+      c_r0 = has_c ? P.row_off[cinst] : 0;   // the instance's whole t
+      c_r1 = has_c ? P.row_off[cinst + 1] : 0;
+      ncs = noc;
+      cb0 = oc0;
+    }
   }
   __syncthreads();
   const int64_t m_tot = P.m_total, n_tot = P.n_total;
@@ -405,14 +424,15 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     for (int k = threadIdx.x; k < nr; k += GCS_NT) qend_r[k] = (int32_t)(q[rlo + k + 1] - base);
   }
   {
-    const int64_t* q = S.LC.qp + (int64_t)rank * (n_tot + 1);
-    const int64_t base = has_c ? q[clo] : 0;
+    // segment `rank` of the tile's columns, or the one segment of the CTA's own
+    const int64_t* q = S.LC.qp + (S.c_split ? (int64_t)rank * (n_tot + 1) : 0);
+    const int64_t base = has_c ? q[cb0] : 0;
     if (threadIdx.x == 0) qb[1] = base;
-    for (int k = threadIdx.x; k < nc; k += GCS_NT) qend_c[k] = (int32_t)(q[clo + k + 1] - base);
+    for (int k = threadIdx.x; k < ncs; k += GCS_NT) qend_c[k] = (int32_t)(q[cb0 + k + 1] - base);
   }
   for (int k = threadIdx.x; k < nor; k += GCS_NT) rho_s[k] = S.rho[rlo + orl + k];
   for (int k = threadIdx.x; k < nr; k += GCS_NT) ps[k] = T(0);
-  for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
+  for (int k = threadIdx.x; k < ncs; k += GCS_NT) ns[k] = T(0);
   for (int i = threadIdx.x; i < ninst; i += GCS_NT) {
     sc[i].state = 0;
     sc[i].alpha = sc[i].alpha_old = sc[i].beta = sc[i].gamma = sc[i].gamma_old = 0.0;
@@ -439,7 +459,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   // (a tile's quads, and so its chunks, fit 31 bits: qend is int32)
   auto seg_total = [&](int sidx) -> int32_t {
     if (sidx == 0) return nr > 0 ? qend_r[nr - 1] : 0;
-    return nc > 0 ? qend_c[nc - 1] : 0;
+    return ncs > 0 ? qend_c[ncs - 1] : 0;
   };
   auto warp_chunks = [&](int sidx, int32_t& c0, int32_t& c1) {
     const int64_t nch = (seg_total(sidx) + CQ - 1) / CQ;
@@ -786,7 +806,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     // reading ps and ns before the last grid barrier)
     const int32_t gbr = has_r ? stage_issue(S.z, r_c0, r_c1) : 0;
     for (int k = threadIdx.x; k < nr; k += GCS_NT) ps[k] = T(0);
-    for (int k = threadIdx.x; k < nc; k += GCS_NT) ns[k] = T(0);
+    for (int k = threadIdx.x; k < ncs; k += GCS_NT) ns[k] = T(0);
     gcg_p_part(P, G, oc0, oc1, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(S.z + c) : T(0); }, sP);
     if (has_r) stage_wait(r_c0, r_c1);
     if (streamer) {
@@ -827,17 +847,18 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     }
     if (!grid_sync()) { leave(); return; }
 
-    // ---- C: partial (A't) of the cluster's columns over this CTA's segment ----
+    // ---- C: (A't) of the CTA's own columns over the whole t, or the partial
+    // of the tile's columns over this CTA's segment of t ----
     const int32_t gbc = has_c ? stage_issue(S.t, c_r0, c_r1) : 0;
     if (has_c) stage_wait(c_r0, c_r1);
     if (streamer) {
-      if (has_c && !bad) consume(1, qend_c, nc, ns, gbc);
+      if (has_c && !bad) consume(1, qend_c, ncs, ns, gbc);
     } else {
       control_c(it);
     }
     __syncthreads();
     if (has_c) fixup(ns);
-    csync();   // every CTA's partial column sums are complete
+    csync();   // every CTA's partial column sums are complete (split C)
     if (cluster_bad()) { leave(); return; }
 
     // ---- update of the owned columns; partials r'z, r'r ----
@@ -850,7 +871,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
         for (int k = threadIdx.x; k < noc; k += GCS_NT) {
           const int64_t j = oc0 + k;
           const T zj = epi[k];
-          const T wj = sig * zj + sP[k] + cluster_total(ns, ocl + k);
+          const T wj = sig * zj + sP[k] + (S.c_split ? cluster_total(ns, ocl + k) : ns[k]);
           const T sj = wj + beta * epi[CTo + k];
           const T pj = zj + beta * epi[2 * CTo + k];
           S.s[j] = sj;
@@ -876,6 +897,8 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   }
 #undef wmbar
 #undef wring
+#undef cb0
+#undef ncs
 #undef rinst
 #undef cinst
 #undef noc

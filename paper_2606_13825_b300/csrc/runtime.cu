@@ -1870,7 +1870,7 @@ struct GcsPlan : PcgPlanBase {
   Prob<T, T> P{};
   GcgTiles G{};
   GcsArgs<T> S{};
-  int grid = 0, device = 0, cs = 1, nslot = 3;
+  int grid = 0, device = 0, cs = 1, nslot = 3, c_split = 0;
   int64_t layout_bytes = 0, quads_r = 0, quads_c = 0;
   unsigned* bar = nullptr;
   int32_t* h_err = nullptr;   // pinned
@@ -2004,10 +2004,12 @@ struct GcsPlan : PcgPlanBase {
       gcs_tiles(ro, arp, K, rt_inst, rt_lo, rt_hi, &irt_lo, &irt_hi, RT);
       gcs_tiles(co, atrp, K, ct_inst, ct_lo, ct_hi, &it_lo, &it_hi, CT);
     };
-    auto smem_for = [&](int c, int ns, int64_t rt, int64_t ct) {
-      const int64_t stage_len = std::max((max_n + c - 1) / c, (max_m + c - 1) / c) + 2 * E;
-      return gcs_smem<T>(ns, stage_len, std::max<int64_t>(rt, 1), std::max<int64_t>(ct, 1),
-                         std::max<int64_t>((rt + c - 1) / c, 1), std::max<int64_t>((ct + c - 1) / c, 1), ninst);
+    // R stages one segment of z; C the whole t (split 0) or one segment (1)
+    auto smem_for = [&](int c, int ns, int64_t rt, int64_t ct, int split) {
+      const int64_t stage_len = std::max((max_n + c - 1) / c, split ? (max_m + c - 1) / c : max_m) + 2 * E;
+      const int64_t cto = std::max<int64_t>((ct + c - 1) / c, 1);
+      return gcs_smem<T>(ns, stage_len, std::max<int64_t>(rt, 1), split ? std::max<int64_t>(ct, 1) : cto,
+                         std::max<int64_t>((rt + c - 1) / c, 1), cto, ninst);
     };
     cs = 0;
     for (int want = 4; want >= 3 && !cs; --want) {
@@ -2017,10 +2019,11 @@ struct GcsPlan : PcgPlanBase {
         CU(cudaFuncGetAttributes(&fa, gcs_kernel(c)));
         const int64_t cap = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
         make_tiles(nsm / c);
-        for (int ns = GCS_MAXSLOT; ns >= want; --ns) {
-          const GcsSmem t = smem_for(c, ns, RT, CT);
-          if (t.total <= cap) { cs = c; nslot = ns; sm = t; break; }
-        }
+        for (int split = 0; split < 2 && !cs; ++split)
+          for (int ns = GCS_MAXSLOT; ns >= want; --ns) {
+            const GcsSmem t = smem_for(c, ns, RT, CT, split);
+            if (t.total <= cap) { cs = c; nslot = ns; sm = t; c_split = split; break; }
+          }
         if (cs) break;
       }
     }
@@ -2050,7 +2053,7 @@ struct GcsPlan : PcgPlanBase {
       const int64_t cap = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
       make_tiles(ncl);
       for (nslot = GCS_MAXSLOT; nslot >= 2; --nslot) {
-        sm = smem_for(cs, nslot, RT, CT);
+        sm = smem_for(cs, nslot, RT, CT, c_split);
         if (sm.total <= cap) break;
       }
       if (nslot < 2) return fail(COSMO_E_INVAL, "streamed CG plan: the instances do not fit shared memory");
@@ -2058,9 +2061,16 @@ struct GcsPlan : PcgPlanBase {
     }
     if (ct_inst.empty()) return fail(COSMO_E_INVAL, "streamed CG plan: no columns");
 
-    // streaming layouts: A by column segment, A' by row segment
+    // streaming layouts: A by column segment (one per CTA of a cluster),
+    // A' whole, its tiles the CTAs' shares of the cluster tiles' columns
+    std::vector<int64_t> own_hi;
+    for (size_t i = 0; i < ct_lo.size(); ++i) {
+      const int64_t len = ct_hi[i] - ct_lo[i];
+      for (int q = 1; q <= cs; ++q) own_hi.push_back(ct_lo[i] + len * q / cs);
+    }
     TRY(build_layout(m, A_rp, A_ci, A_v, d_ro, d_co, cs, rt_hi, S.LR, quads_r, st));
-    TRY(build_layout(n, AT_rp, AT_ci, AT_v, d_co, d_ro, cs, ct_hi, S.LC, quads_c, st));
+    if (c_split) TRY(build_layout(n, AT_rp, AT_ci, AT_v, d_co, d_ro, cs, ct_hi, S.LC, quads_c, st));
+    else TRY(build_layout(n, AT_rp, AT_ci, AT_v, d_co, d_ro, 1, own_hi, S.LC, quads_c, st));
 
     int32_t *d_ct_inst, *d_rt_inst = nullptr;
     int64_t *d_ct_lo, *d_ct_hi, *d_rt_lo = nullptr, *d_rt_hi = nullptr;
@@ -2102,7 +2112,7 @@ struct GcsPlan : PcgPlanBase {
     S.dinv = dinv; S.r = r; S.z = z; S.p = p; S.s = sv; S.t = t;
     S.part_r = part_r; S.part_d = part_d; S.part_c = part_c;
     S.cc_lo = d_cc_lo; S.cc_hi = d_cc_hi; S.cr_lo = d_cr_lo; S.cr_hi = d_cr_hi;
-    S.short_p = short_p; S.nslot = nslot;
+    S.short_p = short_p; S.nslot = nslot; S.c_split = c_split;
     S.RT = (int32_t)std::max<int64_t>(RT, 1); S.CT = (int32_t)std::max<int64_t>(CT, 1);
     S.RTo = (int32_t)std::max<int64_t>((RT + cs - 1) / cs, 1); S.CTo = (int32_t)std::max<int64_t>((CT + cs - 1) / cs, 1);
     S.sm = sm;
