@@ -539,16 +539,19 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     if (bad && threadIdx.x == 0 && stage_uses > 0) bulk::wait(mstage, (stage_uses - 1) & 1, S.wait_limit);
   };
 
-  // grid barrier: cluster barrier, rank 0 arrives on the global counter
-  // (fire-and-forget release add) and polls it (acquire) until every cluster
-  // has arrived, cluster barrier; every CTA of the cluster takes rank 0's
-  // result.  Gives up after the wait limit or when the error word is set.
+  // grid barrier: thread 0 of every CTA adds to the global counter (a
+  // fire-and-forget release add) and polls it (acquire) until every CTA has
+  // arrived; the CTA barrier then extends that to its other threads.  A CTA
+  // passes only when all CTAs have finished the phase, including their
+  // reads of partner CTAs' shared memory.  Gives up after the wait limit or
+  // when the error word is set; the caller then marks the CTA bad and the
+  // cluster leaves together at its next decision point.
   unsigned epoch = 0;
   auto grid_sync = [&]() -> bool {
-    csync();
-    if (rank == 0 && threadIdx.x == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
       ++epoch;
-      const unsigned target = epoch * (gridDim.x / CS);
+      const unsigned target = epoch * gridDim.x;
       asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(B.arrive) : "memory");
       int ok = 1;
       long long t0 = 0;
@@ -561,7 +564,6 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
           int e;
           asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(B.err) : "memory");
           if (e != 0 || clock64() - t0 > B.limit) {
-            asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" :: "l"(B.err), "r"(1) : "memory");
             ok = 0;
             break;
           }
@@ -569,10 +571,8 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
       }
       s_ok = ok;
     }
-    csync();
-    int ok = s_ok;
-    if constexpr (CS > 1) ok = *cooperative_groups::this_cluster().map_shared_rank(&s_ok, 0);
-    return ok != 0;
+    __syncthreads();
+    return s_ok != 0;
   };
 
   // stage gathered[lo, hi) (16-byte groups) into shared memory: thread 0
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     cta_sum2(a0, a1, t0, t1);
     if (threadIdx.x == 0) { S.part_c[b] = t0; S.part_c[gridDim.x + b] = t1; }
   }
-  if (!grid_sync()) { leave(); return; }
+  if (!grid_sync()) fail();
 
   for (int it = 0;; ++it) {
     // ---- R: partial (A z) of the cluster's rows over this CTA's segment ----
@@ -845,7 +845,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
       cta_sum2(a0, a1, t0, t1);
       if (threadIdx.x == 0) { S.part_r[b] = t0; S.part_d[b] = t1; }
     }
-    if (!grid_sync()) { leave(); return; }
+    if (!grid_sync()) fail();
 
     // ---- C: (A't) of the CTA's own columns over the whole t, or the partial
     // of the tile's columns over this CTA's segment of t ----
@@ -893,7 +893,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
         pc[gridDim.x + b] = t1;
       }
     }
-    if (!grid_sync()) { leave(); return; }
+    if (!grid_sync()) fail();
   }
 #undef wmbar
 #undef wring
