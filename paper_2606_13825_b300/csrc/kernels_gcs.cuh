@@ -201,6 +201,8 @@ struct GcsArgs {
   double tol;
   int32_t maxit;
   int32_t short_p;       // P rows of at most 16 entries
+  int32_t p_diag;        // P diagonal (or absent): P z of the owned columns is
+                         // formed where z is, in the update
   int32_t nslot;         // chunk buffers per streaming warp
   int32_t c_split;       // C by segment of t (1) or over the whole t (0)
   int32_t RT, CT;        // largest cluster tile: rows / columns
@@ -785,12 +787,20 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   };
 
 
+  // P_jj of a diagonal P (0 for an empty row or no P)
+  auto pdiag = [&](int64_t j) -> T {
+    if (!P.P_rp) return T(0);
+    const int64_t e0 = __ldg(P.P_rp + j);
+    return __ldg(P.P_rp + j + 1) > e0 ? __ldg(P.P_v + e0) : T(0);
+  };
+
   // ---- zero start (owned columns): x = 0, r = rhs, z = D^-1 rhs, p = s = 0 ----
   {
     T a0 = T(0), a1 = T(0);
     for (int64_t j = oc0 + threadIdx.x; j < oc1; j += GCS_NT) {
       const T bj = S.rhs[j], zj = S.dinv[j] * bj;
       S.x[j] = T(0); S.r[j] = bj; S.z[j] = zj; S.p[j] = T(0); S.s[j] = T(0);
+      if (S.p_diag) sP[j - oc0] = pdiag(j) * zj;
       a0 += bj * zj;
       a1 += bj * bj;
     }
@@ -807,7 +817,10 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     const int32_t gbr = has_r ? stage_issue(S.z, r_c0, r_c1) : 0;
     for (int k = threadIdx.x; k < nr; k += GCS_NT) ps[k] = T(0);
     for (int k = threadIdx.x; k < ncs; k += GCS_NT) ns[k] = T(0);
-    gcg_p_part(P, G, oc0, oc1, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(S.z + c) : T(0); }, sP);
+    if (!S.p_diag)
+      gcg_p_part(P, G, oc0, oc1, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(S.z + c) : T(0); }, sP);
+    else
+      __syncthreads();   // the resets above precede the accumulation
     if (has_r) stage_wait(r_c0, r_c1);
     if (streamer) {
       if (has_r && !bad) consume(0, qend_r, nr, ps, gbr);
@@ -881,6 +894,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
           const T zn = epi[5 * CTo + k] * rj;
           S.r[j] = rj;
           S.z[j] = zn;
+          if (S.p_diag) sP[k] = pdiag(j) * zn;   // P z of the next iteration
           a0 += rj * zn;
           a1 += rj * rj;
         }

@@ -1968,7 +1968,7 @@ struct GcsPlan : PcgPlanBase {
     TRY(a.upload(&d_co, co));
     TRY(a.upload(&d_ro, ro));
     P.ninst = ninst; P.n_total = n; P.m_total = m; P.col_off = d_co; P.row_off = d_ro;
-    int short_p = 1;
+    int short_p = 1, p_diag = 1;
     if (P_rp) {
       int64_t* prp_d;
       int32_t* pci_d = nullptr;
@@ -1982,6 +1982,12 @@ struct GcsPlan : PcgPlanBase {
       }
       P.P_rp = prp_d; P.P_ci = pci_d; P.P_v = pv_d;
       for (int64_t j = 0; j < n && short_p; ++j) short_p = prp[j + 1] - prp[j] <= 16;
+      // diagonal: every row holds at most its diagonal entry
+      std::vector<int32_t> pci(nnz_p);
+      if (nnz_p > 0) CU(cudaMemcpy(pci.data(), P_ci, sizeof(int32_t) * nnz_p, cudaMemcpyDeviceToHost));
+      p_diag = 1;
+      for (int64_t j = 0; j < n && p_diag; ++j)
+        p_diag = prp[j + 1] - prp[j] == 0 || (prp[j + 1] - prp[j] == 1 && pci[prp[j]] == j);
     }
 
     int64_t max_n = 0, max_m = 0;
@@ -2112,7 +2118,7 @@ struct GcsPlan : PcgPlanBase {
     S.dinv = dinv; S.r = r; S.z = z; S.p = p; S.s = sv; S.t = t;
     S.part_r = part_r; S.part_d = part_d; S.part_c = part_c;
     S.cc_lo = d_cc_lo; S.cc_hi = d_cc_hi; S.cr_lo = d_cr_lo; S.cr_hi = d_cr_hi;
-    S.short_p = short_p; S.nslot = nslot; S.c_split = c_split;
+    S.short_p = short_p; S.p_diag = p_diag; S.nslot = nslot; S.c_split = c_split;
     S.RT = (int32_t)std::max<int64_t>(RT, 1); S.CT = (int32_t)std::max<int64_t>(CT, 1);
     S.RTo = (int32_t)std::max<int64_t>((RT + cs - 1) / cs, 1); S.CTo = (int32_t)std::max<int64_t>((CT + cs - 1) / cs, 1);
     S.sm = sm;
