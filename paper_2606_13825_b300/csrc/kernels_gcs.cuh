@@ -203,6 +203,7 @@ struct GcsArgs {
   int32_t short_p;       // P rows of at most 16 entries
   int32_t p_diag;        // P diagonal (or absent): P z of the owned columns is
                          // formed where z is, in the update
+  const T* pd;           // [n] P_jj when p_diag
   int32_t nslot;         // chunk buffers per streaming warp
   int32_t c_split;       // C by segment of t (1) or over the whole t (0)
   int32_t RT, CT;        // largest cluster tile: rows / columns
@@ -787,20 +788,13 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   };
 
 
-  // P_jj of a diagonal P (0 for an empty row or no P)
-  auto pdiag = [&](int64_t j) -> T {
-    if (!P.P_rp) return T(0);
-    const int64_t e0 = __ldg(P.P_rp + j);
-    return __ldg(P.P_rp + j + 1) > e0 ? __ldg(P.P_v + e0) : T(0);
-  };
-
   // ---- zero start (owned columns): x = 0, r = rhs, z = D^-1 rhs, p = s = 0 ----
   {
     T a0 = T(0), a1 = T(0);
     for (int64_t j = oc0 + threadIdx.x; j < oc1; j += GCS_NT) {
       const T bj = S.rhs[j], zj = S.dinv[j] * bj;
       S.x[j] = T(0); S.r[j] = bj; S.z[j] = zj; S.p[j] = T(0); S.s[j] = T(0);
-      if (S.p_diag) sP[j - oc0] = pdiag(j) * zj;
+      if (S.p_diag) sP[j - oc0] = S.pd[j] * zj;
       a0 += bj * zj;
       a1 += bj * bj;
     }
@@ -894,7 +888,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
           const T zn = epi[5 * CTo + k] * rj;
           S.r[j] = rj;
           S.z[j] = zn;
-          if (S.p_diag) sP[k] = pdiag(j) * zn;   // P z of the next iteration
+          if (S.p_diag) sP[k] = S.pd[j] * zn;   // P z of the next iteration
           a0 += rj * zn;
           a1 += rj * rj;
         }

@@ -1969,6 +1969,7 @@ struct GcsPlan : PcgPlanBase {
     TRY(a.upload(&d_ro, ro));
     P.ninst = ninst; P.n_total = n; P.m_total = m; P.col_off = d_co; P.row_off = d_ro;
     int short_p = 1, p_diag = 1;
+    T* pd_dev = nullptr;
     if (P_rp) {
       int64_t* prp_d;
       int32_t* pci_d = nullptr;
@@ -1988,6 +1989,13 @@ struct GcsPlan : PcgPlanBase {
       p_diag = 1;
       for (int64_t j = 0; j < n && p_diag; ++j)
         p_diag = prp[j + 1] - prp[j] == 0 || (prp[j + 1] - prp[j] == 1 && pci[prp[j]] == j);
+      if (p_diag) {   // P_jj as a dense vector (0 for an empty row)
+        std::vector<T> pv(nnz_p), pdh(n, T(0));
+        if (nnz_p > 0) CU(cudaMemcpy(pv.data(), P_v, sizeof(T) * nnz_p, cudaMemcpyDeviceToHost));
+        for (int64_t j = 0; j < n; ++j)
+          if (prp[j + 1] > prp[j]) pdh[j] = pv[prp[j]];
+        TRY(a.upload(&pd_dev, pdh));
+      }
     }
 
     int64_t max_n = 0, max_m = 0;
@@ -2118,7 +2126,11 @@ struct GcsPlan : PcgPlanBase {
     S.dinv = dinv; S.r = r; S.z = z; S.p = p; S.s = sv; S.t = t;
     S.part_r = part_r; S.part_d = part_d; S.part_c = part_c;
     S.cc_lo = d_cc_lo; S.cc_hi = d_cc_hi; S.cr_lo = d_cr_lo; S.cr_hi = d_cr_hi;
-    S.short_p = short_p; S.p_diag = p_diag; S.nslot = nslot; S.c_split = c_split;
+    if (p_diag && !pd_dev) {   // no P: zeros
+      TRY(a.alloc(&pd_dev, n));
+      CU(cudaMemsetAsync(pd_dev, 0, sizeof(T) * n, st));
+    }
+    S.short_p = short_p; S.p_diag = p_diag; S.pd = pd_dev; S.nslot = nslot; S.c_split = c_split;
     S.RT = (int32_t)std::max<int64_t>(RT, 1); S.CT = (int32_t)std::max<int64_t>(CT, 1);
     S.RTo = (int32_t)std::max<int64_t>((RT + cs - 1) / cs, 1); S.CTo = (int32_t)std::max<int64_t>((CT + cs - 1) / cs, 1);
     S.sm = sm;
