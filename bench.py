@@ -246,6 +246,12 @@ def run_linsys(args, n=50000):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
         its.append(int(iters[0]))
+    # per-phase breakdown from one more solve with the plan's phase timer on
+    # (not part of the timed steps)
+    plan.set_timing(True)
+    plan.solve(1e-6, rho, rhs, tol=1e-6, max_iter=2000, x=x, iters=iters)
+    phases = {k: {"mean_us": round(v[0], 3), "slowest_cta_us": round(v[1], 3)} for k, v in plan.timing().items()}
+    plan.set_timing(False)
     m = A.shape[0]
     nnzA, nnzP = A.nnz, d["P"].nnz
     bytes_it = (nnzP + 2 * nnzA) * 8 + 4 * (2 * n + m) + 6 * n * 4
@@ -260,7 +266,7 @@ def run_linsys(args, n=50000):
                          "timing": "CUDA events around each solve (preconditioner + one cooperative "
                                    "launch), the setup iteration and the discarded last matvec "
                                    "included"},
-            "plan": info,
+            "plan": info, "phases_per_iteration": phases,
             "config": {"workload": "App. B linear system", "n": n, "m": m, "nnzA": nnzA,
                        "precision": "float values/vectors, double reductions", "tol": 1e-6,
                        "l2": "A and A' (200 MB) exceed L2 each iteration"}}

@@ -384,6 +384,29 @@ cosmo_status cosmo_pcg_plan_solve(cosmo_pcg_plan* plan, double sigma, const void
 cosmo_status cosmo_pcg_plan_get_info(const cosmo_pcg_plan* plan, cosmo_pcg_plan_info* out);
 cosmo_status cosmo_pcg_plan_destroy(cosmo_pcg_plan* plan);
 
+/* Phase timer of a plan's solves (off by default; no effect on results).
+ * With timing on, thread 0 of every CTA records %globaltimer at the phase
+ * boundaries of the first 64 iterations, and each solve ends by reducing
+ * them; cosmo_pcg_plan_get_timing then returns, per phase, the mean over
+ * CTAs and iterations (mean_us) and the mean over iterations of the slowest
+ * CTA (slowest_us), in microseconds, COSMO_PCG_PHASES entries each (either
+ * may be NULL):
+ *   0 iteration start -> the R stage (the CTA's segment of z) in shared memory
+ *   1 warp 0's share of the R stream (rows of A)
+ *   2 the other warps' R stream finishing, and the cluster barrier
+ *   3 R epilogue (t = rho o Az of the CTA's rows, partial sums)
+ *   4 R -> C grid barrier
+ *   5 the C stage (t) in shared memory
+ *   6 warp 0's share of the C stream (rows of A')
+ *   7 the other warps' C stream finishing, and the cluster barrier
+ *   8 the update of the CTA's columns
+ *   9 C -> R grid barrier
+ * Enabling allocates the stamp buffer (device memory of the plan).
+ * Errors: E_INVAL, E_NOMEM. */
+#define COSMO_PCG_PHASES 10
+cosmo_status cosmo_pcg_plan_set_timing(cosmo_pcg_plan* plan, int32_t enable);
+cosmo_status cosmo_pcg_plan_get_timing(const cosmo_pcg_plan* plan, double* mean_us, double* slowest_us);
+
 /* The same solve as cosmo_pcg_solve, for callers that must not allocate device
  * memory while they run (a controller calling the solver at a fixed rate
  * cannot risk cudaMalloc's latency, implicit synchronisation or failure; a

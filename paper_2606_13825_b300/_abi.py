@@ -61,6 +61,11 @@ class BatchInfo(ctypes.Structure):
                 ("cg_solves", c_int64), ("adj_cg_iters", c_int64), ("adj_cg_solves", c_int64)]
 
 
+PCG_PHASES = ("R stage", "R stream (warp 0)", "R stream rest + cluster barrier", "R epilogue",
+              "R->C grid barrier", "C stage", "C stream (warp 0)", "C stream rest + cluster barrier",
+              "update", "C->R grid barrier")
+
+
 class PcgPlanInfo(ctypes.Structure):
     _fields_ = [("nseg_a", c_int32), ("nseg_at", c_int32), ("grid", c_int32), ("threads", c_int32),
                 ("cluster", c_int32), ("ring_slots", c_int32),
@@ -108,6 +113,8 @@ _SIGS = {
                                        c_int32, c_void_p, c_void_p]),
     "cosmo_pcg_plan_get_info": (c_int32, [c_void_p, POINTER(PcgPlanInfo)]),
     "cosmo_pcg_plan_destroy": (c_int32, [c_void_p]),
+    "cosmo_pcg_plan_set_timing": (c_int32, [c_void_p, c_int32]),
+    "cosmo_pcg_plan_get_timing": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "cosmo_psd_project": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_psd_dk_backward": (c_int32, [c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),

@@ -469,42 +469,6 @@ __global__ void __launch_bounds__(GCG_NT, 4) k_gcg_cols(Prob<T, T> P, GcgTiles G
   }
 }
 
-// ---- shared-memory gathers ------------------------------------------------
-// A warp's 32 gathers of random columns touch 32 different 128-byte lines,
-// and the L1 serves about one line per clock: at the App. B density that, not
-// HBM, bounds the global-gather kernels above.  When the gathered vector of
-// one instance fits in shared memory the persistent kernel below (one
-// 1024-thread CTA per SM) stages it first and gathers from shared memory (a
-// few bank conflicts per warp instead of 32 line lookups).  A column (row)
-// index outside the instance's range reads as zero instead of outside the
-// staged vector.
-constexpr int GCG_NT_SMEM = 1024;
-
-// st[k] = src[gb + k] for the 16-byte groups covering [lo, hi), gb = lo
-// rounded down to a group boundary (returned): 16-byte loads and 16-byte
-// shared-memory stores (no bank conflicts).  src must be 16-byte aligned and
-// readable up to hi rounded up to a group.
-template <class T>
-__device__ __forceinline__ int64_t gcg_stage_aligned(const T* __restrict__ src, int64_t lo, int64_t hi, T* st) {
-  constexpr int E = 16 / sizeof(T);
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int64_t gb = lo & ~(int64_t)(E - 1);
-  const int64_t nv = (hi - gb + E - 1) / E;
-  const V* sv = reinterpret_cast<const V*>(src + gb);
-  V* dv = reinterpret_cast<V*>(st);
-  for (int64_t ib = threadIdx.x; ib < nv; ib += 8 * (int64_t)blockDim.x) {
-    V f[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (ib + q * blockDim.x < nv) f[q] = __ldcg(sv + ib + q * blockDim.x);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (ib + q * blockDim.x < nv) dv[ib + q * blockDim.x] = f[q];
-  }
-  return gb;
-}
-
-
 // update: x += alpha p^, r -= alpha u, z = D^-1 r, p <- p^; the last tile of
 // the instance forms r'z, beta and the state of iteration it + 1.
 template <class T, int NT = GCG_NT>
@@ -561,63 +525,9 @@ __global__ void __launch_bounds__(NT) k_gcg_update(Prob<T, T> P, GcgTiles G, Gcg
 }
 
 
-// off[(h - 1) * m + r] = entries of row r (of instance i) with a column below
-// col_off[i] + h * ceil(n_i / nseg), h = 1 .. nseg - 1 (one warp per row).
-// Column indices must increase along each row; a row where they do not sets
-// *unsorted.
-template <class T>
-__global__ void k_gcg_split(Prob<T, T> P, int nseg, int32_t* __restrict__ off, int32_t* unsorted) {
-  const int lane = threadIdx.x & 31;
-  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= P.m_total) return;
-  int lo = 0, hi = P.ninst;   // instance of row r: row_off[i] <= r < row_off[i + 1]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (P.row_off[mid] <= r) lo = mid; else hi = mid;
-  }
-  const int64_t c0 = P.col_off[lo], nc = P.col_off[lo + 1] - c0;
-  const int64_t w = (nc + nseg - 1) / nseg;
-  const int64_t e0 = P.A_rp[r], e1 = P.A_rp[r + 1];
-  bool bad = false;
-  for (int h = 1; h < nseg; ++h) {
-    const int64_t cut = c0 + min(nc, h * w);
-    int cnt = 0;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-      const int32_t c = P.A_ci[e];
-      cnt += c < cut;
-      if (h == 1 && e + 1 < e1 && P.A_ci[e + 1] <= c) bad = true;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) off[(int64_t)(h - 1) * P.m_total + r] = cnt;
-  }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(unsorted, 1);
-}
-
-// ===========================================================================
-// Persistent grid-wide CG: the whole solve in one cooperative launch.
-//
-// One CTA per SM (GCG_NT_SMEM threads, the gathered vector of an instance in
-// shared memory), each CTA owning one row tile and one column tile.  The
-// iteration is the Chronopoulos-Gear form of Jacobi-PCG, which produces the
-// same iterates as the textbook form in exact arithmetic but needs a single
-// reduction point per iteration, and applies the operator to z = D^-1 r (a
-// vector in its final form when the matvec starts):
-//
-//   R:  t = rho o (A z)                        (z staged in shared memory)
-//   C:  w = sigma z + P z + A't,  delta = z'w  (t staged in shared memory)
-//   U:  beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old)
-//       (beta = 0, alpha = gamma / delta at it = 0)
-//       p = z + beta p,  s = w + beta s  (= M p),  x += alpha p,  r -= alpha s,
-//       z = D^-1 r,  gamma = r'z,  rr = r'r
-//
-// with a grid barrier after each phase.  Every CTA forms every instance's
-// scalars itself from the per-column-tile partials (one warp per instance,
-// lanes over tiles, fixed order): all CTAs hold bitwise-identical scalars and
-// take the same decisions without atomics.  Each barrier wait gives up after
-// a bounded number of clock cycles, sets the error word and returns.
-// ===========================================================================
-
+// Grid barrier words of the streamed solve (zero before the launch): the
+// arrival counter, a spare word, the error word, and the clock cycles a CTA
+// may wait at one barrier.
 struct GridBar {
   unsigned* arrive;   // zero before the launch
   unsigned* gen;      // zero before the launch
@@ -625,283 +535,11 @@ struct GridBar {
   long long limit;    // clock cycles a CTA may wait at one barrier
 };
 
-// All threads of every CTA call this; false when the grid has given up.
-__device__ __forceinline__ bool gcg_grid_barrier(const GridBar& B, unsigned& epoch) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned target = epoch + 1;
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> a(*B.arrive), g(*B.gen);
-    cuda::atomic_ref<int32_t, cuda::thread_scope_device> e(*B.err);
-    if (a.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
-      a.store(0u, cuda::memory_order_relaxed);
-      g.store(target, cuda::memory_order_release);
-    } else {
-      const long long t0 = clock64();
-      while (g.load(cuda::memory_order_acquire) != target) {
-        if (e.load(cuda::memory_order_relaxed) != 0 || clock64() - t0 > B.limit) {
-          e.store(1, cuda::memory_order_relaxed);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    epoch = target;
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-template <class T>
-struct GcgPersist {
-  const T* rhs; T* x; const T* rho; const T* dinv; double sigma;
-  T* r; T* z; T* p; T* s; T* w; T* t;
-  double* part_g;     // [nct] r'z of the column tile
-  double* part_rr;    // [nct] r'r
-  double* part_d;     // [nct] z'w
-  double* part_bb;    // [nct] rhs'rhs
-  int32_t* iters;     // [ninst] or null
-  double tol;
-  int32_t maxit;
-  int32_t short_p;    // P rows of at most 16 entries
-  int64_t stage_len;  // T entries of the staging area
-  int32_t nseg;       // column segments of the R phase
-  const int32_t* seg_off;  // [nseg - 1][m] entries of a row before each segment boundary
-  int64_t sp_off;     // offset of the tile's P z within the staging area (C phase)
-  int64_t ps_off;     // offset of the row partial sums (R phase, [rows per tile])
-};
-
-// per-instance scalars kept in shared memory by every CTA
+// per-instance CG scalars kept in shared memory by every CTA of the streamed solve
 struct GcgScal {
   double gamma, gamma_old, alpha, alpha_old, beta, delta, rr, bb;
   int32_t state;      // 0 iterate, 1 converged, 2 cap reached
   int32_t pad;
 };
-
-enum : int { GS_GAMMA = 0, GS_RR = 1, GS_DELTA = 2, GS_BB = 3 };
-
-// sc[inst].field[q] = sum over the instance's column tiles of part[q] (one
-// warp per instance, lanes over tiles in order, butterfly): identical in
-// every CTA
-template <int NV>
-__device__ __forceinline__ void gcg_inst_sums(const GcgTiles& G, int ninst, double* const (&part)[NV],
-                                              const int (&field)[NV], GcgScal* sc) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x >> 5; i < ninst; i += nw) {
-    const int lo = G.it_lo[i], hi = G.it_hi[i];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double v = 0.0;
-      for (int k = lo + lane; k < hi; k += 32) v += __ldcg(part[q] + k);
-      v = warp_sum(v);
-      if (lane == 0) {
-        if (field[q] == GS_GAMMA) sc[i].gamma = v;
-        else if (field[q] == GS_RR) sc[i].rr = v;
-        else if (field[q] == GS_DELTA) sc[i].delta = v;
-        else sc[i].bb = v;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// VA, VAT: batch widths of the row routine over A and A' (16-byte loads; the
-// host checks the arrays' alignment); long P rows use width 1.
-template <class T, int VA, int VAT>
-__global__ void __launch_bounds__(GCG_NT_SMEM, 1) k_gcg_persist(Prob<T, T> P, GcgTiles G, GcgPersist<T> S,
-                                                                GridBar B) {
-  extern __shared__ double gcg_dyn[];
-  T* stage = reinterpret_cast<T*>(gcg_dyn);
-  GcgScal* sc = reinterpret_cast<GcgScal*>(gcg_dyn + (S.stage_len * sizeof(T) + 7) / 8);
-  __shared__ double sm[2 * (GCG_NT_SMEM / 32)];
-  __shared__ int s_all_done;
-  const int b = blockIdx.x, ninst = P.ninst;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const bool has_c = b < G.nct, has_r = b < G.nrt;
-  const int cinst = has_c ? G.ct_inst[b] : 0, rinst = has_r ? G.rt_inst[b] : 0;
-  const int64_t clo = has_c ? G.ct_lo[b] : 0, chi = has_c ? G.ct_hi[b] : 0;
-  const int64_t rlo = has_r ? G.rt_lo[b] : 0, rhi = has_r ? G.rt_hi[b] : 0;
-  unsigned epoch = 0;
-
-  // zero start: x = 0, r = rhs, z = D^-1 rhs, p = s = 0
-  {
-    T a0 = T(0), a1 = T(0);
-    for (int64_t j = clo + threadIdx.x; j < chi; j += GCG_NT_SMEM) {
-      const T bj = S.rhs[j], zj = S.dinv[j] * bj;
-      S.x[j] = T(0); S.r[j] = bj; S.z[j] = zj; S.p[j] = T(0); S.s[j] = T(0);
-      a0 += bj * zj;
-      a1 += bj * bj;
-    }
-    const T tv[2] = {a0, a1};
-    double acc[2];
-    block_sum_t<2>(tv, acc, sm);
-    if (has_c && threadIdx.x == 0) { S.part_g[b] = acc[0]; S.part_rr[b] = acc[1]; S.part_bb[b] = acc[1]; }
-  }
-  if (!gcg_grid_barrier(B, epoch)) return;
-  {
-    double* const parts[3] = {S.part_g, S.part_rr, S.part_bb};
-    const int fields[3] = {GS_GAMMA, GS_RR, GS_BB};
-    gcg_inst_sums<3>(G, ninst, parts, fields, sc);
-  }
-  for (int i = threadIdx.x; i < ninst; i += GCG_NT_SMEM) {
-    sc[i].state = 0;
-    sc[i].alpha = sc[i].alpha_old = sc[i].beta = sc[i].gamma_old = sc[i].delta = 0.0;
-  }
-  __syncthreads();
-
-  for (int it = 0;; ++it) {
-    // stopping test on the current residual; iteration counts recorded once
-    if (threadIdx.x == 0) s_all_done = 1;
-    __syncthreads();
-    for (int i = threadIdx.x; i < ninst; i += GCG_NT_SMEM) {
-      if (sc[i].state == 0) {
-        const double rr = sc[i].rr;
-        int stt = 0;
-        if (rr <= S.tol * S.tol * sc[i].bb || !(rr == rr)) stt = 1;
-        else if (it >= S.maxit) stt = 2;
-        if (stt) {
-          sc[i].state = stt;
-          if (b == 0 && S.iters) S.iters[i] = it;
-        } else {
-          s_all_done = 0;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_all_done) break;
-
-    // R: t = rho o (A z) over this CTA's rows, z staged one column segment at
-    // a time (at most about 100 KB of shared memory, so that the L1 keeps
-    // room for the loads in flight); row partial sums in shared memory
-    if (has_r && sc[rinst].state == 0) {
-      const int64_t c0 = P.col_off[rinst], nc = P.col_off[rinst + 1] - c0;
-      const int64_t wseg = (nc + S.nseg - 1) / S.nseg;
-      const int64_t m_tot = P.m_total;
-      T* ps = stage + S.ps_off;
-      const T* __restrict__ rho = S.rho;
-      T* __restrict__ t = S.t;
-      for (int h = 0; h < S.nseg; ++h) {
-        const int64_t slo = c0 + min(nc, h * wseg), shi = c0 + min(nc, (h + 1) * wseg);
-        const int64_t gb = gcg_stage_aligned(S.z, slo, shi, stage);
-        __syncthreads();
-        // column indices are int32, so these ranges fit 32 bits
-        const int32_t sloi = (int32_t)slo, gbi = (int32_t)gb;
-        const uint32_t nsi = (uint32_t)(shi - slo);
-        const bool first = h == 0, last = h == S.nseg - 1;
-        gcg_warp_rows_ext<VA>(
-            [&](int64_t r, int64_t& e0, int64_t& e1) {
-              const int64_t b0 = __ldg(P.A_rp + r);
-              e0 = first ? b0 : b0 + __ldg(S.seg_off + (int64_t)(h - 1) * m_tot + r);
-              e1 = last ? __ldg(P.A_rp + r + 1) : b0 + __ldg(S.seg_off + (int64_t)h * m_tot + r);
-            },
-            P.A_ci, P.A_v, G.nnz_a, rlo + wp, rhi, GCG_NT_SMEM / 32,
-            [&](int64_t r) { return last ? __ldg(rho + r) : T(0); },
-            [&](int32_t c) { return (uint32_t)(c - sloi) < nsi ? stage[c - gbi] : T(0); },
-            [&](int64_t r, T rr, T sum) {
-              if (lane == 0) {
-                const T tot = (first ? T(0) : ps[r - rlo]) + sum;
-                if (last) t[r] = rr * tot;
-                else ps[r - rlo] = tot;
-              }
-            });
-        __syncthreads();
-      }
-    }
-    if (!gcg_grid_barrier(B, epoch)) return;
-
-    // C: w = sigma z + P z + A't over this CTA's columns; partial z'w
-    {
-      T dacc = T(0);
-      if (has_c && sc[cinst].state == 0) {
-        const int64_t r0 = P.row_off[cinst], nr = P.row_off[cinst + 1] - r0;
-        T* stv = stage;
-        T* sP = stage + S.sp_off;
-        const int32_t tgbi = (int32_t)gcg_stage_aligned(S.t, r0, r0 + nr, stv);
-        const T* __restrict__ zg = S.z;
-        gcg_p_part<1>(P, G, clo, chi, S.short_p, [&](int32_t c) { return c >= 0 ? __ldcg(zg + c) : T(0); }, sP);
-        const int32_t r0i = (int32_t)r0;
-        const uint32_t nri = (uint32_t)nr;
-        const T sig = (T)S.sigma;
-        gcg_warp_rows_vec<VAT>(
-            P.AT_rp, P.AT_ci, P.AT_v, G.nnz_a, clo + wp, chi, GCG_NT_SMEM / 32,
-            [&](int64_t j) { return __ldcg(zg + j); },
-            [&](int32_t c) { return (uint32_t)(c - r0i) < nri ? stv[c - tgbi] : T(0); },
-            [&](int64_t j, T zj, T sum) {
-              if (lane == 0) {
-                const T wj = sig * zj + sP[j - clo] + sum;
-                S.w[j] = wj;
-                dacc += zj * wj;
-              }
-            });
-      } else {
-        __syncthreads();   // gcg_p_part's barrier, taken by every thread of the CTA
-      }
-      const T tv[1] = {dacc};
-      double acc[1];
-      block_sum_t<1>(tv, acc, sm);
-      if (has_c && threadIdx.x == 0) S.part_d[b] = acc[0];
-    }
-    if (!gcg_grid_barrier(B, epoch)) return;
-    {
-      double* const parts[1] = {S.part_d};
-      const int fields[1] = {GS_DELTA};
-      gcg_inst_sums<1>(G, ninst, parts, fields, sc);
-    }
-    for (int i = threadIdx.x; i < ninst; i += GCG_NT_SMEM) {
-      if (sc[i].state) continue;
-      const double g = sc[i].gamma;
-      double beta = 0.0, den = sc[i].delta;
-      if (it > 0) {
-        beta = sc[i].gamma_old != 0.0 ? g / sc[i].gamma_old : 0.0;
-        den = sc[i].delta - (sc[i].alpha_old != 0.0 ? beta * g / sc[i].alpha_old : 0.0);
-      }
-      sc[i].beta = beta;
-      sc[i].alpha = den > 0.0 ? g / den : 0.0;
-    }
-    __syncthreads();
-
-    // U: update this CTA's columns; partials r'z and r'r
-    {
-      T a0 = T(0), a1 = T(0);
-      if (has_c && sc[cinst].state == 0) {
-        const T alpha = (T)sc[cinst].alpha, beta = (T)sc[cinst].beta;
-        for (int64_t j = clo + threadIdx.x; j < chi; j += GCG_NT_SMEM) {
-          const T pj = S.z[j] + beta * S.p[j];
-          const T sj = S.w[j] + beta * S.s[j];
-          S.p[j] = pj;
-          S.s[j] = sj;
-          S.x[j] += alpha * pj;
-          const T rj = S.r[j] - alpha * sj;
-          const T zj = S.dinv[j] * rj;
-          S.r[j] = rj;
-          S.z[j] = zj;
-          a0 += rj * zj;
-          a1 += rj * rj;
-        }
-      }
-      const T tv[2] = {a0, a1};
-      double acc[2];
-      block_sum_t<2>(tv, acc, sm);
-      if (has_c && threadIdx.x == 0 && sc[cinst].state == 0) { S.part_g[b] = acc[0]; S.part_rr[b] = acc[1]; }
-    }
-    if (!gcg_grid_barrier(B, epoch)) return;
-    for (int i = threadIdx.x; i < ninst; i += GCG_NT_SMEM) {
-      if (sc[i].state == 0) {
-        sc[i].gamma_old = sc[i].gamma;
-        sc[i].alpha_old = sc[i].alpha;
-      }
-    }
-    __syncthreads();
-    {
-      // new gamma and rr (tiles of stopped instances keep their last partials)
-      double* const parts[2] = {S.part_g, S.part_rr};
-      const int fields[2] = {GS_GAMMA, GS_RR};
-      gcg_inst_sums<2>(G, ninst, parts, fields, sc);
-    }
-  }
-}
 
 }  // namespace cosmo

@@ -103,6 +103,13 @@ __device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity, long long 
 
 }  // namespace bulk
 
+// Phase timer stamps (thread 0 of each CTA, when enabled): 0 iteration start,
+// 1 R stage ready, 2 warp 0's R stream done, 3 every warp's R stream done,
+// 4 R epilogue done, 5 past the R->C grid barrier, 6 C stage ready, 7 warp
+// 0's C stream done, 8 every warp's C stream done, 9 update done (the next
+// iteration's 0 is the end of the C->R barrier).
+constexpr int GCS_NSTAMP = 10;
+
 constexpr int GCS_WARPS = 24;                    // streaming warps
 constexpr int GCS_NT = 32 * GCS_WARPS + 32;      // + the control warp (800 threads, 80 registers each)
 constexpr int GCS_MAXSLOT = 6;                   // chunk buffers per streaming warp, at most
@@ -198,6 +205,8 @@ struct GcsArgs {
   const int32_t* cc_lo;  // [ninst] first CTA owning columns of the instance
   const int32_t* cc_hi;
   int32_t* iters;        // [ninst] or null
+  unsigned long long* ts;  // phase timer: [ts_iters][GCS_NSTAMP][grid] globaltimer stamps, or null
+  int32_t ts_iters;
   double tol;
   int32_t maxit;
   int32_t short_p;       // P rows of at most 16 entries
@@ -804,7 +813,16 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
   }
   if (!grid_sync()) fail();
 
+  auto stamp = [&](int it, int k) {
+    if (S.ts && threadIdx.x == 0 && it < S.ts_iters) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      S.ts[((int64_t)it * GCS_NSTAMP + k) * gridDim.x + b] = t;
+    }
+  };
+
   for (int it = 0;; ++it) {
+    stamp(it, 0);
     // ---- R: partial (A z) of the cluster's rows over this CTA's segment ----
     // (the stage copy runs while P z is formed; the partner CTAs finished
     // reading ps and ns before the last grid barrier)
@@ -816,8 +834,10 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     else
       __syncthreads();   // the resets above precede the accumulation
     if (has_r) stage_wait(r_c0, r_c1);
+    stamp(it, 1);
     if (streamer) {
       if (has_r && !bad) consume(0, qend_r, nr, ps, gbr);
+      stamp(it, 2);
     } else {
       control_r(it);
       // the epilogues' operands of the owned columns: z, s, p, x, r, D^-1
@@ -833,6 +853,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
     __syncthreads();
     if (has_r) fixup(ps);
     csync();   // every CTA's partial row sums are complete
+    stamp(it, 3);
     if (cluster_bad() || s_done) { leave(); return; }
     {
       // owned rows: t = rho o (A z); partials sum rho (Az)^2 (rows),
@@ -852,20 +873,25 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
       cta_sum2(a0, a1, t0, t1);
       if (threadIdx.x == 0) { S.part_r[b] = t0; S.part_d[b] = t1; }
     }
+    stamp(it, 4);
     if (!grid_sync()) fail();
+    stamp(it, 5);
 
     // ---- C: (A't) of the CTA's own columns over the whole t, or the partial
     // of the tile's columns over this CTA's segment of t ----
     const int32_t gbc = has_c ? stage_issue(S.t, c_r0, c_r1) : 0;
     if (has_c) stage_wait(c_r0, c_r1);
+    stamp(it, 6);
     if (streamer) {
       if (has_c && !bad) consume(1, qend_c, ncs, ns, gbc);
+      stamp(it, 7);
     } else {
       control_c(it);
     }
     __syncthreads();
     if (has_c) fixup(ns);
     csync();   // every CTA's partial column sums are complete (split C)
+    stamp(it, 8);
     if (cluster_bad()) { leave(); return; }
 
     // ---- update of the owned columns; partials r'z, r'r ----
@@ -901,6 +927,7 @@ __global__ void __launch_bounds__(GCS_NT, 1) k_gcg_stream(Prob<T, T> P, GcgTiles
         pc[gridDim.x + b] = t1;
       }
     }
+    stamp(it, 9);
     if (!grid_sync()) fail();
   }
 #undef wmbar

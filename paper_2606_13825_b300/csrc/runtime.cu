@@ -1535,30 +1535,10 @@ static cosmo_status pcg_solve_t(int32_t ninst, int64_t n, int64_t m, const int64
   return COSMO_OK;
 }
 
-// Grid-wide CG (zero start) for large instances: column / row tiles of 64,
-// three kernels per iteration, convergence read back every 8 iterations (the
+// Grid-wide CG (zero start) for large instances that no streamed plan
+// takes: column / row tiles spread over the SMs, three kernels per iteration
+// gathering from global memory, convergence read back every 8 iterations (the
 // call synchronises the stream on this path).
-// k_gcg_persist<T, va, vat> for batch widths va, vat in {1, 2, 4} (null when
-// not instantiated)
-template <class T>
-static const void* persist_kernel(int va, int vat) {
-  auto pick = [&](auto a_tag) -> const void* {
-    constexpr int VA = decltype(a_tag)::value;
-    if (vat == 1) return (const void*)k_gcg_persist<T, VA, 1>;
-    if (vat == 2) return (const void*)k_gcg_persist<T, VA, 2>;
-    if constexpr (sizeof(T) == 4) {
-      if (vat == 4) return (const void*)k_gcg_persist<T, VA, 4>;
-    }
-    return nullptr;
-  };
-  if (va == 1) return pick(std::integral_constant<int, 1>{});
-  if (va == 2) return pick(std::integral_constant<int, 2>{});
-  if constexpr (sizeof(T) == 4) {
-    if (va == 4) return pick(std::integral_constant<int, 4>{});
-  }
-  return nullptr;
-}
-
 template <class T>
 static cosmo_status pcg_solve_grid_t(int32_t ninst, int64_t n, int64_t m, const int64_t* col_off_d,
                                      const int64_t* row_off_d, const Prob<T, T>& P0, double sigma,
@@ -1587,84 +1567,19 @@ static cosmo_status pcg_solve_grid_t(int32_t ninst, int64_t n, int64_t m, const 
     const int64_t mean = rows > 0 ? nnz / rows : 0;
     return mean >= 384 ? 4 : mean >= 128 ? 2 : 1;
   };
-  int64_t max_n = 0, max_m = 0;
-  for (int32_t i = 0; i < ninst; ++i) {
-    max_n = std::max(max_n, co[i + 1] - co[i]);
-    max_m = std::max(max_m, ro[i + 1] - ro[i]);
-  }
   int dev = 0, nsm = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
 
-  // Tiles of `mult`-aligned rows (columns) that never cross an instance;
-  // `count` tiles of an instance with `len` rows at tile size t.
-  auto tiles_at = [&](const std::vector<int64_t>& off, int64_t t) {
-    int64_t c = 0;
-    for (int32_t i = 0; i < ninst; ++i) c += (off[i + 1] - off[i] + t - 1) / t;
-    return c;
-  };
-  // Persistent path: one CTA per SM, at most nsm row tiles and nsm column
-  // tiles, the staged vectors in shared memory.
-  const size_t SMEM_CAP = 220 * 1024;
-  // (ends: with at most nsm instances, tiles as long as the longest instance
-  // give at most nsm tiles)
-  int64_t RT = std::max<int64_t>(32, ((m + nsm - 1) / nsm + 31) / 32 * 32);
-  int64_t CT = std::max<int64_t>(32, ((n + nsm - 1) / nsm + 31) / 32 * 32);
-  if (ninst <= nsm) {
-    while (tiles_at(ro, RT) > nsm) RT += 32;
-    while (tiles_at(co, CT) > nsm) CT += 32;
-  }
-  // Staging layout (T entries): R phase: a column segment of z (at most
-  // SEG_BYTES, so that about 124 KB of L1 stays free for the loads in flight)
-  // plus 2 x 16 bytes of alignment slack, then the row partial sums [RT];
-  // C phase: t over the instance's rows (+ slack), then the tile's P z [CT].
-  const int64_t E = 16 / (int64_t)sizeof(T);
-  const int64_t SEG_BYTES = 100 * 1024;
-  const int nseg = (int)std::max<int64_t>(1, (max_n * (int64_t)sizeof(T) + SEG_BYTES - 1) / SEG_BYTES);
-  const int64_t seg_stage = (max_n + nseg - 1) / nseg + 2 * E;
-  const int64_t sp_off = max_m + 2 * E;
-  const int64_t stage_len = std::max(seg_stage + RT, sp_off + CT);
-  const size_t persist_smem = ((size_t)stage_len * sizeof(T) + 7) / 8 * 8 + sizeof(GcgScal) * ninst;
-  // the persistent kernel is instantiated for batch widths (A, A') in
-  // {1, 2, 4}^2 (at most 2 for double values) and 16-byte aligned arrays
-  const bool all_aligned = aligned(P0.A_ci, P0.A_v) && aligned(P0.AT_ci, P0.AT_v) &&
-                           (!P0.P_rp || aligned(P0.P_ci, P0.P_v));
-  const int vmax = sizeof(T) == 4 ? 4 : 2;
-  // (the R phase streams each row one column segment at a time)
-  const int pva = std::min(vq_for(nnz_a / nseg, m), vmax), pvat = std::min(vq_for(nnz_a, n), vmax);
-  const void* pkern = persist_kernel<T>(pva, pvat);
-  bool persist = all_aligned && pkern && ninst <= nsm && persist_smem <= SMEM_CAP;
-  if (persist) {
-    CU(cudaFuncSetAttribute(pkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem));
-    int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pkern, GCG_NT_SMEM, persist_smem));
-    persist = per_sm >= 1;
-  }
   DevArena a;
-  int32_t* seg_off = nullptr;
-  if (persist && nseg > 1) {
-    // entries of each row before each segment boundary; needs sorted rows
-    int32_t* unsorted;
-    TRY(a.alloc(&seg_off, (int64_t)(nseg - 1) * std::max<int64_t>(m, 1)));
-    TRY(a.alloc(&unsorted, 1));
-    CU(cudaMemsetAsync(unsorted, 0, sizeof(int32_t), st));
-    if (m > 0) {
-      k_gcg_split<T><<<(int)((m * 32 + 255) / 256), 256, 0, st>>>(P0, nseg, seg_off, unsorted);
-      ++g_launches;
-    }
-    int32_t h_unsorted = 0;
-    CU(cudaMemcpyAsync(&h_unsorted, unsorted, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (h_unsorted) persist = false;   // global gathers need no sorted rows
-  }
-  // Fallback: 256-thread CTAs gathering from global memory, tiles sized for
-  // about four resident CTAs per SM (a multiple of 8, at most 256).
+  // 256-thread CTAs gathering from global memory, tiles sized for about four
+  // resident CTAs per SM (a multiple of 8, at most 256).
   auto tile_global = [&](int64_t total) {
     int64_t t = (total + 4 * nsm - 1) / (4 * nsm);
     t = (t + 7) / 8 * 8;
     return std::min<int64_t>(std::max<int64_t>(t, 8), 256);
   };
-  const int64_t RTILE = persist ? RT : tile_global(m), CTILE = persist ? CT : tile_global(n);
+  const int64_t RTILE = tile_global(m), CTILE = tile_global(n);
 
   std::vector<int32_t> ct_inst, rt_inst, it_lo(ninst), it_hi(ninst), rt_first;
   std::vector<int64_t> ct_lo, ct_hi, rt_lo, rt_hi;
@@ -1674,9 +1589,9 @@ static cosmo_status pcg_solve_grid_t(int32_t ninst, int64_t n, int64_t m, const 
       ct_inst.push_back(i); ct_lo.push_back(c); ct_hi.push_back(std::min(co[i + 1], c + CTILE));
     }
     it_hi[i] = (int32_t)ct_inst.size();
-    // the global path needs a row tile per instance (possibly empty): it records the iteration count
+    // a row tile per instance (possibly empty): it records the iteration count
     bool first = true;
-    for (int64_t q = ro[i]; q < ro[i + 1] || (first && !persist); q += RTILE) {
+    for (int64_t q = ro[i]; q < ro[i + 1] || first; q += RTILE) {
       rt_inst.push_back(i); rt_lo.push_back(q); rt_hi.push_back(std::min(ro[i + 1], q + RTILE));
       rt_first.push_back(first ? 1 : 0);
       first = false;
@@ -1706,36 +1621,6 @@ static cosmo_status pcg_solve_grid_t(int32_t ninst, int64_t n, int64_t m, const 
   TRY(a.alloc(&dinv, n));
   k_precond_csr<T, T><<<grid_for(n, 256), 256, 0, st>>>(P, sigma, (const T*)rho, dinv);
   ++g_launches;
-
-  if (persist) {
-    GcgPersist<T> S{};
-    T *rr, *zz, *pp, *ss, *ww, *tt;
-    // z and t are staged in 16-byte groups: padded to whole groups past the end
-    TRY(a.alloc(&rr, n)); TRY(a.alloc(&zz, n + 2 * E)); TRY(a.alloc(&pp, n)); TRY(a.alloc(&ss, n));
-    TRY(a.alloc(&ww, n)); TRY(a.alloc(&tt, std::max<int64_t>(m, 1) + 2 * E));
-    CU(cudaMemsetAsync(zz, 0, sizeof(T) * (n + 2 * E), st));
-    CU(cudaMemsetAsync(tt, 0, sizeof(T) * (std::max<int64_t>(m, 1) + 2 * E), st));
-    double *pg, *prr, *pd, *pbb;
-    TRY(a.alloc(&pg, G.nct)); TRY(a.alloc(&prr, G.nct)); TRY(a.alloc(&pd, G.nct)); TRY(a.alloc(&pbb, G.nct));
-    unsigned* bar;
-    TRY(a.alloc(&bar, 4));   // arrive, generation, error word
-    CU(cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st));
-    S.rhs = (const T*)rhs; S.x = (T*)x; S.rho = (const T*)rho; S.dinv = dinv; S.sigma = sigma;
-    S.r = rr; S.z = zz; S.p = pp; S.s = ss; S.w = ww; S.t = tt;
-    S.part_g = pg; S.part_rr = prr; S.part_d = pd; S.part_bb = pbb;
-    S.iters = iters; S.tol = tol; S.maxit = maxit; S.short_p = short_p; S.stage_len = stage_len;
-    S.nseg = nseg; S.seg_off = seg_off; S.sp_off = sp_off; S.ps_off = seg_stage;
-    GridBar B{bar, bar + 1, reinterpret_cast<int32_t*>(bar + 2), 2000000000LL};   // about 1 s at 2 GHz
-    const int grid = std::max(G.nct, G.nrt);
-    void* args[] = {(void*)&P, (void*)&G, (void*)&S, (void*)&B};
-    CU(cudaLaunchCooperativeKernel(pkern, dim3(grid), dim3(GCG_NT_SMEM), args, persist_smem, st));
-    ++g_launches;
-    int32_t herr = 0;
-    CU(cudaMemcpyAsync(&herr, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (herr) return fail(COSMO_E_TIMEOUT, "grid CG: a grid barrier wait gave up");
-    return COSMO_OK;
-  }
 
   using T2 = typename Vec2<T>::type;
   GcgState<T> S{};
@@ -1799,6 +1684,8 @@ struct PcgPlanBase {
   virtual cosmo_status solve(double sigma, const void* rho, const void* rhs, void* x, double tol,
                              int32_t maxit, int32_t* iters, cudaStream_t st) = 0;
   virtual void info(cosmo_pcg_plan_info* out) const = 0;
+  virtual cosmo_status set_timing(int enable) = 0;
+  virtual void get_timing(double* mean_us, double* slowest_us) const = 0;
 };
 
 // Contiguous tiles of the items [off[i], off[i+1]) of every instance, at
@@ -1874,6 +1761,11 @@ struct GcsPlan : PcgPlanBase {
   int64_t layout_bytes = 0, quads_r = 0, quads_c = 0;
   unsigned* bar = nullptr;
   int32_t* h_err = nullptr;   // pinned
+  // phase timer (off unless set_timing): stamps of the first kTsIters
+  // iterations, and the last solve's per-phase means / slowest CTA
+  static constexpr int kTsIters = 64;
+  unsigned long long* ts = nullptr;
+  double ph_mean[COSMO_PCG_PHASES] = {}, ph_max[COSMO_PCG_PHASES] = {};
 
   ~GcsPlan() override {
     if (h_err) cudaFreeHost(h_err);
@@ -2161,6 +2053,9 @@ struct GcsPlan : PcgPlanBase {
     GcsArgs<T> A = S;
     A.rhs = (const T*)rhs; A.x = (T*)x; A.rho = (const T*)rho; A.sigma = sigma;
     A.tol = tol; A.maxit = maxit; A.iters = iters;
+    A.ts = ts;
+    A.ts_iters = kTsIters;
+    if (ts) CU(cudaMemsetAsync(ts, 0, sizeof(unsigned long long) * kTsIters * GCS_NSTAMP * grid, st));
     GridBar B{bar, bar + 1, reinterpret_cast<int32_t*>(bar + 2), 2000000000LL};
     // all clusters resident (cooperative), CS CTAs per cluster
     cudaLaunchConfig_t cfg{};
@@ -2185,7 +2080,57 @@ struct GcsPlan : PcgPlanBase {
     CU(cudaMemcpyAsync(h_err, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (*h_err) return fail(COSMO_E_TIMEOUT, "streamed CG: a wait gave up");
+    if (ts) TRY(reduce_timing());
     return COSMO_OK;
+  }
+
+  cosmo_status set_timing(int enable) override {
+    if (enable && !ts) {
+      TRY(a.alloc(&ts, (int64_t)kTsIters * GCS_NSTAMP * grid));
+    } else if (!enable) {
+      ts = nullptr;   // the buffer stays in the plan's arena until it is destroyed
+    }
+    return COSMO_OK;
+  }
+
+  // phase k spans stamps k -> k + 1 (the last: stamp 9 -> the next
+  // iteration's 0); mean over CTAs and over iterations 1 .. the last full
+  // one, and the mean over those iterations of the slowest CTA
+  cosmo_status reduce_timing() {
+    std::vector<unsigned long long> h((size_t)kTsIters * GCS_NSTAMP * grid);
+    CU(cudaMemcpy(h.data(), ts, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    auto at = [&](int it, int k, int b) { return h[((size_t)it * GCS_NSTAMP + k) * grid + b]; };
+    for (int ph = 0; ph < COSMO_PCG_PHASES; ++ph) {
+      double sum = 0.0, smax = 0.0;
+      int cnt = 0;
+      for (int it = 1; it + 1 < kTsIters; ++it) {
+        double s1 = 0.0, mx = 0.0;
+        int nb = 0;
+        for (int b = 0; b < grid; ++b) {
+          const unsigned long long t0 = at(it, ph, b);
+          const unsigned long long t1 = ph + 1 < GCS_NSTAMP ? at(it, ph + 1, b) : at(it + 1, 0, b);
+          if (!t0 || !t1 || t1 < t0) continue;
+          s1 += (double)(t1 - t0);
+          mx = std::max(mx, (double)(t1 - t0));
+          ++nb;
+        }
+        if (nb == grid) {
+          sum += s1 / nb;
+          smax += mx;
+          ++cnt;
+        }
+      }
+      ph_mean[ph] = cnt ? sum / cnt * 1e-3 : 0.0;
+      ph_max[ph] = cnt ? smax / cnt * 1e-3 : 0.0;
+    }
+    return COSMO_OK;
+  }
+
+  void get_timing(double* mean_us, double* slowest_us) const override {
+    for (int ph = 0; ph < COSMO_PCG_PHASES; ++ph) {
+      if (mean_us) mean_us[ph] = ph_mean[ph];
+      if (slowest_us) slowest_us[ph] = ph_max[ph];
+    }
   }
 
   void info(cosmo_pcg_plan_info* o) const override {
@@ -2315,6 +2260,19 @@ cosmo_status cosmo_pcg_plan_get_info(const cosmo_pcg_plan* plan, cosmo_pcg_plan_
   g_err.clear();
   if (!plan || !plan->impl || !out) return fail(COSMO_E_INVAL, "plan or out is NULL");
   plan->impl->info(out);
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_pcg_plan_set_timing(cosmo_pcg_plan* plan, int32_t enable) {
+  g_err.clear();
+  if (!plan || !plan->impl) return fail(COSMO_E_INVAL, "plan is NULL");
+  return plan->impl->set_timing(enable);
+}
+
+cosmo_status cosmo_pcg_plan_get_timing(const cosmo_pcg_plan* plan, double* mean_us, double* slowest_us) {
+  g_err.clear();
+  if (!plan || !plan->impl) return fail(COSMO_E_INVAL, "plan is NULL");
+  plan->impl->get_timing(mean_us, slowest_us);
   return COSMO_OK;
 }
 

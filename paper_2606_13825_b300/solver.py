@@ -447,6 +447,18 @@ class PcgPlan:
         check(lib().cosmo_pcg_plan_get_info(self._h, byref(inf)))
         return {f: getattr(inf, f) for f, _ in inf._fields_}
 
+    def set_timing(self, enable=True):
+        """Phase timer of the following solves (see timing())."""
+        check(lib().cosmo_pcg_plan_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self):
+        """Per-phase times of the last timed solve, microseconds:
+        {phase: (mean over CTAs and iterations, mean of the slowest CTA)}."""
+        mean = (ctypes.c_double * len(_abi.PCG_PHASES))()
+        slow = (ctypes.c_double * len(_abi.PCG_PHASES))()
+        check(lib().cosmo_pcg_plan_get_timing(self._h, ctypes.cast(mean, c_void_p), ctypes.cast(slow, c_void_p)))
+        return {name: (mean[k], slow[k]) for k, name in enumerate(_abi.PCG_PHASES)}
+
     def solve(self, sigma, rho, rhs, tol=1e-8, max_iter=500, x=None, iters=None):
         """x = (P + sigma I + A'D(rho)A)^-1 rhs from x = 0; returns (x,
         iterations per block).  x and iters may be given to reuse buffers."""

@@ -237,3 +237,26 @@ def test_pcg_plan_general_p_unsorted_empty_rows(precision):
         err = np.abs(x[c:c + n] - ref).max() / np.abs(ref).max()
         assert err < (1e-8 if precision == "fp64" else 5e-3), (k, err, iters)
         c, r = c + n, r + m
+
+
+def test_pcg_plan_phase_timer():
+    """The phase timer reports positive phase times whose sum is close to the
+    time per iteration, and leaves the result bitwise unchanged."""
+    _need_gpu()
+    d = linsys_instance(20000, seed=6120, density=0.01, row_sampler=True)
+    sysm, plan = _plan([(d["P"], d["A"])], "mixed")
+    t = lambda a: torch.tensor(a, dtype=sysm.dtype, device="cuda")
+    rho, rhs = t(d["rho"] + 0.05), t(np.random.default_rng(11).standard_normal(20000))
+    x0, it0 = plan.solve(1e-6, rho, rhs, tol=1e-6, max_iter=3000)
+    plan.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x1, it1 = plan.solve(1e-6, rho, rhs, tol=1e-6, max_iter=3000)
+    e1.record()
+    torch.cuda.synchronize()
+    assert torch.equal(x0, x1) and torch.equal(it0, it1)
+    ph = plan.timing()
+    assert len(ph) == 10 and all(v[0] > 0 and v[1] >= v[0] for v in ph.values()), ph
+    per_it = 1e3 * e0.elapsed_time(e1) / int(it1[0])
+    total = sum(v[0] for v in ph.values())
+    assert 0.5 * per_it < total < 1.5 * per_it, (total, per_it, ph)
