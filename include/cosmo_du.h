@@ -207,6 +207,40 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
 cosmo_status cosmo_batch_destroy(cosmo_batch* batch);
 cosmo_status cosmo_batch_get_info(const cosmo_batch* batch, cosmo_batch_info* out);
 
+/* Solve to tolerance: the vanilla COSMO baseline of Sec. 4 (App. D: the
+ * unrolled iteration with the OSQP-style residual-balancing rho heuristic,
+ * a zero or given start, alpha fixed).  Each instance has one scalar rho_i
+ * (rho_eq_scale * rho_i on zero-cone rows); every check_every iterations the
+ * KKT residuals are measured in the infinity norm and normalised OSQP-style,
+ *   rbar_p = ||Ax + s - b|| / max(||Ax||, ||s||, ||b||),
+ *   rbar_d = ||Px + q - A'y|| / max(||Px||, ||q||, ||A'y||)
+ * (a zero scale counts as 1; the sign of r_d as in cosmo_residuals).  An
+ * instance has converged at the first check with rbar_p <= eps and rbar_d
+ * <= eps.  At every rebalance_every-th iteration (a multiple of check_every;
+ * 0 keeps rho fixed) an unconverged instance's rho_i is multiplied by
+ * f = sqrt(rbar_p / rbar_d) when f > rebalance_tol or f < 1 / rebalance_tol,
+ * then clipped to [rho_min, rho_max].  The loop ends when every instance has
+ * converged or after max_iter iterations; converged instances keep
+ * iterating until then.  The paper leaves the check and rebalancing
+ * intervals and the threshold open; cosmo_solve_params_default sets sigma
+ * 1e-6, alpha 1.6, rho0 0.1, rho_eq_scale 1e3, eps 1e-3, rebalance_tol 5,
+ * rho in [1e-6, 1e6], max_iter 5000, checks and rebalancing every 25
+ * iterations.
+ * x [n], s [m], y [m]: device, the start in and the final iterate out.
+ * iters [ninst] (host, may be NULL): the iteration count of each instance's
+ * first converged check, -1 if it never converged.  rbar_p, rbar_d, rho
+ * [ninst] (host, may be NULL): the normalised residuals at the last check
+ * and the final rho_i.  Runs the forward of the batch (no tape) in chunks of
+ * check_every steps, synchronising the stream at every check.
+ * Errors: E_INVAL, E_NOMEM, E_CUDA (and those of cosmo_forward). */
+typedef struct {
+  double sigma, alpha, rho0, rho_eq_scale, eps, rebalance_tol, rho_min, rho_max;
+  int32_t max_iter, check_every, rebalance_every, pad;
+} cosmo_solve_params;
+cosmo_status cosmo_solve_params_default(cosmo_solve_params* p);
+cosmo_status cosmo_solve(cosmo_batch* batch, const cosmo_solve_params* prm, void* x, void* s, void* y,
+                         int32_t* iters, double* rbar_p, double* rbar_d, double* rho, void* stream);
+
 /* Unroll K iterations from (x0, s0, y0) (NULL = zero start).
  *   sigma_host: host [K] (NULL = 1e-6 every step, the value of Sec. 2.2)
  *   rho:   dev real [K][m_total], per-row penalties before rectification

@@ -232,6 +232,74 @@ def forward(problem, rho, alpha, sigma, x0=None, s0=None, y0=None, keep=True):
     return tr
 
 
+# ------------------------------------------------------ solve to tolerance --
+def kkt_normalised(problem, x, s, y):
+    """OSQP-style normalised KKT residuals in the infinity norm (App. D, the
+    policy features; the quantities COSMO and OSQP stop on):
+        rbar_p = ||Ax + s - b|| / max(||Ax||, ||s||, ||b||)
+        rbar_d = ||Px + q - A'y|| / max(||Px||, ||q||, ||A'y||)
+    with r_d signed as in `residuals` and a zero scale counted as 1."""
+    inf = lambda v: float(np.max(np.abs(v))) if np.size(v) else 0.0
+    ax = problem.A @ x if problem.m else np.zeros(0)
+    px = problem.P @ x
+    aty = problem.A.T @ y if problem.m else np.zeros(problem.n)
+    sp = max(inf(ax), inf(s), inf(problem.b))
+    sd = max(inf(px), inf(problem.q), inf(aty))
+    rp = inf(ax + s - problem.b) if problem.m else 0.0
+    rd = inf(px + problem.q - aty)
+    return rp / (sp if sp > 0 else 1.0), rd / (sd if sd > 0 else 1.0)
+
+
+def rebalance(rho, rbar_p, rbar_d, tol, rho_min, rho_max):
+    """OSQP-style residual balancing of a scalar rho: the factor
+    f = sqrt(rbar_p / rbar_d) is applied when it leaves [1/tol, tol], and
+    the result clipped to [rho_min, rho_max]."""
+    if rbar_p > 0.0 and rbar_d > 0.0:
+        f = np.sqrt(rbar_p / rbar_d)
+        if f > tol or f < 1.0 / tol:
+            rho = min(max(rho * f, rho_min), rho_max)
+    return rho
+
+
+def solve_to_tolerance(problem, eps=1e-3, rho0=0.1, rho_eq_scale=1e3, alpha=1.6, sigma=1e-6, max_iter=5000,
+                       check_every=25, rebalance_every=25, rebalance_tol=5.0, rho_min=1e-6, rho_max=1e6,
+                       x0=None, s0=None, y0=None, run_to=None):
+    """The vanilla COSMO baseline (Sec. 4, App. D): the iteration of Sec. 2.2
+    with one scalar rho (rho_eq_scale * rho on zero-cone rows), alpha fixed,
+    the stop test on `kkt_normalised` every `check_every` iterations, and
+    `rebalance` at every `rebalance_every`-th iteration until converged (the
+    check and rebalancing schedule is this build's reading; the paper leaves
+    it open).  With run_to, the iteration continues to that count with rho
+    frozen after convergence (the behaviour of a batch that waits for its
+    slowest instance).  Returns dict(iters (-1 if never converged), x, s, y,
+    rbar_p, rbar_d, rho, rho_hist)."""
+    m = problem.m
+    x = np.zeros(problem.n) if x0 is None else np.array(x0, dtype=np.float64)
+    s = np.zeros(m) if s0 is None else np.array(s0, dtype=np.float64)
+    y = np.zeros(m) if y0 is None else np.array(y0, dtype=np.float64)
+    zero_rows = np.zeros(m, dtype=bool)
+    for t, d, r0, r1 in problem.cone_offsets():
+        if t == ZERO:
+            zero_rows[r0:r1] = True
+    end = max_iter if run_to is None else run_to
+    rho, it, conv, rbp, rbd, hist = rho0, 0, -1, np.inf, np.inf, [rho0]
+    while it < end:
+        c = min(check_every, end - it)
+        rho_row = np.where(zero_rows, rho_eq_scale * rho, rho)
+        tr = forward(problem, np.tile(rho_row, (c, 1)), np.full(c, alpha), sigma, x, s, y, keep=False)
+        x, s, y = tr.xs[-1], tr.ss[-1], tr.ys[-1]
+        it += c
+        rbp, rbd = kkt_normalised(problem, x, s, y)
+        if conv < 0 and rbp <= eps and rbd <= eps:
+            conv = it
+        if conv < 0 and rebalance_every > 0 and it % rebalance_every == 0:
+            rho = rebalance(rho, rbp, rbd, rebalance_tol, rho_min, rho_max)
+            hist.append(rho)
+        if conv >= 0 and run_to is None:
+            break
+    return dict(iters=conv, x=x, s=s, y=y, rbar_p=rbp, rbar_d=rbd, rho=rho, rho_hist=hist)
+
+
 # --------------------------------------------------------------- backward --
 def backward(problem, tr, gx=None, gs=None, gy=None, gloss=0.0, tau=None, glogratio=0.0):
     """Reverse pass through ``forward``.

@@ -66,6 +66,13 @@ PCG_PHASES = ("R stage", "R stream (warp 0)", "R stream rest + cluster barrier",
               "update", "C->R grid barrier")
 
 
+class SolveParams(ctypes.Structure):
+    _fields_ = [("sigma", c_double), ("alpha", c_double), ("rho0", c_double), ("rho_eq_scale", c_double),
+                ("eps", c_double), ("rebalance_tol", c_double), ("rho_min", c_double), ("rho_max", c_double),
+                ("max_iter", c_int32), ("check_every", c_int32), ("rebalance_every", c_int32),
+                ("pad", c_int32)]
+
+
 class PcgPlanInfo(ctypes.Structure):
     _fields_ = [("nseg_a", c_int32), ("nseg_at", c_int32), ("grid", c_int32), ("threads", c_int32),
                 ("cluster", c_int32), ("ring_slots", c_int32),
@@ -107,6 +114,9 @@ _SIGS = {
     "cosmo_pcg_solve_noalloc": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
                                 [c_double, c_void_p, c_void_p, c_void_p, c_int32, c_double,
                                  c_int32, c_void_p, c_void_p]),
+    "cosmo_solve_params_default": (c_int32, [POINTER(SolveParams)]),
+    "cosmo_solve": (c_int32, [c_void_p, POINTER(SolveParams), c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_pcg_plan_create": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
                               [POINTER(c_void_p), c_void_p]),
     "cosmo_pcg_plan_solve": (c_int32, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_double,

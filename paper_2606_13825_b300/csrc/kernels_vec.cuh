@@ -838,4 +838,104 @@ __global__ void k_broadcast(int32_t K, int32_t w, const double* __restrict__ src
     dst[e] = (T)src[e / w];
 }
 
+// ---------------------------------------------------------------------------
+// Solve to tolerance (the vanilla COSMO baseline of Sec. 4 / App. D): KKT
+// residual infinity norms, the stop test and OSQP-style residual balancing
+// of one scalar rho per instance.
+// ---------------------------------------------------------------------------
+
+// per instance (one CTA): ||Ax + s - b||, ||Ax||, ||s||, ||b||,
+// ||Px + q - A'y||, ||Px||, ||q||, ||A'y||, all infinity norms, into
+// nrm[k * ninst + inst] (FP64; the maxima are exact in any order)
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_kkt_inf(Prob<T, V> P, const T* __restrict__ x, const T* __restrict__ s,
+                                                const T* __restrict__ y, double* __restrict__ nrm) {
+  __shared__ double sm[8][NT / 32];
+  const int32_t inst = blockIdx.x;
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
+    T ax = T(0);
+    for (int64_t e = P.A_rp[r]; e < P.A_rp[r + 1]; ++e) ax += (T)ldv(P.A_v, e) * x[P.A_ci[e]];
+    v[0] = fmax(v[0], fabs((double)(ax + s[r] - P.b[r])));
+    v[1] = fmax(v[1], fabs((double)ax));
+    v[2] = fmax(v[2], fabs((double)s[r]));
+    v[3] = fmax(v[3], fabs((double)P.b[r]));
+  }
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    T px = T(0), aty = T(0);
+    if (P.P_rp)
+      for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e) px += (T)ldv(P.P_v, e) * x[P.P_ci[e]];
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) aty += (T)ldv(P.AT_v, e) * y[P.AT_ci[e]];
+    v[4] = fmax(v[4], fabs((double)(px + P.q[j] - aty)));
+    v[5] = fmax(v[5], fabs((double)px));
+    v[6] = fmax(v[6], fabs((double)P.q[j]));
+    v[7] = fmax(v[7], fabs((double)aty));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    if (lane == 0) sm[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double mx = 0.0;
+    for (int q = 0; q < NT / 32; ++q) mx = fmax(mx, sm[threadIdx.x][q]);
+    nrm[(int64_t)threadIdx.x * P.ninst + inst] = mx;
+  }
+}
+
+struct SolveCtl {
+  double eps;            // stop when both normalised residuals are <= eps
+  double tol;            // rebalance when the ratio leaves [1/tol, tol]
+  double rho_min, rho_max;
+  int32_t it;            // iterations done
+  int32_t rebalance;     // 1: rebalance at this check
+};
+
+// one thread per instance: normalised residuals rbar_p = ||r_p|| / max(||Ax||,
+// ||s||, ||b||), rbar_d = ||r_d|| / max(||Px||, ||q||, ||A'y||) (a zero
+// scale counts as 1); first iteration count at which both are <= eps; for
+// unconverged instances at a rebalancing check rho <- rho sqrt(rbar_p /
+// rbar_d) when that factor leaves [1/tol, tol], clipped to [rho_min,
+// rho_max]; *running counts the unconverged instances
+__global__ void k_solve_update(int32_t ninst, const double* __restrict__ nrm, SolveCtl c, double* __restrict__ rho,
+                               int32_t* __restrict__ conv_it, double* __restrict__ rbp, double* __restrict__ rbd,
+                               int32_t* __restrict__ running) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  auto at = [&](int k) { return nrm[(int64_t)k * ninst + i]; };
+  const double sp = fmax(fmax(at(1), at(2)), at(3)), sd = fmax(fmax(at(5), at(6)), at(7));
+  const double p = at(0) / (sp > 0.0 ? sp : 1.0), d = at(4) / (sd > 0.0 ? sd : 1.0);
+  rbp[i] = p;
+  rbd[i] = d;
+  const bool done = p <= c.eps && d <= c.eps;
+  if (done && conv_it[i] < 0) conv_it[i] = c.it;
+  if (conv_it[i] >= 0) return;
+  atomicAdd(running, 1);
+  if (c.rebalance && p > 0.0 && d > 0.0) {
+    const double f = sqrt(p / d);
+    if (f > c.tol || f < 1.0 / c.tol) rho[i] = fmin(fmax(rho[i] * f, c.rho_min), c.rho_max);
+  }
+}
+
+// rho rows of K steps from the instances' scalars (x eq on zero-cone rows),
+// alpha of K steps
+template <class T, class V>
+__global__ void k_solve_fill(Prob<T, V> P, int32_t K, const double* __restrict__ rho, double eq, double alpha,
+                             T* __restrict__ rho_rows, T* __restrict__ alpha_k) {
+  const int64_t tot = (int64_t)K * P.m_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % P.m_total;
+    const double v = rho[P.row_inst[r]] * (P.row_kind[r] == K_ZERO ? eq : 1.0);
+    rho_rows[e] = (T)v;
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)K * P.ninst;
+       e += (int64_t)gridDim.x * blockDim.x)
+    alpha_k[e] = (T)alpha;
+}
+
 }  // namespace cosmo

@@ -351,6 +351,8 @@ struct Impl {
                                 cudaStream_t st) = 0;
   virtual cosmo_status residuals(const void* x, const void* s, const void* y, double* rp2,
                                  double* rd2, double* obj, cudaStream_t st) = 0;
+  virtual cosmo_status solve(const cosmo_solve_params& p, void* x, void* s, void* y, int32_t* iters,
+                             double* rbp, double* rbd, double* rho, cudaStream_t st) = 0;
   virtual cosmo_status rho_from_log(int32_t K, const double* lr, double eq, void* rho,
                                     cudaStream_t st) = 0;
   virtual cosmo_status rho_from_log_bwd(int32_t K, const void* rho, const void* grho,
@@ -441,6 +443,7 @@ struct ImplT : Impl {
 
   explicit ImplT(const cosmo_options& o, HostPlan& hp) : opt(o), h(hp) {}
   ~ImplT() override {
+    if (sv_run_h) cudaFreeHost(sv_run_h);
     for (auto& bk : buckets) { if (bk.s) cudaStreamDestroy(bk.s); if (bk.done) cudaEventDestroy(bk.done); }
     if (ev_fork) cudaEventDestroy(ev_fork);
     for (auto& r : prof_pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -1083,6 +1086,64 @@ struct ImplT : Impl {
     return COSMO_OK;
   }
 
+  // ---- solve to tolerance (vanilla COSMO with residual balancing) ----
+  DevArena sarena;                      // solve buffers, sized for sv_c steps per chunk
+  int32_t sv_c = 0;
+  T *sv_rho = nullptr, *sv_alpha = nullptr;
+  double *sv_rhoi = nullptr, *sv_nrm = nullptr, *sv_rbp = nullptr, *sv_rbd = nullptr;
+  int32_t *sv_conv = nullptr, *sv_run = nullptr, *sv_run_h = nullptr;
+
+  cosmo_status solve(const cosmo_solve_params& p, void* x, void* s, void* y, int32_t* iters, double* rbp,
+                     double* rbd, double* rho, cudaStream_t st) override {
+    const int c = p.check_every;
+    if (!x || !s || !y || !(p.sigma > 0.0) || !(p.alpha > 0.0 && p.alpha < 2.0) || !(p.rho0 > 0.0) ||
+        !(p.rho_eq_scale > 0.0) || !(p.eps > 0.0) || !(p.rebalance_tol >= 1.0) || !(p.rho_min > 0.0) ||
+        !(p.rho_max >= p.rho_min) || p.max_iter < 1 || c < 1 || p.rebalance_every < 0 ||
+        (p.rebalance_every > 0 && p.rebalance_every % c != 0))
+      return fail(COSMO_E_INVAL, "bad arguments to cosmo_solve");
+    const int64_t m = h.m;
+    const int32_t ni = h.ninst;
+    if (sv_c != c) {
+      if (sv_run_h) { cudaFreeHost(sv_run_h); sv_run_h = nullptr; }
+      sarena.release();
+      TRY(sarena.alloc(&sv_rho, (int64_t)c * std::max<int64_t>(m, 1)));
+      TRY(sarena.alloc(&sv_alpha, (int64_t)c * ni));
+      TRY(sarena.alloc(&sv_rhoi, ni)); TRY(sarena.alloc(&sv_nrm, 8 * (int64_t)ni));
+      TRY(sarena.alloc(&sv_rbp, ni)); TRY(sarena.alloc(&sv_rbd, ni));
+      TRY(sarena.alloc(&sv_conv, ni)); TRY(sarena.alloc(&sv_run, 1));
+      CU(cudaMallocHost(&sv_run_h, sizeof(int32_t)));
+      sv_c = c;
+    }
+    std::vector<double> r0(ni, p.rho0);
+    CU(cudaMemcpyAsync(sv_rhoi, r0.data(), sizeof(double) * ni, cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(sv_conv, 0xff, sizeof(int32_t) * ni, st));   // -1: not yet converged
+    std::vector<double> sig(c, p.sigma);
+    int32_t it = 0;
+    while (it < p.max_iter) {
+      const int32_t kk = std::min(c, p.max_iter - it);
+      k_solve_fill<T, V><<<grid_for((int64_t)kk * std::max<int64_t>(m, ni), 256), 256, 0, st>>>(
+          P, kk, sv_rhoi, p.rho_eq_scale, p.alpha, sv_rho, sv_alpha);
+      TRY(forward(kk, sig.data(), sv_rho, sv_alpha, x, s, y, x, s, y, nullptr, 0, st));
+      it += kk;
+      k_kkt_inf<T, V, 256><<<ni, 256, 0, st>>>(P, (const T*)x, (const T*)s, (const T*)y, sv_nrm);
+      CU(cudaMemsetAsync(sv_run, 0, sizeof(int32_t), st));
+      SolveCtl ctl{p.eps, p.rebalance_tol, p.rho_min, p.rho_max, it,
+                   p.rebalance_every > 0 && it % p.rebalance_every == 0 ? 1 : 0};
+      k_solve_update<<<(ni + 127) / 128, 128, 0, st>>>(ni, sv_nrm, ctl, sv_rhoi, sv_conv, sv_rbp, sv_rbd, sv_run);
+      CU(cudaGetLastError());
+      launched += 3; g_launches += 3;
+      CU(cudaMemcpyAsync(sv_run_h, sv_run, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      if (*sv_run_h == 0) break;
+    }
+    if (iters) CU(cudaMemcpyAsync(iters, sv_conv, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, st));
+    if (rbp) CU(cudaMemcpyAsync(rbp, sv_rbp, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+    if (rbd) CU(cudaMemcpyAsync(rbd, sv_rbd, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+    if (rho) CU(cudaMemcpyAsync(rho, sv_rhoi, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return COSMO_OK;
+  }
+
   cosmo_status residuals(const void* x, const void* s, const void* y, double* rp2, double* rd2,
                          double* obj, cudaStream_t st) override {
     if (!x || !s || !y) return fail(COSMO_E_INVAL, "x, s, y are required");
@@ -1284,6 +1345,31 @@ cosmo_status cosmo_residuals(cosmo_batch* b, const void* x, const void* s, const
                              double* rp2, double* rd2, double* obj, void* stream) {
   BATCH_GUARD(b);
   return b->impl->residuals(x, s, y, rp2, rd2, obj, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_solve_params_default(cosmo_solve_params* p) {
+  g_err.clear();
+  if (!p) return fail(COSMO_E_INVAL, "p is NULL");
+  p->sigma = 1e-6;
+  p->alpha = 1.6;
+  p->rho0 = 0.1;
+  p->rho_eq_scale = 1e3;
+  p->eps = 1e-3;
+  p->rebalance_tol = 5.0;
+  p->rho_min = 1e-6;
+  p->rho_max = 1e6;
+  p->max_iter = 5000;
+  p->check_every = 25;
+  p->rebalance_every = 25;
+  p->pad = 0;
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_solve(cosmo_batch* b, const cosmo_solve_params* prm, void* x, void* s, void* y,
+                         int32_t* iters, double* rbar_p, double* rbar_d, double* rho, void* stream) {
+  BATCH_GUARD(b);
+  if (!prm) return fail(COSMO_E_INVAL, "prm is NULL");
+  return b->impl->solve(*prm, x, s, y, iters, rbar_p, rbar_d, rho, (cudaStream_t)stream);
 }
 
 cosmo_status cosmo_rho_from_log(cosmo_batch* b, int32_t K, const double* log_rho, double eq_scale,

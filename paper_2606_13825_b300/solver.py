@@ -176,6 +176,29 @@ class CosmoBatch:
     def zeros(self, *shape, dtype=None):
         return torch.zeros(*shape, dtype=dtype or self.dtype, device=self.device)
 
+    def solve(self, x0=None, s0=None, y0=None, **params):
+        """Solve every instance to tolerance with the vanilla COSMO baseline
+        (residual-balancing rho, cosmo_solve).  Keyword arguments override
+        fields of the C parameter struct (eps, rho0, alpha, sigma, max_iter,
+        check_every, rebalance_every, rebalance_tol, rho_min, rho_max,
+        rho_eq_scale).  Returns (x, s, y, iters, rbar_p, rbar_d, rho) with
+        numpy arrays per instance (iters -1: not converged)."""
+        prm = _abi.SolveParams()
+        check(lib().cosmo_solve_params_default(byref(prm)))
+        for k, v in params.items():
+            if not hasattr(prm, k) or k == "pad":
+                raise TypeError(f"unknown parameter {k}")
+            setattr(prm, k, v)
+        x = x0.clone().contiguous() if x0 is not None else self.zeros(self.n_total)
+        s = s0.clone().contiguous() if s0 is not None else self.zeros(self.m_total)
+        y = y0.clone().contiguous() if y0 is not None else self.zeros(self.m_total)
+        iters = np.zeros(self.ninst, np.int32)
+        rbp, rbd, rho = (np.zeros(self.ninst) for _ in range(3))
+        p = lambda a: a.ctypes.data_as(c_void_p)
+        check(lib().cosmo_solve(self._h, byref(prm), _tp(x), _tp(s), _tp(y), p(iters), p(rbp), p(rbd), p(rho),
+                                _stream()))
+        return x, s, y, iters, rbp, rbd, rho
+
     def forward(self, K, rho, alpha, x0=None, s0=None, y0=None, sigma=None, tape=True,
                 want_loss=True):
         """Unroll K steps; returns (xK, sK, yK, loss) tensors (loss double)."""

@@ -293,3 +293,58 @@ def test_logratio_loss_definition():
         rp, rd = cosmo.residuals(pr, tr.xs[k], tr.ss[k], tr.ys[k])
         terms.append(np.log(rd @ rd / (rd0 @ rd0) + rp @ rp / (rp0 @ rp0)))
     assert abs(cosmo.loss_logratio(pr, tr.xs, tr.ss, tr.ys) - sum(terms)) < 1e-12 * abs(sum(terms))
+
+
+# ---- the vanilla COSMO baseline: solve to tolerance (Sec. 4, App. D) ------
+
+def test_kkt_normalised_vanishes_at_planted_kkt_point():
+    """The SOCP generator plants a primal-dual solution (x0, s0, y0) with
+    b = Ax0 + s0 and q = -Px0 + A'y0: both normalised residuals are zero
+    there, and grow linearly when the dual is perturbed."""
+    from oracle import cosmo as oc
+    pr = socp_problem(4310, n=40, m=70, density=0.1, m_M=10, n_soc=4, soc_lo=1, soc_hi=7)
+    x0, s0, y0 = pr.meta["x0"], pr.meta["s0"], pr.meta["y0"]
+    rp, rd = oc.kkt_normalised(pr, x0, s0, y0)
+    assert rp < 1e-14 and rd < 1e-14
+    dy = np.zeros(pr.m)
+    dy[3] = 1e-3
+    rp2, rd2 = oc.kkt_normalised(pr, x0, s0, y0 + dy)
+    aty = np.abs(pr.A.T @ (y0 + dy)).max()
+    scale = max(np.abs(pr.P @ x0).max(), np.abs(pr.q).max(), aty)
+    assert rp2 < 1e-14 and abs(rd2 - np.abs(pr.A.T @ dy).max() / scale) < 1e-14
+
+
+def test_rebalance_rule():
+    """rho * sqrt(rbar_p / rbar_d) outside [1/tol, tol], unchanged inside,
+    clipped to the bounds."""
+    from oracle.cosmo import rebalance
+    assert rebalance(0.1, 1e-2, 1e-4, 5.0, 1e-6, 1e6) == pytest.approx(1.0)      # factor 10
+    assert rebalance(0.1, 4e-4, 1e-4, 5.0, 1e-6, 1e6) == 0.1                     # factor 2: kept
+    assert rebalance(0.1, 1e-6, 1e-2, 5.0, 1e-6, 1e6) == pytest.approx(1e-3)     # factor 1/100
+    assert rebalance(0.5, 1.0, 1e-8, 5.0, 1e-6, 1e3) == 1e3                      # clipped
+    assert rebalance(0.1, 0.0, 1e-2, 5.0, 1e-6, 1e6) == 0.1                      # zero residual: kept
+
+
+@pytest.mark.parametrize("graph,value", [("cycle5", 2.5 * (1 + np.cos(np.pi / 5))), ("complete5", 25 / 4)])
+def test_solve_to_tolerance_maxcut_closed_forms(graph, value):
+    """Solved to eps = 1e-4 the max-cut SDP reaches the closed-form value
+    (odd cycle (n/2)(1 + cos(pi/n)), complete graph n^2/4), and at the
+    reported iteration count both normalised residuals meet eps while one
+    check earlier they did not."""
+    from oracle import cosmo as oc
+    from synth import cycle_graph, complete_graph
+    pr = maxcut_problem(5, cycle_graph(5) if graph == "cycle5" else complete_graph(5))
+    r = oc.solve_to_tolerance(pr, eps=1e-4, check_every=5, rebalance_every=25)
+    assert r["iters"] > 0 and r["rbar_p"] <= 1e-4 and r["rbar_d"] <= 1e-4
+    assert abs(-oc.objective(pr, r["x"]) - value) < 1e-3 * value
+    prev = oc.solve_to_tolerance(pr, eps=1e-4, check_every=5, rebalance_every=25, max_iter=r["iters"] - 5)
+    assert prev["iters"] == -1
+
+
+def test_solve_run_to_freezes_rho_after_convergence():
+    from oracle import cosmo as oc
+    pr = socp_problem(4320, n=30, m=50, density=0.15, m_M=8, n_soc=3, soc_lo=2, soc_hi=6)
+    a = oc.solve_to_tolerance(pr, eps=1e-3, check_every=10, rebalance_every=10)
+    b = oc.solve_to_tolerance(pr, eps=1e-3, check_every=10, rebalance_every=10, run_to=a["iters"] + 100)
+    assert a["iters"] > 0 and b["iters"] == a["iters"] and b["rho"] == a["rho"]
+    assert b["rbar_p"] <= 1e-3 * 1.5 and b["rbar_d"] <= 1e-3 * 1.5
