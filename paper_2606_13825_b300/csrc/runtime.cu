@@ -573,13 +573,12 @@ struct ImplT : Impl {
         while (e < h.psd_sched.size() && class_of(h.psd_p[h.psd_sched[e]]) == cls) ++e;
         const int method = cls == 1000 ? 1 : 0;
         const int nt = method ? 256 : cls;
-        const int fnt = 2 * nt;   // the forward's CTA size (see enqueue_step)
         Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr,
-                  method == 0 && (int64_t)psd_fwd_smem_warm<T>(p0, fnt) <= (int64_t)maxs, method};
+                  method == 0 && (int64_t)psd_fwd_smem_warm<T>(p0, nt) <= (int64_t)maxs, method};
         CU(cudaStreamCreateWithFlags(&bk.s, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
         if (method == 0) {
-          const size_t fs = psd_fwd_smem<T>(p0, fnt), bs = psd_bwd_smem<T>(p0, nt);
+          const size_t fs = psd_fwd_smem<T>(p0, nt), bs = psd_bwd_smem<T>(p0, nt);
           if ((int64_t)fs > maxs || (int64_t)bs > maxs)
             return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
                         p0, std::max(fs, bs), maxs);
@@ -597,7 +596,6 @@ struct ImplT : Impl {
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
-      CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -813,17 +811,13 @@ struct ImplT : Impl {
           return;
         }
         const T* up = (opt.eig_warm_start && bk.warm_fits) ? U_prev : nullptr;
-        // the forward takes twice the backward's threads per block: about
-        // one 2x2 block of a Jacobi round per thread, twice the warps to hide
-        // the rounds' shared-memory and arithmetic latency
-        const int fnt = 2 * bk.nt;
-        const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, fnt) : psd_fwd_smem<T>(bk.maxp, fnt);
-        if (fnt == 1024)
-          k_psd_fwd<T, V, 1024><<<bk.count, 1024, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
-        else if (fnt == 512)
+        const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.nt) : psd_fwd_smem<T>(bk.maxp, bk.nt);
+        if (bk.nt == 512)
           k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
-        else
+        else if (bk.nt == 256)
           k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
+        else
+          k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
       });
     }
   }
