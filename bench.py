@@ -80,7 +80,7 @@ def workload_spec(name, rank=0):
         return dict(probs=probs, K=40, opts={"use_graph": 1}, value_type="f32", learn_start=True,
                     metric="unrolled fwd+bwd instance-iters/sec (covariance steering, batched mixed precision)",
                     desc="covariance-steering stand-in SDPs: 512 instances (seeds 5000+j), nx=4, nu=2, T=20, "
-                         "PSD blocks 20x p8 + 20x p6 + p4; K=40; learned warm start and log rho_k / alpha_k; "
+                         "PSD blocks 20x p8 + 20x p6 + p4; K=40; App. E warm-start network and log rho_k / alpha_k; "
                          "one CUDA graph per forward / backward")
     raise ValueError(name)
 
@@ -310,6 +310,79 @@ def run_solve(args):
     return 0
 
 
+def ws_flops(F, O, H=64):
+    """Algorithmic flops per element of the warm-start network (App. E):
+    forward 2H(F + H + O); reverse pass (layer recompute, both cotangents)
+    2H(F + 2H + O); weight sums 2(F + 1)H + 2(H + 1)H + 2(H + 1)O."""
+    fwd = 2 * H * (F + H + O)
+    bwd = 2 * H * (F + 2 * H + O)
+    red = 2 * (F + 1) * H + 2 * (H + 1) * H + 2 * (H + 1) * O
+    return fwd, bwd, red
+
+
+def run_warmstart(args):
+    """The App. E warm-start network over the sparse-SOCP batch (64 instances,
+    n = 5000, m = 8000: 320k variables and 512k rows): features, both MLPs
+    forward, and the reverse pass to both parameter gradients.  Timed with
+    CUDA events on the current stream; ALU roofline of the reverse-pass
+    kernel of the constraint MLP (FP32 FMA on the CUDA cores)."""
+    import torch
+    from paper_2606_13825_b300 import CosmoBatch, WarmStartNet, lib
+    torch.cuda.set_device(0)
+    probs = workload_spec("socp", 0)["probs"]
+    b = CosmoBatch(probs, precision="mixed", value_type="bf16")
+    net = WarmStartNet(dtype=torch.float32, device="cuda", generator=torch.Generator().manual_seed(3))
+    with torch.no_grad():   # a trained-looking output layer (nonzero)
+        net.theta_x[-65:].normal_(0, 0.1)
+        net.theta_c[-130:].normal_(0, 0.1)
+    g = torch.Generator(device="cuda").manual_seed(4)
+    gx = torch.randn(b.n_total, device="cuda", generator=g)
+    gs = torch.randn(b.m_total, device="cuda", generator=g)
+    gy = torch.randn(b.m_total, device="cuda", generator=g)
+    tx, tc = net.theta_x.detach(), net.theta_c.detach()
+
+    def step():
+        b.ws_forward(tx, tc)
+        b.ws_backward(tx, tc, gx, gs, gy)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    b.profile("ws_bwd")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = lib().cosmo_kernel_launch_count()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (lib().cosmo_kernel_launch_count() - n0) // args.steps
+    N = b.n_total + b.m_total
+    fx, bx, rx = ws_flops(8, 1)
+    fc, bc, rc = ws_flops(12, 2)
+    flops = b.n_total * (fx + bx + rx) + b.m_total * (fc + bc + rc)
+    line = {"metric": "warm-start network fwd+bwd elements/s (App. E, sparse-SOCP batch)",
+            "value": N / (ms * 1e-3), "unit": "elements/s", "higher_is_better": True, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "gpu_launches": int(launches) * args.steps,
+            "gflop_per_step": flops / 1e9, "tflops": flops / (ms * 1e-3) / 1e12,
+            "config": {"workload": "sparse SOCP 64 x (n=5000, m=8000), features + MLP_x / MLP_c forward + "
+                                   "reverse to both parameter gradients", "precision": "FP32",
+                       "n_total": b.n_total, "m_total": b.m_total}}
+    tot_ms, nl = b.profile_read("ws_bwd")
+    b.profile(enable=False)
+    # FP32 FMA peak of the CUDA cores at the maximum SM clock (2 flops per lane-cycle)
+    peak = FP32_LANES_PER_SM * N_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    bwd_s = tot_ms * 1e-3 / args.steps   # both reverse-pass launches of one step
+    ach = (b.n_total * bx + b.m_total * bc) / bwd_s / 1e12
+    line["roofline"] = {"bound": "alu", "kernel": "k_ws_bwd (both MLPs)", "achieved": ach, "peak": peak,
+                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": nl,
+                        "share_of_step": bwd_s / (ms * 1e-3)}
+    print(json.dumps(line))
+    return 0
+
+
 # --------------------------------------------------------------------- ours --
 def psd_flops(probs):
     """Algorithmic flops of one PSD-projection launch: symmetric eigen-
@@ -330,11 +403,12 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run only W steps of the workload (the command profiled under ncu)")
     ap.add_argument("--workload", default="maxcut",
-                    choices=["maxcut", "lovasz", "socp", "covsteer", "linsys", "maxcut_solve"],
+                    choices=["maxcut", "lovasz", "socp", "covsteer", "linsys", "maxcut_solve", "warmstart"],
                     help="maxcut: the batched differentiable max-cut step (the headline metric); "
                          "lovasz / socp / covsteer: the paper's other classes at their stated sizes; "
                          "linsys: the App. B reduced-system CG at n=5e4 (HBM roofline of SpMV/CG); "
-                         "maxcut_solve: the vanilla COSMO baseline solving the max-cut batch to 1e-3")
+                         "maxcut_solve: the vanilla COSMO baseline solving the max-cut batch to 1e-3; "
+                         "warmstart: the App. E warm-start network forward + reverse on the SOCP batch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -342,6 +416,8 @@ def main():
         return run_linsys(args)
     if args.workload == "maxcut_solve":
         return run_solve(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -366,20 +442,21 @@ def main():
                    use_graph=use_graph, **opts)
     lr = torch.full((K,), math.log(0.1), dtype=torch.float64, device=dev, requires_grad=True)
     ak = torch.full((K,), 1.6, dtype=torch.float64, device=dev, requires_grad=True)
-    starts = None
+    net = None
     if spec["learn_start"]:
-        starts = [torch.zeros(nn, dtype=torch.float32, device=dev, requires_grad=True)
-                  for nn in (b.n_total, b.m_total, b.m_total)]
+        # the App. E warm-start network (its output layer starts at zero)
+        from paper_2606_13825_b300 import WarmStartNet
+        net = WarmStartNet(dtype=torch.float32, device=dev, generator=torch.Generator().manual_seed(11))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(batch=b):
         lr.grad = None
         ak.grad = None
         kw = {}
-        if starts:
-            for t_ in starts:
-                t_.grad = None
-            kw = dict(x0=starts[0], s0=starts[1], y0=starts[2])
+        if net is not None:
+            net.zero_grad(set_to_none=True)
+            x0, s0, y0 = net(batch)
+            kw = dict(x0=x0, s0=s0, y0=y0)
         L, _ = unrolled_residual_loss(batch, lr, ak, **kw)
         L.backward()
         return L

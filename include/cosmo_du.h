@@ -241,6 +241,34 @@ cosmo_status cosmo_solve_params_default(cosmo_solve_params* p);
 cosmo_status cosmo_solve(cosmo_batch* batch, const cosmo_solve_params* prm, void* x, void* s, void* y,
                          int32_t* iters, double* rbar_p, double* rbar_d, double* rho, void* stream);
 
+/* Warm-start network of App. E: two shared ReLU MLPs (two hidden layers of
+ * width 64) predict the initial iterate elementwise,
+ *   x0_j         = MLP_x([q_j, P_jj, ||A_{:,j}||_2, nnz(A_{:,j}), ctx])
+ *   (s0_r, y0_r) = MLP_c([b_r, ||A_{r,:}||_2, nnz(A_{r,:}), onehot5(cone of
+ *                         row r: zero, nonneg, box, soc, psd), ctx])
+ * with ctx = (log(1 + ||q||_inf), log(1 + ||b||_inf), log(1 + n_i),
+ * log(1 + m_i)) of the element's instance.  A layer is h = relu(W' u + b);
+ * the output layer is affine.  Parameters of an MLP with F inputs and O
+ * outputs, flattened in this order: W1 [F][64], b1 [64], W2 [64][64],
+ * b2 [64], W3 [64][O], b3 [O] (F = 8, O = 1 for MLP_x; F = 12, O = 2 for
+ * MLP_c); cosmo_ws_sizes gives the two lengths (4801 and 5122).
+ * All arrays are device memory of the batch's real type.
+ * cosmo_ws_forward: theta_x, theta_c in; x0 [n], s0 [m], y0 [m] out (s0,
+ * y0 may be NULL when m = 0).  cosmo_ws_backward: the gradients of
+ * <gx0, x0> + <gs0, s0> + <gy0, y0> with respect to theta_x and theta_c,
+ * written to gtheta_x, gtheta_c (same layouts); the weight gradients are
+ * summed over elements in a fixed order (bitwise reproducible).  The first
+ * backward allocates 256 reals per element of max(n, m) for the reverse
+ * pass; features are recomputed from the batch on every call.  Both are
+ * asynchronous on stream.  Errors: E_INVAL (a NULL operand), E_NOMEM,
+ * E_CUDA. */
+cosmo_status cosmo_ws_sizes(int32_t* n_theta_x, int32_t* n_theta_c);
+cosmo_status cosmo_ws_forward(cosmo_batch* batch, const void* theta_x, const void* theta_c, void* x0,
+                              void* s0, void* y0, void* stream);
+cosmo_status cosmo_ws_backward(cosmo_batch* batch, const void* theta_x, const void* theta_c,
+                               const void* gx0, const void* gs0, const void* gy0, void* gtheta_x,
+                               void* gtheta_c, void* stream);
+
 /* Unroll K iterations from (x0, s0, y0) (NULL = zero start).
  *   sigma_host: host [K] (NULL = 1e-6 every step, the value of Sec. 2.2)
  *   rho:   dev real [K][m_total], per-row penalties before rectification

@@ -117,6 +117,9 @@ _SIGS = {
     "cosmo_solve_params_default": (c_int32, [POINTER(SolveParams)]),
     "cosmo_solve": (c_int32, [c_void_p, POINTER(SolveParams), c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cosmo_ws_sizes": (c_int32, [POINTER(c_int32), POINTER(c_int32)]),
+    "cosmo_ws_forward": (c_int32, [c_void_p] * 7),
+    "cosmo_ws_backward": (c_int32, [c_void_p] * 9),
     "cosmo_pcg_plan_create": (c_int32, [c_int32, c_int32, c_int64, c_int64] + [c_void_p] * 11 +
                               [POINTER(c_void_p), c_void_p]),
     "cosmo_pcg_plan_solve": (c_int32, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_double,

@@ -1,0 +1,241 @@
+// Warm-start network of App. E: the initial iterate predicted elementwise by
+// two shared ReLU MLPs (two hidden layers of width 64), one per decision
+// variable from phi_j = [q_j, P_jj, ||A_{:,j}||_2, nnz(A_{:,j}), ctx], one per
+// constraint row from psi_r = [b_r, ||A_{r,:}||_2, nnz(A_{r,:}), onehot(cone of
+// r), ctx], with the instance context ctx = (log(1 + ||q||_inf), log(1 +
+// ||b||_inf), log(1 + n_i), log(1 + m_i)).
+//
+// Parameters of an MLP with F inputs and O outputs, flattened: W1 [F][64],
+// b1 [64], W2 [64][64], b2 [64], W3 [64][O], b3 [O]; a layer is
+// h = relu(W' u + b).  Features are stored feature-major ([F][N]) so that a
+// thread per element reads them coalesced.  The forward and the per-element
+// reverse pass keep a hidden layer (64 values) in registers and the weights
+// in shared memory (every lane reads the same weight: a broadcast).  The
+// weight gradients are sums over elements of outer products; they are formed
+// by a chunked reduction in a fixed order (bitwise reproducible).
+#pragma once
+
+#include "common.cuh"
+
+namespace cosmo {
+
+constexpr int WS_H = 64;
+constexpr int WS_NFX = 8;
+constexpr int WS_NFC = 12;
+__host__ __device__ constexpr int ws_nparams(int F, int O) { return F * WS_H + WS_H + WS_H * WS_H + WS_H + WS_H * O + O; }
+
+// ctx[4 i + k] of instance i (one CTA per instance; maxima in double)
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_ws_ctx(Prob<T, V> P, T* __restrict__ ctx) {
+  __shared__ double sm[2][NT / 32];
+  const int i = blockIdx.x;
+  const int64_t c0 = P.col_off[i], c1 = P.col_off[i + 1], r0 = P.row_off[i], r1 = P.row_off[i + 1];
+  double qm = 0.0, bm = 0.0;
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) qm = fmax(qm, fabs((double)P.q[j]));
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) bm = fmax(bm, fabs((double)P.b[r]));
+  for (int o = 16; o > 0; o >>= 1) {
+    qm = fmax(qm, __shfl_xor_sync(0xffffffffu, qm, o));
+    bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = qm; sm[1][threadIdx.x >> 5] = bm; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NT / 32; ++w) { qm = fmax(qm, sm[0][w]); bm = fmax(bm, sm[1][w]); }
+    ctx[4 * i + 0] = (T)log1p(qm);
+    ctx[4 * i + 1] = (T)log1p(bm);
+    ctx[4 * i + 2] = (T)log1p((double)(c1 - c0));
+    ctx[4 * i + 3] = (T)log1p((double)(r1 - r0));
+  }
+}
+
+// FX [8][n] and FC [12][m] (feature-major)
+template <class T, class V>
+__global__ void k_ws_feat(Prob<T, V> P, const T* __restrict__ ctx, T* __restrict__ FX, T* __restrict__ FC) {
+  const int64_t n = P.n_total, m = P.m_total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n + m; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < n) {
+      const int64_t j = e;
+      const int i = P.col_inst[j];
+      double cn = 0.0;
+      for (int64_t k = P.AT_rp[j]; k < P.AT_rp[j + 1]; ++k) {
+        const double a = (double)ldv(P.AT_v, k);
+        cn += a * a;
+      }
+      FX[0 * n + j] = P.q[j];
+      FX[1 * n + j] = P.Pdiag[j];
+      FX[2 * n + j] = (T)sqrt(cn);
+      FX[3 * n + j] = (T)(P.AT_rp[j + 1] - P.AT_rp[j]);
+      for (int k = 0; k < 4; ++k) FX[(4 + k) * n + j] = ctx[4 * i + k];
+    } else {
+      const int64_t r = e - n;
+      const int i = P.row_inst[r];
+      double rn = 0.0;
+      for (int64_t k = P.A_rp[r]; k < P.A_rp[r + 1]; ++k) {
+        const double a = (double)ldv(P.A_v, k);
+        rn += a * a;
+      }
+      FC[0 * m + r] = P.b[r];
+      FC[1 * m + r] = (T)sqrt(rn);
+      FC[2 * m + r] = (T)(P.A_rp[r + 1] - P.A_rp[r]);
+      const int kind = P.row_kind[r];
+      for (int k = 0; k < 5; ++k) FC[(3 + k) * m + r] = kind == k ? T(1) : T(0);
+      for (int k = 0; k < 4; ++k) FC[(8 + k) * m + r] = ctx[4 * i + k];
+    }
+  }
+}
+
+// the parameters into shared memory (all threads of the CTA)
+template <class T, int F, int O>
+__device__ __forceinline__ T* ws_load_params(const T* __restrict__ theta, T* sm) {
+  for (int k = threadIdx.x; k < ws_nparams(F, O); k += blockDim.x) sm[k] = theta[k];
+  __syncthreads();
+  return sm;
+}
+
+// h1 = relu(W1' x + b1) of element e
+template <class T, int F>
+__device__ __forceinline__ void ws_layer1(const T* __restrict__ X, int64_t N, int64_t e, const T* W1, const T* b1,
+                                          T (&h1)[WS_H]) {
+  T x[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) x[f] = X[f * N + e];
+#pragma unroll
+  for (int i = 0; i < WS_H; ++i) {
+    T z = b1[i];
+#pragma unroll
+    for (int f = 0; f < F; ++f) z += W1[f * WS_H + i] * x[f];
+    h1[i] = z > T(0) ? z : T(0);
+  }
+}
+
+// out[o][e] for every element (thread per element; up to two outputs)
+template <class T, int F, int O>
+__global__ void __launch_bounds__(128) k_ws_fwd(int64_t N, const T* __restrict__ X, const T* __restrict__ theta,
+                                                T* __restrict__ out0, T* __restrict__ out1) {
+  extern __shared__ __align__(16) unsigned char ws_sm[];
+  const T* w = ws_load_params<T, F, O>(theta, reinterpret_cast<T*>(ws_sm));
+  const T *W1 = w, *b1 = W1 + F * WS_H, *W2 = b1 + WS_H, *b2 = W2 + WS_H * WS_H, *W3 = b2 + WS_H, *b3 = W3 + WS_H * O;
+  // one element per thread: in a grid-stride loop the compiler hoists the
+  // loop-invariant weight reads into registers and spills
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < N) {
+    T h1[WS_H];
+    ws_layer1<T, F>(X, N, e, W1, b1, h1);
+    T o0 = b3[0], o1 = O > 1 ? b3[O - 1] : T(0);
+#pragma unroll 1
+    for (int j = 0; j < WS_H; ++j) {
+      T z = b2[j];
+#pragma unroll
+      for (int i = 0; i < WS_H; ++i) z += W2[i * WS_H + j] * h1[i];
+      if (z > T(0)) {
+        o0 += W3[j * O] * z;
+        if (O > 1) o1 += W3[j * O + 1] * z;
+      }
+    }
+    out0[e] = o0;
+    if (O > 1) out1[e] = o1;
+  }
+}
+
+// reverse pass per element, for the cotangent G [O][N] of the outputs:
+// H1 = relu(z1), D1 = dL/dz1, H2 = relu(z2), D2 = dL/dz2, each [64][N]
+template <class T, int F, int O>
+__global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, const T* __restrict__ X, const T* __restrict__ theta,
+                                                const T* __restrict__ G, T* __restrict__ H1, T* __restrict__ D1,
+                                                T* __restrict__ H2, T* __restrict__ D2) {
+  extern __shared__ __align__(16) unsigned char ws_sm[];
+  const T* w = ws_load_params<T, F, O>(theta, reinterpret_cast<T*>(ws_sm));
+  const T *W1 = w, *b1 = W1 + F * WS_H, *W2 = b1 + WS_H, *b2 = W2 + WS_H * WS_H, *W3 = b2 + WS_H;
+  // Two phases so that at most 64 values of a thread are live (fp64 would
+  // spill with h1 and d2 both in registers): the layer-2 cotangent goes to
+  // D2 and is read back by the same thread for layer 1.
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < N) {
+    T h[WS_H];
+    ws_layer1<T, F>(X, N, e, W1, b1, h);
+    T g[O];
+#pragma unroll
+    for (int o = 0; o < O; ++o) g[o] = G[o * N + e];
+#pragma unroll 1
+    for (int j = 0; j < WS_H; ++j) {
+      T z = b2[j];
+#pragma unroll
+      for (int i = 0; i < WS_H; ++i) z += W2[i * WS_H + j] * h[i];
+      T gz = T(0);
+#pragma unroll
+      for (int o = 0; o < O; ++o) gz += W3[j * O + o] * g[o];
+      H2[j * N + e] = z > T(0) ? z : T(0);
+      D2[j * N + e] = z > T(0) ? gz : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < WS_H; ++i) H1[i * N + e] = h[i];
+    // h now accumulates W2 d2
+#pragma unroll
+    for (int i = 0; i < WS_H; ++i) h[i] = T(0);
+#pragma unroll 1
+    for (int j = 0; j < WS_H; ++j) {
+      const T d = D2[j * N + e];
+#pragma unroll
+      for (int i = 0; i < WS_H; ++i) h[i] += W2[i * WS_H + j] * d;
+    }
+#pragma unroll
+    for (int i = 0; i < WS_H; ++i) D1[i * N + e] = H1[i * N + e] > T(0) ? h[i] : T(0);   // [z1 > 0] = [h1 > 0]
+  }
+}
+
+constexpr int WS_CHUNK = 2048;   // elements per CTA of the weight-gradient reduction
+constexpr int WS_TILE = 32;      // elements staged in shared memory at a time
+
+// part[c][a * KB + b] = sum over elements n of chunk c (in order) of
+// A'[a][n] B[b][n], where A' is A [KA][N] with a row of ones appended when
+// `ones` is set (the bias gradient lands right after the weight gradient,
+// as in the parameter layout), B [KB][N]; KA + ones <= 65, KB <= 64.
+// 256 threads, each owning up to 17 (a, b) pairs.
+template <class T>
+__global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__ A, int KA, int ones,
+                                                const T* __restrict__ B, int KB, double* __restrict__ part) {
+  __shared__ T sa[WS_H + 1][WS_TILE + 1], sb[WS_H][WS_TILE + 1];
+  const int64_t n0 = (int64_t)blockIdx.x * WS_CHUNK, n1 = min(N, n0 + WS_CHUNK);
+  const int ka = KA + ones, npair = ka * KB;
+  double acc[17];
+#pragma unroll
+  for (int q = 0; q < 17; ++q) acc[q] = 0.0;
+  for (int64_t t0 = n0; t0 < n1; t0 += WS_TILE) {
+    const int tl = (int)min((int64_t)WS_TILE, n1 - t0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < (WS_H + 1) * WS_TILE; k += 256) {
+      const int a = k / WS_TILE, t = k % WS_TILE;
+      if (a < ka) sa[a][t] = t < tl ? (a < KA ? A[a * N + t0 + t] : T(1)) : T(0);
+      if (a < KB) sb[a][t] = t < tl ? B[a * N + t0 + t] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 17; ++q) {
+      const int pr = threadIdx.x + 256 * q;
+      if (pr < npair) {
+        const int a = pr / KB, b = pr % KB;
+        T s = T(0);
+#pragma unroll 8
+        for (int t = 0; t < WS_TILE; ++t) s += sa[a][t] * sb[b][t];
+        acc[q] += (double)s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 17; ++q) {
+    const int pr = threadIdx.x + 256 * q;
+    if (pr < npair) part[(int64_t)blockIdx.x * npair + pr] = acc[q];
+  }
+}
+
+// out[k] = sum over chunks c (in order) of part[c][k]
+template <class T>
+__global__ void k_ws_sum(int nchunk, int npair, const double* __restrict__ part, T* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npair) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * npair + k];
+  out[k] = (T)s;
+}
+
+}  // namespace cosmo

@@ -26,6 +26,7 @@
 #include "kernels_gcs.cuh"
 #include "kernels_tc.cuh"
 #include "kernels_vec.cuh"
+#include "kernels_ws.cuh"
 
 using namespace cosmo;
 
@@ -353,6 +354,10 @@ struct Impl {
                                  double* rd2, double* obj, cudaStream_t st) = 0;
   virtual cosmo_status solve(const cosmo_solve_params& p, void* x, void* s, void* y, int32_t* iters,
                              double* rbp, double* rbd, double* rho, cudaStream_t st) = 0;
+  virtual cosmo_status ws_forward(const void* tx, const void* tc, void* x0, void* s0, void* y0,
+                                  cudaStream_t st) = 0;
+  virtual cosmo_status ws_backward(const void* tx, const void* tc, const void* gx0, const void* gs0,
+                                   const void* gy0, void* gtx, void* gtc, cudaStream_t st) = 0;
   virtual cosmo_status rho_from_log(int32_t K, const double* lr, double eq, void* rho,
                                     cudaStream_t st) = 0;
   virtual cosmo_status rho_from_log_bwd(int32_t K, const void* rho, const void* grho,
@@ -1144,6 +1149,94 @@ struct ImplT : Impl {
     return COSMO_OK;
   }
 
+  // ---- warm-start network (App. E) ----
+  DevArena warena;   // features and reverse-pass buffers, allocated on first use
+  T *ws_ctx = nullptr, *ws_fx = nullptr, *ws_fc = nullptr, *ws_g = nullptr;
+  T *ws_h1 = nullptr, *ws_d1 = nullptr, *ws_h2 = nullptr, *ws_d2 = nullptr;
+  double* ws_part = nullptr;
+  bool ws_feat_ok = false, ws_bwd_ok = false;
+
+  // ctx and the feature matrices, recomputed on every call (q and b are read
+  // from the batch as they stand)
+  cosmo_status ws_features(cudaStream_t st) {
+    if (!ws_feat_ok) {
+      TRY(warena.alloc(&ws_ctx, 4 * (int64_t)h.ninst));
+      TRY(warena.alloc(&ws_fx, (int64_t)WS_NFX * h.n));
+      TRY(warena.alloc(&ws_fc, (int64_t)WS_NFC * h.m));
+      ws_feat_ok = true;
+    }
+    launch("ws_feat", k_ws_ctx<T, V, 256>, h.ninst, 256, 0, st, P, ws_ctx);
+    if (h.n + h.m > 0) launch("ws_feat", k_ws_feat<T, V>, grid_for(h.n + h.m, 256), 256, 0, st, P, (const T*)ws_ctx,
+                              ws_fx, ws_fc);
+    CU(cudaGetLastError());
+    launched += 2; g_launches += 2;
+    return COSMO_OK;
+  }
+
+  cosmo_status ws_forward(const void* tx, const void* tc, void* x0, void* s0, void* y0,
+                          cudaStream_t st) override {
+    if (!tx || !tc || !x0 || (h.m > 0 && (!s0 || !y0)))
+      return fail(COSMO_E_INVAL, "bad arguments to cosmo_ws_forward");
+    TRY(ws_features(st));
+    if (h.n > 0)
+      launch("ws_fwd", k_ws_fwd<T, WS_NFX, 1>, (int)((h.n + 127) / 128), 128, sizeof(T) * ws_nparams(WS_NFX, 1), st,
+             h.n, (const T*)ws_fx, (const T*)tx, (T*)x0, (T*)nullptr);
+    if (h.m > 0)
+      launch("ws_fwd", k_ws_fwd<T, WS_NFC, 2>, (int)((h.m + 127) / 128), 128, sizeof(T) * ws_nparams(WS_NFC, 2), st,
+             h.m, (const T*)ws_fc, (const T*)tc, (T*)s0, (T*)y0);
+    CU(cudaGetLastError());
+    launched += 2; g_launches += 2;
+    return COSMO_OK;
+  }
+
+  // gtheta of one MLP from its features X [F][N] and output cotangent G [O][N]
+  template <int F, int O>
+  cosmo_status ws_mlp_backward(int64_t N, const T* X, const T* theta, const T* G, T* gtheta, cudaStream_t st) {
+    if (N == 0) {
+      CU(cudaMemsetAsync(gtheta, 0, sizeof(T) * ws_nparams(F, O), st));
+      return COSMO_OK;
+    }
+    launch("ws_bwd", k_ws_bwd<T, F, O>, (int)((N + 127) / 128), 128, sizeof(T) * ws_nparams(F, O), st, N, X, theta,
+           G, ws_h1, ws_d1, ws_h2, ws_d2);
+    const int nch = (int)((N + WS_CHUNK - 1) / WS_CHUNK);
+    // [W1; b1] = [X; 1] D1', [W2; b2] = [H1; 1] D2', [W3; b3] = [H2; 1] G'
+    const T* As[3] = {X, ws_h1, ws_h2};
+    const T* Bs[3] = {ws_d1, ws_d2, G};
+    const int KA[3] = {F, WS_H, WS_H}, KB[3] = {WS_H, WS_H, O};
+    int64_t off = 0;
+    for (int l = 0; l < 3; ++l) {
+      const int np = (KA[l] + 1) * KB[l];
+      launch("ws_grad", k_ws_atb<T>, nch, 256, 0, st, N, As[l], KA[l], 1, Bs[l], KB[l], ws_part);
+      launch("ws_grad", k_ws_sum<T>, (np + 255) / 256, 256, 0, st, nch, np, (const double*)ws_part, gtheta + off);
+      off += np;
+    }
+    CU(cudaGetLastError());
+    launched += 7; g_launches += 7;
+    return COSMO_OK;
+  }
+
+  cosmo_status ws_backward(const void* tx, const void* tc, const void* gx0, const void* gs0, const void* gy0,
+                           void* gtx, void* gtc, cudaStream_t st) override {
+    if (!tx || !tc || !gx0 || !gtx || !gtc || (h.m > 0 && (!gs0 || !gy0)))
+      return fail(COSMO_E_INVAL, "bad arguments to cosmo_ws_backward");
+    if (!ws_bwd_ok) {
+      const int64_t nmax = std::max<int64_t>(std::max(h.n, h.m), 1);
+      TRY(warena.alloc(&ws_g, 2 * std::max<int64_t>(h.m, 1)));
+      TRY(warena.alloc(&ws_h1, WS_H * nmax)); TRY(warena.alloc(&ws_d1, WS_H * nmax));
+      TRY(warena.alloc(&ws_h2, WS_H * nmax)); TRY(warena.alloc(&ws_d2, WS_H * nmax));
+      TRY(warena.alloc(&ws_part, (nmax + WS_CHUNK - 1) / WS_CHUNK * (int64_t)(WS_H + 1) * WS_H));
+      ws_bwd_ok = true;
+    }
+    TRY(ws_features(st));
+    TRY((ws_mlp_backward<WS_NFX, 1>(h.n, ws_fx, (const T*)tx, (const T*)gx0, (T*)gtx, st)));
+    if (h.m > 0) {
+      CU(cudaMemcpyAsync(ws_g, gs0, sizeof(T) * h.m, cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(ws_g + h.m, gy0, sizeof(T) * h.m, cudaMemcpyDeviceToDevice, st));
+    }
+    TRY((ws_mlp_backward<WS_NFC, 2>(h.m, ws_fc, (const T*)tc, ws_g, (T*)gtc, st)));
+    return COSMO_OK;
+  }
+
   cosmo_status residuals(const void* x, const void* s, const void* y, double* rp2, double* rd2,
                          double* obj, cudaStream_t st) override {
     if (!x || !s || !y) return fail(COSMO_E_INVAL, "x, s, y are required");
@@ -1201,7 +1294,7 @@ struct ImplT : Impl {
     o->n_psd = (int32_t)h.psd_p.size();
     o->max_psd_p = h.max_p;
     o->psd_u_entries = h.sum_p2;
-    o->device_bytes = arena.bytes + tarena.bytes;
+    o->device_bytes = arena.bytes + tarena.bytes + sarena.bytes + warena.bytes;
     o->last_K = K;
     o->tape_valid = tape_valid ? 1 : 0;
     o->kernels_launched = launched;
@@ -1370,6 +1463,25 @@ cosmo_status cosmo_solve(cosmo_batch* b, const cosmo_solve_params* prm, void* x,
   BATCH_GUARD(b);
   if (!prm) return fail(COSMO_E_INVAL, "prm is NULL");
   return b->impl->solve(*prm, x, s, y, iters, rbar_p, rbar_d, rho, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_ws_sizes(int32_t* n_theta_x, int32_t* n_theta_c) {
+  if (!n_theta_x || !n_theta_c) return fail(COSMO_E_INVAL, "NULL output");
+  *n_theta_x = ws_nparams(WS_NFX, 1);
+  *n_theta_c = ws_nparams(WS_NFC, 2);
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_ws_forward(cosmo_batch* b, const void* theta_x, const void* theta_c, void* x0, void* s0,
+                              void* y0, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->ws_forward(theta_x, theta_c, x0, s0, y0, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_ws_backward(cosmo_batch* b, const void* theta_x, const void* theta_c, const void* gx0,
+                               const void* gs0, const void* gy0, void* gtheta_x, void* gtheta_c, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->ws_backward(theta_x, theta_c, gx0, gs0, gy0, gtheta_x, gtheta_c, (cudaStream_t)stream);
 }
 
 cosmo_status cosmo_rho_from_log(cosmo_batch* b, int32_t K, const double* log_rho, double eq_scale,

@@ -199,6 +199,23 @@ class CosmoBatch:
                                 _stream()))
         return x, s, y, iters, rbp, rbd, rho
 
+    def ws_forward(self, theta_x, theta_c):
+        """Warm start (x0, s0, y0) predicted by the App. E network
+        (cosmo_ws_forward); theta_x, theta_c flat parameter tensors."""
+        x0, s0, y0 = self.zeros(self.n_total), self.zeros(self.m_total), self.zeros(self.m_total)
+        check(lib().cosmo_ws_forward(self._h, _tp(theta_x.contiguous()), _tp(theta_c.contiguous()), _tp(x0),
+                                     _tp(s0), _tp(y0), _stream()))
+        return x0, s0, y0
+
+    def ws_backward(self, theta_x, theta_c, gx0, gs0, gy0):
+        """(gtheta_x, gtheta_c) of <gx0, x0> + <gs0, s0> + <gy0, y0>."""
+        gtx, gtc = torch.empty_like(theta_x), torch.empty_like(theta_c)
+        c = lambda t, n: self.zeros(n) if t is None else t.contiguous()
+        check(lib().cosmo_ws_backward(self._h, _tp(theta_x.contiguous()), _tp(theta_c.contiguous()),
+                                      _tp(c(gx0, self.n_total)), _tp(c(gs0, self.m_total)),
+                                      _tp(c(gy0, self.m_total)), _tp(gtx), _tp(gtc), _stream()))
+        return gtx, gtc
+
     def forward(self, K, rho, alpha, x0=None, s0=None, y0=None, sigma=None, tape=True,
                 want_loss=True):
         """Unroll K steps; returns (xK, sK, yK, loss) tensors (loss double)."""
@@ -268,7 +285,8 @@ class CosmoBatch:
 
     KERNEL_CLASSES = ("rho_check", "rho_rectify", "alpha_check", "precond", "rhs", "pcg", "post",
                       "soc_fwd", "psd_fwd", "residuals", "loss_seed", "bwd_gproj", "soc_bwd",
-                      "psd_bwd", "bwd_relax", "pcg_adj", "bwd_solve", "rect_adjoint")
+                      "psd_bwd", "bwd_relax", "pcg_adj", "bwd_solve", "rect_adjoint", "ws_feat", "ws_fwd",
+                      "ws_bwd", "ws_grad")
 
     def profile(self, kernel=None, enable=True):
         """Time launches with CUDA events: kernel=None every class, a class
@@ -355,6 +373,54 @@ class AlphaBroadcast(torch.autograd.Function):
     @staticmethod
     def backward(ctx, galpha):
         return None, ctx.batch.alpha_reduce(galpha).to(ctx.adtype)
+
+
+def ws_sizes():
+    """(len(theta_x), len(theta_c)) of the warm-start network."""
+    a, b = c_int32(), c_int32()
+    check(lib().cosmo_ws_sizes(byref(a), byref(b)))
+    return a.value, b.value
+
+
+class WarmStart(torch.autograd.Function):
+    """(theta_x, theta_c) -> (x0, s0, y0) of the App. E warm-start network."""
+
+    @staticmethod
+    def forward(ctx, batch, theta_x, theta_c):
+        ctx.batch = batch
+        ctx.save_for_backward(theta_x, theta_c)
+        return batch.ws_forward(theta_x, theta_c)
+
+    @staticmethod
+    def backward(ctx, gx0, gs0, gy0):
+        tx, tc = ctx.saved_tensors
+        gtx, gtc = ctx.batch.ws_backward(tx, tc, gx0, gs0, gy0)
+        return None, gtx, gtc
+
+
+class WarmStartNet(torch.nn.Module):
+    """The two MLPs of the App. E warm start as trainable flat parameters:
+    He-normal hidden layers, zero biases and a zero output layer, so that an
+    untrained network gives the zero start."""
+
+    H = 64
+
+    def __init__(self, dtype=torch.float32, device="cuda", generator=None):
+        super().__init__()
+        self.theta_x = torch.nn.Parameter(self._init(8, 1, dtype, generator).to(device))
+        self.theta_c = torch.nn.Parameter(self._init(12, 2, dtype, generator).to(device))
+
+    @classmethod
+    def _init(cls, F, O, dtype, gen):
+        H = cls.H
+        w1 = torch.randn(F * H, generator=gen, dtype=torch.float64) * (2.0 / F) ** 0.5
+        w2 = torch.randn(H * H, generator=gen, dtype=torch.float64) * (2.0 / H) ** 0.5
+        z = torch.zeros
+        return torch.cat([w1, z(H, dtype=torch.float64), w2, z(H, dtype=torch.float64),
+                          z(H * O + O, dtype=torch.float64)]).to(dtype)
+
+    def forward(self, batch):
+        return WarmStart.apply(batch, self.theta_x, self.theta_c)
 
 
 def unrolled_residual_loss(batch, log_rho, alpha_k, sigma=1e-6, eq_scale=1e3, x0=None, s0=None,
