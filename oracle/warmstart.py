@@ -83,9 +83,9 @@ def features(problem):
     return Phi, Psi
 
 
-def mlp_forward(theta, X, O):
+def mlp_forward(theta, X, O, H=HIDDEN):
     """Outputs [N][O] and the activations the reverse pass needs."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta, X.shape[1], O)
+    W1, b1, W2, b2, W3, b3 = unpack(theta, X.shape[1], O, H)
     z1 = X @ W1 + b1
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W2 + b2
@@ -94,10 +94,10 @@ def mlp_forward(theta, X, O):
     return out, (X, z1, h1, z2, h2)
 
 
-def mlp_backward(theta, cache, G, O):
+def mlp_backward(theta, cache, G, O, H=HIDDEN):
     """Gradient of sum(G * out) with respect to theta (same layout)."""
     X, z1, h1, z2, h2 = cache
-    W1, b1, W2, b2, W3, b3 = unpack(theta, X.shape[1], O)
+    W1, b1, W2, b2, W3, b3 = unpack(theta, X.shape[1], O, H)
     gW3 = h2.T @ G
     gb3 = G.sum(axis=0)
     d2 = (G @ W3.T) * (z2 > 0.0)
