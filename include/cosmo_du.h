@@ -241,6 +241,48 @@ cosmo_status cosmo_solve_params_default(cosmo_solve_params* p);
 cosmo_status cosmo_solve(cosmo_batch* batch, const cosmo_solve_params* prm, void* x, void* s, void* y,
                          int32_t* iters, double* rbar_p, double* rbar_d, double* rho, void* stream);
 
+/* Closed-loop hyperparameter policy of App. E.  Step k of the unrolled
+ * iteration uses, per row, rho^k = exp(span sig(l^k_rho) + log 1e-3) (span =
+ * log 1e3 - log 1e-3: rho in (1e-3, 1e3)) before the SOC / PSD
+ * rectification, and per instance alpha^k = 2 sig(l^k_alpha).  The logits
+ * are recurrent, l^{k+1} = l^k + MLP(xi^k), with ReLU MLPs of 32 x 32 hidden
+ * units and one output: per row on
+ *   xi_rho = [l_rho, s, y, rbar_p, log(||rbar_d||_inf + 1e-12), delta_p, delta_d]
+ * and per instance on
+ *   xi_alpha = [l_alpha, log(||rbar_p||_inf + 1e-12), log(||rbar_d||_inf +
+ *               1e-12), log(||delta_p||_inf + 1e-12), log(||delta_d||_inf + 1e-12)]
+ * of the iterate k: rbar_p = (Ax + s - b) / max(||Ax||, ||s||, ||b||) and
+ * rbar_d = (Px + q - A'y) / max(||Px||, ||q||, ||A'y||) (infinity norms, a
+ * zero scale counts as 1), delta_d = s^k - s^{k-1}, delta_p = s^k - s~^k
+ * (s~ before relaxation; both zero at k = 0).  K steps evaluate the policy
+ * K - 1 times.  l0 [5] = initial logits (zero rows, orthant and box rows,
+ * SOC rows, PSD rows, alpha); the defaults rho = (100, 0.1, 0.1, 0.1) and
+ * alpha = 1.6 correspond to logit((log rho + log 1e3) / span) and logit(0.8).
+ * Parameter layout of each MLP: W1 [F][32], b1 [32], W2 [32][32], b2 [32],
+ * W3 [32][1], b3 [1] (F = 7 and 5; cosmo_policy_sizes: 1345 and 1281).
+ * cosmo_policy_forward: as cosmo_forward, with the per-step rho and alpha
+ * produced by the policy on the device inside the unrolled sequence (one
+ * CUDA graph with use_graph); theta_rho, theta_alpha, l0 are device arrays
+ * of the batch's real type, copied at the call.  cosmo_policy_backward: the
+ * gradients of <gx, x^K> + <gs, s^K> + <gy, y^K> + sum_i gloss_i loss_i with
+ * respect to theta_rho, theta_alpha, l0 (device, same layouts) and, if not
+ * NULL, the start (gx0, gs0, gy0), with the features built from the solver
+ * state held constant: the gradient reaches the policy through rho^k,
+ * alpha^k and the logit recurrence (the l input of each MLP stays live).
+ * Parameter sums run in a fixed order.  cosmo_policy_schedule copies the
+ * rho [K][m] (before rectification) and alpha [K][ninst] of the last policy
+ * forward.  Errors: E_INVAL, E_STATE (backward without a taped policy
+ * forward), E_NOMEM, E_CUDA. */
+cosmo_status cosmo_policy_sizes(int32_t* n_theta_rho, int32_t* n_theta_alpha);
+cosmo_status cosmo_policy_forward(cosmo_batch* batch, int32_t K, const double* sigma_host,
+                                  const void* theta_rho, const void* theta_alpha, const void* l0,
+                                  const void* x0, const void* s0, const void* y0, void* xK, void* sK,
+                                  void* yK, double* loss, int32_t record_tape, void* stream);
+cosmo_status cosmo_policy_backward(cosmo_batch* batch, const void* gx, const void* gs, const void* gy,
+                                   const double* gloss, void* gtheta_rho, void* gtheta_alpha, void* gl0,
+                                   void* gx0, void* gs0, void* gy0, void* stream);
+cosmo_status cosmo_policy_schedule(cosmo_batch* batch, void* rho, void* alpha, void* stream);
+
 /* Warm-start network of App. E: two shared ReLU MLPs (two hidden layers of
  * width 64) predict the initial iterate elementwise,
  *   x0_j         = MLP_x([q_j, P_jj, ||A_{:,j}||_2, nnz(A_{:,j}), ctx])

@@ -12,7 +12,8 @@ def __getattr__(name):
     # lazy: keep `import paper_2606_13825_b300` free of torch / CUDA work
     if name in ("CosmoBatch", "CosmoUnroll", "RhoFromLog", "AlphaBroadcast",
                 "unrolled_residual_loss", "psd_project", "psd_dk_backward", "pack",
-                "validate", "default_options", "WarmStart", "WarmStartNet", "ws_sizes"):
+                "validate", "default_options", "WarmStart", "WarmStartNet", "ws_sizes",
+                "PolicyUnroll", "HyperPolicy", "policy_sizes", "policy_default_l0"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -117,6 +117,10 @@ _SIGS = {
     "cosmo_solve_params_default": (c_int32, [POINTER(SolveParams)]),
     "cosmo_solve": (c_int32, [c_void_p, POINTER(SolveParams), c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cosmo_policy_sizes": (c_int32, [POINTER(c_int32), POINTER(c_int32)]),
+    "cosmo_policy_forward": (c_int32, [c_void_p, c_int32, POINTER(c_double)] + [c_void_p] * 10 + [c_int32, c_void_p]),
+    "cosmo_policy_backward": (c_int32, [c_void_p] * 12),
+    "cosmo_policy_schedule": (c_int32, [c_void_p] * 4),
     "cosmo_ws_sizes": (c_int32, [POINTER(c_int32), POINTER(c_int32)]),
     "cosmo_ws_forward": (c_int32, [c_void_p] * 7),
     "cosmo_ws_backward": (c_int32, [c_void_p] * 9),

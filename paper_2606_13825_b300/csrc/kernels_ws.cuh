@@ -22,7 +22,7 @@ namespace cosmo {
 constexpr int WS_H = 64;
 constexpr int WS_NFX = 8;
 constexpr int WS_NFC = 12;
-__host__ __device__ constexpr int ws_nparams(int F, int O) { return F * WS_H + WS_H + WS_H * WS_H + WS_H + WS_H * O + O; }
+__host__ __device__ constexpr int ws_nparams(int F, int O, int H = WS_H) { return F * H + H + H * H + H + H * O + O; }
 
 // ctx[4 i + k] of instance i (one CTA per instance; maxima in double)
 template <class T, class V, int NT>
@@ -85,25 +85,25 @@ __global__ void k_ws_feat(Prob<T, V> P, const T* __restrict__ ctx, T* __restrict
 }
 
 // the parameters into shared memory (all threads of the CTA)
-template <class T, int F, int O>
+template <class T, int F, int O, int H = WS_H>
 __device__ __forceinline__ T* ws_load_params(const T* __restrict__ theta, T* sm) {
-  for (int k = threadIdx.x; k < ws_nparams(F, O); k += blockDim.x) sm[k] = theta[k];
+  for (int k = threadIdx.x; k < ws_nparams(F, O, H); k += blockDim.x) sm[k] = theta[k];
   __syncthreads();
   return sm;
 }
 
-// h1 = relu(W1' x + b1) of element e
-template <class T, int F>
-__device__ __forceinline__ void ws_layer1(const T* __restrict__ X, int64_t N, int64_t e, const T* W1, const T* b1,
-                                          T (&h1)[WS_H]) {
+// h1 = relu(W1' x + b1) of element e (features X[f * ld + e])
+template <class T, int F, int H = WS_H>
+__device__ __forceinline__ void ws_layer1(const T* __restrict__ X, int64_t ld, int64_t e, const T* W1, const T* b1,
+                                          T (&h1)[H]) {
   T x[F];
 #pragma unroll
-  for (int f = 0; f < F; ++f) x[f] = X[f * N + e];
+  for (int f = 0; f < F; ++f) x[f] = X[f * ld + e];
 #pragma unroll
-  for (int i = 0; i < WS_H; ++i) {
+  for (int i = 0; i < H; ++i) {
     T z = b1[i];
 #pragma unroll
-    for (int f = 0; f < F; ++f) z += W1[f * WS_H + i] * x[f];
+    for (int f = 0; f < F; ++f) z += W1[f * H + i] * x[f];
     h1[i] = z > T(0) ? z : T(0);
   }
 }
@@ -137,30 +137,32 @@ __global__ void __launch_bounds__(128) k_ws_fwd(int64_t N, const T* __restrict__
   }
 }
 
-// reverse pass per element, for the cotangent G [O][N] of the outputs:
-// H1 = relu(z1), D1 = dL/dz1, H2 = relu(z2), D2 = dL/dz2, each [64][N]
-template <class T, int F, int O>
-__global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, const T* __restrict__ X, const T* __restrict__ theta,
-                                                const T* __restrict__ G, T* __restrict__ H1, T* __restrict__ D1,
-                                                T* __restrict__ H2, T* __restrict__ D2) {
+// reverse pass per element e < N, for the cotangent G[o * ldg + e] of the
+// outputs, features X[f * ldx + e]: H1 = relu(z1), D1 = dL/dz1, H2 =
+// relu(z2), D2 = dL/dz2, each [H][N]
+template <class T, int F, int O, int H = WS_H>
+__global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, int64_t ldx, const T* __restrict__ X,
+                                                const T* __restrict__ theta, const T* __restrict__ G, int64_t ldg,
+                                                T* __restrict__ H1, T* __restrict__ D1, T* __restrict__ H2,
+                                                T* __restrict__ D2) {
   extern __shared__ __align__(16) unsigned char ws_sm[];
-  const T* w = ws_load_params<T, F, O>(theta, reinterpret_cast<T*>(ws_sm));
-  const T *W1 = w, *b1 = W1 + F * WS_H, *W2 = b1 + WS_H, *b2 = W2 + WS_H * WS_H, *W3 = b2 + WS_H;
+  const T* w = ws_load_params<T, F, O, H>(theta, reinterpret_cast<T*>(ws_sm));
+  const T *W1 = w, *b1 = W1 + F * H, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H;
   // Two phases so that at most 64 values of a thread are live (fp64 would
   // spill with h1 and d2 both in registers): the layer-2 cotangent goes to
   // D2 and is read back by the same thread for layer 1.
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e < N) {
-    T h[WS_H];
-    ws_layer1<T, F>(X, N, e, W1, b1, h);
+    T h[H];
+    ws_layer1<T, F, H>(X, ldx, e, W1, b1, h);
     T g[O];
 #pragma unroll
-    for (int o = 0; o < O; ++o) g[o] = G[o * N + e];
+    for (int o = 0; o < O; ++o) g[o] = G[o * ldg + e];
 #pragma unroll 1
-    for (int j = 0; j < WS_H; ++j) {
+    for (int j = 0; j < H; ++j) {
       T z = b2[j];
 #pragma unroll
-      for (int i = 0; i < WS_H; ++i) z += W2[i * WS_H + j] * h[i];
+      for (int i = 0; i < H; ++i) z += W2[i * H + j] * h[i];
       T gz = T(0);
 #pragma unroll
       for (int o = 0; o < O; ++o) gz += W3[j * O + o] * g[o];
@@ -168,18 +170,18 @@ __global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, const T* __restrict__
       D2[j * N + e] = z > T(0) ? gz : T(0);
     }
 #pragma unroll
-    for (int i = 0; i < WS_H; ++i) H1[i * N + e] = h[i];
+    for (int i = 0; i < H; ++i) H1[i * N + e] = h[i];
     // h now accumulates W2 d2
 #pragma unroll
-    for (int i = 0; i < WS_H; ++i) h[i] = T(0);
+    for (int i = 0; i < H; ++i) h[i] = T(0);
 #pragma unroll 1
-    for (int j = 0; j < WS_H; ++j) {
+    for (int j = 0; j < H; ++j) {
       const T d = D2[j * N + e];
 #pragma unroll
-      for (int i = 0; i < WS_H; ++i) h[i] += W2[i * WS_H + j] * d;
+      for (int i = 0; i < H; ++i) h[i] += W2[i * H + j] * d;
     }
 #pragma unroll
-    for (int i = 0; i < WS_H; ++i) D1[i * N + e] = H1[i * N + e] > T(0) ? h[i] : T(0);   // [z1 > 0] = [h1 > 0]
+    for (int i = 0; i < H; ++i) D1[i * N + e] = H1[i * N + e] > T(0) ? h[i] : T(0);   // [z1 > 0] = [h1 > 0]
   }
 }
 
@@ -187,13 +189,14 @@ constexpr int WS_CHUNK = 2048;   // elements per CTA of the weight-gradient redu
 constexpr int WS_TILE = 32;      // elements staged in shared memory at a time
 
 // part[c][a * KB + b] = sum over elements n of chunk c (in order) of
-// A'[a][n] B[b][n], where A' is A [KA][N] with a row of ones appended when
+// A'[a][n] B[b][n] (rows lda, ldb apart), where A' is A [KA][N] with a row of ones appended when
 // `ones` is set (the bias gradient lands right after the weight gradient,
 // as in the parameter layout), B [KB][N]; KA + ones <= 65, KB <= 64.
 // 256 threads, each owning up to 17 (a, b) pairs.
 template <class T>
-__global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__ A, int KA, int ones,
-                                                const T* __restrict__ B, int KB, double* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__ A, int64_t lda, int KA, int ones,
+                                                const T* __restrict__ B, int64_t ldb, int KB,
+                                                double* __restrict__ part) {
   __shared__ T sa[WS_H + 1][WS_TILE + 1], sb[WS_H][WS_TILE + 1];
   const int64_t n0 = (int64_t)blockIdx.x * WS_CHUNK, n1 = min(N, n0 + WS_CHUNK);
   const int ka = KA + ones, npair = ka * KB;
@@ -205,8 +208,8 @@ __global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__
     __syncthreads();
     for (int k = threadIdx.x; k < (WS_H + 1) * WS_TILE; k += 256) {
       const int a = k / WS_TILE, t = k % WS_TILE;
-      if (a < ka) sa[a][t] = t < tl ? (a < KA ? A[a * N + t0 + t] : T(1)) : T(0);
-      if (a < KB) sb[a][t] = t < tl ? B[a * N + t0 + t] : T(0);
+      if (a < ka) sa[a][t] = t < tl ? (a < KA ? A[a * lda + t0 + t] : T(1)) : T(0);
+      if (a < KB) sb[a][t] = t < tl ? B[a * ldb + t0 + t] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -228,12 +231,12 @@ __global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__
   }
 }
 
-// out[k] = sum over chunks c (in order) of part[c][k]
+// out[k] (+)= sum over chunks c (in order) of part[c][k]
 template <class T>
-__global__ void k_ws_sum(int nchunk, int npair, const double* __restrict__ part, T* __restrict__ out) {
+__global__ void k_ws_sum(int nchunk, int npair, const double* __restrict__ part, T* __restrict__ out, int accumulate) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= npair) return;
-  double s = 0.0;
+  double s = accumulate ? (double)out[k] : 0.0;
   for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * npair + k];
   out[k] = (T)s;
 }

@@ -27,6 +27,7 @@
 #include "kernels_tc.cuh"
 #include "kernels_vec.cuh"
 #include "kernels_ws.cuh"
+#include "kernels_pol.cuh"
 
 using namespace cosmo;
 
@@ -354,6 +355,12 @@ struct Impl {
                                  double* rd2, double* obj, cudaStream_t st) = 0;
   virtual cosmo_status solve(const cosmo_solve_params& p, void* x, void* s, void* y, int32_t* iters,
                              double* rbp, double* rbd, double* rho, cudaStream_t st) = 0;
+  virtual cosmo_status pol_forward(int32_t K, const double* sigma, const void* tr, const void* ta,
+                                   const void* l0, const void* x0, const void* s0, const void* y0, void* xK,
+                                   void* sK, void* yK, double* loss, int32_t tape, cudaStream_t st) = 0;
+  virtual cosmo_status pol_backward(const void* gx, const void* gs, const void* gy, const double* gl, void* gtr,
+                                    void* gta, void* gl0, void* gx0, void* gs0, void* gy0, cudaStream_t st) = 0;
+  virtual cosmo_status pol_schedule(void* rho, void* alpha, cudaStream_t st) = 0;
   virtual cosmo_status ws_forward(const void* tx, const void* tc, void* x0, void* s0, void* y0,
                                   cudaStream_t st) = 0;
   virtual cosmo_status ws_backward(const void* tx, const void* tc, const void* gx0, const void* gs0,
@@ -840,6 +847,8 @@ struct ImplT : Impl {
       }
       enqueue_step(k, slot, warm, uprev, st);
       if (lr_track) enqueue_norms(slot + 1, k + 1, st);
+      // xi^{k+1} from z^{k+1}, s^k and s~^{k+1} gives the parameters of step k + 2
+      if (pol_mode && k + 1 <= K - 2) enqueue_pol(k + 1, slot + 1, st_s(slot), sts + (int64_t)slot * h.m, st);
     }
   }
 
@@ -860,7 +869,8 @@ struct ImplT : Impl {
 
   // whole forward: prep, all segments with checkpoints, optional loss
   void enqueue_forward(bool want_loss, cudaStream_t st) {
-    enqueue_prep(st);
+    if (pol_mode) enqueue_pol_prep(st);
+    else enqueue_prep(st);
     lr_track = want_loss && opt.loss_kind == 1;
     if (lr_track) enqueue_norms(0, 0, st);
     for (int32_t seg = 0; seg < nseg; ++seg) {
@@ -1010,7 +1020,7 @@ struct ImplT : Impl {
                        const void* x0, const void* s0, const void* y0, void* xK, void* sK,
                        void* yK, double* loss, int32_t tape, cudaStream_t st) override {
     if (K_ < 1) return fail(COSMO_E_INVAL, "K must be >= 1");
-    if (!rho || !alpha) return fail(COSMO_E_INVAL, "rho and alpha are required");
+    if (!pol_mode && (!rho || !alpha)) return fail(COSMO_E_INVAL, "rho and alpha are required");
     TRY(ensure_tape(K_));
     std::vector<double> sg(K, 1e-6);
     if (sigma)
@@ -1021,8 +1031,11 @@ struct ImplT : Impl {
     sigma_h = sg;
     const int64_t n = h.n, m = h.m;
     CU(cudaMemcpyAsync(sigma_dev, sg.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(rho_in, rho, sizeof(T) * K * m, cudaMemcpyDeviceToDevice, st));
-    CU(cudaMemcpyAsync(alpha_in, alpha, sizeof(T) * K * h.ninst, cudaMemcpyDeviceToDevice, st));
+    if (!pol_mode) {
+      CU(cudaMemcpyAsync(rho_in, rho, sizeof(T) * K * m, cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(alpha_in, alpha, sizeof(T) * K * h.ninst, cudaMemcpyDeviceToDevice, st));
+    }
+    pol_valid = false;
     if (x0) CU(cudaMemcpyAsync(st_x(0), x0, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
     else CU(cudaMemsetAsync(st_x(0), 0, sizeof(T) * n, st));
     if (s0) CU(cudaMemcpyAsync(st_s(0), s0, sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
@@ -1030,9 +1043,10 @@ struct ImplT : Impl {
     if (y0) CU(cudaMemcpyAsync(st_y(0), y0, sizeof(T) * m, cudaMemcpyDeviceToDevice, st));
     else CU(cudaMemsetAsync(st_y(0), 0, sizeof(T) * m, st));
     const bool want_loss = loss != nullptr || tape;
-    const bool reuse = gfwd_key[0] == K && gfwd_key[1] == (int)want_loss && gfwd_sigma == sg;
+    const bool reuse = gfwd_key[0] == K && gfwd_key[1] == (int)want_loss && gfwd_key[2] == (int)pol_mode &&
+                       gfwd_sigma == sg;
     TRY(run_seq(gfwd, gfwd_nk, reuse, [&](cudaStream_t s) { enqueue_forward(want_loss, s); }, st));
-    gfwd_key[0] = K; gfwd_key[1] = (int)want_loss; gfwd_sigma = sg;
+    gfwd_key[0] = K; gfwd_key[1] = (int)want_loss; gfwd_key[2] = (int)pol_mode; gfwd_sigma = sg;
     seg_in_buffer = nseg - 1;
     tape_valid = tape != 0;
     loss_valid = want_loss;
@@ -1189,30 +1203,39 @@ struct ImplT : Impl {
     return COSMO_OK;
   }
 
-  // gtheta of one MLP from its features X [F][N] and output cotangent G [O][N]
-  template <int F, int O>
-  cosmo_status ws_mlp_backward(int64_t N, const T* X, const T* theta, const T* G, T* gtheta, cudaStream_t st) {
+  // gtheta (+)= the parameter gradient of an MLP (F inputs, H x H hidden,
+  // O outputs) over elements e < N with features X[f * ldx + e] and output
+  // cotangent G[o * ldg + e]; h1..d2 hold H x N reals, part the chunk partials
+  template <int F, int O, int H>
+  cosmo_status mlp_bwd(int64_t N, const T* X, int64_t ldx, const T* theta, const T* G, int64_t ldg, T* gtheta,
+                       int acc, T* h1, T* d1, T* h2, T* d2, double* part, const char* tag, cudaStream_t st) {
     if (N == 0) {
-      CU(cudaMemsetAsync(gtheta, 0, sizeof(T) * ws_nparams(F, O), st));
+      if (!acc) CU(cudaMemsetAsync(gtheta, 0, sizeof(T) * ws_nparams(F, O, H), st));
       return COSMO_OK;
     }
-    launch("ws_bwd", k_ws_bwd<T, F, O>, (int)((N + 127) / 128), 128, sizeof(T) * ws_nparams(F, O), st, N, X, theta,
-           G, ws_h1, ws_d1, ws_h2, ws_d2);
+    launch(tag, k_ws_bwd<T, F, O, H>, (int)((N + 127) / 128), 128, sizeof(T) * ws_nparams(F, O, H), st, N, ldx, X,
+           theta, G, ldg, h1, d1, h2, d2);
     const int nch = (int)((N + WS_CHUNK - 1) / WS_CHUNK);
     // [W1; b1] = [X; 1] D1', [W2; b2] = [H1; 1] D2', [W3; b3] = [H2; 1] G'
-    const T* As[3] = {X, ws_h1, ws_h2};
-    const T* Bs[3] = {ws_d1, ws_d2, G};
-    const int KA[3] = {F, WS_H, WS_H}, KB[3] = {WS_H, WS_H, O};
+    const T* As[3] = {X, h1, h2};
+    const T* Bs[3] = {d1, d2, G};
+    const int64_t lda[3] = {ldx, N, N}, ldb[3] = {N, N, ldg};
+    const int KA[3] = {F, H, H}, KB[3] = {H, H, O};
     int64_t off = 0;
     for (int l = 0; l < 3; ++l) {
       const int np = (KA[l] + 1) * KB[l];
-      launch("ws_grad", k_ws_atb<T>, nch, 256, 0, st, N, As[l], KA[l], 1, Bs[l], KB[l], ws_part);
-      launch("ws_grad", k_ws_sum<T>, (np + 255) / 256, 256, 0, st, nch, np, (const double*)ws_part, gtheta + off);
+      launch("ws_grad", k_ws_atb<T>, nch, 256, 0, st, N, As[l], lda[l], KA[l], 1, Bs[l], ldb[l], KB[l], part);
+      launch("ws_grad", k_ws_sum<T>, (np + 255) / 256, 256, 0, st, nch, np, (const double*)part, gtheta + off, acc);
       off += np;
     }
     CU(cudaGetLastError());
     launched += 7; g_launches += 7;
     return COSMO_OK;
+  }
+
+  template <int F, int O>
+  cosmo_status ws_mlp_backward(int64_t N, const T* X, const T* theta, const T* G, T* gtheta, cudaStream_t st) {
+    return mlp_bwd<F, O, WS_H>(N, X, N, theta, G, N, gtheta, 0, ws_h1, ws_d1, ws_h2, ws_d2, ws_part, "ws_bwd", st);
   }
 
   cosmo_status ws_backward(const void* tx, const void* tc, const void* gx0, const void* gs0, const void* gy0,
@@ -1234,6 +1257,125 @@ struct ImplT : Impl {
       CU(cudaMemcpyAsync(ws_g + h.m, gy0, sizeof(T) * h.m, cudaMemcpyDeviceToDevice, st));
     }
     TRY((ws_mlp_backward<WS_NFC, 2>(h.m, ws_fc, (const T*)tc, ws_g, (T*)gtc, st)));
+    return COSMO_OK;
+  }
+
+  // ---- closed-loop hyperparameter policy (App. E) ----
+  DevArena parena;   // sized for pol_K steps
+  int32_t pol_K = 0;
+  bool pol_mode = false, pol_valid = false;
+  int64_t pol_ch = 0;   // elements per chunk of the MLP reverse pass
+  T *pol_tr = nullptr, *pol_ta = nullptr, *pol_l0 = nullptr;
+  T *pol_Xr = nullptr, *pol_Jr = nullptr, *pol_Gr = nullptr, *pol_lr = nullptr, *pol_glr = nullptr;
+  T *pol_Xa = nullptr, *pol_Ja = nullptr, *pol_Ga = nullptr, *pol_la = nullptr, *pol_gla = nullptr;
+  T *pol_sc = nullptr, *pol_h1 = nullptr, *pol_d1 = nullptr, *pol_h2 = nullptr, *pol_d2 = nullptr;
+  double* pol_part = nullptr;
+
+  cosmo_status pol_alloc(int32_t K_) {
+    if (pol_K == K_) return COSMO_OK;
+    parena.release();
+    pol_K = 0;
+    const int64_t m = h.m, ni = h.ninst, Nr = (int64_t)(K_ - 1) * m, Na = (int64_t)(K_ - 1) * ni;
+    TRY(parena.alloc(&pol_tr, ws_nparams(POL_NFR, 1, POL_H)));
+    TRY(parena.alloc(&pol_ta, ws_nparams(POL_NFA, 1, POL_H)));
+    TRY(parena.alloc(&pol_l0, 5));
+    TRY(parena.alloc(&pol_Xr, POL_NFR * Nr)); TRY(parena.alloc(&pol_Jr, Nr)); TRY(parena.alloc(&pol_Gr, Nr));
+    TRY(parena.alloc(&pol_lr, (int64_t)K_ * m)); TRY(parena.alloc(&pol_glr, m));
+    TRY(parena.alloc(&pol_Xa, POL_NFA * Na)); TRY(parena.alloc(&pol_Ja, Na)); TRY(parena.alloc(&pol_Ga, Na));
+    TRY(parena.alloc(&pol_la, (int64_t)K_ * ni)); TRY(parena.alloc(&pol_gla, ni));
+    TRY(parena.alloc(&pol_sc, 2 * ni));
+    pol_ch = std::max<int64_t>(std::min<int64_t>(std::max(Nr, Na), (int64_t)1 << 21), 1);
+    TRY(parena.alloc(&pol_h1, POL_H * pol_ch)); TRY(parena.alloc(&pol_d1, POL_H * pol_ch));
+    TRY(parena.alloc(&pol_h2, POL_H * pol_ch)); TRY(parena.alloc(&pol_d2, POL_H * pol_ch));
+    TRY(parena.alloc(&pol_part, (pol_ch + WS_CHUNK - 1) / WS_CHUNK * (int64_t)(POL_H + 1) * POL_H));
+    pol_K = K_;
+    return COSMO_OK;
+  }
+
+  // rho_rect and dinv of step k from rho_in[k] (the policy's rho is positive
+  // and finite by construction)
+  void enqueue_step_params(int32_t k, cudaStream_t st) {
+    const int64_t om = (int64_t)k * h.m;
+    launch("rho_check", k_rho_copy_check<T, V>, grid_for(h.m, 256), 256, 0, st, P, 1, (const T*)(rho_in + om),
+           rho_rect + om, flags);
+    if (P.nrect)
+      launch("rho_rectify", k_rho_rectify<T, V>, grid_for((int64_t)P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, 1,
+             (const T*)(rho_in + om), rho_rect + om);
+    launch("precond", k_precond<T, V>, grid_for(h.n, 256), 256, 0, st, P, 1, (const double*)(sigma_dev + k),
+           (const T*)(rho_rect + om), dinv + (int64_t)k * h.n);
+  }
+
+  // l^0, the parameters of step 0, and xi^0 -> parameters of step 1
+  void enqueue_pol_prep(cudaStream_t st) {
+    launch("pol_fwd", k_pol_init<T, V>, grid_for(std::max<int64_t>(h.m, h.ninst), 256), 256, 0, st, P,
+           (const T*)pol_l0, pol_lr, rho_in, pol_la, alpha_in);
+    enqueue_step_params(0, st);
+    if (K >= 2) enqueue_pol(0, 0, nullptr, nullptr, st);
+  }
+
+  // xi^j of the state in `slot` (s^{j-1} = sprev, s~^j = stil; null at j = 0)
+  // -> l^{j+1}, the parameters of step j + 1
+  void enqueue_pol(int32_t j, int slot, const T* sprev, const T* stil, cudaStream_t st) {
+    const int64_t m = h.m, ni = h.ninst, Nr = (int64_t)(K - 1) * m, Na = (int64_t)(K - 1) * ni;
+    launch("pol_fwd", k_pol_inst<T, V, 256>, (int)ni, 256, 0, st, P, (const T*)st_x(slot), (const T*)st_s(slot),
+           (const T*)st_y(slot), sprev, stil, (const T*)pol_ta, (const T*)(pol_la + j * ni), pol_la + (j + 1) * ni,
+           alpha_in + (j + 1) * ni, pol_Xa + j * ni, Na, pol_Ja + j * ni, pol_sc);
+    if (m > 0)
+      launch("pol_fwd", k_pol_rows<T, V>, (int)((m + 127) / 128), 128, sizeof(T) * ws_nparams(POL_NFR, 1, POL_H), st,
+             P, (const T*)st_x(slot), (const T*)st_s(slot), (const T*)st_y(slot), sprev, stil, (const T*)pol_tr,
+             (const T*)(pol_lr + j * m), pol_lr + (j + 1) * m, rho_in + (j + 1) * m, pol_Xr + j * m, Nr,
+             pol_Jr + j * m, (const T*)pol_sc);
+    enqueue_step_params(j + 1, st);
+  }
+
+  cosmo_status pol_forward(int32_t K_, const double* sigma, const void* tr, const void* ta, const void* l0,
+                           const void* x0, const void* s0, const void* y0, void* xK, void* sK, void* yK, double* loss,
+                           int32_t tape, cudaStream_t st) override {
+    if (K_ < 1) return fail(COSMO_E_INVAL, "K must be >= 1");
+    if (!tr || !ta || !l0) return fail(COSMO_E_INVAL, "theta_rho, theta_alpha and l0 are required");
+    TRY(ensure_tape(K_));
+    TRY(pol_alloc(K_));
+    CU(cudaMemcpyAsync(pol_tr, tr, sizeof(T) * ws_nparams(POL_NFR, 1, POL_H), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(pol_ta, ta, sizeof(T) * ws_nparams(POL_NFA, 1, POL_H), cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(pol_l0, l0, sizeof(T) * 5, cudaMemcpyDeviceToDevice, st));
+    pol_mode = true;
+    const cosmo_status r = forward(K_, sigma, nullptr, nullptr, x0, s0, y0, xK, sK, yK, loss, tape, st);
+    pol_mode = false;
+    pol_valid = r == COSMO_OK && tape != 0;
+    return r;
+  }
+
+  cosmo_status pol_backward(const void* gx, const void* gs, const void* gy, const double* gl, void* gtr, void* gta,
+                            void* gl0, void* gx0, void* gs0, void* gy0, cudaStream_t st) override {
+    if (!pol_valid) return fail(COSMO_E_STATE, "policy backward needs a policy forward with record_tape=1");
+    if (!gtr || !gta || !gl0) return fail(COSMO_E_INVAL, "gtheta_rho, gtheta_alpha and gl0 are required");
+    TRY(backward(gx, gs, gy, gl, nullptr, nullptr, gx0, gs0, gy0, st));
+    const int64_t m = h.m, ni = h.ninst, Nr = (int64_t)(K - 1) * m, Na = (int64_t)(K - 1) * ni;
+    if (m > 0)
+      launch("pol_bwd", k_pol_scan<T, false>, (int)((m + 255) / 256), 256, 0, st, K, m, (const T*)grho_all,
+             (const T*)pol_lr, (const T*)pol_Jr, pol_Gr, pol_glr);
+    launch("pol_bwd", k_pol_scan<T, true>, (int)((ni + 255) / 256), 256, 0, st, K, ni, (const T*)galpha_all,
+           (const T*)pol_la, (const T*)pol_Ja, pol_Ga, pol_gla);
+    launch("pol_bwd", k_pol_l0<T, V>, 1, 256, 0, st, P, (const T*)pol_glr, (const T*)pol_gla, (T*)gl0);
+    CU(cudaGetLastError());
+    launched += 3; g_launches += 3;
+    if (Nr == 0) TRY((mlp_bwd<POL_NFR, 1, POL_H>(0, pol_Xr, 0, pol_tr, pol_Gr, 0, (T*)gtr, 0, pol_h1, pol_d1,
+                                                  pol_h2, pol_d2, pol_part, "pol_bwd", st)));
+    for (int64_t e0 = 0; e0 < Nr; e0 += pol_ch)
+      TRY((mlp_bwd<POL_NFR, 1, POL_H>(std::min(pol_ch, Nr - e0), pol_Xr + e0, Nr, pol_tr, pol_Gr + e0, Nr, (T*)gtr,
+                                      e0 > 0, pol_h1, pol_d1, pol_h2, pol_d2, pol_part, "pol_bwd", st)));
+    if (Na == 0) TRY((mlp_bwd<POL_NFA, 1, POL_H>(0, pol_Xa, 0, pol_ta, pol_Ga, 0, (T*)gta, 0, pol_h1, pol_d1,
+                                                  pol_h2, pol_d2, pol_part, "pol_bwd", st)));
+    for (int64_t e0 = 0; e0 < Na; e0 += pol_ch)
+      TRY((mlp_bwd<POL_NFA, 1, POL_H>(std::min(pol_ch, Na - e0), pol_Xa + e0, Na, pol_ta, pol_Ga + e0, Na, (T*)gta,
+                                      e0 > 0, pol_h1, pol_d1, pol_h2, pol_d2, pol_part, "pol_bwd", st)));
+    return COSMO_OK;
+  }
+
+  cosmo_status pol_schedule(void* rho, void* alpha, cudaStream_t st) override {
+    if (pol_K == 0 || K != pol_K) return fail(COSMO_E_STATE, "no policy forward");
+    if (rho) CU(cudaMemcpyAsync(rho, rho_in, sizeof(T) * K * h.m, cudaMemcpyDeviceToDevice, st));
+    if (alpha) CU(cudaMemcpyAsync(alpha, alpha_in, sizeof(T) * K * h.ninst, cudaMemcpyDeviceToDevice, st));
     return COSMO_OK;
   }
 
@@ -1294,7 +1436,7 @@ struct ImplT : Impl {
     o->n_psd = (int32_t)h.psd_p.size();
     o->max_psd_p = h.max_p;
     o->psd_u_entries = h.sum_p2;
-    o->device_bytes = arena.bytes + tarena.bytes + sarena.bytes + warena.bytes;
+    o->device_bytes = arena.bytes + tarena.bytes + sarena.bytes + warena.bytes + parena.bytes;
     o->last_K = K;
     o->tape_valid = tape_valid ? 1 : 0;
     o->kernels_launched = launched;
@@ -1463,6 +1605,35 @@ cosmo_status cosmo_solve(cosmo_batch* b, const cosmo_solve_params* prm, void* x,
   BATCH_GUARD(b);
   if (!prm) return fail(COSMO_E_INVAL, "prm is NULL");
   return b->impl->solve(*prm, x, s, y, iters, rbar_p, rbar_d, rho, (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_policy_sizes(int32_t* n_theta_rho, int32_t* n_theta_alpha) {
+  if (!n_theta_rho || !n_theta_alpha) return fail(COSMO_E_INVAL, "NULL output");
+  *n_theta_rho = ws_nparams(POL_NFR, 1, POL_H);
+  *n_theta_alpha = ws_nparams(POL_NFA, 1, POL_H);
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_policy_forward(cosmo_batch* b, int32_t K, const double* sigma_host, const void* theta_rho,
+                                  const void* theta_alpha, const void* l0, const void* x0, const void* s0,
+                                  const void* y0, void* xK, void* sK, void* yK, double* loss, int32_t record_tape,
+                                  void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->pol_forward(K, sigma_host, theta_rho, theta_alpha, l0, x0, s0, y0, xK, sK, yK, loss, record_tape,
+                              (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_policy_backward(cosmo_batch* b, const void* gx, const void* gs, const void* gy,
+                                   const double* gloss, void* gtheta_rho, void* gtheta_alpha, void* gl0, void* gx0,
+                                   void* gs0, void* gy0, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->pol_backward(gx, gs, gy, gloss, gtheta_rho, gtheta_alpha, gl0, gx0, gs0, gy0,
+                               (cudaStream_t)stream);
+}
+
+cosmo_status cosmo_policy_schedule(cosmo_batch* b, void* rho, void* alpha, void* stream) {
+  BATCH_GUARD(b);
+  return b->impl->pol_schedule(rho, alpha, (cudaStream_t)stream);
 }
 
 cosmo_status cosmo_ws_sizes(int32_t* n_theta_x, int32_t* n_theta_c) {

@@ -8,6 +8,7 @@ provides device memory and streams; every step of the method runs in the
 library's CUDA kernels.
 """
 import ctypes
+import math
 from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
 from dataclasses import dataclass
 from typing import Optional, Sequence
@@ -199,6 +200,44 @@ class CosmoBatch:
                                 _stream()))
         return x, s, y, iters, rbp, rbd, rho
 
+    def policy_forward(self, K, theta_rho, theta_alpha, l0, x0=None, s0=None, y0=None, sigma=None, tape=True,
+                       want_loss=True):
+        """Unroll K steps with the closed-loop policy of App. E choosing rho^k,
+        alpha^k (cosmo_policy_forward); returns (xK, sK, yK, loss)."""
+        K = int(K)
+        xK, sK, yK = self.zeros(self.n_total), self.zeros(self.m_total), self.zeros(self.m_total)
+        loss = self.zeros(self.ninst, dtype=torch.float64) if want_loss else None
+        sig = None
+        if sigma is not None:
+            sarr = np.broadcast_to(np.asarray(sigma, np.float64), (K,)).copy()
+            sig = sarr.ctypes.data_as(POINTER(c_double))
+        c = lambda t: None if t is None else t.contiguous()
+        check(lib().cosmo_policy_forward(self._h, K, sig, _tp(c(theta_rho)), _tp(c(theta_alpha)), _tp(c(l0)),
+                                         _tp(c(x0)), _tp(c(s0)), _tp(c(y0)), _tp(xK), _tp(sK), _tp(yK), _tp(loss),
+                                         1 if tape else 0, _stream()))
+        self.K = K
+        return xK, sK, yK, loss
+
+    def policy_backward(self, gxK=None, gsK=None, gyK=None, gloss=None, want_start=True):
+        """Gradients of the last policy forward: dict gtheta_rho, gtheta_alpha,
+        gl0 and (want_start) gx0, gs0, gy0."""
+        nr, na = policy_sizes()
+        out = {"gtheta_rho": self.zeros(nr), "gtheta_alpha": self.zeros(na), "gl0": self.zeros(5)}
+        for k, nn in (("gx0", self.n_total), ("gs0", self.m_total), ("gy0", self.m_total)):
+            out[k] = self.zeros(nn) if want_start else None
+        c = lambda t: None if t is None else t.contiguous()
+        check(lib().cosmo_policy_backward(self._h, _tp(c(gxK)), _tp(c(gsK)), _tp(c(gyK)), _tp(c(gloss)),
+                                          _tp(out["gtheta_rho"]), _tp(out["gtheta_alpha"]), _tp(out["gl0"]),
+                                          _tp(out["gx0"]), _tp(out["gs0"]), _tp(out["gy0"]), _stream()))
+        return out
+
+    def policy_schedule(self):
+        """(rho [K][m] before rectification, alpha [K][ninst]) of the last policy forward."""
+        K = self.K
+        rho, alpha = self.zeros(K, self.m_total), self.zeros(K, self.ninst)
+        check(lib().cosmo_policy_schedule(self._h, _tp(rho), _tp(alpha), _stream()))
+        return rho, alpha
+
     def ws_forward(self, theta_x, theta_c):
         """Warm start (x0, s0, y0) predicted by the App. E network
         (cosmo_ws_forward); theta_x, theta_c flat parameter tensors."""
@@ -286,7 +325,7 @@ class CosmoBatch:
     KERNEL_CLASSES = ("rho_check", "rho_rectify", "alpha_check", "precond", "rhs", "pcg", "post",
                       "soc_fwd", "psd_fwd", "residuals", "loss_seed", "bwd_gproj", "soc_bwd",
                       "psd_bwd", "bwd_relax", "pcg_adj", "bwd_solve", "rect_adjoint", "ws_feat", "ws_fwd",
-                      "ws_bwd", "ws_grad")
+                      "ws_bwd", "ws_grad", "pol_fwd", "pol_bwd")
 
     def profile(self, kernel=None, enable=True):
         """Time launches with CUDA events: kernel=None every class, a class
@@ -373,6 +412,69 @@ class AlphaBroadcast(torch.autograd.Function):
     @staticmethod
     def backward(ctx, galpha):
         return None, ctx.batch.alpha_reduce(galpha).to(ctx.adtype)
+
+
+def policy_sizes():
+    """(len(theta_rho), len(theta_alpha)) of the hyperparameter policy."""
+    a, b = c_int32(), c_int32()
+    check(lib().cosmo_policy_sizes(byref(a), byref(b)))
+    return a.value, b.value
+
+
+POLICY_RHO_MIN, POLICY_RHO_MAX = 1e-3, 1e3
+
+
+def policy_default_l0():
+    """Initial logits (zero rows, orthant and box rows, SOC rows, PSD rows,
+    alpha) of the defaults rho = (100, 0.1, 0.1, 0.1), alpha = 1.6."""
+    span = math.log(POLICY_RHO_MAX) - math.log(POLICY_RHO_MIN)
+    lg = lambda p: math.log(p / (1.0 - p))
+    return [lg((math.log(r) - math.log(POLICY_RHO_MIN)) / span) for r in (100.0, 0.1, 0.1, 0.1)] + [lg(0.8)]
+
+
+class PolicyUnroll(torch.autograd.Function):
+    """(theta_rho, theta_alpha, l0, x0, s0, y0) -> (x^K, s^K, y^K, loss[ninst])
+    of the closed-loop unroll."""
+
+    @staticmethod
+    def forward(ctx, batch, K, sigma, theta_rho, theta_alpha, l0, x0, s0, y0):
+        ctx.batch = batch
+        ctx.has_start = (x0 is not None, s0 is not None, y0 is not None)
+        return batch.policy_forward(K, theta_rho, theta_alpha, l0, x0, s0, y0, sigma=sigma, tape=True)
+
+    @staticmethod
+    def backward(ctx, gx, gs, gy, gloss):
+        g = ctx.batch.policy_backward(gx, gs, gy, gloss, want_start=any(ctx.has_start))
+        hx, hs, hy = ctx.has_start
+        return (None, None, None, g["gtheta_rho"], g["gtheta_alpha"], g["gl0"], g["gx0"] if hx else None,
+                g["gs0"] if hs else None, g["gy0"] if hy else None)
+
+
+class HyperPolicy(torch.nn.Module):
+    """The App. E hyperparameter policy as trainable parameters: two 32x32
+    ReLU MLPs (He-normal hidden layers, zero biases, zero output layer) and
+    the learnable initial logits, so that an untrained policy runs COSMO
+    with its default rho and alpha."""
+
+    H = 32
+
+    def __init__(self, dtype=torch.float32, device="cuda", generator=None):
+        super().__init__()
+        self.theta_rho = torch.nn.Parameter(self._init(7, dtype, generator).to(device))
+        self.theta_alpha = torch.nn.Parameter(self._init(5, dtype, generator).to(device))
+        self.l0 = torch.nn.Parameter(torch.tensor(policy_default_l0(), dtype=dtype, device=device))
+
+    @classmethod
+    def _init(cls, F, dtype, gen):
+        H = cls.H
+        f64 = torch.float64
+        w1 = torch.randn(F * H, generator=gen, dtype=f64) * (2.0 / F) ** 0.5
+        w2 = torch.randn(H * H, generator=gen, dtype=f64) * (2.0 / H) ** 0.5
+        return torch.cat([w1, torch.zeros(H, dtype=f64), w2, torch.zeros(H, dtype=f64),
+                          torch.zeros(H + 1, dtype=f64)]).to(dtype)
+
+    def forward(self, batch, K, sigma=None, x0=None, s0=None, y0=None):
+        return PolicyUnroll.apply(batch, K, sigma, self.theta_rho, self.theta_alpha, self.l0, x0, s0, y0)
 
 
 def ws_sizes():
