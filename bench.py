@@ -383,6 +383,72 @@ def run_warmstart(args):
     return 0
 
 
+def run_policy(args):
+    """The batched max-cut workload (256 instances, n ~ U{20..80}, K = 50,
+    mixed precision, one CUDA graph per forward / backward) trained through
+    the closed-loop hyperparameter policy of App. E instead of free per-step
+    log rho_k / alpha_k: forward (the policy evaluated on the device after
+    every step) + backward to the policy parameters.  CUDA events on the
+    current stream, L2 flushed between steps outside the events; the policy
+    kernels' own time from a direct-launch copy of the batch."""
+    import torch
+    from paper_2606_13825_b300 import CosmoBatch, HyperPolicy, lib
+    torch.cuda.set_device(0)
+    probs = workload_spec("maxcut", 0)["probs"]
+    K = K_UNROLL
+    res = {}
+    for graph in (1, 0):
+        b = CosmoBatch(probs, precision="mixed", use_graph=graph)
+        pol = HyperPolicy(dtype=torch.float32, device="cuda", generator=torch.Generator().manual_seed(7))
+        with torch.no_grad():   # a trained-looking output layer
+            g = torch.Generator(device="cuda").manual_seed(8)
+            pol.theta_rho[-33:].normal_(0, 0.05, generator=g)
+            pol.theta_alpha[-33:].normal_(0, 0.05, generator=g)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def step():
+            pol.zero_grad(set_to_none=True)
+            L = pol(b, K)[3].sum()
+            L.backward()
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        assert not b.status().any(), "device flags raised during warm-up"
+        if not graph:
+            b.profile()
+        st = torch.cuda.current_stream()
+        ms = []
+        n0 = lib().cosmo_kernel_launch_count()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            step()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[graph] = dict(ms=float(np.median(ms)), launches=(lib().cosmo_kernel_launch_count() - n0) // args.steps)
+        if not graph:
+            reads = {c: b.profile_read(c, reset=False) for c in b.KERNEL_CLASSES}
+            res["kernels"] = {c: round(v[0] / args.steps, 4) for c, v in reads.items() if v[1]}
+    t = res[1]["ms"]
+    kern = res.get("kernels", {})
+    line = {"metric": "closed-loop policy fwd+bwd instance-iters/sec (max-cut 256, K=50, mixed precision)",
+            "value": len(probs) * K / (t * 1e-3), "unit": "instance-iters/s", "higher_is_better": True,
+            "ms_per_step": t, "steps": args.steps, "warmup": args.warmup, "gpu_launches": int(res[1]["launches"]),
+            "direct_launch_ms_per_step": res[0]["ms"], "kernel_ms_per_step_direct": kern,
+            "policy_share_direct": (kern.get("pol_fwd", 0) + kern.get("pol_bwd", 0) + kern.get("ws_grad", 0))
+            / res[0]["ms"],
+            "config": {"workload": WORKLOAD.replace("learnable log rho_k / alpha_k",
+                                                    "App. E closed-loop policy (32x32 MLPs, learnable l0)"),
+                       "precision": "float iterates and policy, double reductions",
+                       "l2": "flushed between steps (256 MB write, outside the events)",
+                       "launch": "one CUDA graph per forward / backward"}}
+    print(json.dumps(line))
+    return 0
+
+
 # --------------------------------------------------------------------- ours --
 def psd_flops(probs):
     """Algorithmic flops of one PSD-projection launch: symmetric eigen-
@@ -403,12 +469,14 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run only W steps of the workload (the command profiled under ncu)")
     ap.add_argument("--workload", default="maxcut",
-                    choices=["maxcut", "lovasz", "socp", "covsteer", "linsys", "maxcut_solve", "warmstart"],
+                    choices=["maxcut", "lovasz", "socp", "covsteer", "linsys", "maxcut_solve", "warmstart",
+                             "maxcut_policy"],
                     help="maxcut: the batched differentiable max-cut step (the headline metric); "
                          "lovasz / socp / covsteer: the paper's other classes at their stated sizes; "
                          "linsys: the App. B reduced-system CG at n=5e4 (HBM roofline of SpMV/CG); "
                          "maxcut_solve: the vanilla COSMO baseline solving the max-cut batch to 1e-3; "
-                         "warmstart: the App. E warm-start network forward + reverse on the SOCP batch")
+                         "warmstart: the App. E warm-start network forward + reverse on the SOCP batch; "
+                         "maxcut_policy: the max-cut step trained through the App. E closed-loop policy")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -418,6 +486,8 @@ def main():
         return run_solve(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "maxcut_policy":
+        return run_policy(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

@@ -188,47 +188,96 @@ __global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, int64_t ldx, const T*
 constexpr int WS_CHUNK = 2048;   // elements per CTA of the weight-gradient reduction
 constexpr int WS_TILE = 32;      // elements staged in shared memory at a time
 
-// part[c][a * KB + b] = sum over elements n of chunk c (in order) of
-// A'[a][n] B[b][n] (rows lda, ldb apart), where A' is A [KA][N] with a row of ones appended when
-// `ones` is set (the bias gradient lands right after the weight gradient,
-// as in the parameter layout), B [KB][N]; KA + ones <= 65, KB <= 64.
-// 256 threads, each owning up to 17 (a, b) pairs.
-template <class T>
+// part[c][a * KB + b] = sum over elements n of chunk c of A'[a][n] B[b][n]
+// (rows lda, ldb apart), where A' is A [KA][N] with a row of ones appended
+// when `ones` is set (the bias gradient lands right after the weight
+// gradient, as in the parameter layout), B [KB][N]; KA + ones <= RI * TY,
+// KB <= RJ * TX (at most 80 x 64).  256 threads as G = 256 / (TY TX) groups
+// of TY x TX: thread (g, ty, tx) owns rows ty + TY i (i < RI) and columns
+// tx + TX j (j < RJ) and takes the elements t = g, g + G, ... of each staged
+// 32-element tile, summed in T per tile and then in double; the G group
+// partials are added in group order at the end (bitwise reproducible).  The
+// shape (RI, RJ, TY, TX) is picked per output size so that few threads idle.
+template <class T, int RI, int RJ, int TY, int TX>
 __global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__ A, int64_t lda, int KA, int ones,
                                                 const T* __restrict__ B, int64_t ldb, int KB,
                                                 double* __restrict__ part) {
-  __shared__ T sa[WS_H + 1][WS_TILE + 1], sb[WS_H][WS_TILE + 1];
+  constexpr int G = 256 / (TY * TX), NR = RI * TY, NC = RJ * TX;
+  static_assert(G * TY * TX == 256 && NR <= 80 && NC <= 64, "thread shape");
+  constexpr int RA = 81, RB = 65;   // odd row lengths: the transposing stores are conflict-free
+  __shared__ __align__(16) unsigned char atb_sm[sizeof(T) * WS_TILE * (RA + RB)];
+  T(*sa)[RA] = reinterpret_cast<T(*)[RA]>(atb_sm);
+  T(*sb)[RB] = reinterpret_cast<T(*)[RB]>(atb_sm + sizeof(T) * WS_TILE * RA);
   const int64_t n0 = (int64_t)blockIdx.x * WS_CHUNK, n1 = min(N, n0 + WS_CHUNK);
-  const int ka = KA + ones, npair = ka * KB;
-  double acc[17];
+  const int ka = KA + ones;
+  const int g = threadIdx.x / (TY * TX), l = threadIdx.x % (TY * TX), ty = l / TX, tx = l % TX;
+  double acc[RI][RJ];
 #pragma unroll
-  for (int q = 0; q < 17; ++q) acc[q] = 0.0;
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int j = 0; j < RJ; ++j) acc[i][j] = 0.0;
   for (int64_t t0 = n0; t0 < n1; t0 += WS_TILE) {
     const int tl = (int)min((int64_t)WS_TILE, n1 - t0);
     __syncthreads();
-    for (int k = threadIdx.x; k < (WS_H + 1) * WS_TILE; k += 256) {
+    for (int k = threadIdx.x; k < NR * WS_TILE; k += 256) {
       const int a = k / WS_TILE, t = k % WS_TILE;
-      if (a < ka) sa[a][t] = t < tl ? (a < KA ? A[a * lda + t0 + t] : T(1)) : T(0);
-      if (a < KB) sb[a][t] = t < tl ? B[a * ldb + t0 + t] : T(0);
+      sa[t][a] = (a < ka && t < tl) ? (a < KA ? A[a * lda + t0 + t] : T(1)) : T(0);
+    }
+    for (int k = threadIdx.x; k < NC * WS_TILE; k += 256) {
+      const int b = k / WS_TILE, t = k % WS_TILE;
+      sb[t][b] = (b < KB && t < tl) ? B[b * ldb + t0 + t] : T(0);
     }
     __syncthreads();
+    T s[RI][RJ];
 #pragma unroll
-    for (int q = 0; q < 17; ++q) {
-      const int pr = threadIdx.x + 256 * q;
-      if (pr < npair) {
-        const int a = pr / KB, b = pr % KB;
-        T s = T(0);
-#pragma unroll 8
-        for (int t = 0; t < WS_TILE; ++t) s += sa[a][t] * sb[b][t];
-        acc[q] += (double)s;
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) s[i][j] = T(0);
+#pragma unroll 4
+    for (int t = g; t < WS_TILE; t += G) {
+      T av[RI], bv[RJ];
+#pragma unroll
+      for (int i = 0; i < RI; ++i) av[i] = sa[t][ty + TY * i];
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) bv[j] = sb[t][tx + TX * j];
+#pragma unroll
+      for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < RJ; ++j) s[i][j] += av[i] * bv[j];
+    }
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) acc[i][j] += (double)s[i][j];
+  }
+  const int npair = ka * KB;
+  if (G > 1) {
+    // group partials through shared memory (the staging buffers), summed in group order
+    static_assert(G == 1 || (size_t)G * NR * NC * sizeof(double) <= sizeof(atb_sm), "reduction space");
+    double* red = reinterpret_cast<double*>(atb_sm);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) red[(g * NR + ty + TY * i) * NC + tx + TX * j] = acc[i][j];
+    __syncthreads();
+    for (int k = threadIdx.x; k < NR * NC; k += 256) {
+      const int a = k / NC, b = k % NC;
+      if (a < ka && b < KB) {
+        double v = 0.0;
+        for (int q = 0; q < G; ++q) v += red[(q * NR + a) * NC + b];
+        part[(int64_t)blockIdx.x * npair + a * KB + b] = v;
       }
     }
+    return;
   }
 #pragma unroll
-  for (int q = 0; q < 17; ++q) {
-    const int pr = threadIdx.x + 256 * q;
-    if (pr < npair) part[(int64_t)blockIdx.x * npair + pr] = acc[q];
-  }
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int j = 0; j < RJ; ++j) {
+      const int a = ty + TY * i, b = tx + TX * j;
+      if (a < ka && b < KB) part[(int64_t)blockIdx.x * npair + a * KB + b] = acc[i][j];
+    }
 }
 
 // out[k] (+)= sum over chunks c (in order) of part[c][k]

@@ -1203,6 +1203,27 @@ struct ImplT : Impl {
     return COSMO_OK;
   }
 
+  // the weight-sum kernel with the thread shape fitted to the (KA + 1) x KB output
+  void atb(int nch, int64_t N, const T* A, int64_t lda, int KA, const T* B, int64_t ldb, int KB, double* part,
+           cudaStream_t st) {
+    const int ka = KA + 1;
+#define COSMO_ATB(RI, RJ, TY, TX) \
+  launch("ws_grad", k_ws_atb<T, RI, RJ, TY, TX>, nch, 256, 0, st, N, A, lda, KA, 1, B, ldb, KB, part)
+    if (KB <= 2) {
+      if (ka <= 48) COSMO_ATB(3, 1, 16, 2);
+      else COSMO_ATB(5, 1, 16, 2);
+    } else if (KB <= 32) {
+      if (ka <= 8) COSMO_ATB(1, 2, 8, 16);
+      else if (ka <= 16) COSMO_ATB(1, 2, 16, 16);
+      else if (ka <= 48) COSMO_ATB(3, 2, 16, 16);
+      else COSMO_ATB(5, 2, 16, 16);
+    } else {
+      if (ka <= 16) COSMO_ATB(1, 4, 16, 16);
+      else COSMO_ATB(5, 4, 16, 16);
+    }
+#undef COSMO_ATB
+  }
+
   // gtheta (+)= the parameter gradient of an MLP (F inputs, H x H hidden,
   // O outputs) over elements e < N with features X[f * ldx + e] and output
   // cotangent G[o * ldg + e]; h1..d2 hold H x N reals, part the chunk partials
@@ -1224,7 +1245,7 @@ struct ImplT : Impl {
     int64_t off = 0;
     for (int l = 0; l < 3; ++l) {
       const int np = (KA[l] + 1) * KB[l];
-      launch("ws_grad", k_ws_atb<T>, nch, 256, 0, st, N, As[l], lda[l], KA[l], 1, Bs[l], ldb[l], KB[l], part);
+      atb(nch, N, As[l], lda[l], KA[l], Bs[l], ldb[l], KB[l], part, st);
       launch("ws_grad", k_ws_sum<T>, (np + 255) / 256, 256, 0, st, nch, np, (const double*)part, gtheta + off, acc);
       off += np;
     }
