@@ -185,10 +185,11 @@ __global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, int64_t ldx, const T*
   }
 }
 
-constexpr int WS_CHUNK = 2048;   // elements per CTA of the weight-gradient reduction
+constexpr int WS_MAXCH = 148 * 4;   // CTAs of the weight-gradient reduction: 4 per SM
 constexpr int WS_TILE = 32;      // elements staged in shared memory at a time
 
-// part[c][a * KB + b] = sum over elements n of chunk c of A'[a][n] B[b][n]
+// part[c][a * KB + b] = sum over elements n of chunk c (elements c * chunk
+// up to (c + 1) * chunk, chunk a multiple of 32) of A'[a][n] B[b][n]
 // (rows lda, ldb apart), where A' is A [KA][N] with a row of ones appended
 // when `ones` is set (the bias gradient lands right after the weight
 // gradient, as in the parameter layout), B [KB][N]; KA + ones <= RI * TY,
@@ -199,8 +200,8 @@ constexpr int WS_TILE = 32;      // elements staged in shared memory at a time
 // partials are added in group order at the end (bitwise reproducible).  The
 // shape (RI, RJ, TY, TX) is picked per output size so that few threads idle.
 template <class T, int RI, int RJ, int TY, int TX>
-__global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__ A, int64_t lda, int KA, int ones,
-                                                const T* __restrict__ B, int64_t ldb, int KB,
+__global__ void __launch_bounds__(256) k_ws_atb(int64_t N, int64_t chunk, const T* __restrict__ A, int64_t lda,
+                                                int KA, int ones, const T* __restrict__ B, int64_t ldb, int KB,
                                                 double* __restrict__ part) {
   constexpr int G = 256 / (TY * TX), NR = RI * TY, NC = RJ * TX;
   static_assert(G * TY * TX == 256 && NR <= 80 && NC <= 64, "thread shape");
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) k_ws_atb(int64_t N, const T* __restrict__
   __shared__ __align__(16) unsigned char atb_sm[sizeof(T) * WS_TILE * (RA + RB)];
   T(*sa)[RA] = reinterpret_cast<T(*)[RA]>(atb_sm);
   T(*sb)[RB] = reinterpret_cast<T(*)[RB]>(atb_sm + sizeof(T) * WS_TILE * RA);
-  const int64_t n0 = (int64_t)blockIdx.x * WS_CHUNK, n1 = min(N, n0 + WS_CHUNK);
+  const int64_t n0 = (int64_t)blockIdx.x * chunk, n1 = min(N, n0 + chunk);
   const int ka = KA + ones;
   const int g = threadIdx.x / (TY * TX), l = threadIdx.x % (TY * TX), ty = l / TX, tx = l % TX;
   double acc[RI][RJ];

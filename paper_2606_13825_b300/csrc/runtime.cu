@@ -1204,11 +1204,11 @@ struct ImplT : Impl {
   }
 
   // the weight-sum kernel with the thread shape fitted to the (KA + 1) x KB output
-  void atb(int nch, int64_t N, const T* A, int64_t lda, int KA, const T* B, int64_t ldb, int KB, double* part,
-           cudaStream_t st) {
+  void atb(int nch, int64_t chunk, int64_t N, const T* A, int64_t lda, int KA, const T* B, int64_t ldb, int KB,
+           double* part, cudaStream_t st) {
     const int ka = KA + 1;
 #define COSMO_ATB(RI, RJ, TY, TX) \
-  launch("ws_grad", k_ws_atb<T, RI, RJ, TY, TX>, nch, 256, 0, st, N, A, lda, KA, 1, B, ldb, KB, part)
+  launch("ws_grad", k_ws_atb<T, RI, RJ, TY, TX>, nch, 256, 0, st, N, chunk, A, lda, KA, 1, B, ldb, KB, part)
     if (KB <= 2) {
       if (ka <= 48) COSMO_ATB(3, 1, 16, 2);
       else COSMO_ATB(5, 1, 16, 2);
@@ -1236,7 +1236,9 @@ struct ImplT : Impl {
     }
     launch(tag, k_ws_bwd<T, F, O, H>, (int)((N + 127) / 128), 128, sizeof(T) * ws_nparams(F, O, H), st, N, ldx, X,
            theta, G, ldg, h1, d1, h2, d2);
-    const int nch = (int)((N + WS_CHUNK - 1) / WS_CHUNK);
+    // elements per CTA: a multiple of 32 giving at most WS_MAXCH CTAs
+    const int64_t chunk = ((N + WS_MAXCH - 1) / WS_MAXCH + WS_TILE - 1) / WS_TILE * WS_TILE;
+    const int nch = (int)((N + chunk - 1) / chunk);
     // [W1; b1] = [X; 1] D1', [W2; b2] = [H1; 1] D2', [W3; b3] = [H2; 1] G'
     const T* As[3] = {X, h1, h2};
     const T* Bs[3] = {d1, d2, G};
@@ -1245,7 +1247,7 @@ struct ImplT : Impl {
     int64_t off = 0;
     for (int l = 0; l < 3; ++l) {
       const int np = (KA[l] + 1) * KB[l];
-      atb(nch, N, As[l], lda[l], KA[l], Bs[l], ldb[l], KB[l], part, st);
+      atb(nch, chunk, N, As[l], lda[l], KA[l], Bs[l], ldb[l], KB[l], part, st);
       launch("ws_grad", k_ws_sum<T>, (np + 255) / 256, 256, 0, st, nch, np, (const double*)part, gtheta + off, acc);
       off += np;
     }
@@ -1268,7 +1270,7 @@ struct ImplT : Impl {
       TRY(warena.alloc(&ws_g, 2 * std::max<int64_t>(h.m, 1)));
       TRY(warena.alloc(&ws_h1, WS_H * nmax)); TRY(warena.alloc(&ws_d1, WS_H * nmax));
       TRY(warena.alloc(&ws_h2, WS_H * nmax)); TRY(warena.alloc(&ws_d2, WS_H * nmax));
-      TRY(warena.alloc(&ws_part, (nmax + WS_CHUNK - 1) / WS_CHUNK * (int64_t)(WS_H + 1) * WS_H));
+      TRY(warena.alloc(&ws_part, (int64_t)WS_MAXCH * (WS_H + 1) * WS_H));
       ws_bwd_ok = true;
     }
     TRY(ws_features(st));
@@ -1308,7 +1310,7 @@ struct ImplT : Impl {
     pol_ch = std::max<int64_t>(std::min<int64_t>(std::max(Nr, Na), (int64_t)1 << 21), 1);
     TRY(parena.alloc(&pol_h1, POL_H * pol_ch)); TRY(parena.alloc(&pol_d1, POL_H * pol_ch));
     TRY(parena.alloc(&pol_h2, POL_H * pol_ch)); TRY(parena.alloc(&pol_d2, POL_H * pol_ch));
-    TRY(parena.alloc(&pol_part, (pol_ch + WS_CHUNK - 1) / WS_CHUNK * (int64_t)(POL_H + 1) * POL_H));
+    TRY(parena.alloc(&pol_part, (int64_t)WS_MAXCH * (POL_H + 1) * POL_H));
     pol_K = K_;
     return COSMO_OK;
   }

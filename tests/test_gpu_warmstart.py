@@ -2,9 +2,9 @@
 cosmo_ws_backward) against the oracle, instance by instance.
 
 The batch holds every cone kind, an all-zero row of A, max-cut instances
-with PSD blocks and one SOCP with m = 2600 rows, so the constraint MLP runs
-over more than one 2048-element reduction chunk with a ragged tail and both
-MLPs over several 128-thread tiles.  Parameters are random in every layer
+with PSD blocks and one SOCP with m = 2600 rows, so both MLPs run over
+several 128-thread tiles and the weight sums over many 32-element reduction
+chunks with a ragged tail.  Parameters are random in every layer
 (an untrained network has a zero output layer, which would hide layers 1
 and 2 from the test).
 
