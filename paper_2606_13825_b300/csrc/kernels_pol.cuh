@@ -31,8 +31,12 @@ constexpr double POL_LOG_RHO_MIN = -6.907755278982137;   // log(1e-3)
 constexpr double POL_SPAN = 13.815510557964274;          // log(1e3) - log(1e-3)
 constexpr double POL_EPS = 1e-12;
 
-__host__ __device__ inline double pol_sig(double z) { return 1.0 / (1.0 + exp(-z)); }
-__device__ inline double pol_rho(double l) { return exp(POL_SPAN * pol_sig(l) + POL_LOG_RHO_MIN); }
+// the squash in the iterate type (FP64 throughput is a small fraction of
+// FP32 on this part; the mixed-precision path keeps FP32 here)
+template <class T>
+__device__ inline T pol_sig(T z) { return T(1) / (T(1) + exp(-z)); }
+template <class T>
+__device__ inline T pol_rho(T l) { return exp(T(POL_SPAN) * pol_sig(l) + T(POL_LOG_RHO_MIN)); }
 // slot of l0 for a cone kind: zero 0, orthant and box 1, soc 2, psd 3
 __device__ inline int pol_slot(int kind) { return kind == 0 ? 0 : kind <= 2 ? 1 : kind == 3 ? 2 : 3; }
 
@@ -77,17 +81,13 @@ __global__ void k_pol_init(Prob<T, V> P, const T* __restrict__ l0, T* __restrict
   if (e < P.m_total) {
     const T l = l0[pol_slot(P.row_kind[e])];
     lr[e] = l;
-    rho[e] = (T)pol_rho((double)l);
+    rho[e] = pol_rho(l);
   }
   if (e < P.ninst) {
     la[e] = l0[4];
-    alpha[e] = (T)(2.0 * pol_sig((double)l0[4]));
+    alpha[e] = T(2) * pol_sig(l0[4]);
   }
 }
-
-struct PolStep {
-  int64_t ldr, lda;   // leading dimensions of the row and instance feature arrays
-};
 
 // per instance (one CTA): the infinity norms of the features, the instance
 // scalars 1/scale_p and log(||rbar_d|| + eps) for the row kernel, and the
@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(NT) k_pol_inst(Prob<T, V> P, const T* __restri
     if (lane == 0) sm[k][w] = v[k];
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (w != 0) return;
+  // warp 0: every lane forms the same norms and features; lane j then owns
+  // hidden unit j of both layers of the alpha MLP (32 units)
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
     double mx = 0.0;
@@ -144,17 +146,38 @@ __global__ void __launch_bounds__(NT) k_pol_inst(Prob<T, V> P, const T* __restri
   scp = scp > 0.0 ? scp : 1.0;
   scd = scd > 0.0 ? scd : 1.0;
   const double lgd = log(v[4] / scd + POL_EPS);
-  sc[inst] = (T)(1.0 / scp);
-  sc[P.ninst + inst] = (T)lgd;
-  T xi[POL_NFA] = {la[inst], (T)log(v[0] / scp + POL_EPS), (T)lgd, (T)log(v[8] + POL_EPS), (T)log(v[9] + POL_EPS)};
+  const T xi[POL_NFA] = {la[inst], (T)log(v[0] / scp + POL_EPS), (T)lgd, (T)log(v[8] + POL_EPS),
+                         (T)log(v[9] + POL_EPS)};
+  if (lane == 0) {
+    sc[inst] = (T)(1.0 / scp);
+    sc[P.ninst + inst] = (T)lgd;
+  }
+  if (lane < POL_NFA) Xa[lane * lda + inst] = xi[lane];
+  const T *W1 = theta, *b1 = W1 + POL_NFA * POL_H, *W2 = b1 + POL_H, *b2 = W2 + POL_H * POL_H, *W3 = b2 + POL_H,
+          *b3 = W3 + POL_H;
+  T z1 = b1[lane];
 #pragma unroll
-  for (int f = 0; f < POL_NFA; ++f) Xa[f * lda + inst] = xi[f];
-  T out, J;
-  pol_mlp<T, POL_NFA>(xi, theta, out, J);   // weights read from global (one thread)
-  const T l = la[inst] + out;
-  la_next[inst] = l;
-  alpha_next[inst] = (T)(2.0 * pol_sig((double)l));
-  Ja[inst] = J;
+  for (int f = 0; f < POL_NFA; ++f) z1 += W1[f * POL_H + lane] * xi[f];
+  const T h1 = z1 > T(0) ? z1 : T(0), t1 = z1 > T(0) ? W1[lane] : T(0);
+  T z2 = b2[lane], dz2 = T(0);
+#pragma unroll 8
+  for (int i = 0; i < POL_H; ++i) {
+    const T hi = __shfl_sync(0xffffffffu, h1, i), ti = __shfl_sync(0xffffffffu, t1, i);
+    z2 += W2[i * POL_H + lane] * hi;
+    dz2 += W2[i * POL_H + lane] * ti;
+  }
+  T o = z2 > T(0) ? W3[lane] * z2 : T(0), J = z2 > T(0) ? W3[lane] * dz2 : T(0);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    o += __shfl_xor_sync(0xffffffffu, o, d);
+    J += __shfl_xor_sync(0xffffffffu, J, d);
+  }
+  if (lane == 0) {
+    const T l = la[inst] + b3[0] + o;
+    la_next[inst] = l;
+    alpha_next[inst] = T(2) * pol_sig(l);
+    Ja[inst] = J;
+  }
 }
 
 // per row (thread per row, 128 per CTA): xi_rho^k, the rho MLP, l^{k+1},
@@ -182,7 +205,7 @@ __global__ void __launch_bounds__(128) k_pol_rows(Prob<T, V> P, const T* __restr
   pol_mlp<T, POL_NFR>(xi, w, out, J);
   const T l = lr[r] + out;
   lr_next[r] = l;
-  rho_next[r] = (T)pol_rho((double)l);
+  rho_next[r] = pol_rho(l);
   Jr[r] = J;
 }
 
@@ -191,9 +214,11 @@ __global__ void __launch_bounds__(128) k_pol_rows(Prob<T, V> P, const T* __restr
 //   G[k][e] = g (the cotangent of the MLP output at step k, k < K - 1),
 //   g <- g (1 + J[k][e]) + gp[k][e] dp/dl (l^k[e])
 // where p = rho (squashed) or alpha; gl0[e] = g at the end
+// (p = the stored rho or alpha of each step: drho/dl = rho span sig (1 -
+// sig), dalpha/dl = 2 sig (1 - sig); g carried in double)
 template <class T, bool ALPHA>
-__global__ void k_pol_scan(int32_t K, int64_t N, const T* __restrict__ gp, const T* __restrict__ l,
-                           const T* __restrict__ J, T* __restrict__ G, T* __restrict__ gl0) {
+__global__ void k_pol_scan(int32_t K, int64_t N, const T* __restrict__ gp, const T* __restrict__ p,
+                           const T* __restrict__ l, const T* __restrict__ J, T* __restrict__ G, T* __restrict__ gl0) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N) return;
   double g = 0.0;
@@ -203,9 +228,9 @@ __global__ void k_pol_scan(int32_t K, int64_t N, const T* __restrict__ gp, const
       G[o] = (T)g;
       g *= 1.0 + (double)J[o];
     }
-    const double sg = pol_sig((double)l[o]);
-    const double dp = ALPHA ? 2.0 * sg * (1.0 - sg) : exp(POL_SPAN * sg + POL_LOG_RHO_MIN) * POL_SPAN * sg * (1.0 - sg);
-    g += (double)gp[o] * dp;
+    const T sg = pol_sig(l[o]);
+    const T dp = (ALPHA ? T(2) : p[o] * T(POL_SPAN)) * sg * (T(1) - sg);
+    g += (double)gp[o] * (double)dp;
   }
   gl0[e] = (T)g;
 }

@@ -281,14 +281,25 @@ __global__ void __launch_bounds__(256) k_ws_atb(int64_t N, int64_t chunk, const 
     }
 }
 
-// out[k] (+)= sum over chunks c (in order) of part[c][k]
+// out[k] (+)= sum over chunks c of part[c][k]: 32 outputs per CTA of 256
+// threads, warp q adding the chunks c = q, q + 8, ... in order, then the
+// eight warp sums added in warp order (a fixed order: bitwise reproducible)
 template <class T>
-__global__ void k_ws_sum(int nchunk, int npair, const double* __restrict__ part, T* __restrict__ out, int accumulate) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= npair) return;
-  double s = accumulate ? (double)out[k] : 0.0;
-  for (int c = 0; c < nchunk; ++c) s += part[(int64_t)c * npair + k];
-  out[k] = (T)s;
+__global__ void __launch_bounds__(256) k_ws_sum(int nchunk, int npair, const double* __restrict__ part,
+                                                T* __restrict__ out, int accumulate) {
+  __shared__ double sm[8][32];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5, k = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (k < npair)
+    for (int c = q; c < nchunk; c += 8) s += part[(int64_t)c * npair + k];
+  sm[q][lane] = s;
+  __syncthreads();
+  if (q == 0 && k < npair) {
+    double v = accumulate ? (double)out[k] : 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += sm[w][lane];
+    out[k] = (T)v;
+  }
 }
 
 }  // namespace cosmo

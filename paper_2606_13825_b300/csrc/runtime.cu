@@ -1248,7 +1248,7 @@ struct ImplT : Impl {
     for (int l = 0; l < 3; ++l) {
       const int np = (KA[l] + 1) * KB[l];
       atb(nch, chunk, N, As[l], lda[l], KA[l], Bs[l], ldb[l], KB[l], part, st);
-      launch("ws_grad", k_ws_sum<T>, (np + 255) / 256, 256, 0, st, nch, np, (const double*)part, gtheta + off, acc);
+      launch("ws_grad", k_ws_sum<T>, (np + 31) / 32, 256, 0, st, nch, np, (const double*)part, gtheta + off, acc);
       off += np;
     }
     CU(cudaGetLastError());
@@ -1376,9 +1376,9 @@ struct ImplT : Impl {
     const int64_t m = h.m, ni = h.ninst, Nr = (int64_t)(K - 1) * m, Na = (int64_t)(K - 1) * ni;
     if (m > 0)
       launch("pol_bwd", k_pol_scan<T, false>, (int)((m + 255) / 256), 256, 0, st, K, m, (const T*)grho_all,
-             (const T*)pol_lr, (const T*)pol_Jr, pol_Gr, pol_glr);
+             (const T*)rho_in, (const T*)pol_lr, (const T*)pol_Jr, pol_Gr, pol_glr);
     launch("pol_bwd", k_pol_scan<T, true>, (int)((ni + 255) / 256), 256, 0, st, K, ni, (const T*)galpha_all,
-           (const T*)pol_la, (const T*)pol_Ja, pol_Ga, pol_gla);
+           (const T*)alpha_in, (const T*)pol_la, (const T*)pol_Ja, pol_Ga, pol_gla);
     launch("pol_bwd", k_pol_l0<T, V>, 1, 256, 0, st, P, (const T*)pol_glr, (const T*)pol_gla, (T*)gl0);
     CU(cudaGetLastError());
     launched += 3; g_launches += 3;
