@@ -75,6 +75,24 @@ def workload_spec(name, rank=0):
                          "P=M'M+1e-3 I (M 500x5000 density 1e-3), 200 SOCs d ~ U{3..50} + orthant, planted "
                          "solution; K=100; BF16 A values (P FP32), FP32 iterates, CG tol 1e-6; "
                          "loss ||r_p^K||^2+||r_d^K||^2")
+    if name in ("lyapunov", "kalman", "mpc"):
+        from synth import lyapunov_problem, robust_kalman_problem, robust_mpc_problem
+        if name == "lyapunov":
+            probs = [lyapunov_problem(6000 + rank * 64 + j, n=40) for j in range(64)]
+            desc = "minimum-trace Lyapunov LMIs: 64 instances (seeds 6000+j), n=40 (svec 820, two 40x40 PSD blocks)"
+        elif name == "kalman":
+            probs = [robust_kalman_problem(7000 + rank * 256 + j, N=100) for j in range(256)]
+            desc = "robust Kalman smoothers: 256 instances (seeds 7000+j), N=100 (n=1004, m=1000, 100 SOC(3))"
+        else:
+            probs = [robust_mpc_problem(8000 + rank * 512 + j, N=50) for j in range(512)]
+            desc = "robust MPC: 512 instances (seeds 8000+j), N=50 (n=203, m=505, 51 SOCs)"
+        # 64 Lyapunov instances fill 64 of 148 SMs with one CG CTA each: a
+        # cluster of 2 per instance measured 1051 -> 823 ms per step; the
+        # SOCP classes (256 / 512 instances, short rows) are faster unclustered
+        opts = {"use_graph": 1, "cg_cluster": 2 if name == "lyapunov" else 1}
+        return dict(probs=probs, K=50, opts=opts, value_type="f32", learn_start=False,
+                    metric=f"unrolled fwd+bwd instance-iters/sec ({name}, batched mixed precision)",
+                    desc=desc + "; K=50; learnable log rho_k / alpha_k; loss ||r_p^K||^2+||r_d^K||^2")
     if name == "covsteer":
         probs = [covsteer_problem(5000 + rank * 512 + j) for j in range(512)]
         return dict(probs=probs, K=40, opts={"use_graph": 1}, value_type="f32", learn_start=True,
@@ -475,10 +493,11 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run only W steps of the workload (the command profiled under ncu)")
     ap.add_argument("--workload", default="maxcut",
-                    choices=["maxcut", "lovasz", "socp", "covsteer", "linsys", "maxcut_solve", "warmstart",
-                             "maxcut_policy"],
+                    choices=["maxcut", "lovasz", "socp", "covsteer", "lyapunov", "kalman", "mpc", "linsys",
+                             "maxcut_solve", "warmstart", "maxcut_policy"],
                     help="maxcut: the batched differentiable max-cut step (the headline metric); "
-                         "lovasz / socp / covsteer: the paper's other classes at their stated sizes; "
+                         "lovasz / socp / covsteer / lyapunov / kalman / mpc: the paper's other classes at "
+                         "their stated sizes; "
                          "linsys: the App. B reduced-system CG at n=5e4 (HBM roofline of SpMV/CG); "
                          "maxcut_solve: the vanilla COSMO baseline solving the max-cut batch to 1e-3; "
                          "warmstart: the App. E warm-start network forward + reverse on the SOCP batch; "

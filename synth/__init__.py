@@ -17,11 +17,14 @@ from .generators import (erdos_renyi, maxcut_problem, lovasz_problem,
                          socp_problem, covsteer_problem, linsys_instance,
                          clustered_symmetric, random_graph_batch,
                          cycle_graph, complete_graph, empty_graph)
+from .classes import (lyapunov_problem, robust_kalman_problem, robust_mpc_problem,
+                      hurwitz_matrix, kalman_matrices, mpc_tightening)
 
 __all__ = [
     "ConicProblem", "ZERO", "NONNEG", "BOX", "SOC", "PSD", "CONE_NAMES",
     "svec_index", "svec_len", "erdos_renyi", "maxcut_problem",
     "lovasz_problem", "socp_problem", "covsteer_problem", "linsys_instance",
     "clustered_symmetric", "random_graph_batch", "cycle_graph",
-    "complete_graph", "empty_graph",
+    "complete_graph", "empty_graph", "lyapunov_problem", "robust_kalman_problem",
+    "robust_mpc_problem", "hurwitz_matrix", "kalman_matrices", "mpc_tightening",
 ]
