@@ -149,9 +149,11 @@ typedef struct {
                                (re-orthogonalised by one Newton-Schulz step) */
   int32_t dk_tensor_cores;  /* 1: MIXED-precision DK backward of blocks of order <= 80 on
                                the tensor cores (tcgen05, split-TF32 products); 0: CUDA cores */
-  int32_t cg_cluster;       /* CTAs per instance in the CG: 0 automatic (2 or 4 for fewer
-                               than 74 / 37 instances with >= 8192 rows + columns, else 1);
-                               1, 2 or 4 forced */
+  int32_t cg_cluster;       /* CTAs per instance in the CG: 0 automatic (1 with the
+                               instance's vectors in shared memory when 5 n_i + m_i reals
+                               fit in 200 KB; else 2 or 4 for fewer than 74 / 37 instances
+                               with >= 8192 rows + columns, else 1); 1 (shared-memory
+                               vectors when they fit), 2 or 4 forced */
   int32_t loss_kind;        /* per-instance loss of cosmo_forward / cotangent of
                                cosmo_backward: 0 ||r_p^K||^2 + ||r_d^K||^2; 1 the log-residual
                                loss of Sec. 4, sum_{k=1..K} log(||r_d^k||^2/||r_d^0||^2 +

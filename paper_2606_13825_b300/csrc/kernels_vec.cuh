@@ -350,6 +350,154 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
   }
 }
 
+// cta_csr_rows_c with the gathered vector in shared memory: entry c of the
+// instance-local vector xl is column (c + base) of the batch
+template <class T, class V, class F>
+__device__ __forceinline__ void cta_csr_rows_local(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                   const V* __restrict__ val, const T* xl, int64_t base, int64_t r0,
+                                                   int64_t r1, F f) {
+  constexpr int U = 8;
+  const int64_t step = blockDim.x;
+  for (int64_t rb = r0 + threadIdx.x; rb < r1; rb += 2 * step) {
+    int64_t e[2], eend[2];
+    T acc[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t r = rb + u * step;
+      const bool ok = r < r1;
+      e[u] = ok ? rp[r] : 0;
+      eend[u] = ok ? rp[r + 1] : 0;
+      acc[u] = T(0);
+    }
+    while (e[0] < eend[0] || e[1] < eend[1]) {
+      int32_t c[2][U];
+      T v[2][U];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t idx = e[u] + k;
+          const bool ok = idx < eend[u];
+          c[u][k] = ok ? (int32_t)(ci[idx] - base) : -1;
+          v[u][k] = ok ? (T)ldv(val, idx) : T(0);
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+          if (c[u][k] >= 0) acc[u] += v[u][k] * xl[c[u][k]];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) e[u] = min(e[u] + U, eend[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t r = rb + u * step;
+      if (r < r1) f(r, acc[u]);
+    }
+  }
+}
+
+// k_pcg (one CTA per instance) with the instance's vectors x, r, p, u, the
+// Jacobi diagonal and t = rho o (A v) in shared memory: the matrix streams
+// from L2 / HBM while every gather and update stays on chip.  The same
+// arithmetic in the same order as k_pcg, so the iterates are identical.
+// Dynamic shared memory: (5 n_i + m_i) reals for the largest instance.
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_smem(Prob<T, V> P, CgArgs<T> a) {
+  __shared__ double sm[3 * (NT / 32)];
+  extern __shared__ __align__(16) unsigned char cg_sm[];
+  const int32_t inst = P.cg_sched ? P.cg_sched[blockIdx.x] : P.inst_sched[blockIdx.x];
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  if (c1 == c0) return;
+  const int64_t nl = c1 - c0;
+  T* sx = reinterpret_cast<T*>(cg_sm);
+  T* sr = sx + nl;
+  T* sp = sr + nl;
+  T* su = sp + nl;
+  T* sd = su + nl;
+  T* st = sd + nl;
+  const T sig = (T)a.sigma;
+  const T* __restrict__ rho = a.rho;
+  // u = (P + sigma I + A' D(rho) A) v on the instance, v and u in shared memory
+  auto matvec = [&](const T* v, T* u) {
+    cta_csr_rows_local<T, V>(P.A_rp, P.A_ci, P.A_v, v, c0, r0, r1,
+                             [&](int64_t r, T acc) { st[r - r0] = rho[r] * acc; });
+    __syncthreads();
+    if (P.P_rp) {
+      cta_csr_rows_local<T, T>(P.P_rp, P.P_ci, P.P_v, v, c0, c0, c1,
+                               [&](int64_t j, T acc) { u[j - c0] = sig * v[j - c0] + acc; });
+      cta_csr_rows_local<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)st, r0, c0, c1,
+                               [&](int64_t j, T acc) { u[j - c0] += acc; });
+    } else {
+      cta_csr_rows_local<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)st, r0, c0, c1,
+                               [&](int64_t j, T acc) { u[j - c0] = sig * v[j - c0] + acc; });
+    }
+    __syncthreads();
+  };
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    sd[j - c0] = a.dinv[j];
+    sx[j - c0] = a.zero_start ? T(0) : (a.x0 ? a.x0[j] : a.x[j]);
+  }
+  __syncthreads();
+  if (!a.zero_start) matvec(sx, su);
+  double s3[3] = {0.0, 0.0, 0.0};   // rz, rr, bb
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    const int64_t l = j - c0;
+    const T bj = a.rhs[j];
+    const T rj = a.zero_start ? bj : bj - su[l];
+    const T zj = sd[l] * rj;
+    sr[l] = rj;
+    sp[l] = zj;
+    s3[0] += (double)rj * (double)zj;
+    s3[1] += (double)rj * (double)rj;
+    s3[2] += (double)bj * (double)bj;
+  }
+  block_sum<3>(s3, sm);
+  double rz = s3[0], rr = s3[1];
+  const double thr = a.tol * a.tol * s3[2];
+  int32_t it = 0;
+  if (s3[2] == 0.0) {
+    for (int64_t l = threadIdx.x; l < nl; l += NT) sx[l] = T(0);
+    rr = 0.0;
+  }
+  while (rr > thr && it < a.maxit) {
+    matvec(sp, su);
+    double s1[1] = {0.0};
+    for (int64_t l = threadIdx.x; l < nl; l += NT) s1[0] += (double)sp[l] * (double)su[l];
+    block_sum<1>(s1, sm);
+    if (!(s1[0] > 0.0)) break;  // breakdown (p = 0 or non-finite): stop, flagged below
+    const T al = (T)(rz / s1[0]);
+    double s2[2] = {0.0, 0.0};
+    for (int64_t l = threadIdx.x; l < nl; l += NT) {
+      sx[l] += al * sp[l];
+      const T rj = sr[l] - al * su[l];
+      sr[l] = rj;
+      const T zj = sd[l] * rj;
+      s2[0] += (double)rj * (double)zj;
+      s2[1] += (double)rj * (double)rj;
+    }
+    block_sum<2>(s2, sm);
+    const T be = (T)(s2[0] / rz);
+    rz = s2[0];
+    rr = s2[1];
+    for (int64_t l = threadIdx.x; l < nl; l += NT) sp[l] = sd[l] * sr[l] + be * sp[l];
+    __syncthreads();
+    ++it;
+  }
+  __syncthreads();
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) a.x[j] = sx[j - c0];
+  if (threadIdx.x == 0) {
+    if (rr > thr) atomicOr(&a.flags[inst], a.flag_bit);
+    if (!(rr == rr)) atomicOr(&a.flags[inst], F_NONFINITE);
+    if (a.iters) a.iters[inst] = it;
+    if (a.stats) {
+      atomicAdd(&a.stats[0], (unsigned long long)it);
+      atomicAdd(&a.stats[1], 1ull);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // a5, a6 (separable cones), a8: s~ = b - A x~, relaxation, projection of
 // v = alpha s~ + (1-alpha) s + y/rho on zero / orthant / box rows, dual update;

@@ -211,6 +211,7 @@ struct HostPlan {
   std::vector<uint8_t> diag_inst;
   std::vector<int32_t> cg_sched;
   int32_t cg_nt = 256;      // threads of a CG CTA
+  int64_t cg_vec = 0;       // max over CG instances of 5 n_i + m_i (reals of the shared-memory CG)
   int32_t cg_cs = 1;        // CTAs per instance (thread-block cluster) in the CG
   int64_t sum_p = 0, sum_p2 = 0;
   int32_t max_p = 0;
@@ -328,6 +329,7 @@ static void build_plan(const cosmo_problem* pr, HostPlan& h) {
     if (!h.diag_inst[i]) {
       h.cg_sched.push_back(i);
       cg_max = std::max(cg_max, (h.row_off[i + 1] - h.row_off[i]) + (h.col_off[i + 1] - h.col_off[i]));
+      h.cg_vec = std::max(h.cg_vec, 5 * (h.col_off[i + 1] - h.col_off[i]) + (h.row_off[i + 1] - h.row_off[i]));
     }
   // large instances take 512-thread CG CTAs (more rows in flight per SpMV);
   // many small ones 256 (two CTAs resident per SM)
@@ -552,6 +554,9 @@ struct ImplT : Impl {
     CU(cudaMemset(stats, 0, sizeof(unsigned long long) * 6));
     TRY(arena.alloc(&xi, n)); TRY(arena.alloc(&cg_r, n)); TRY(arena.alloc(&cg_p, n));
     TRY(arena.alloc(&cg_u, n)); TRY(arena.alloc(&cg_t, m));
+    // the shared-memory CG may take up to CG_SMEM_MAX bytes (set outside any graph capture)
+    CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     for (int i = 0; i < 2; ++i) {
       TRY(arena.alloc(&xb[i], n)); TRY(arena.alloc(&sb[i], m)); TRY(arena.alloc(&yb[i], m));
     }
@@ -704,8 +709,21 @@ struct ImplT : Impl {
   }
 
   // CG launch: one CTA or one cluster of cg_cs CTAs per instance
+  // one CTA per instance with the vectors in shared memory when they fit
+  static constexpr size_t CG_SMEM_MAX = 200 * 1024;
+  size_t cg_smem_bytes() const { return (size_t)h.cg_vec * sizeof(T); }
+
+  // automatic choice: the shared-memory kernel whenever the vectors fit
+  // (measured on the 64-instance SOCP batch: 1326 ms per step against 1528
+  // with clusters of 2 over global vectors), clusters for larger instances
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
-    const int cs = opt.cg_cluster > 0 ? opt.cg_cluster : h.cg_cs;
+    const size_t smb = cg_smem_bytes();
+    const int cs = opt.cg_cluster > 0 ? opt.cg_cluster : (smb <= CG_SMEM_MAX ? 1 : h.cg_cs);
+    if (cs == 1 && smb <= CG_SMEM_MAX) {
+      if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
+      else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
+      return;
+    }
     if (cs == 4)
       launch_cluster(tag, k_pcg<T, V, 512, 4>, P.n_cg * 4, 512, 0, st, 4, P, ca);
     else if (cs == 2)
