@@ -498,6 +498,157 @@ __global__ void __launch_bounds__(NT) k_pcg_smem(Prob<T, V> P, CgArgs<T> a) {
   }
 }
 
+// A CSR block of one instance staged in shared memory with local indices
+template <class V>
+struct SmemCsr {
+  const int32_t* rp;   // [rows + 1], from 0
+  const int32_t* ci;   // local column indices
+  const V* v;
+};
+
+// bytes of the staged copy of rows [r0, r1) of a batch CSR matrix (each array 16-byte aligned)
+__host__ __device__ inline size_t smem_csr_bytes(int64_t rows, int64_t nnz, size_t vsize) {
+  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  return al(sizeof(int32_t) * (rows + 1)) + al(sizeof(int32_t) * nnz) + al(vsize * nnz);
+}
+
+// copy rows [r0, r1) of (rp, ci, val) to shared memory at *cur, columns shifted by -cbase
+template <class V>
+__device__ inline SmemCsr<V> stage_csr(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                       const V* __restrict__ val, int64_t r0, int64_t r1, int64_t cbase,
+                                       unsigned char*& cur) {
+  auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const int64_t e0 = rp[r0], nnz = rp[r1] - e0, rows = r1 - r0;
+  int32_t* srp = reinterpret_cast<int32_t*>(cur);
+  cur += al(sizeof(int32_t) * (rows + 1));
+  int32_t* sci = reinterpret_cast<int32_t*>(cur);
+  cur += al(sizeof(int32_t) * nnz);
+  V* sv = reinterpret_cast<V*>(cur);
+  cur += al(sizeof(V) * nnz);
+  for (int64_t r = threadIdx.x; r <= rows; r += blockDim.x) srp[r] = (int32_t)(rp[r0 + r] - e0);
+  for (int64_t e = threadIdx.x; e < nnz; e += blockDim.x) {
+    sci[e] = (int32_t)(ci[e0 + e] - cbase);
+    sv[e] = val[e0 + e];
+  }
+  return SmemCsr<V>{srp, sci, sv};
+}
+
+// plain (shared-memory) loads of a staged value: ldv's non-coherent global
+// loads must not be used on shared memory
+__device__ __forceinline__ float smv(const float* p, int32_t i) { return p[i]; }
+__device__ __forceinline__ double smv(const double* p, int32_t i) { return p[i]; }
+__device__ __forceinline__ float smv(const __nv_bfloat16* p, int32_t i) { return __bfloat162float(p[i]); }
+
+// out = f(row, sum over the row's entries in order of val * xl[col]), thread per row
+template <class T, class V, class F>
+__device__ __forceinline__ void smem_csr_rows(const SmemCsr<V>& M, const T* xl, int64_t rows, F f) {
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+    T acc = T(0);
+    for (int32_t e = M.rp[r]; e < M.rp[r + 1]; ++e) acc += (T)smv(M.v, e) * xl[M.ci[e]];
+    f(r, acc);
+  }
+}
+
+// k_pcg_smem with the instance's A, A' and P staged in shared memory as
+// well: every phase of an iteration stays on chip (small instances, where
+// the dependent row-pointer / index / gather loads from L2 bound the
+// iteration).  Same sums in the same order per row and per dot product.
+template <class T, class V, int NT>
+__global__ void __launch_bounds__(NT) k_pcg_local(Prob<T, V> P, CgArgs<T> a) {
+  __shared__ double sm[3 * (NT / 32)];
+  extern __shared__ __align__(16) unsigned char cg_sm[];
+  const int32_t inst = P.cg_sched ? P.cg_sched[blockIdx.x] : P.inst_sched[blockIdx.x];
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  if (c1 == c0) return;
+  const int64_t nl = c1 - c0, ml = r1 - r0;
+  T* sx = reinterpret_cast<T*>(cg_sm);
+  T* sr = sx + nl;
+  T* sp = sr + nl;
+  T* su = sp + nl;
+  T* sd = su + nl;
+  T* st = sd + nl;
+  unsigned char* cur = cg_sm + ((sizeof(T) * (5 * nl + ml) + 15) & ~(size_t)15);
+  const SmemCsr<V> mA = stage_csr<V>(P.A_rp, P.A_ci, P.A_v, r0, r1, c0, cur);
+  const SmemCsr<V> mAT = stage_csr<V>(P.AT_rp, P.AT_ci, P.AT_v, c0, c1, r0, cur);
+  SmemCsr<T> mP{nullptr, nullptr, nullptr};
+  if (P.P_rp) mP = stage_csr<T>(P.P_rp, P.P_ci, P.P_v, c0, c1, c0, cur);
+  const T sig = (T)a.sigma;
+  const T* __restrict__ rho = a.rho;
+  auto matvec = [&](const T* v, T* u) {
+    smem_csr_rows<T, V>(mA, v, ml, [&](int64_t r, T acc) { st[r] = rho[r0 + r] * acc; });
+    __syncthreads();
+    if (P.P_rp) {
+      smem_csr_rows<T, T>(mP, v, nl, [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+      smem_csr_rows<T, V>(mAT, (const T*)st, nl, [&](int64_t j, T acc) { u[j] += acc; });
+    } else {
+      smem_csr_rows<T, V>(mAT, (const T*)st, nl, [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+    }
+    __syncthreads();
+  };
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    sd[j - c0] = a.dinv[j];
+    sx[j - c0] = a.zero_start ? T(0) : (a.x0 ? a.x0[j] : a.x[j]);
+  }
+  __syncthreads();
+  if (!a.zero_start) matvec(sx, su);
+  double s3[3] = {0.0, 0.0, 0.0};   // rz, rr, bb
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
+    const int64_t l = j - c0;
+    const T bj = a.rhs[j];
+    const T rj = a.zero_start ? bj : bj - su[l];
+    const T zj = sd[l] * rj;
+    sr[l] = rj;
+    sp[l] = zj;
+    s3[0] += (double)rj * (double)zj;
+    s3[1] += (double)rj * (double)rj;
+    s3[2] += (double)bj * (double)bj;
+  }
+  block_sum<3>(s3, sm);
+  double rz = s3[0], rr = s3[1];
+  const double thr = a.tol * a.tol * s3[2];
+  int32_t it = 0;
+  if (s3[2] == 0.0) {
+    for (int64_t l = threadIdx.x; l < nl; l += NT) sx[l] = T(0);
+    rr = 0.0;
+  }
+  while (rr > thr && it < a.maxit) {
+    matvec(sp, su);
+    double s1[1] = {0.0};
+    for (int64_t l = threadIdx.x; l < nl; l += NT) s1[0] += (double)sp[l] * (double)su[l];
+    block_sum<1>(s1, sm);
+    if (!(s1[0] > 0.0)) break;  // breakdown (p = 0 or non-finite): stop, flagged below
+    const T al = (T)(rz / s1[0]);
+    double s2[2] = {0.0, 0.0};
+    for (int64_t l = threadIdx.x; l < nl; l += NT) {
+      sx[l] += al * sp[l];
+      const T rj = sr[l] - al * su[l];
+      sr[l] = rj;
+      const T zj = sd[l] * rj;
+      s2[0] += (double)rj * (double)zj;
+      s2[1] += (double)rj * (double)rj;
+    }
+    block_sum<2>(s2, sm);
+    const T be = (T)(s2[0] / rz);
+    rz = s2[0];
+    rr = s2[1];
+    for (int64_t l = threadIdx.x; l < nl; l += NT) sp[l] = sd[l] * sr[l] + be * sp[l];
+    __syncthreads();
+    ++it;
+  }
+  __syncthreads();
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) a.x[j] = sx[j - c0];
+  if (threadIdx.x == 0) {
+    if (rr > thr) atomicOr(&a.flags[inst], a.flag_bit);
+    if (!(rr == rr)) atomicOr(&a.flags[inst], F_NONFINITE);
+    if (a.iters) a.iters[inst] = it;
+    if (a.stats) {
+      atomicAdd(&a.stats[0], (unsigned long long)it);
+      atomicAdd(&a.stats[1], 1ull);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // a5, a6 (separable cones), a8: s~ = b - A x~, relaxation, projection of
 // v = alpha s~ + (1-alpha) s + y/rho on zero / orthant / box rows, dual update;

@@ -557,6 +557,17 @@ struct ImplT : Impl {
     // the shared-memory CG may take up to CG_SMEM_MAX bytes (set outside any graph capture)
     CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    CU(cudaFuncSetAttribute(k_pcg_local<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    CU(cudaFuncSetAttribute(k_pcg_local<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    // shared memory of the CG with the instance's matrices staged too (largest CG instance)
+    cg_local = 0;
+    for (int32_t i : h.cg_sched) {
+      const int64_t ni = h.col_off[i + 1] - h.col_off[i], mi = h.row_off[i + 1] - h.row_off[i];
+      const int64_t nnzA = h.A_rp[h.row_off[i + 1]] - h.A_rp[h.row_off[i]];
+      size_t b = ((sizeof(T) * (5 * ni + mi) + 15) & ~(size_t)15) + 2 * smem_csr_bytes(std::max(ni, mi), nnzA, sizeof(V));
+      if (h.has_P) b += smem_csr_bytes(ni, h.P_rp[h.col_off[i + 1]] - h.P_rp[h.col_off[i]], sizeof(T));
+      cg_local = std::max(cg_local, b);
+    }
     for (int i = 0; i < 2; ++i) {
       TRY(arena.alloc(&xb[i], n)); TRY(arena.alloc(&sb[i], m)); TRY(arena.alloc(&yb[i], m));
     }
@@ -711,6 +722,7 @@ struct ImplT : Impl {
   // CG launch: one CTA or one cluster of cg_cs CTAs per instance
   // one CTA per instance with the vectors in shared memory when they fit
   static constexpr size_t CG_SMEM_MAX = 200 * 1024;
+  size_t cg_local = 0;   // bytes of k_pcg_local for the largest CG instance
   size_t cg_smem_bytes() const { return (size_t)h.cg_vec * sizeof(T); }
 
   // automatic choice: the shared-memory kernel whenever the vectors fit
@@ -719,6 +731,11 @@ struct ImplT : Impl {
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
     const size_t smb = cg_smem_bytes();
     const int cs = opt.cg_cluster > 0 ? opt.cg_cluster : (smb <= CG_SMEM_MAX ? 1 : h.cg_cs);
+    if (cs == 1 && cg_local <= CG_SMEM_MAX) {
+      if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
+      else launch(tag, k_pcg_local<T, V, 256>, P.n_cg, 256, cg_local, st, P, ca);
+      return;
+    }
     if (cs == 1 && smb <= CG_SMEM_MAX) {
       if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
       else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
