@@ -602,9 +602,8 @@ def main():
         dom_ms, dom_n = b.profile_read(dom, reset=True)
         b.profile(enable=False)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
+        from paper_2606_13825_b300.dist import max_over_ranks
+        total_ms = max_over_ranks(total_ms, device=dev)
     ms_per_step = total_ms / args.steps
     value = world * n_inst * K * args.steps / (total_ms / 1e3)
 
