@@ -18,7 +18,11 @@
 namespace cosmo {
 
 constexpr int WSTC_KT = 32;                          // elements per staged K tile
-constexpr int WSTC_SBO = (WSTC_KT / 4) * 32 + 4;     // floats per 8-row group (1040 B)
+// K-adjacent core matrices 36 floats (144 B) apart instead of 32: a warp's
+// staging stores (one row, 32 consecutive elements = 8 core matrices) then
+// fall on 32 different banks instead of 8-way on four
+constexpr int WSTC_LBO = 36;                         // floats between K-adjacent core matrices
+constexpr int WSTC_SBO = (WSTC_KT / 4) * WSTC_LBO + 4;   // floats per 8-row group (1168 B)
 constexpr int WSTC_GA = 10;                          // row groups staged for A' (80 rows)
 constexpr int WSTC_TAIL = 16 - WSTC_GA;              // an M = 128 A operand reads 16 groups
 constexpr int WSTC_WAIT = 1 << 22;
@@ -31,7 +35,7 @@ __host__ __device__ inline size_t ws_tc_smem(int N) {
 }
 
 __device__ __forceinline__ int ws_tc_at(int r, int c) {
-  return (r >> 3) * WSTC_SBO + (c >> 2) * 32 + (r & 7) * 4 + (c & 3);
+  return (r >> 3) * WSTC_SBO + (c >> 2) * WSTC_LBO + (r & 7) * 4 + (c & 3);
 }
 
 template <int N>
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(256) k_ws_atb_tc(int64_t Ntot, int64_t chunk, 
     __syncthreads();
     tc::fence_after();
     if (tid == 0) {
-      const uint32_t idesc = tc::idesc_tf32(128, N), sbo = WSTC_SBO * 4u;
+      const uint32_t idesc = tc::idesc_tf32(128, N), sbo = WSTC_SBO * 4u, lbo = WSTC_LBO * 4u;
       const float* As[3] = {Ah, Ah, Al};
       const float* Bs[3] = {Bh, Bl, Bh};
 #pragma unroll
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(256) k_ws_atb_tc(int64_t Ntot, int64_t chunk, 
         const uint32_t a0 = tc::smem_u32(As[pr]), b0 = tc::smem_u32(Bs[pr]);
 #pragma unroll
         for (int ks = 0; ks < WSTC_KT / 8; ++ks)
-          tc::mma_tf32(taddr, tc::desc(a0 + ks * 256u, 128u, sbo), tc::desc(b0 + ks * 256u, 128u, sbo), idesc,
+          tc::mma_tf32(taddr, tc::desc(a0 + ks * 2u * lbo, lbo, sbo), tc::desc(b0 + ks * 2u * lbo, lbo, sbo), idesc,
                        (any || pr || ks) ? 1u : 0u);
       }
       tc::commit(mbar);

@@ -560,6 +560,8 @@ struct ImplT : Impl {
     CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     CU(cudaFuncSetAttribute(k_pcg_local<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     CU(cudaFuncSetAttribute(k_pcg_local<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    if constexpr (std::is_same<T, float>::value)   // tensor-core weight sums: 48 KB + the padded layout
+      CU(cudaFuncSetAttribute(k_ws_atb_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_tc_smem(64)));
     // shared memory of the CG with the instance's matrices staged too (largest CG instance)
     cg_local = 0;
     for (int32_t i : h.cg_sched) {
