@@ -1246,14 +1246,18 @@ struct ImplT : Impl {
            double* part, cudaStream_t st) {
     const int ka = KA + 1;
     if constexpr (std::is_same<T, float>::value) {
-      // FP32 blocks 33..64 columns wide: split-TF32 products on the tensor
+      // FP32 blocks 17..64 columns wide: split-TF32 products on the tensor
       // cores (chunk is a multiple of 32).  Measured: the warm start's 9x64
-      // and 65x64 blocks 3.3 -> 2.9 ms per step; the policy's 32-wide and
-      // narrower blocks were slower there (each K tile waits for its MMAs)
-      // and stay on the CUDA cores.
-      if (opt.dk_tensor_cores && KB > 32) {
-        launch("ws_grad", k_ws_atb_tc<64>, nch, 256, ws_tc_smem(64), st, N, chunk, A, lda, KA, 1, B, ldb, KB, part,
-               flags);
+      // and 65x64 blocks 3.3 -> 2.6 ms per step; the policy's 32-wide ones
+      // 13.8 -> 12.9 ms once the staging was bank-conflict free; the 65x2
+      // and 33x1 output-layer blocks stay on the CUDA cores.
+      if (opt.dk_tensor_cores && KB > 16) {
+        if (KB > 32)
+          launch("ws_grad", k_ws_atb_tc<64>, nch, 256, ws_tc_smem(64), st, N, chunk, A, lda, KA, 1, B, ldb, KB, part,
+                 flags);
+        else
+          launch("ws_grad", k_ws_atb_tc<32>, nch, 256, ws_tc_smem(32), st, N, chunk, A, lda, KA, 1, B, ldb, KB, part,
+                 flags);
         return;
       }
     }
