@@ -281,6 +281,55 @@ __global__ void __launch_bounds__(256) k_ws_atb(int64_t N, int64_t chunk, const 
     }
 }
 
+// The weight sums of a thin block (KB <= 2 columns: the output layers),
+// part[c][a * KB + b] = sum over the elements n of chunk c of A'[a][n] B[b][n]
+// with A' = [A; 1]: every thread streams its elements (n = n0 + tid, + 256,
+// ...) with coalesced reads, 16 rows of A' at a time held in registers,
+// sums in T per thread and over the warp (butterfly), then in double over
+// the eight warps in warp order (bitwise reproducible).
+template <class T>
+__global__ void __launch_bounds__(256) k_ws_atb_thin(int64_t N, int64_t chunk, const T* __restrict__ A, int64_t lda,
+                                                     int KA, int ones, const T* __restrict__ B, int64_t ldb, int KB,
+                                                     double* __restrict__ part) {
+  constexpr int RB = 16;
+  __shared__ double sm[8][RB * 2];
+  const int64_t n0 = (int64_t)blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+  const int ka = KA + ones, npair = ka * KB, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* out = part + (int64_t)blockIdx.x * npair;
+  for (int a0 = 0; a0 < ka; a0 += RB) {
+    T acc[RB][2];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) acc[i][0] = acc[i][1] = T(0);
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += 256) {
+      const T g0 = B[n], g1 = KB > 1 ? B[ldb + n] : T(0);
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int a = a0 + i;
+        const T x = a < KA ? A[a * lda + n] : (a < ka ? T(1) : T(0));
+        acc[i][0] += x * g0;
+        acc[i][1] += x * g1;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        if (b < KB) {   // warp butterfly in T (full-rate pipe), the warps combined in double
+          const T v = warp_allsum(acc[i][b]);
+          if (lane == 0) sm[w][2 * i + b] = (double)v;
+        }
+    __syncthreads();
+    if (threadIdx.x < 2 * RB) {
+      const int i = threadIdx.x >> 1, b = threadIdx.x & 1, a = a0 + i;
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += sm[q][threadIdx.x];
+      if (a < ka && b < KB) out[a * KB + b] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // out[k] (+)= sum over chunks c of part[c][k]: 32 outputs per CTA of 256
 // threads, warp q adding the chunks c = q, q + 8, ... in order, then the
 // eight warp sums added in warp order (a fixed order: bitwise reproducible)

@@ -1245,6 +1245,10 @@ struct ImplT : Impl {
   void atb(int nch, int64_t chunk, int64_t N, const T* A, int64_t lda, int KA, const T* B, int64_t ldb, int KB,
            double* part, cudaStream_t st) {
     const int ka = KA + 1;
+    if (KB <= 2) {   // output-layer blocks: a streaming column sum
+      launch("ws_grad", k_ws_atb_thin<T>, nch, 256, 0, st, N, chunk, A, lda, KA, 1, B, ldb, KB, part);
+      return;
+    }
     if constexpr (std::is_same<T, float>::value) {
       // FP32 blocks 17..64 columns wide: split-TF32 products on the tensor
       // cores (chunk is a multiple of 32).  Measured: the warm start's 9x64
