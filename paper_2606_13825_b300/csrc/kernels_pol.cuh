@@ -103,51 +103,53 @@ __global__ void __launch_bounds__(NT) k_pol_inst(Prob<T, V> P, const T* __restri
   const int32_t inst = blockIdx.x;
   const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
   const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
-  // r_p, Ax, s, b, r_d, Px, q, A'y, delta_p, delta_d
-  double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // r_p, Ax, s, b, r_d, Px, q, A'y, delta_p, delta_d: maxima of |.| in the
+  // iterate type (exact: a maximum does not round), widened at the end
+  T v[10] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
     T ax = T(0);
     for (int64_t e = P.A_rp[r]; e < P.A_rp[r + 1]; ++e) ax += (T)ldv(P.A_v, e) * x[P.A_ci[e]];
-    v[0] = fmax(v[0], fabs((double)(ax + s[r] - P.b[r])));
-    v[1] = fmax(v[1], fabs((double)ax));
-    v[2] = fmax(v[2], fabs((double)s[r]));
-    v[3] = fmax(v[3], fabs((double)P.b[r]));
-    if (stil) v[8] = fmax(v[8], fabs((double)(s[r] - stil[r])));
-    if (sprev) v[9] = fmax(v[9], fabs((double)(s[r] - sprev[r])));
+    v[0] = fmax(v[0], fabs(ax + s[r] - P.b[r]));
+    v[1] = fmax(v[1], fabs(ax));
+    v[2] = fmax(v[2], fabs(s[r]));
+    v[3] = fmax(v[3], fabs(P.b[r]));
+    if (stil) v[8] = fmax(v[8], fabs(s[r] - stil[r]));
+    if (sprev) v[9] = fmax(v[9], fabs(s[r] - sprev[r]));
   }
   for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
     T px = T(0), aty = T(0);
     if (P.P_rp)
       for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e) px += (T)ldv(P.P_v, e) * x[P.P_ci[e]];
     for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) aty += (T)ldv(P.AT_v, e) * y[P.AT_ci[e]];
-    v[4] = fmax(v[4], fabs((double)(px + P.q[j] - aty)));
-    v[5] = fmax(v[5], fabs((double)px));
-    v[6] = fmax(v[6], fabs((double)P.q[j]));
-    v[7] = fmax(v[7], fabs((double)aty));
+    v[4] = fmax(v[4], fabs(px + P.q[j] - aty));
+    v[5] = fmax(v[5], fabs(px));
+    v[6] = fmax(v[6], fabs(P.q[j]));
+    v[7] = fmax(v[7], fabs(aty));
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-    if (lane == 0) sm[k][w] = v[k];
+    if (lane == 0) sm[k][w] = (double)v[k];
   }
   __syncthreads();
   if (w != 0) return;
   // warp 0: every lane forms the same norms and features; lane j then owns
   // hidden unit j of both layers of the alpha MLP (32 units)
+  double vd[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
     double mx = 0.0;
     for (int q = 0; q < NT / 32; ++q) mx = fmax(mx, sm[k][q]);
-    v[k] = mx;
+    vd[k] = mx;
   }
-  double scp = fmax(fmax(v[1], v[2]), v[3]), scd = fmax(fmax(v[5], v[6]), v[7]);
+  double scp = fmax(fmax(vd[1], vd[2]), vd[3]), scd = fmax(fmax(vd[5], vd[6]), vd[7]);
   scp = scp > 0.0 ? scp : 1.0;
   scd = scd > 0.0 ? scd : 1.0;
-  const double lgd = log(v[4] / scd + POL_EPS);
-  const T xi[POL_NFA] = {la[inst], (T)log(v[0] / scp + POL_EPS), (T)lgd, (T)log(v[8] + POL_EPS),
-                         (T)log(v[9] + POL_EPS)};
+  const double lgd = log(vd[4] / scd + POL_EPS);
+  const T xi[POL_NFA] = {la[inst], (T)log(vd[0] / scp + POL_EPS), (T)lgd, (T)log(vd[8] + POL_EPS),
+                         (T)log(vd[9] + POL_EPS)};
   if (lane == 0) {
     sc[inst] = (T)(1.0 / scp);
     sc[P.ninst + inst] = (T)lgd;
