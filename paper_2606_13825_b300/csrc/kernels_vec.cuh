@@ -1153,31 +1153,32 @@ __global__ void __launch_bounds__(NT) k_kkt_inf(Prob<T, V> P, const T* __restric
   const int32_t inst = blockIdx.x;
   const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
   const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // maxima of |.| in the iterate type (exact: a maximum does not round), widened at the end
+  T v[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
     T ax = T(0);
     for (int64_t e = P.A_rp[r]; e < P.A_rp[r + 1]; ++e) ax += (T)ldv(P.A_v, e) * x[P.A_ci[e]];
-    v[0] = fmax(v[0], fabs((double)(ax + s[r] - P.b[r])));
-    v[1] = fmax(v[1], fabs((double)ax));
-    v[2] = fmax(v[2], fabs((double)s[r]));
-    v[3] = fmax(v[3], fabs((double)P.b[r]));
+    v[0] = fmax(v[0], fabs(ax + s[r] - P.b[r]));
+    v[1] = fmax(v[1], fabs(ax));
+    v[2] = fmax(v[2], fabs(s[r]));
+    v[3] = fmax(v[3], fabs(P.b[r]));
   }
   for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
     T px = T(0), aty = T(0);
     if (P.P_rp)
       for (int64_t e = P.P_rp[j]; e < P.P_rp[j + 1]; ++e) px += (T)ldv(P.P_v, e) * x[P.P_ci[e]];
     for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) aty += (T)ldv(P.AT_v, e) * y[P.AT_ci[e]];
-    v[4] = fmax(v[4], fabs((double)(px + P.q[j] - aty)));
-    v[5] = fmax(v[5], fabs((double)px));
-    v[6] = fmax(v[6], fabs((double)P.q[j]));
-    v[7] = fmax(v[7], fabs((double)aty));
+    v[4] = fmax(v[4], fabs(px + P.q[j] - aty));
+    v[5] = fmax(v[5], fabs(px));
+    v[6] = fmax(v[6], fabs(P.q[j]));
+    v[7] = fmax(v[7], fabs(aty));
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-    if (lane == 0) sm[k][w] = v[k];
+    if (lane == 0) sm[k][w] = (double)v[k];
   }
   __syncthreads();
   if (threadIdx.x < 8) {
