@@ -9,7 +9,9 @@
 // issues D += A_hi B_hi' + A_hi B_lo' + A_lo B_hi' (tcgen05.mma kind::tf32,
 // M = 128, N = 16 / 32 / 64, K = 8 per instruction) into an FP32
 // accumulator in tensor memory; the chunk's D is read back with
-// tcgen05.ld.  A fixed instruction sequence: the sums are reproducible.
+// tcgen05.ld.  The next tile's global loads are issued into registers while
+// the current tile's MMAs run.  A fixed instruction sequence: the sums are
+// reproducible.
 #pragma once
 
 #include "common.cuh"
@@ -61,25 +63,43 @@ __global__ void __launch_bounds__(256) k_ws_atb_tc(int64_t Ntot, int64_t chunk, 
   const uint32_t taddr = *tslot;
   const int ka = KA + ones;
   const int64_t n0 = (int64_t)blockIdx.x * chunk, n1 = min(Ntot, n0 + chunk);
+  // Software pipeline: each thread holds the next K tile's values in
+  // registers (A': f = tid + 256 u over the 80 x 32 rows x elements; B: over
+  // N x 32), loaded while the current tile's MMAs run.
+  constexpr int NA = WSTC_GA * 8 * WSTC_KT / 256, NB = N * WSTC_KT / 256;
+  float ra[NA], rb[NB];
+  auto load_tile = [&](int64_t t0) {
+    const int tl = (int)min((int64_t)WSTC_KT, n1 - t0);
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int f = tid + 256 * u, a = f / WSTC_KT, t = f % WSTC_KT;
+      ra[u] = (a < ka && t < tl) ? (a < KA ? A[a * lda + t0 + t] : 1.f) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int f = tid + 256 * u, b = f / WSTC_KT, t = f % WSTC_KT;
+      rb[u] = (b < KB && t < tl) ? B[b * ldb + t0 + t] : 0.f;
+    }
+  };
   uint32_t parity = 0;
   bool ok = true, any = false;
+  if (n0 < n1) load_tile(n0);
   for (int64_t t0 = n0; t0 < n1 && ok; t0 += WSTC_KT) {
-    const int tl = (int)min((int64_t)WSTC_KT, n1 - t0);
-    for (int f = tid; f < WSTC_GA * 8 * WSTC_KT; f += 256) {
-      const int a = f / WSTC_KT, t = f % WSTC_KT;
-      const float v = (a < ka && t < tl) ? (a < KA ? A[a * lda + t0 + t] : 1.f) : 0.f;
-      const float hi = tc::tf32(v);
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int f = tid + 256 * u, a = f / WSTC_KT, t = f % WSTC_KT;
+      const float hi = tc::tf32(ra[u]);
       const int idx = ws_tc_at(a, t);
       Ah[idx] = hi;
-      Al[idx] = tc::tf32(v - hi);
+      Al[idx] = tc::tf32(ra[u] - hi);
     }
-    for (int f = tid; f < N * WSTC_KT; f += 256) {
-      const int b = f / WSTC_KT, t = f % WSTC_KT;
-      const float v = (b < KB && t < tl) ? B[b * ldb + t0 + t] : 0.f;
-      const float hi = tc::tf32(v);
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int f = tid + 256 * u, b = f / WSTC_KT, t = f % WSTC_KT;
+      const float hi = tc::tf32(rb[u]);
       const int idx = ws_tc_at(b, t);
       Bh[idx] = hi;
-      Bl[idx] = tc::tf32(v - hi);
+      Bl[idx] = tc::tf32(rb[u] - hi);
     }
     tc::fence_proxy_async();   // the operand stores, visible to the tensor cores
     tc::fence_before();
@@ -99,6 +119,7 @@ __global__ void __launch_bounds__(256) k_ws_atb_tc(int64_t Ntot, int64_t chunk, 
       }
       tc::commit(mbar);
     }
+    if (t0 + WSTC_KT < n1) load_tile(t0 + WSTC_KT);   // in flight during the MMAs
     // CTA-uniform (the epilogue's tcgen05.ld runs in every thread of a warp);
     // the wait also frees the operand buffers for the next tile
     ok = __syncthreads_and(tc::mbar_wait(mbar, parity, WSTC_WAIT));
