@@ -41,7 +41,7 @@ __device__ inline T pol_rho(T l) { return exp(T(POL_SPAN) * pol_sig(l) + T(POL_L
 __device__ inline int pol_slot(int kind) { return kind == 0 ? 0 : kind <= 2 ? 1 : kind == 3 ? 2 : 3; }
 
 // MLP (F inputs, 32x32, one output) of one element, weights w in shared
-// memory; J = d out / d x[0]
+// memory as ws_load_params lays them out (W2 transposed); J = d out / d x[0]
 template <class T, int F>
 __device__ __forceinline__ void pol_mlp(const T (&x)[F], const T* w, T& out, T& J) {
   const T *W1 = w, *b1 = W1 + F * POL_H, *W2 = b1 + POL_H, *b2 = W2 + POL_H * POL_H, *W3 = b2 + POL_H,
@@ -58,12 +58,9 @@ __device__ __forceinline__ void pol_mlp(const T (&x)[F], const T* w, T& out, T& 
   T o = b3[0], j1 = T(0);
 #pragma unroll 1
   for (int j = 0; j < POL_H; ++j) {
-    T z = b2[j], dz = T(0);
-#pragma unroll
-    for (int i = 0; i < POL_H; ++i) {
-      z += W2[i * POL_H + j] * h[i];
-      dz += W2[i * POL_H + j] * t[i];
-    }
+    // W2 transposed in shared memory (ws_load_params): row j is column j
+    const T z = ws_dot<T, POL_H>(b2[j], W2 + j * POL_H, h);
+    const T dz = ws_dot<T, POL_H>(T(0), W2 + j * POL_H, t);
     if (z > T(0)) {
       o += W3[j] * z;
       j1 += W3[j] * dz;

@@ -84,12 +84,63 @@ __global__ void k_ws_feat(Prob<T, V> P, const T* __restrict__ ctx, T* __restrict
   }
 }
 
-// the parameters into shared memory (all threads of the CTA)
+// the parameters into shared memory (all threads of the CTA), with W2
+// stored transposed (row j of the copy = column j of W2: the inner loops
+// over i read it with 16-byte vector loads)
 template <class T, int F, int O, int H = WS_H>
 __device__ __forceinline__ T* ws_load_params(const T* __restrict__ theta, T* sm) {
-  for (int k = threadIdx.x; k < ws_nparams(F, O, H); k += blockDim.x) sm[k] = theta[k];
+  constexpr int o2 = F * H + H;
+  for (int k = threadIdx.x; k < ws_nparams(F, O, H); k += blockDim.x) {
+    const int d = k - o2;
+    sm[(d >= 0 && d < H * H) ? o2 + (d % H) * H + d / H : k] = theta[k];
+  }
   __syncthreads();
   return sm;
+}
+
+// z + sum_i w[i] h[i] in order of i (w: 16-byte aligned shared memory)
+template <class T, int H>
+__device__ __forceinline__ T ws_dot(T z, const T* w, const T (&h)[H]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < H / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(w)[q];
+      z += v.x * h[4 * q];
+      z += v.y * h[4 * q + 1];
+      z += v.z * h[4 * q + 2];
+      z += v.w * h[4 * q + 3];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < H / 2; ++q) {
+      const double2 v = reinterpret_cast<const double2*>(w)[q];
+      z += v.x * h[2 * q];
+      z += v.y * h[2 * q + 1];
+    }
+  }
+  return z;
+}
+
+// h[i] += w[i] d for every i (w: 16-byte aligned shared memory)
+template <class T, int H>
+__device__ __forceinline__ void ws_axpy(T (&h)[H], const T* w, T d) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < H / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(w)[q];
+      h[4 * q] += v.x * d;
+      h[4 * q + 1] += v.y * d;
+      h[4 * q + 2] += v.z * d;
+      h[4 * q + 3] += v.w * d;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < H / 2; ++q) {
+      const double2 v = reinterpret_cast<const double2*>(w)[q];
+      h[2 * q] += v.x * d;
+      h[2 * q + 1] += v.y * d;
+    }
+  }
 }
 
 // h1 = relu(W1' x + b1) of element e (features X[f * ld + e])
@@ -124,9 +175,7 @@ __global__ void __launch_bounds__(128) k_ws_fwd(int64_t N, const T* __restrict__
     T o0 = b3[0], o1 = O > 1 ? b3[O - 1] : T(0);
 #pragma unroll 1
     for (int j = 0; j < WS_H; ++j) {
-      T z = b2[j];
-#pragma unroll
-      for (int i = 0; i < WS_H; ++i) z += W2[i * WS_H + j] * h1[i];
+      const T z = ws_dot<T, WS_H>(b2[j], W2 + j * WS_H, h1);   // W2 transposed in shared memory
       if (z > T(0)) {
         o0 += W3[j * O] * z;
         if (O > 1) o1 += W3[j * O + 1] * z;
@@ -160,9 +209,7 @@ __global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, int64_t ldx, const T*
     for (int o = 0; o < O; ++o) g[o] = G[o * ldg + e];
 #pragma unroll 1
     for (int j = 0; j < H; ++j) {
-      T z = b2[j];
-#pragma unroll
-      for (int i = 0; i < H; ++i) z += W2[i * H + j] * h[i];
+      const T z = ws_dot<T, H>(b2[j], W2 + j * H, h);   // W2 transposed in shared memory
       T gz = T(0);
 #pragma unroll
       for (int o = 0; o < O; ++o) gz += W3[j * O + o] * g[o];
@@ -176,9 +223,7 @@ __global__ void __launch_bounds__(128) k_ws_bwd(int64_t N, int64_t ldx, const T*
     for (int i = 0; i < H; ++i) h[i] = T(0);
 #pragma unroll 1
     for (int j = 0; j < H; ++j) {
-      const T d = D2[j * N + e];
-#pragma unroll
-      for (int i = 0; i < H; ++i) h[i] += W2[i * H + j] * d;
+      ws_axpy<T, H>(h, W2 + j * H, D2[j * N + e]);
     }
 #pragma unroll
     for (int i = 0; i < H; ++i) D1[i * N + e] = H1[i * N + e] > T(0) ? h[i] : T(0);   // [z1 > 0] = [h1 > 0]
