@@ -153,7 +153,11 @@ typedef struct {
                                instance's vectors in shared memory when 5 n_i + m_i reals
                                fit in 200 KB; else 2 or 4 for fewer than 74 / 37 instances
                                with >= 8192 rows + columns, else 1); 1 (shared-memory
-                               vectors when they fit), 2 or 4 forced */
+                               vectors when they fit), 2 or 4 forced; one CTA per instance
+                               forced: -1 vectors in shared memory, -2 vectors and the
+                               instance's A, A' and P in shared memory, -3 global-memory
+                               vectors (-1 / -2 fail with E_INVAL at creation when the
+                               data does not fit in 200 KB) */
   int32_t loss_kind;        /* per-instance loss of cosmo_forward / cotangent of
                                cosmo_backward: 0 ||r_p^K||^2 + ||r_d^K||^2; 1 the log-residual
                                loss of Sec. 4, sum_{k=1..K} log(||r_d^k||^2/||r_d^0||^2 +
@@ -523,11 +527,20 @@ cosmo_status cosmo_pcg_plan_get_timing(const cosmo_pcg_plan* plan, double* mean_
  * array of COSMO_PCG_NOALLOC_MAX_BYTES bytes, which every GPU that loads the
  * library holds until the process exits; larger problems return E_INVAL.
  * The call makes no cudaMalloc / cudaFree / allocating library call.
- * The first call on each device looks up the array's device address with
- * that device current, so make it before any stream capture.  All calls
- * share the array (it keeps the previous call's contents; the call clears
- * what must start at zero): calls that overlap on the GPU race on it and
- * must be ordered by the caller. */
+ * It always runs the CG as one CTA per instance over global-memory vectors
+ * (cosmo_pcg_solve may pick a grid-wide CG for a few large zero-start
+ * instances: the same iteration, but its reduction order, and so its
+ * iteration count, can differ, and it is much faster there).
+ * A solve that reached max_iter is reported only as iters[i] == max_iter:
+ * the per-instance flag words live in the shared array and are not returned.
+ * The first call in each CUDA context looks up the array's device address
+ * with that context current and caches it per context handle, so make it
+ * before any stream capture; a context created later (after cudaDeviceReset,
+ * or another context the caller makes current) gets its own lookup, unless
+ * the driver hands the new context the handle value of a destroyed one.
+ * All calls share the array (it keeps the previous call's contents; the call
+ * clears what must start at zero): calls that overlap on the GPU race on it
+ * and must be ordered by the caller. */
 #define COSMO_PCG_NOALLOC_MAX_BYTES (16 * 1024 * 1024)
 cosmo_status cosmo_pcg_solve_noalloc(int32_t precision, int32_t ninst, int64_t n, int64_t m,
                                      const int64_t* col_off, const int64_t* row_off,

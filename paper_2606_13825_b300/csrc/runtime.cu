@@ -571,6 +571,10 @@ struct ImplT : Impl {
       if (h.has_P) b += smem_csr_bytes(ni, h.P_rp[h.col_off[i + 1]] - h.P_rp[h.col_off[i]], sizeof(T));
       cg_local = std::max(cg_local, b);
     }
+    if (P.n_cg && ((opt.cg_cluster == -1 && cg_smem_bytes() > CG_SMEM_MAX) ||
+                   (opt.cg_cluster == -2 && cg_local > CG_SMEM_MAX)))
+      return fail(COSMO_E_INVAL, "cg_cluster %d: the CG's shared-memory data (%zu B) exceeds %zu B",
+                  opt.cg_cluster, opt.cg_cluster == -1 ? cg_smem_bytes() : cg_local, CG_SMEM_MAX);
     for (int i = 0; i < 2; ++i) {
       TRY(arena.alloc(&xb[i], n)); TRY(arena.alloc(&sb[i], m)); TRY(arena.alloc(&yb[i], m));
     }
@@ -731,8 +735,28 @@ struct ImplT : Impl {
   // automatic choice: the shared-memory kernel whenever the vectors fit
   // (measured on the 64-instance SOCP batch: 1326 ms per step against 1528
   // with clusters of 2 over global vectors), clusters for larger instances
+  //
+  // cg_cluster < 0 forces one CTA-per-instance variant: -1 the vectors in
+  // shared memory (k_pcg_smem), -2 vectors and matrices in shared memory
+  // (k_pcg_local), -3 global-memory vectors (k_pcg); batch creation rejects a
+  // forced variant that does not fit.
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
     const size_t smb = cg_smem_bytes();
+    if (opt.cg_cluster == -1) {
+      if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
+      else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
+      return;
+    }
+    if (opt.cg_cluster == -2) {
+      if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
+      else launch(tag, k_pcg_local<T, V, 256>, P.n_cg, 256, cg_local, st, P, ca);
+      return;
+    }
+    if (opt.cg_cluster == -3) {
+      if (h.cg_nt == 512) launch(tag, k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
+      else launch(tag, k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+      return;
+    }
     const int cs = opt.cg_cluster > 0 ? opt.cg_cluster : (smb <= CG_SMEM_MAX ? 1 : h.cg_cs);
     if (cs == 1 && cg_local <= CG_SMEM_MAX) {
       if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
@@ -1585,7 +1609,7 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
     return fail(COSMO_E_INVAL, "unknown value type %d", o.value_type);
   if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
-      !(o.cg_cluster == 0 || o.cg_cluster == 1 || o.cg_cluster == 2 || o.cg_cluster == 4) ||
+      !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
       !(o.loss_kind == 0 || o.loss_kind == 1))
     return fail(COSMO_E_INVAL, "invalid options");
   TRY(validate(prob));
@@ -2775,34 +2799,65 @@ cosmo_status cosmo_psd_dk_backward(int32_t precision, int32_t nblk, const int32_
 // loads it until the process exits.
 //
 // Host code may not pass g_pcg_scratch itself to a kernel: on the host that
-// name is only a stand-in for the device symbol.  The first call on each
-// device looks up the symbol's device address (cudaGetSymbolAddress, with that
-// device current) and caches it; that first call should therefore happen
-// before any stream capture.  Every call shares the one array, so calls that
+// name is only a stand-in for the device symbol.  The first call in each CUDA
+// context looks up the symbol's device address (cudaGetSymbolAddress, with
+// that context's device current) and caches it per context; that first call
+// should therefore happen before any stream capture.  Every call shares the one array, so calls that
 // overlap on the GPU (different streams, or different host threads on the
 // same device) race on it; the caller must order them.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_pcg_scratch[COSMO_PCG_NOALLOC_MAX_BYTES];
 
 static std::mutex g_scratch_mu;
-static void* g_scratch_addr[64] = {nullptr};
+// (context, device address) of the array, one entry per driver context that
+// has called: a context created after cudaDeviceReset, or a non-primary
+// context made current by the caller, gets its own lookup instead of a stale
+// address.  The context handle comes from the driver's cuCtxGetCurrent,
+// reached through the runtime's entry-point query (no link against libcuda).
+struct ScratchEntry { void* ctx; void* addr; };
+static ScratchEntry g_scratch_cache[64];
+static int g_scratch_n = 0;
+
+// the calling thread's current driver context (null when the runtime has not
+// made one current yet)
+static cosmo_status current_context(void** ctx) {
+  typedef int (*CtxGetCurrentFn)(void**);
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) {
+      cudaGetLastError();
+      return fail(COSMO_E_CUDA, "driver entry point cuCtxGetCurrent unavailable");
+    }
+    fn = reinterpret_cast<CtxGetCurrentFn>(f);
+  }
+  *ctx = nullptr;
+  if (fn(ctx) != 0) return fail(COSMO_E_CUDA, "cuCtxGetCurrent failed");
+  return COSMO_OK;
+}
 
 static cosmo_status scratch_address(void** out) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(COSMO_E_INVAL, "device ordinal %d not supported", dev);
+  void* ctx = nullptr;
+  TRY(current_context(&ctx));
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return fail(COSMO_E_CUDA, "cudaGetSymbolAddress of the solve scratch failed on device %d: %s",
-                  dev, cudaGetErrorString(e));
-    }
-    g_scratch_addr[dev] = p;
+  if (ctx)
+    for (int i = 0; i < g_scratch_n && i < 64; ++i)
+      if (g_scratch_cache[i].ctx == ctx) { *out = g_scratch_cache[i].addr; return COSMO_OK; }
+  // the lookup also makes the device's primary context current if none was
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return fail(COSMO_E_CUDA, "cudaGetSymbolAddress of the solve scratch failed on device %d: %s",
+                dev, cudaGetErrorString(e));
   }
-  *out = g_scratch_addr[dev];
+  if (!ctx) TRY(current_context(&ctx));
+  if (ctx) g_scratch_cache[g_scratch_n++ % 64] = ScratchEntry{ctx, p};   // a full table reuses its oldest slot
+  *out = p;
   return COSMO_OK;
 }
 

@@ -121,3 +121,59 @@ def test_backward_central_differences(which, loss):
         fd = (f(h) - f(-h)) / (2 * h)
         an = g_r @ u_r + g_a @ u_a + g_l0 @ u_l
         assert an == pytest.approx(fd, rel=1e-5, abs=1e-7 * max(1.0, abs(L))), (t, an, fd)
+
+
+def test_policy_recurrence_by_value():
+    """Two closed-loop steps with small nonzero MLP weights, checked by value:
+    l^1 = l^0 + MLP(xi^0) and l^2 = l^1 + MLP(xi^1).  Each MLP routes one
+    weighted sum of its features through hidden unit 0 of layer 1 and unit 1
+    of layer 2 (W2[0][1] is the only nonzero entry of W2), so a transposed W2
+    zeroes the update, a dropped ReLU lets the negative sums through, and the
+    output bias is visible on every row."""
+    pr = _problems()[1]
+    H = op.H
+
+    def theta(F, w, scale):
+        t = np.zeros(op.n_params(F))
+        t[0:F * H:H] = w                               # W1[f][0] = w_f
+        o = F * H + H
+        t[o + 0 * H + 1] = 2.0                         # W2[0][1]
+        o += H * H + H
+        t[o + 1] = scale                               # W3[1][0]
+        t[o + H] = 0.01                                # b3
+        return t
+
+    wr = np.array([0.3, -0.2, 0.1, 0.5, 0.05, 0.4, -0.3])
+    wa = np.array([0.2, 0.1, -0.05, 0.02, -0.01])
+    tr_, ta_ = theta(op.NF_RHO, wr, 0.25), theta(op.NF_ALPHA, wa, -0.5)
+    l0 = op.default_l0()
+
+    def mlp(w, scale, xi):        # the network above, written out: scale * 2 relu(w . xi) + b3
+        return scale * 2.0 * np.maximum(xi @ w, 0.0) + 0.01
+
+    K = 3
+    tr, rho, alpha, tape = op.policy_forward(pr, tr_, ta_, l0, K)
+    l_r = l0[op.row_slots(pr)]
+    l_a = l0[4]
+    # xi^0 at the zero start: s = y = 0, rbar_p = -b / ||b||_inf, ||rbar_d||_inf = 1 (r_d = q)
+    b = pr.b
+    rbp = -b / np.abs(b).max()
+    xr0 = np.stack([l_r, np.zeros(pr.m), np.zeros(pr.m), rbp, np.full(pr.m, np.log(1.0 + op.EPS)),
+                    np.zeros(pr.m), np.zeros(pr.m)], axis=1)
+    xa0 = np.array([l_a, np.log(1.0 + op.EPS), np.log(1.0 + op.EPS), np.log(op.EPS), np.log(op.EPS)])
+    assert np.allclose(tape.xi_rho[0], xr0, rtol=0, atol=1e-15)
+    assert np.allclose(tape.xi_alpha[0], xa0, rtol=0, atol=1e-15)
+    l_r1 = l_r + mlp(wr, 0.25, xr0)
+    l_a1 = l_a + mlp(wa, -0.5, xa0)
+    assert np.allclose(tape.l_rho[1], l_r1, rtol=1e-15, atol=1e-15)
+    assert tape.l_alpha[1] == pytest.approx(l_a1, rel=1e-15)
+    assert np.allclose(rho[1], op.squash_rho(l_r1), rtol=1e-14, atol=0)
+    assert alpha[1] == pytest.approx(op.squash_alpha(l_a1), rel=1e-14)
+    # the updates are not trivial: some rows are cut by the ReLU, some not
+    assert np.ptp(l_r1 - l_r) > 1e-3
+    # step 2 from the features of iterate 1 (their values are pinned by hand above)
+    xr1, xa1 = op.features(pr, tr.xs[1], tr.ss[1], tr.ys[1], tr.ss[0], tr.steps[0].st, l_r1, l_a1)
+    l_r2 = l_r1 + mlp(wr, 0.25, xr1)
+    l_a2 = l_a1 + mlp(wa, -0.5, xa1)
+    assert np.allclose(tape.l_rho[2], l_r2, rtol=1e-14, atol=1e-14)
+    assert tape.l_alpha[2] == pytest.approx(l_a2, rel=1e-14)

@@ -23,20 +23,22 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-def _noalloc(system, sigma, rho, rhs, tol, max_iter):
+def _noalloc(system, sigma, rho, rhs, tol, max_iter, x0=None):
     from paper_2606_13825_b300 import _abi
     from paper_2606_13825_b300.solver import _tp, _stream
-    x = torch.zeros_like(rhs)
+    x = x0.clone() if x0 is not None else torch.zeros_like(rhs)
     iters = torch.zeros(system.ninst, dtype=torch.int32, device=rhs.device)
     prec = _abi.PREC_FP64 if system.precision == "fp64" else _abi.PREC_MIXED
     st = _abi.lib().cosmo_pcg_solve_noalloc(prec, system.ninst, system.n, system.m, *system.args(),
-                                            float(sigma), _tp(rho), _tp(rhs), _tp(x), 0, float(tol),
+                                            float(sigma), _tp(rho), _tp(rhs), _tp(x), 0 if x0 is None else 1,
+                                            float(tol),
                                             int(max_iter), _tp(iters), _stream())
     return st, x, iters
 
 
+@pytest.mark.parametrize("warm", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_noalloc_matches_allocating_solve_twice(precision):
+def test_noalloc_matches_allocating_solve_twice(precision, warm):
     _need_gpu()
     from paper_2606_13825_b300 import _abi
     from paper_2606_13825_b300.solver import ReducedSystem, pcg_solve
@@ -52,8 +54,10 @@ def test_noalloc_matches_allocating_solve_twice(precision):
     rho_t = torch.tensor(rho, dtype=dt, device="cuda")
     for call in range(2):
         rhs = torch.tensor(rng.standard_normal(system.n), dtype=dt, device="cuda")
-        x_ref, it_ref = pcg_solve(system, 1e-6, rho_t, rhs, tol=tol, max_iter=2000)
-        st, x, it = _noalloc(system, 1e-6, rho_t, rhs, tol, 2000)
+        # a warm start runs a product with x0 into the array's vectors before the CG
+        x0 = torch.tensor(rng.standard_normal(system.n), dtype=dt, device="cuda") if warm else None
+        x_ref, it_ref = pcg_solve(system, 1e-6, rho_t, rhs, x0=x0, tol=tol, max_iter=2000)
+        st, x, it = _noalloc(system, 1e-6, rho_t, rhs, tol, 2000, x0=x0)
         torch.cuda.synchronize()
         assert st == _abi.COSMO_OK, _abi.lib().cosmo_last_error()
         err = float((x - x_ref).abs().max() / x_ref.abs().max())
