@@ -163,6 +163,14 @@ typedef struct {
                                loss of Sec. 4, sum_{k=1..K} log(||r_d^k||^2/||r_d^0||^2 +
                                ||r_p^k||^2/||r_p^0||^2), k = 0 norms held constant, a term with
                                a zero k = 0 norm dropped */
+  int32_t eig_variant;      /* Jacobi kernel of the PSD projection: 0 automatic (2), 1 the
+                               matrix and eigenvectors by index (two barriers per round),
+                               2 the matrix in round-robin slot order as 2x2 tiles with the
+                               next round's rotations formed in the same pass (one barrier
+                               per round).  Both give the eigen-decomposition to eig_tol. */
+  int32_t eig_threads;      /* CTA size of the Jacobi projection: 0 by block order (128 up
+                               to p = 32, 256 up to 56, 512 above), or 128, 256, 512 for
+                               every block */
 } cosmo_options;
 
 typedef struct {
@@ -195,7 +203,8 @@ const char* cosmo_last_error(void);
 /* Fill *opt with defaults for a precision mode: MIXED cg_tol 1e-8, FP64 1e-10;
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
  * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
- * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0; loss_kind 0.
+ * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0; loss_kind 0;
+ * eig_variant 0; eig_threads 0.
  * Returns COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 

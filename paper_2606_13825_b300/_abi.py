@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("dk_gap_tau", c_double), ("eig_jacobi_max_p", c_int32),
                 ("eig_max_sweeps", c_int32), ("eig_tol", c_double), ("use_graph", c_int32),
                 ("device", c_int32), ("eig_warm_start", c_int32), ("dk_tensor_cores", c_int32),
-                ("cg_cluster", c_int32), ("loss_kind", c_int32)]
+                ("cg_cluster", c_int32), ("loss_kind", c_int32), ("eig_variant", c_int32),
+                ("eig_threads", c_int32)]
 
 
 class BatchInfo(ctypes.Structure):

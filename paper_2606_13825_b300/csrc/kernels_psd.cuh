@@ -11,6 +11,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "kernels_jt.cuh"
 
 namespace cosmo {
 
@@ -492,6 +493,159 @@ __global__ void __launch_bounds__(NT) k_psd_fwd(Prob<T, V> P, PsdIterIO<T> io, T
     for (int q = 0; q < nsel; ++q) {
       const int k = sel[q];
       acc += A[k * ld + k] * Vm[i * ld + k] * Vm[j * ld + k];
+    }
+    const int64_t r = row0 + e;
+    const T sh = al * io.st[r] + (T(1) - al) * io.s[r];
+    T out;
+    if (usepos) {
+      out = acc;
+    } else {
+      T sij = sh + io.y[r] / rh;            // svec entry of S
+      if (i != j) sij *= (T)kInvSqrt2;
+      out = sij - acc;
+    }
+    if (i != j) out *= (T)kSqrt2;
+    const T yn = io.y[r] + rh * (sh - out);
+    io.sn[r] = out;
+    io.yn[r] = yn;
+    if (!finite_(yn)) atomicOr(&flags[inst], F_NONFINITE);
+  }
+}
+
+// a7 with the slot-layout Jacobi solver of kernels_jt.cuh: the same
+// projection, relaxation input and fused dual update as k_psd_fwd; the
+// eigenvectors are kept by row (Vt), the warm start's products are formed in
+// that layout, and the solver works on 2x2 tiles with one barrier per round.
+// 64 registers per thread at most, so that two CTAs of 512 threads (or a
+// 512- and a 256-thread CTA of different size classes) share an SM
+template <class T, class V, int NT, int IPT>
+__global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V> P, PsdIterIO<T> io, T* lam_slot,
+                                                   T* U_slot, double tol, int max_sweeps,
+                                                   int32_t* flags, int sched_off,
+                                                   unsigned long long* stats, const T* U_prev) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int blk = P.psd_sched[sched_off + blockIdx.x];
+  const int p = P.psd_p[blk];
+  const int pe = psd_pe(p), np = pe / 2, ldv = jt_ldv(p), lds = jt_lds(p), ntri = jt_ntri(p);
+  const int64_t row0 = P.psd_row0[blk];
+  JtSmem<T> sm(smraw, p);
+  T* Vt = sm.Vt;
+  T* S = sm.S;
+  T* X = sm.X;
+  const int inst = io.row_inst[row0];
+  const T al = io.alpha[inst], rh = io.rho[row0];
+  const int d = p * (p + 1) / 2;
+  const bool warm = U_prev != nullptr;
+  for (int e = threadIdx.x; e < pe * ldv; e += NT) {
+    const int i = e / ldv, j = e - i * ldv;
+    Vt[e] = (!warm && i == j && i < p) ? T(1) : T(0);
+  }
+  __syncthreads();
+  if (warm) {
+    // previous step's eigenvectors as rows, then one Newton-Schulz step
+    // Vt <- 1.5 Vt - 0.5 (Vt Vt') Vt to restore orthogonality
+    const T* Up = U_prev + P.psd_uoff[blk];
+    for (int e = threadIdx.x; e < p * p; e += NT) {
+      const int j = e / p, i = e - j * p;
+      Vt[j * ldv + i] = Up[e];
+    }
+    __syncthreads();
+    smem_gemm_auto<T>(p, Vt, ldv, 1, Vt, 1, ldv, [&](int i, int j, T v) { X[i * lds + j] = v; });
+    __syncthreads();
+    smem_gemm_auto<T>(p, X, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += NT) {
+      const int i = e / p, j = e - i * p;
+      Vt[i * ldv + j] = T(1.5) * Vt[i * ldv + j] - T(0.5) * S[i * lds + j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < d; e += NT) {
+    int i, j;
+    svec_ij(e, i, j);
+    const int64_t r = row0 + e;
+    T v = al * io.st[r] + (T(1) - al) * io.s[r] + io.y[r] / rh;
+    if (i != j) v *= (T)kInvSqrt2;
+    S[i * lds + j] = v;
+    S[j * lds + i] = v;
+  }
+  __syncthreads();
+  if (warm) {
+    // B = V' S V (upper triangle read below), nearly diagonal when the
+    // iterate moved little: C = Vt S into X, then C Vt' into S
+    smem_gemm_auto<T>(p, Vt, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+    __syncthreads();
+    smem_gemm_auto<T>(p, X, lds, 1, Vt, 1, ldv, [&](int i, int j, T v) { S[i * lds + j] = v; });
+    __syncthreads();
+  }
+  // tiles of round 0 (slot layout) from the upper triangle of S
+  JtQuad<T>* tb0 = reinterpret_cast<JtQuad<T>*>(X);
+  JtQuad<T>* tb1 = tb0 + ntri;
+  for (int e = threadIdx.x; e < ntri; e += NT) {
+    int k, l;
+    svec_ij(e, k, l);
+    const int a0 = jt_slot_index(0, 2 * k, np), a1 = jt_slot_index(0, 2 * k + 1, np);
+    const int b0 = jt_slot_index(0, 2 * l, np), b1 = jt_slot_index(0, 2 * l + 1, np);
+    auto at = [&](int i, int j) -> T {
+      if (i >= p || j >= p) return T(0);
+      return i <= j ? S[i * lds + j] : S[j * lds + i];
+    };
+    JtQuad<T> q;
+    q.aa = at(a0, b0); q.ab = at(a0, b1); q.ba = at(a1, b0); q.bb = at(a1, b1);
+    tb0[e] = q;
+  }
+  __syncthreads();
+  auto off = [&](const void* q) { return (uint32_t)(reinterpret_cast<uintptr_t>(q) - reinterpret_cast<uintptr_t>(smraw)); };
+  uint32_t fin_off = off(tb0);
+  const int sweeps = jt_solve<T, NT, IPT>(smraw, off(tb0), off(tb1), off(Vt), off(sm.rec), sm.red, p, tol,
+                                          max_sweeps, &fin_off);
+  const JtQuad<T>* fin = reinterpret_cast<const JtQuad<T>*>(smraw + fin_off);
+  if (threadIdx.x == 0) {
+    if (sweeps < 0) atomicOr(&flags[inst], F_EIG_CAP);
+    if (stats) {
+      atomicAdd(&stats[0], (unsigned long long)(sweeps < 0 ? -sweeps : sweeps));
+      atomicAdd(&stats[1], 1ull);
+    }
+  }
+  T* lamv = sm.lamv;
+  for (int s = threadIdx.x; s < pe; s += NT) {
+    const int i = jt_slot_index(0, s, np);
+    if (i < p) {
+      const JtQuad<T> q = fin[jt_tile(s >> 1, s >> 1)];
+      lamv[i] = (s & 1) ? q.bb : q.aa;
+    }
+  }
+  __syncthreads();
+  // tape: eigenvalues and eigenvectors (column-major per block: column k = row k of Vt)
+  T* lam = lam_slot + P.psd_loff[blk];
+  T* U = U_slot + P.psd_uoff[blk];
+  for (int k = threadIdx.x; k < p; k += NT) lam[k] = lamv[k];
+  for (int e = threadIdx.x; e < p * p; e += NT) {
+    const int k = e / p, i = e - k * p;
+    U[e] = Vt[k * ldv + i];
+  }
+  // reconstruction from the smaller of the positive / non-positive sets
+  int* sel = sm.sel;
+  if (threadIdx.x == 0) {
+    int npos = 0;
+    for (int k = 0; k < p; ++k) npos += lamv[k] > T(0);
+    const bool usepos = npos <= p - npos;
+    int c = 0;
+    for (int k = 0; k < p; ++k)
+      if ((lamv[k] > T(0)) == usepos) sel[c++] = k;
+    sel[p] = c;
+    sel[p + 1] = usepos;
+  }
+  __syncthreads();
+  const int nsel = sel[p];
+  const bool usepos = sel[p + 1] != 0;
+  for (int e = threadIdx.x; e < d; e += NT) {
+    int i, j;
+    svec_ij(e, i, j);
+    T acc = T(0);
+    for (int q = 0; q < nsel; ++q) {
+      const int k = sel[q];
+      acc += lamv[k] * Vt[k * ldv + i] * Vt[k * ldv + j];
     }
     const int64_t r = row0 + e;
     const T sh = al * io.st[r] + (T(1) - al) * io.s[r];

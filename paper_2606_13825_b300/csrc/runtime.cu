@@ -443,7 +443,9 @@ struct ImplT : Impl {
   // launched with its own CTA size on a forked stream
   // method 0: CTA-resident Jacobi + shared-memory DK; method 1 (large blocks):
   // tridiagonal + QL in the tape slot + global-memory DK
-  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; bool warm_fits; int method; };
+  // fnt / tpt / variant: CTA size, per-thread work bound and Jacobi kernel of the forward
+  struct Bucket { int start, count, maxp, nt; cudaStream_t s; cudaEvent_t done; bool warm_fits; int method;
+                  int fnt, tpt, variant; };
   T* dk_work = nullptr;  // 2 x sum p^2: DK scratch of large blocks
   std::vector<Bucket> buckets;
   cudaEvent_t ev_fork = nullptr;
@@ -591,9 +593,13 @@ struct ImplT : Impl {
       // Blocks above the cutoff (option eig_jacobi_max_p; by default the
       // largest p whose warm-started Jacobi and DK fit in shared memory) take
       // the large-block path with 256 threads.
+      const int variant = opt.eig_variant == 0 ? 2 : opt.eig_variant;
+      auto fwd_threads = [&](int p) { return opt.eig_threads ? opt.eig_threads : (p > 56 ? 512 : (p > 32 ? 256 : 128)); };
       auto fits_jacobi = [&](int p) {
-        const int nt = p > 56 ? 512 : (p > 32 ? 256 : 128);
-        return (int64_t)psd_fwd_smem_warm<T>(p, nt) <= maxs && (int64_t)psd_bwd_smem<T>(p, nt) <= maxs;
+        const int nt = p > 56 ? 512 : (p > 32 ? 256 : 128), fnt = fwd_threads(p);
+        if ((int64_t)psd_bwd_smem<T>(p, nt) > maxs) return false;
+        if (variant == 2) return (int64_t)jt_smem<T>(p, fnt) <= maxs && jt_ipt(p, fnt) <= 8 && p <= 180;
+        return (int64_t)psd_fwd_smem_warm<T>(p, fnt) <= maxs;
       };
       auto class_of = [&](int p) {
         const bool big = opt.eig_jacobi_max_p > 0 ? (p > opt.eig_jacobi_max_p || !fits_jacobi(p)) : !fits_jacobi(p);
@@ -608,12 +614,14 @@ struct ImplT : Impl {
         while (e < h.psd_sched.size() && class_of(h.psd_p[h.psd_sched[e]]) == cls) ++e;
         const int method = cls == 1000 ? 1 : 0;
         const int nt = method ? 256 : cls;
+        const int fnt = method ? 256 : fwd_threads(p0);
         Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr,
-                  method == 0 && (int64_t)psd_fwd_smem_warm<T>(p0, nt) <= (int64_t)maxs, method};
+                  method == 0 && (variant == 2 || (int64_t)psd_fwd_smem_warm<T>(p0, fnt) <= (int64_t)maxs), method,
+                  fnt, jt_ipt(p0, fnt) <= 2 ? 2 : (jt_ipt(p0, fnt) <= 4 ? 4 : 8), variant};
         CU(cudaStreamCreateWithFlags(&bk.s, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
         if (method == 0) {
-          const size_t fs = psd_fwd_smem<T>(p0, nt), bs = psd_bwd_smem<T>(p0, nt);
+          const size_t fs = variant == 2 ? jt_smem<T>(p0, fnt) : psd_fwd_smem<T>(p0, fnt), bs = psd_bwd_smem<T>(p0, nt);
           if ((int64_t)fs > maxs || (int64_t)bs > maxs)
             return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
                         p0, std::max(fs, bs), maxs);
@@ -631,6 +639,12 @@ struct ImplT : Impl {
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+#define COSMO_JT_ATTR(NT_, IPT_) \
+      CU(cudaFuncSetAttribute(k_psd_fwd_jt<T, V, NT_, IPT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs))
+      COSMO_JT_ATTR(128, 2); COSMO_JT_ATTR(128, 4); COSMO_JT_ATTR(128, 8);
+      COSMO_JT_ATTR(256, 2); COSMO_JT_ATTR(256, 4); COSMO_JT_ATTR(256, 8);
+      COSMO_JT_ATTR(512, 2); COSMO_JT_ATTR(512, 4); COSMO_JT_ATTR(512, 8);
+#undef COSMO_JT_ATTR
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -885,10 +899,24 @@ struct ImplT : Impl {
           return;
         }
         const T* up = (opt.eig_warm_start && bk.warm_fits) ? U_prev : nullptr;
-        const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.nt) : psd_fwd_smem<T>(bk.maxp, bk.nt);
-        if (bk.nt == 512)
+        if (bk.variant == 2) {
+          const size_t sm = jt_smem<T>(bk.maxp, bk.fnt);
+#define COSMO_JT_LAUNCH(NT_, IPT_)                                                                  \
+  k_psd_fwd_jt<T, V, NT_, IPT_><<<bk.count, NT_, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol,        \
+                                                          opt.eig_max_sweeps, flags, bk.start, stats, up)
+#define COSMO_JT_IPT(NT_)                                                                           \
+  { if (bk.tpt == 2) COSMO_JT_LAUNCH(NT_, 2); else if (bk.tpt == 4) COSMO_JT_LAUNCH(NT_, 4); else COSMO_JT_LAUNCH(NT_, 8); }
+          if (bk.fnt == 512) COSMO_JT_IPT(512)
+          else if (bk.fnt == 256) COSMO_JT_IPT(256)
+          else COSMO_JT_IPT(128)
+#undef COSMO_JT_IPT
+#undef COSMO_JT_LAUNCH
+          return;
+        }
+        const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.fnt) : psd_fwd_smem<T>(bk.maxp, bk.fnt);
+        if (bk.fnt == 512)
           k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
-        else if (bk.nt == 256)
+        else if (bk.fnt == 256)
           k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
         else
           k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
@@ -1586,6 +1614,8 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->eig_warm_start = 1;
   o->dk_tensor_cores = 1;
   o->cg_cluster = 0;
+  o->eig_variant = 0;
+  o->eig_threads = 0;
   o->loss_kind = 0;
   return COSMO_OK;
 }
@@ -1610,7 +1640,8 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
   if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
       !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
-      !(o.loss_kind == 0 || o.loss_kind == 1))
+      !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 2 ||
+      !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512))
     return fail(COSMO_E_INVAL, "invalid options");
   TRY(validate(prob));
   int ndev = 0;
