@@ -169,8 +169,8 @@ typedef struct {
                                next round's rotations formed in the same pass (one barrier
                                per round).  Both give the eigen-decomposition to eig_tol. */
   int32_t eig_threads;      /* CTA size of the Jacobi projection: 0 by block order (128 up
-                               to p = 32, 256 up to 56, 512 above), or 128, 256, 512 for
-                               every block */
+                               to p = 32, 256 up to 56, 512 above), or 128, 256, 512 (or
+                               1024 with eig_variant 2) for every block */
 } cosmo_options;
 
 typedef struct {

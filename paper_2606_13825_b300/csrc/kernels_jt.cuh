@@ -12,12 +12,14 @@
 //
 // Layout: A is stored by slots, as 2x2 tiles (slots 2k, 2k+1) x (2l, 2l+1),
 // upper triangle k <= l only, four values per tile (aa, ab, ba, bb; the ba
-// entry of a diagonal tile is unused).  A round updates every tile by the
+// entry of a diagonal tile is unused) kept in four planes of ntri values, so
+// that the scattered single-value writes of neighbouring threads land in
+// neighbouring words (no bank conflicts).  A round updates every tile by the
 // two-sided rotation of its two pairs, J_k' X J_l (Golub & Van Loan,
 // Alg. 8.5.1 for the 2x2 Schur rotation), and writes each of the four results
 // straight into the position the permutation gives it in the next round, in
-// a second tile buffer: a tile is one vector load, its destinations are four
-// fixed addresses each thread computes once.
+// a second tile buffer: its destinations are four fixed addresses each
+// thread computes once.
 //
 // The next round's rotations come out of the same pass: each pair of round
 // rd+1 couples two slots that sat in one off-diagonal tile of round rd, so the
@@ -182,9 +184,13 @@ __device__ __forceinline__ T jt_diag_b(const JtQuad<T>& q, JtRot<T> r) {
 
 // Shared-memory accesses by byte offset from the kernel's shared array: with
 // the array itself as the base the compiler keeps 32-bit shared addressing.
+// tile E of the buffer at byte offset buf (four planes of ntri values)
 template <class T>
-__device__ __forceinline__ JtQuad<T> jt_ldq(const unsigned char* sm, uint32_t off) {
-  return *reinterpret_cast<const JtQuad<T>*>(sm + off);
+__device__ __forceinline__ JtQuad<T> jt_ldq(const unsigned char* sm, uint32_t buf, uint32_t E, uint32_t ntri) {
+  const T* b = reinterpret_cast<const T*>(sm + buf);
+  JtQuad<T> q;
+  q.aa = b[E]; q.ab = b[ntri + E]; q.ba = b[2 * ntri + E]; q.bb = b[3 * ntri + E];
+  return q;
 }
 template <class T>
 __device__ __forceinline__ JtRot<T> jt_ldr(const unsigned char* sm, uint32_t off) {
@@ -251,17 +257,18 @@ template <class T, int NT, int IPT>
 __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_t tb1, uint32_t vt,
                                         uint32_t recb, double* red, int p, double tol, int max_sweeps,
                                         uint32_t* fin) {
-  constexpr uint32_t QB = sizeof(JtQuad<T>), RB = sizeof(JtRot<T>), TB = sizeof(T);
+  constexpr uint32_t RB = sizeof(JtRot<T>), TB = sizeof(T);
   const int pe = p + (p & 1), np = pe / 2, m = pe - 1;
   const int ldv = jt_ldv(p), p4 = ldv / 4;
   const uint32_t VB = (uint32_t)ldv * TB;
-  const int noff = np * (np - 1) / 2, nitems = noff + np * p4;
+  const int noff = np * (np - 1) / 2, nitems = noff + np * p4, ntri = np * (np + 1) / 2;
+  const uint32_t nt_ = (uint32_t)ntri;
   const bool odd = (p & 1) != 0;   // pair 0 holds the padding index
   const int tid = threadIdx.x;
   auto dst_of = [&](int s, int t) -> uint32_t {   // element offset of slot pair (s, t) next round
     const int a = jt_next_slot(s, np), b = jt_next_slot(t, np);
     const int lo = a < b ? a : b, hi = a < b ? b : a;
-    return (uint32_t)(4 * jt_tile(lo >> 1, hi >> 1) + 2 * (lo & 1) + (hi & 1));
+    return (uint32_t)((2 * (lo & 1) + (hi & 1)) * ntri + jt_tile(lo >> 1, hi >> 1));
   };
   // ---- items: tile (kind 1): d0 = E | k << 12 | l << 20 | 1 << 28, d1/d2 = destinations;
   //             chunk (kind 2): d0 = c4 | k << 12 | 2 << 28, d1/d2 = current row indices a, b
@@ -320,11 +327,11 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
       if ((d0[u] >> 28) != 1) continue;
-      const JtQuad<T> x = jt_ldq<T>(sm, cur + (d0[u] & 0xfffu) * QB);
+      const JtQuad<T> x = jt_ldq<T>(sm, cur, d0[u] & 0xfffu, nt_);
       part[0] += T(2) * (x.aa * x.aa + x.ab * x.ab + x.ba * x.ba + x.bb * x.bb);
     }
     if (tid < np) {
-      const JtQuad<T> x = jt_ldq<T>(sm, cur + (g1 >> 16) * QB);
+      const JtQuad<T> x = jt_ldq<T>(sm, cur, g1 >> 16, nt_);
       part[0] += T(2) * x.ab * x.ab;
       part[1] += x.aa * x.aa + x.bb * x.bb;
     }
@@ -338,7 +345,7 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
     if (tid < np) {
       JtRot<T> r{T(1), T(0)};
       if (!(odd && tid == 0)) {
-        const JtQuad<T> x = jt_ldq<T>(sm, cur + (g1 >> 16) * QB);
+        const JtQuad<T> x = jt_ldq<T>(sm, cur, g1 >> 16, nt_);
         r = jt_rotation(x.aa, x.ab, x.bb, thresh);
       }
       *reinterpret_cast<JtRot<T>*>(sm + recb + (uint32_t)(rb * np + tid) * RB) = r;
@@ -352,7 +359,7 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
         const uint32_t kind = d0[u] >> 28;
         if (kind == 1) {
           const uint32_t k = (d0[u] >> 12) & 0xffu, l = (d0[u] >> 20) & 0xffu;
-          const JtQuad<T> x = jt_ldq<T>(sm, cur + (d0[u] & 0xfffu) * QB);
+          const JtQuad<T> x = jt_ldq<T>(sm, cur, d0[u] & 0xfffu, nt_);
           const JtRot<T> rk = jt_ldr<T>(sm, rc + k * RB), rl = jt_ldr<T>(sm, rc + l * RB);
           // rows of pair k, then columns of pair l
           const T y00 = rk.c * x.aa - rk.s * x.ba, y01 = rk.c * x.ab - rk.s * x.bb;
@@ -374,7 +381,7 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
       }
       if (tid < np) {
         // diagonal tile of pair tid: the rotation annihilates its coupling
-        const JtQuad<T> x = jt_ldq<T>(sm, cur + (g1 >> 16) * QB);
+        const JtQuad<T> x = jt_ldq<T>(sm, cur, g1 >> 16, nt_);
         const JtRot<T> r = jt_ldr<T>(sm, rc + (uint32_t)tid * RB);
         jt_st<T>(sm, nxt + (g0 & 0xffffu) * TB, jt_diag_a(x, r));
         jt_st<T>(sm, nxt + (g0 >> 16) * TB, r.s != T(0) ? T(0) : x.ab);
@@ -384,10 +391,10 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
           if (!(g2 >> 31)) {
             const uint32_t k = (g2 >> 12) & 0xffu, l = (g2 >> 20) & 0xffu, q = (g2 >> 28) & 3u;
             const bool srow = (g2 >> 30) & 1u;
-            const JtQuad<T> t = jt_ldq<T>(sm, cur + (g2 & 0xfffu) * QB);
+            const JtQuad<T> t = jt_ldq<T>(sm, cur, g2 & 0xfffu, nt_);
             const JtRot<T> rk = jt_ldr<T>(sm, rc + k * RB), rl = jt_ldr<T>(sm, rc + l * RB);
-            const JtQuad<T> dk = jt_ldq<T>(sm, cur + (uint32_t)jt_tile(k, k) * QB);
-            const JtQuad<T> dl = jt_ldq<T>(sm, cur + (uint32_t)jt_tile(l, l) * QB);
+            const JtQuad<T> dk = jt_ldq<T>(sm, cur, (uint32_t)jt_tile(k, k), nt_);
+            const JtQuad<T> dl = jt_ldq<T>(sm, cur, (uint32_t)jt_tile(l, l), nt_);
             // the coupling entry (row i = q >> 1 of pair k, column j = q & 1 of pair l)
             const T y0 = (q >> 1) ? rk.s * t.aa + rk.c * t.ba : rk.c * t.aa - rk.s * t.ba;
             const T y1 = (q >> 1) ? rk.s * t.ab + rk.c * t.bb : rk.c * t.ab - rk.s * t.bb;

@@ -578,9 +578,9 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
     smem_gemm_auto<T>(p, X, lds, 1, Vt, 1, ldv, [&](int i, int j, T v) { S[i * lds + j] = v; });
     __syncthreads();
   }
-  // tiles of round 0 (slot layout) from the upper triangle of S
-  JtQuad<T>* tb0 = reinterpret_cast<JtQuad<T>*>(X);
-  JtQuad<T>* tb1 = tb0 + ntri;
+  // tiles of round 0 (slot layout, four planes of ntri values) from the upper triangle of S
+  T* tb0 = X;
+  T* tb1 = X + 4 * ntri;
   for (int e = threadIdx.x; e < ntri; e += NT) {
     int k, l;
     svec_ij(e, k, l);
@@ -590,16 +590,17 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
       if (i >= p || j >= p) return T(0);
       return i <= j ? S[i * lds + j] : S[j * lds + i];
     };
-    JtQuad<T> q;
-    q.aa = at(a0, b0); q.ab = at(a0, b1); q.ba = at(a1, b0); q.bb = at(a1, b1);
-    tb0[e] = q;
+    tb0[e] = at(a0, b0);
+    tb0[ntri + e] = at(a0, b1);
+    tb0[2 * ntri + e] = at(a1, b0);
+    tb0[3 * ntri + e] = at(a1, b1);
   }
   __syncthreads();
   auto off = [&](const void* q) { return (uint32_t)(reinterpret_cast<uintptr_t>(q) - reinterpret_cast<uintptr_t>(smraw)); };
   uint32_t fin_off = off(tb0);
   const int sweeps = jt_solve<T, NT, IPT>(smraw, off(tb0), off(tb1), off(Vt), off(sm.rec), sm.red, p, tol,
                                           max_sweeps, &fin_off);
-  const JtQuad<T>* fin = reinterpret_cast<const JtQuad<T>*>(smraw + fin_off);
+  const T* fin = reinterpret_cast<const T*>(smraw + fin_off);
   if (threadIdx.x == 0) {
     if (sweeps < 0) atomicOr(&flags[inst], F_EIG_CAP);
     if (stats) {
@@ -611,8 +612,8 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
   for (int s = threadIdx.x; s < pe; s += NT) {
     const int i = jt_slot_index(0, s, np);
     if (i < p) {
-      const JtQuad<T> q = fin[jt_tile(s >> 1, s >> 1)];
-      lamv[i] = (s & 1) ? q.bb : q.aa;
+      const int E = jt_tile(s >> 1, s >> 1);
+      lamv[i] = (s & 1) ? fin[3 * ntri + E] : fin[E];
     }
   }
   __syncthreads();

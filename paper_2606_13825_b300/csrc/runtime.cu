@@ -644,6 +644,7 @@ struct ImplT : Impl {
       COSMO_JT_ATTR(128, 2); COSMO_JT_ATTR(128, 4); COSMO_JT_ATTR(128, 8);
       COSMO_JT_ATTR(256, 2); COSMO_JT_ATTR(256, 4); COSMO_JT_ATTR(256, 8);
       COSMO_JT_ATTR(512, 2); COSMO_JT_ATTR(512, 4); COSMO_JT_ATTR(512, 8);
+      COSMO_JT_ATTR(1024, 2); COSMO_JT_ATTR(1024, 4); COSMO_JT_ATTR(1024, 8);
 #undef COSMO_JT_ATTR
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -906,7 +907,8 @@ struct ImplT : Impl {
                                                           opt.eig_max_sweeps, flags, bk.start, stats, up)
 #define COSMO_JT_IPT(NT_)                                                                           \
   { if (bk.tpt == 2) COSMO_JT_LAUNCH(NT_, 2); else if (bk.tpt == 4) COSMO_JT_LAUNCH(NT_, 4); else COSMO_JT_LAUNCH(NT_, 8); }
-          if (bk.fnt == 512) COSMO_JT_IPT(512)
+          if (bk.fnt == 1024) COSMO_JT_IPT(1024)
+          else if (bk.fnt == 512) COSMO_JT_IPT(512)
           else if (bk.fnt == 256) COSMO_JT_IPT(256)
           else COSMO_JT_IPT(128)
 #undef COSMO_JT_IPT
@@ -1641,7 +1643,8 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
       !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
       !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 2 ||
-      !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512))
+      !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512 ||
+        (o.eig_threads == 1024 && o.eig_variant != 1)))
     return fail(COSMO_E_INVAL, "invalid options");
   TRY(validate(prob));
   int ndev = 0;
