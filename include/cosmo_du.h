@@ -171,7 +171,39 @@ typedef struct {
   int32_t eig_threads;      /* CTA size of the Jacobi projection: 0 by block order (128 up
                                to p = 32, 256 up to 56, 512 above), or 128, 256, 512 (or
                                1024 with eig_variant 2) for every block */
+  int32_t autotune;         /* 1: at batch creation, time the candidate launch
+                               configurations of what the options leave automatic and keep
+                               the fastest (see cosmo_tuning); 0: shape rules only */
 } cosmo_options;
+
+/* Launch configuration of a batch: the PSD size classes (blocks sorted by
+ * order, largest first, split where the CTA-size rule changes) with the
+ * eigensolver and CTA size of each, and the CG kernel.  Filled by the shape
+ * rules, or by the autotuner (option autotune = 1), which at batch creation
+ * times on the device, with synthetic data of the batch's own shapes:
+ *   - per class, the slot-layout Jacobi at CTA sizes 128 / 256 / 512 / 1024
+ *     (those that fit; projection of a perturbed block warm-started from the
+ *     eigenvectors of the unperturbed one), and for classes of order >= 48
+ *     the tridiagonal + QL path, each with its backward (Daleckii-Krein)
+ *     kernel;
+ *   - the CG kernel: one CTA per instance with the instance's data in shared
+ *     memory (-2), its vectors in shared memory (-1), global vectors (-3),
+ *     or clusters of 2 / 4 CTAs (20 iterations of the batch's operator);
+ * keeping the fastest.  A choice is cached per process for the same device,
+ * precision and shapes.  Only what the options leave automatic is tuned
+ * (eig_threads 0, eig_variant 0 or 2, eig_jacobi_max_p 0, cg_cluster 0). */
+#define COSMO_MAX_PSD_CLASSES 8
+typedef struct {
+  int32_t n_classes;
+  int32_t class_maxp[COSMO_MAX_PSD_CLASSES];     /* largest order of the class */
+  int32_t class_count[COSMO_MAX_PSD_CLASSES];    /* blocks in the class */
+  int32_t class_method[COSMO_MAX_PSD_CLASSES];   /* 0 Jacobi in shared memory (eig_variant),
+                                                    1 tridiagonal + implicit QL */
+  int32_t class_threads[COSMO_MAX_PSD_CLASSES];  /* CTA size of the projection */
+  int32_t cg_kernel;        /* 0 the shape rule (or no CG), else a cg_cluster value */
+  int32_t tuned;            /* 1 if the autotuner chose this configuration */
+  double tune_ms;           /* host time spent tuning at creation (0 if cached or off) */
+} cosmo_tuning;
 
 typedef struct {
   int32_t ninst;
@@ -204,9 +236,19 @@ const char* cosmo_last_error(void);
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
  * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
  * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0; loss_kind 0;
- * eig_variant 0; eig_threads 0.
+ * eig_variant 0; eig_threads 0; autotune 0.
  * Returns COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
+
+/* The batch's launch configuration (see cosmo_tuning).  Errors: E_INVAL. */
+cosmo_status cosmo_batch_get_tuning(const cosmo_batch* b, cosmo_tuning* out);
+
+/* Impose a launch configuration, e.g. one read from another batch of the same
+ * shapes: n_classes and class_maxp / class_count must match this batch's
+ * classes; every method / CTA size / CG kernel must fit (E_INVAL otherwise,
+ * nothing changed).  Recorded CUDA graphs are dropped and captured again.
+ * Synchronises the device. */
+cosmo_status cosmo_batch_set_tuning(cosmo_batch* b, const cosmo_tuning* t);
 
 /* Validate a problem on the host without touching the device (CSR bounds and
  * block-diagonal structure, cone rows summing to each instance's row count,

@@ -49,7 +49,17 @@ class Options(ctypes.Structure):
                 ("eig_max_sweeps", c_int32), ("eig_tol", c_double), ("use_graph", c_int32),
                 ("device", c_int32), ("eig_warm_start", c_int32), ("dk_tensor_cores", c_int32),
                 ("cg_cluster", c_int32), ("loss_kind", c_int32), ("eig_variant", c_int32),
-                ("eig_threads", c_int32)]
+                ("eig_threads", c_int32), ("autotune", c_int32)]
+
+
+MAX_PSD_CLASSES = 8
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("n_classes", c_int32), ("class_maxp", c_int32 * MAX_PSD_CLASSES),
+                ("class_count", c_int32 * MAX_PSD_CLASSES), ("class_method", c_int32 * MAX_PSD_CLASSES),
+                ("class_threads", c_int32 * MAX_PSD_CLASSES), ("cg_kernel", c_int32), ("tuned", c_int32),
+                ("tune_ms", c_double)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -90,6 +100,8 @@ _SIGS = {
     "cosmo_batch_create": (c_int32, [POINTER(Problem), POINTER(Options), POINTER(c_void_p)]),
     "cosmo_batch_destroy": (c_int32, [c_void_p]),
     "cosmo_batch_get_info": (c_int32, [c_void_p, POINTER(BatchInfo)]),
+    "cosmo_batch_get_tuning": (c_int32, [c_void_p, POINTER(Tuning)]),
+    "cosmo_batch_set_tuning": (c_int32, [c_void_p, POINTER(Tuning)]),
     "cosmo_forward": (c_int32, [c_void_p, c_int32, POINTER(c_double), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_int32, c_void_p]),

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <random>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -379,6 +381,8 @@ struct Impl {
   virtual cosmo_status profile_enable(const char* tag) = 0;
   virtual cosmo_status profile_read(const char* tag, double* ms, int64_t* n, int32_t reset) = 0;
   virtual size_t real_size() const = 0;
+  virtual void get_tuning(cosmo_tuning* t) const = 0;
+  virtual cosmo_status set_tuning(const cosmo_tuning& t) = 0;
 };
 
 // device staging of cosmo_step_host, owned by the batch so repeated steps
@@ -634,6 +638,7 @@ struct ImplT : Impl {
         q = e;
       }
       if (any_big) TRY(arena.alloc(&dk_work, 2 * h.sum_p2));
+      smem_max = maxs;
       CU(cudaFuncSetAttribute(k_psd_fwd_tql<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
       CU(cudaFuncSetAttribute(k_psd_fwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -653,6 +658,252 @@ struct ImplT : Impl {
         CU(cudaFuncSetAttribute(k_psd_bwd_tc<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)dk_tc_smem(DK_TC_MAXP)));
     }
+    if (opt.autotune) TRY(tune());
+    return COSMO_OK;
+  }
+
+  // ------------------------------------------------------------- tuning --
+  // Candidate launch configurations are timed with CUDA events on synthetic
+  // data of the batch's own shapes (see cosmo_tuning in the header); the
+  // choice is cached per process under a key of the device, the types and
+  // the shapes.
+  int smem_max = 0;
+  bool tuned = false;
+  double tune_ms = 0.0;
+  struct TuneResult { std::vector<int> method, fnt; int cg = 0; };
+  static std::mutex& tune_mu() { static std::mutex m; return m; }
+  static std::vector<std::pair<std::string, TuneResult>>& tune_cache() {
+    static std::vector<std::pair<std::string, TuneResult>> c;
+    return c;
+  }
+  std::string tune_key() const {
+    uint64_t hsh = 1469598103934665603ull;   // FNV-1a over the class orders in schedule order
+    for (int32_t blk : h.psd_sched) { hsh ^= (uint64_t)h.psd_p[blk]; hsh *= 1099511628211ull; }
+    char buf[512];
+    snprintf(buf, sizeof buf, "%d|%zu|%zu|%d|%d|%d|%d|%llx|%zu|cg%d,%lld,%zu,%d,%lld,%lld,%lld,%lld", opt.device,
+             sizeof(T), sizeof(V), opt.eig_warm_start, opt.dk_tensor_cores, opt.eig_jacobi_max_p, opt.eig_variant,
+             (unsigned long long)hsh, buckets.size(), P.n_cg, (long long)h.cg_vec, cg_local, h.cg_nt,
+             (long long)h.A_ci.size(), (long long)h.P_ci.size(), (long long)h.n, (long long)h.m);
+    return std::string(buf);
+  }
+  bool jt_fits(int p, int fnt) const {
+    return fnt > 32 * jt_pair_warps(p) && (int64_t)jt_smem<T>(p, fnt) <= smem_max && jt_ipt(p, fnt) <= 8 && p <= 180;
+  }
+  bool ql_fits(int p) const { return (int64_t)tql_smem<T>(p, 256) <= smem_max; }
+  bool bwd_fits(const Bucket& bk) const {
+    if (std::is_same<T, float>::value && opt.dk_tensor_cores && bk.maxp <= DK_TC_MAXP) return true;
+    return (int64_t)psd_bwd_smem<T>(bk.maxp, bk.nt) <= smem_max;
+  }
+  static int ipt_class(int p, int fnt) {
+    const int i = jt_ipt(p, fnt);
+    return i <= 2 ? 2 : (i <= 4 ? 4 : 8);
+  }
+  // a class's configuration: method 0 = Jacobi (this batch's variant), 1 = QL
+  cosmo_status config_bucket(Bucket& bk, int method, int fnt) {
+    if (method == 1) {
+      if (!ql_fits(bk.maxp)) return fail(COSMO_E_INVAL, "order %d does not fit the QL path", bk.maxp);
+      if (!dk_work) TRY(arena.alloc(&dk_work, 2 * h.sum_p2));
+      bk.method = 1;
+      bk.fnt = 256;
+      return COSMO_OK;
+    }
+    const int variant = opt.eig_variant == 0 ? 2 : opt.eig_variant;
+    const bool ok = variant == 2 ? jt_fits(bk.maxp, fnt)
+                                 : (fnt <= 512 && fnt >= 128 && (int64_t)psd_fwd_smem_warm<T>(bk.maxp, fnt) <= smem_max);
+    Bucket t = bk;
+    t.method = 0;
+    if (!ok || !bwd_fits(t)) return fail(COSMO_E_INVAL, "order %d does not fit Jacobi with %d threads", bk.maxp, fnt);
+    bk.method = 0;
+    bk.variant = variant;
+    bk.fnt = fnt;
+    bk.tpt = ipt_class(bk.maxp, fnt);
+    bk.warm_fits = true;
+    return COSMO_OK;
+  }
+  void drop_graphs() {
+    if (gfwd) { cudaGraphExecDestroy(gfwd); gfwd = nullptr; }
+    if (gbwd) { cudaGraphExecDestroy(gbwd); gbwd = nullptr; }
+    gfwd_key[0] = -1;
+  }
+  cosmo_status apply_tune(const TuneResult& r) {
+    for (size_t i = 0; i < buckets.size(); ++i) TRY(config_bucket(buckets[i], r.method[i], r.fnt[i]));
+    cg_mode = r.cg;
+    drop_graphs();
+    return COSMO_OK;
+  }
+  template <class F>
+  float time_min(cudaStream_t st, F fn) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fn();
+    float best = 3.0e38f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, st);
+      fn();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+  }
+  cosmo_status tune() {
+    const auto t0 = std::chrono::steady_clock::now();
+    const std::string key = tune_key();
+    {
+      std::lock_guard<std::mutex> lk(tune_mu());
+      for (auto& e : tune_cache())
+        if (e.first == key) {
+          TRY(apply_tune(e.second));
+          tuned = true;
+          tune_ms = 0.0;
+          return COSMO_OK;
+        }
+    }
+    TuneResult res;
+    cudaStream_t st = nullptr;
+    CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cosmo_status status = tune_run(st, res);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (status != COSMO_OK) return status;
+    if (e != cudaSuccess) return fail(COSMO_E_CUDA, "tuning: %s", cudaGetErrorString(e));
+    TRY(apply_tune(res));
+    {
+      std::lock_guard<std::mutex> lk(tune_mu());
+      tune_cache().push_back(std::make_pair(key, res));
+    }
+    tuned = true;
+    tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return COSMO_OK;
+  }
+  cosmo_status tune_run(cudaStream_t st, TuneResult& res) {
+    DevArena ta;
+    res.method.resize(buckets.size());
+    res.fnt.resize(buckets.size());
+    for (size_t i = 0; i < buckets.size(); ++i) { res.method[i] = buckets[i].method; res.fnt[i] = buckets[i].fnt; }
+    res.cg = cg_mode;
+    std::mt19937_64 rng(20260613ull);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    const bool tune_psd = P.npsd > 0 && opt.eig_threads == 0 && opt.eig_variant != 1;
+    const bool tune_cg = P.n_cg > 0 && opt.cg_cluster == 0;
+    const int64_t m = h.m, n = h.n, ni = h.ninst;
+    if (tune_psd) {
+      // a random symmetric iterate per block, and a perturbation of it (5%)
+      // projected warm-started from the first one's eigenvectors
+      std::vector<double> v0(m), v1(m), gv(m);
+      for (int64_t r = 0; r < m; ++r) { v0[r] = nd(rng); v1[r] = v0[r] + 0.05 * nd(rng); gv[r] = nd(rng); }
+      T *s0, *s1, *zero, *one_r, *one_a, *sn, *yn, *lam, *U0, *U1, *g, *vb;
+      int32_t* fl;
+      TRY(ta.upload(&s0, conv<T>(v0))); TRY(ta.upload(&s1, conv<T>(v1))); TRY(ta.upload(&g, conv<T>(gv)));
+      TRY(ta.upload(&one_r, std::vector<T>(m, T(1)))); TRY(ta.upload(&one_a, std::vector<T>(ni, T(1))));
+      TRY(ta.alloc(&zero, m)); TRY(ta.alloc(&sn, m)); TRY(ta.alloc(&yn, m)); TRY(ta.alloc(&vb, m));
+      TRY(ta.alloc(&lam, h.sum_p)); TRY(ta.alloc(&U0, h.sum_p2)); TRY(ta.alloc(&U1, h.sum_p2));
+      TRY(ta.alloc(&fl, ni));
+      CU(cudaMemsetAsync(zero, 0, sizeof(T) * m, st));
+      CU(cudaMemsetAsync(fl, 0, sizeof(int32_t) * ni, st));
+      const PsdIterIO<T> io0{s0, zero, zero, one_r, one_a, sn, yn, P.row_inst};
+      const PsdIterIO<T> io1{s1, zero, zero, one_r, one_a, sn, yn, P.row_inst};
+      const PsdBwdIO<T> bio{g, vb, P.row_inst};
+      for (size_t i = 0; i < buckets.size(); ++i) {
+        const Bucket base = buckets[i];
+        psd_fwd_bucket(base, st, io0, lam, U0, nullptr, fl, nullptr);
+        CU(cudaGetLastError());
+        float best = 3.0e38f;
+        float bwd[2] = {-1.f, -1.f};
+        std::vector<std::pair<int, int>> cands;
+        for (int fnt : {128, 256, 512, 1024}) cands.push_back(std::make_pair(0, fnt));
+        if (opt.eig_jacobi_max_p == 0 && base.maxp >= 48) cands.push_back(std::make_pair(1, 256));
+        for (const auto& c : cands) {
+          Bucket bk = base;
+          if (c.first == 1 ? !ql_fits(bk.maxp) : !jt_fits(bk.maxp, c.second)) continue;
+          if (config_bucket(bk, c.first, c.second) != COSMO_OK) { g_err.clear(); continue; }
+          const T* up = bk.method == 0 && opt.eig_warm_start ? U0 : nullptr;
+          const float f = time_min(st, [&]() { psd_fwd_bucket(bk, st, io1, lam, U1, up, fl, nullptr); });
+          CU(cudaGetLastError());
+          if (bwd[bk.method] < 0.f) {
+            bwd[bk.method] = time_min(st, [&]() { psd_bwd_bucket(bk, st, bio, lam, U1, fl); });
+            CU(cudaGetLastError());
+          }
+          if (f + bwd[bk.method] < best) {
+            best = f + bwd[bk.method];
+            res.method[i] = bk.method;
+            res.fnt[i] = bk.fnt;
+          }
+        }
+      }
+    }
+    if (tune_cg) {
+      // 20 iterations of the batch's operator, rho = 0.1 (1e2 on zero-cone rows)
+      std::vector<double> rh(m), bv(n);
+      for (int64_t r = 0; r < m; ++r) rh[r] = h.row_kind[r] == K_ZERO ? 100.0 : 0.1;
+      for (int64_t j = 0; j < n; ++j) bv[j] = nd(rng);
+      T *rho, *dv, *rhs, *x;
+      int32_t* fl;
+      double* sig;
+      TRY(ta.upload(&rho, conv<T>(rh))); TRY(ta.upload(&rhs, conv<T>(bv)));
+      TRY(ta.upload(&sig, std::vector<double>(1, 1e-6)));
+      TRY(ta.alloc(&dv, n)); TRY(ta.alloc(&x, n)); TRY(ta.alloc(&fl, ni));
+      CU(cudaMemsetAsync(fl, 0, sizeof(int32_t) * ni, st));
+      k_precond<T, V><<<grid_for(n, 256), 256, 0, st>>>(P, 1, (const double*)sig, (const T*)rho, dv);
+      CgArgs<T> ca{};
+      ca.rhs = rhs; ca.x = x; ca.x0 = nullptr; ca.rho = rho; ca.dinv = dv; ca.sigma = 1e-6;
+      ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = 1e-30; ca.maxit = 20; ca.zero_start = 1;
+      ca.flag_bit = F_CG_CAP; ca.flags = fl; ca.iters = nullptr; ca.stats = nullptr;
+      std::vector<int> cands;
+      if (cg_local <= CG_SMEM_MAX) cands.push_back(-2);
+      if (cg_smem_bytes() <= CG_SMEM_MAX) cands.push_back(-1);
+      cands.push_back(-3);
+      cands.push_back(2);
+      cands.push_back(4);
+      const int keep = cg_mode;
+      float best = 3.0e38f;
+      for (int c : cands) {
+        cg_mode = c;
+        const float t = time_min(st, [&]() { launch_pcg("tune", st, ca); });
+        CU(cudaGetLastError());
+        if (t < best) { best = t; res.cg = c; }
+      }
+      cg_mode = keep;
+    }
+    return COSMO_OK;
+  }
+  void get_tuning(cosmo_tuning* t) const override {
+    memset(t, 0, sizeof(*t));
+    t->n_classes = (int32_t)std::min<size_t>(buckets.size(), COSMO_MAX_PSD_CLASSES);
+    for (int i = 0; i < t->n_classes; ++i) {
+      t->class_maxp[i] = buckets[i].maxp;
+      t->class_count[i] = buckets[i].count;
+      t->class_method[i] = buckets[i].method;
+      t->class_threads[i] = buckets[i].fnt;
+    }
+    t->cg_kernel = opt.cg_cluster != 0 ? opt.cg_cluster : cg_mode;
+    t->tuned = tuned ? 1 : 0;
+    t->tune_ms = tune_ms;
+  }
+  cosmo_status set_tuning(const cosmo_tuning& t) override {
+    if (t.n_classes != (int32_t)buckets.size() || buckets.size() > COSMO_MAX_PSD_CLASSES)
+      return fail(COSMO_E_INVAL, "tuning has %d classes, the batch %zu", t.n_classes, buckets.size());
+    for (size_t i = 0; i < buckets.size(); ++i)
+      if (t.class_maxp[i] != buckets[i].maxp || t.class_count[i] != buckets[i].count ||
+          !(t.class_method[i] == 0 || t.class_method[i] == 1))
+        return fail(COSMO_E_INVAL, "tuning class %zu does not match the batch", i);
+    const int cg = t.cg_kernel;
+    if (!(cg >= -3 && cg <= 4 && cg != 3) || (cg == -1 && cg_smem_bytes() > CG_SMEM_MAX) ||
+        (cg == -2 && cg_local > CG_SMEM_MAX))
+      return fail(COSMO_E_INVAL, "tuning: CG kernel %d not available", cg);
+    std::vector<Bucket> nb = buckets;
+    for (size_t i = 0; i < nb.size(); ++i) TRY(config_bucket(nb[i], t.class_method[i], t.class_threads[i]));
+    CU(cudaDeviceSynchronize());
+    buckets = nb;
+    cg_mode = cg;
+    tuned = t.tuned != 0;
+    tune_ms = t.tune_ms;
+    drop_graphs();
     return COSMO_OK;
   }
 
@@ -755,24 +1006,26 @@ struct ImplT : Impl {
   // shared memory (k_pcg_smem), -2 vectors and matrices in shared memory
   // (k_pcg_local), -3 global-memory vectors (k_pcg); batch creation rejects a
   // forced variant that does not fit.
+  int cg_mode = 0;   // the CG kernel chosen by tuning (a cg_cluster value; 0: the shape rule)
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
     const size_t smb = cg_smem_bytes();
-    if (opt.cg_cluster == -1) {
+    const int mode = opt.cg_cluster != 0 ? opt.cg_cluster : cg_mode;
+    if (mode == -1) {
       if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
       else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
       return;
     }
-    if (opt.cg_cluster == -2) {
+    if (mode == -2) {
       if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
       else launch(tag, k_pcg_local<T, V, 256>, P.n_cg, 256, cg_local, st, P, ca);
       return;
     }
-    if (opt.cg_cluster == -3) {
+    if (mode == -3) {
       if (h.cg_nt == 512) launch(tag, k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
       else launch(tag, k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
       return;
     }
-    const int cs = opt.cg_cluster > 0 ? opt.cg_cluster : (smb <= CG_SMEM_MAX ? 1 : h.cg_cs);
+    const int cs = mode > 0 ? mode : (smb <= CG_SMEM_MAX ? 1 : h.cg_cs);
     if (cs == 1 && cg_local <= CG_SMEM_MAX) {
       if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
       else launch(tag, k_pcg_local<T, V, 256>, P.n_cg, 256, cg_local, st, P, ca);
@@ -894,36 +1147,61 @@ struct ImplT : Impl {
     if (P.npsd) {
       PsdIterIO<T> io{stt, st_s(slot), st_y(slot), rho, alpha, st_s(slot + 1), st_y(slot + 1), P.row_inst};
       psd_group("psd_fwd", st, [&](const Bucket& bk, cudaStream_t s) {
-        if (bk.method == 1) {
-          k_psd_fwd_tql<T, V, 256><<<bk.count, 256, tql_smem<T>(bk.maxp, 256), s>>>(
-              P, io, sp.lam, sp.U, flags, bk.start, stats, 30 * 4);
-          return;
-        }
-        const T* up = (opt.eig_warm_start && bk.warm_fits) ? U_prev : nullptr;
-        if (bk.variant == 2) {
-          const size_t sm = jt_smem<T>(bk.maxp, bk.fnt);
-#define COSMO_JT_LAUNCH(NT_, IPT_)                                                                  \
-  k_psd_fwd_jt<T, V, NT_, IPT_><<<bk.count, NT_, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol,        \
-                                                          opt.eig_max_sweeps, flags, bk.start, stats, up)
-#define COSMO_JT_IPT(NT_)                                                                           \
-  { if (bk.tpt == 2) COSMO_JT_LAUNCH(NT_, 2); else if (bk.tpt == 4) COSMO_JT_LAUNCH(NT_, 4); else COSMO_JT_LAUNCH(NT_, 8); }
-          if (bk.fnt == 1024) COSMO_JT_IPT(1024)
-          else if (bk.fnt == 512) COSMO_JT_IPT(512)
-          else if (bk.fnt == 256) COSMO_JT_IPT(256)
-          else COSMO_JT_IPT(128)
-#undef COSMO_JT_IPT
-#undef COSMO_JT_LAUNCH
-          return;
-        }
-        const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.fnt) : psd_fwd_smem<T>(bk.maxp, bk.fnt);
-        if (bk.fnt == 512)
-          k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
-        else if (bk.fnt == 256)
-          k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
-        else
-          k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, sp.lam, sp.U, opt.eig_tol, opt.eig_max_sweeps, flags, bk.start, stats, up);
+        psd_fwd_bucket(bk, s, io, sp.lam, sp.U, (opt.eig_warm_start && bk.warm_fits) ? U_prev : nullptr, flags, stats);
       });
     }
+  }
+
+  // the forward projection of one PSD class (kernel chosen by the class's method / variant / CTA size)
+  void psd_fwd_bucket(const Bucket& bk, cudaStream_t s, const PsdIterIO<T>& io, T* lam, T* U, const T* up,
+                      int32_t* fl, unsigned long long* stt) {
+    if (bk.method == 1) {
+      k_psd_fwd_tql<T, V, 256><<<bk.count, 256, tql_smem<T>(bk.maxp, 256), s>>>(P, io, lam, U, fl, bk.start, stt, 30 * 4);
+      return;
+    }
+    if (bk.variant == 2) {
+      const size_t sm = jt_smem<T>(bk.maxp, bk.fnt);
+#define COSMO_JT_LAUNCH(NT_, IPT_) \
+  k_psd_fwd_jt<T, V, NT_, IPT_><<<bk.count, NT_, sm, s>>>(P, io, lam, U, opt.eig_tol, opt.eig_max_sweeps, fl, bk.start, stt, up)
+#define COSMO_JT_IPT(NT_) \
+  { if (bk.tpt == 2) COSMO_JT_LAUNCH(NT_, 2); else if (bk.tpt == 4) COSMO_JT_LAUNCH(NT_, 4); else COSMO_JT_LAUNCH(NT_, 8); }
+      if (bk.fnt == 1024) COSMO_JT_IPT(1024)
+      else if (bk.fnt == 512) COSMO_JT_IPT(512)
+      else if (bk.fnt == 256) COSMO_JT_IPT(256)
+      else COSMO_JT_IPT(128)
+#undef COSMO_JT_IPT
+#undef COSMO_JT_LAUNCH
+      return;
+    }
+    const size_t sm = up ? psd_fwd_smem_warm<T>(bk.maxp, bk.fnt) : psd_fwd_smem<T>(bk.maxp, bk.fnt);
+    if (bk.fnt == 512)
+      k_psd_fwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, lam, U, opt.eig_tol, opt.eig_max_sweeps, fl, bk.start, stt, up);
+    else if (bk.fnt == 256)
+      k_psd_fwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, lam, U, opt.eig_tol, opt.eig_max_sweeps, fl, bk.start, stt, up);
+    else
+      k_psd_fwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, lam, U, opt.eig_tol, opt.eig_max_sweeps, fl, bk.start, stt, up);
+  }
+
+  // the Daleckii-Krein backward of one PSD class
+  void psd_bwd_bucket(const Bucket& bk, cudaStream_t s, const PsdBwdIO<T>& io, const T* lam, const T* U,
+                      int32_t* fl) {
+    if (bk.method == 1) {
+      k_psd_bwd_global<T, V, 256><<<bk.count, 256, 0, s>>>(P, io, lam, U, dk_work, opt.dk_gap_tau, bk.start);
+      return;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (opt.dk_tensor_cores && bk.maxp <= DK_TC_MAXP) {
+        k_psd_bwd_tc<V><<<bk.count, DK_TC_NT, dk_tc_smem(bk.maxp), s>>>(P, io, lam, U, opt.dk_gap_tau, bk.start, fl);
+        return;
+      }
+    }
+    const size_t sm = psd_bwd_smem<T>(bk.maxp, bk.nt);
+    if (bk.nt == 512)
+      k_psd_bwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, lam, U, opt.dk_gap_tau, bk.start);
+    else if (bk.nt == 256)
+      k_psd_bwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, lam, U, opt.dk_gap_tau, bk.start);
+    else
+      k_psd_bwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, lam, U, opt.dk_gap_tau, bk.start);
   }
 
   // run steps [k0, k1) of segment seg (slot 0 holds z^{k0})
@@ -1006,27 +1284,7 @@ struct ImplT : Impl {
     if (P.nsoc) launch("soc_bwd", k_soc_bwd<T, V>, grid_for((int64_t)P.nsoc * 32, 256, INT32_MAX), 256, 0, st, P, q);
     if (P.npsd) {
       PsdBwdIO<T> io{gproj, vbar, P.row_inst};
-      psd_group("psd_bwd", st, [&](const Bucket& bk, cudaStream_t s) {
-        if (bk.method == 1) {
-          k_psd_bwd_global<T, V, 256><<<bk.count, 256, 0, s>>>(P, io, q.lam, q.U, dk_work,
-                                                               opt.dk_gap_tau, bk.start);
-          return;
-        }
-        if constexpr (std::is_same<T, float>::value) {
-          if (opt.dk_tensor_cores && bk.maxp <= DK_TC_MAXP) {
-            k_psd_bwd_tc<V><<<bk.count, DK_TC_NT, dk_tc_smem(bk.maxp), s>>>(P, io, q.lam, q.U, opt.dk_gap_tau,
-                                                                            bk.start, flags);
-            return;
-          }
-        }
-        const size_t sm = psd_bwd_smem<T>(bk.maxp, bk.nt);
-        if (bk.nt == 512)
-          k_psd_bwd<T, V, 512><<<bk.count, 512, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
-        else if (bk.nt == 256)
-          k_psd_bwd<T, V, 256><<<bk.count, 256, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
-        else
-          k_psd_bwd<T, V, 128><<<bk.count, 128, sm, s>>>(P, io, q.lam, q.U, opt.dk_gap_tau, bk.start);
-      });
+      psd_group("psd_bwd", st, [&](const Bucket& bk, cudaStream_t s) { psd_bwd_bucket(bk, s, io, q.lam, q.U, flags); });
     }
     launch("bwd_relax", k_bwd_relax<T, V, 256>, h.ninst, 256, 0, st, P, q);
     CgArgs<T> ca{};
@@ -1618,6 +1876,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->cg_cluster = 0;
   o->eig_variant = 0;
   o->eig_threads = 0;
+  o->autotune = 0;
   o->loss_kind = 0;
   return COSMO_OK;
 }
@@ -1643,6 +1902,7 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
       !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
       !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 2 ||
+      !(o.autotune == 0 || o.autotune == 1) ||
       !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512 ||
         (o.eig_threads == 1024 && o.eig_variant != 1)))
     return fail(COSMO_E_INVAL, "invalid options");
@@ -1682,6 +1942,20 @@ cosmo_status cosmo_batch_destroy(cosmo_batch* b) {
   cudaDeviceSynchronize();
   delete b;
   return COSMO_OK;
+}
+
+cosmo_status cosmo_batch_get_tuning(const cosmo_batch* b, cosmo_tuning* out) {
+  g_err.clear();
+  if (!b || !out) return fail(COSMO_E_INVAL, "null argument");
+  b->impl->get_tuning(out);
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_batch_set_tuning(cosmo_batch* b, const cosmo_tuning* t) {
+  g_err.clear();
+  if (!b || !t) return fail(COSMO_E_INVAL, "null argument");
+  CU(cudaSetDevice(b->opt.device));
+  return b->impl->set_tuning(*t);
 }
 
 cosmo_status cosmo_batch_get_info(const cosmo_batch* b, cosmo_batch_info* out) {

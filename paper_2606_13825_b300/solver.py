@@ -174,6 +174,34 @@ class CosmoBatch:
         check(lib().cosmo_batch_get_info(self._h, byref(inf)))
         return {f: getattr(inf, f) for f, _ in inf._fields_}
 
+    def tuning(self):
+        """The launch configuration (PSD classes with their eigensolver method
+        and CTA size, the CG kernel), as chosen by the shape rules or by the
+        autotuner (option autotune=1)."""
+        t = _abi.Tuning()
+        check(lib().cosmo_batch_get_tuning(self._h, byref(t)))
+        k = t.n_classes
+        return {"classes": [{"maxp": t.class_maxp[i], "count": t.class_count[i],
+                             "method": "jacobi" if t.class_method[i] == 0 else "ql",
+                             "threads": t.class_threads[i]} for i in range(k)],
+                "cg_kernel": t.cg_kernel, "tuned": bool(t.tuned), "tune_ms": t.tune_ms}
+
+    def set_tuning(self, tuning):
+        """Impose a configuration returned by tuning() (of this batch or of
+        another batch of the same shapes)."""
+        t = _abi.Tuning()
+        cl = tuning["classes"]
+        t.n_classes = len(cl)
+        for i, c in enumerate(cl):
+            t.class_maxp[i] = c["maxp"]
+            t.class_count[i] = c["count"]
+            t.class_method[i] = 0 if c["method"] == "jacobi" else 1
+            t.class_threads[i] = c["threads"]
+        t.cg_kernel = tuning["cg_kernel"]
+        t.tuned = 1 if tuning.get("tuned") else 0
+        t.tune_ms = float(tuning.get("tune_ms", 0.0))
+        check(lib().cosmo_batch_set_tuning(self._h, byref(t)))
+
     def zeros(self, *shape, dtype=None):
         return torch.zeros(*shape, dtype=dtype or self.dtype, device=self.device)
 
