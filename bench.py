@@ -53,8 +53,10 @@ def workload_spec(name, rank=0):
     from synth import (lovasz_problem, random_graph_batch, cycle_graph, complete_graph,
                        socp_problem, covsteer_problem)
     if name == "maxcut":
-        return dict(probs=problems(rank), K=K_UNROLL, opts={}, value_type="f32", learn_start=False,
-                    metric=METRIC, desc=WORKLOAD)
+        # the library defaults (one CUDA graph per forward / backward) with the
+        # autotuner choosing the Jacobi CTA sizes of the PSD size classes
+        return dict(probs=problems(rank), K=K_UNROLL, opts={"use_graph": 1, "autotune": 1}, value_type="f32",
+                    learn_start=False, metric=METRIC, desc=WORKLOAD)
     if name == "lovasz":
         graphs = random_graph_batch(64, 3000 + rank * 64, 100, 200, 0.5, 0.5)
         probs = [lovasz_problem(nv, e) for nv, e in graphs]
@@ -225,7 +227,21 @@ def _smallest_job(K):
 
 
 # ------------------------------------------------------------ App. B CG --
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on the B300s (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except Exception:
+        return 6400.0, "fallback 6.4 TB/s (of fallback)"
+
+
 def run_linsys(args, n=50000):
+    print(json.dumps(linsys_record(args, n)))
+    return 0
+
+
+def linsys_record(args, n=50000):
     """Reduced-system solve (P + sigma I + A'D(rho)A) x = A'(rho o b) of the
     App. B instance (P diagonal U(0,10), A n/2 x n with 1% N(0,1) nonzeros,
     rho ~ U(0,1)), mixed precision, through a prepared plan (streamed layout
@@ -257,6 +273,9 @@ def run_linsys(args, n=50000):
         return 0
     stream = torch.cuda.current_stream()
     times, its = [], []
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -265,6 +284,7 @@ def run_linsys(args, n=50000):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e-3)
         its.append(int(iters[0]))
+    clk = clocks.stop()
     # per-phase breakdown from one more solve with the plan's phase timer on
     # (not part of the timed steps)
     plan.set_timing(True)
@@ -275,22 +295,21 @@ def run_linsys(args, n=50000):
     nnzA, nnzP = A.nnz, d["P"].nnz
     bytes_it = (nnzP + 2 * nnzA) * 8 + 4 * (2 * n + m) + 6 * n * 4
     t_it = sum(times) / sum(its)
-    peak = 6478.6
+    peak, peak_src = measured_hbm_gbs()
     line = {"metric": "App. B reduced-system CG iterations/sec (n=5e4, m=n/2, A 1% dense)",
             "value": 1.0 / t_it, "unit": "CG iterations/s", "iterations_per_solve": its[0],
             "ms_per_solve": 1e3 * float(np.mean(times)), "plan_build_s": t_plan,
             "roofline": {"bound": "hbm", "achieved": bytes_it / t_it / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": bytes_it / t_it / 1e9 / peak,
-                         "bytes_per_iteration": bytes_it, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                         "bytes_per_iteration": bytes_it, "peak_source": peak_src,
                          "timing": "CUDA events around each solve (preconditioner + one cooperative "
                                    "launch), the setup iteration and the discarded last matvec "
                                    "included"},
-            "plan": info, "phases_per_iteration": phases,
+            "clocks": clk, "plan": info, "phases_per_iteration": phases,
             "config": {"workload": "App. B linear system", "n": n, "m": m, "nnzA": nnzA,
                        "precision": "float values/vectors, double reductions", "tol": 1e-6,
                        "l2": "A and A' (200 MB) exceed L2 each iteration"}}
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_solve(args):
@@ -490,7 +509,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-instance-per-launch forms")
+    ap.add_argument("--no-linsys", action="store_true", help="skip the App. B CG record")
     ap.add_argument("--profile", action="store_true",
                     help="run only W steps of the workload (the command profiled under ncu)")
     ap.add_argument("--workload", default="maxcut",
@@ -557,6 +577,13 @@ def main():
         L.backward()
         return L
 
+    has_psd = any(ct == 4 for p in probs for (ct, _) in p.cones)
+    dom = "psd_fwd" if has_psd else "pcg"          # dominant kernel class
+    # CUDA events around every launch group of the dominant class: with CUDA
+    # graphs they are event nodes of the recorded graphs, read back after
+    # each replay, so the roofline kernel is timed inside the timed region
+    if not args.profile:
+        b.profile(dom)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -566,11 +593,7 @@ def main():
         return 0
 
     # ---------------- timed region: K steps, L2 flushed between steps -------
-    has_psd = any(ct == 4 for p in probs for (ct, _) in p.cones)
-    dom = "psd_fwd" if has_psd else "pcg"          # dominant kernel class
-    if not use_graph:
-        b.profile(dom)
-        b.profile_read(dom, reset=True)
+    b.profile_read(dom, reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -596,12 +619,8 @@ def main():
     t_wall = time.perf_counter() - t_wall
     launches = lib().cosmo_kernel_launch_count() - n0
     clk = clocks.stop()
-    # the roofline kernel is timed live in the timed region (direct launches);
-    # graph-launched workloads time it in a separate direct-launch batch below
-    dom_ms, dom_n = (0.0, 0)
-    if not use_graph:
-        dom_ms, dom_n = b.profile_read(dom, reset=True)
-        b.profile(enable=False)
+    # the roofline kernel, timed live in the timed region
+    dom_ms, dom_n = b.profile_read(dom, reset=True)
     if dist:
         from paper_2606_13825_b300.dist import max_over_ranks
         total_ms = max_over_ranks(total_ms, device=dev)
@@ -619,10 +638,12 @@ def main():
             "adjoint_cg_iters_per_solve": inf["adj_cg_iters"] / max(inf["adj_cg_solves"], 1)}
 
     # ---------------- per-kernel breakdown (one extra step, all classes) ----
+    tuning = b.tuning()
     bb = b
     if use_graph:
         bb = CosmoBatch(probs, precision="mixed", value_type=spec["value_type"], device=local,
-                        use_graph=0, **opts)
+                        use_graph=0, **dict(opts, autotune=0))
+        bb.set_tuning(tuning)
         step(bb)
         torch.cuda.synchronize()
     bb.profile(None)
@@ -634,9 +655,8 @@ def main():
         ms, n = bb.profile_read(kname, reset=False)
         if n:
             breakdown[kname] = round(ms, 4)
-    if use_graph:
-        dom_ms, dom_n = bb.profile_read(dom, reset=False)
     bb.profile(enable=False)
+    b.profile(enable=False)
 
     # ---------------- roofline of the dominant kernel ------------------------
     avg_s = dom_ms / max(dom_n, 1) / 1e3
@@ -660,16 +680,11 @@ def main():
         it_per_solve = inf0["cg_iters"] / max(inf0["cg_solves"], 1)
         bytes_per_it = (2 * nnzA + nnzP) * (vb + 4) + 8 * 4 * sum(p.A.shape[1] for p in probs)
         bytes_launch = bytes_per_it * it_per_solve
-        peak = 6478.6
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                peak = float(json.load(f).get("hbm_gbs", peak))
-        except Exception:
-            pass
+        peak, peak_src = measured_hbm_gbs()
         achieved = bytes_launch / avg_s / 1e9
         roof = {"kernel": "pcg (Jacobi-PCG, CTA per instance, matrix-free SpMV with A, A', P)",
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3, "launches_timed": dom_n,
                 "algorithmic_count": "per CG iteration (2 nnz(A) + nnz(P)) x (value + int32 index) "
                                      "+ 8 n x 4 bytes, times the mean CG iterations per solve"}
@@ -693,13 +708,15 @@ def main():
            "api": "cosmo_step_host (host log_rho_k, alpha_k in; loss and gradients out; pinned)"}
 
     # ---------------- plain FP64 one-instance-per-launch GPU form ------------
-    plain = None
-    if not args.no_plain:
+    def one_instance_form(precision):
+        """One instance per batch and per launch (direct launches), on a
+        seeded sample of the workload's instances."""
         rng = np.random.default_rng(1)
         sample = rng.choice(n_inst, size=min(8, n_inst) if args.workload == "maxcut" else 2, replace=False)
         tot, iters = 0.0, 0
+        o1 = {k: v for k, v in opts.items() if k not in ("autotune",)}
         for i in sample:
-            b1 = CosmoBatch([probs[i]], precision="fp64", device=local, use_graph=0, **opts)
+            b1 = CosmoBatch([probs[i]], precision=precision, device=local, use_graph=0, **o1)
             l1 = torch.full((K,), math.log(0.1), dtype=torch.float64, device=dev, requires_grad=True)
             a1 = torch.full((K,), 1.6, dtype=torch.float64, device=dev, requires_grad=True)
             L, _ = unrolled_residual_loss(b1, l1, a1)
@@ -715,13 +732,21 @@ def main():
             tot += e0.elapsed_time(e1) / 1e3
             iters += K
             del b1
-        plain = {"value": iters / tot, "unit": "instance-iters/s",
-                 "sample": f"{len(sample)} instances (seeded choice, n={sorted(int(probs[i].A.shape[1]) for i in sample)}), "
-                           f"each its own FP64 batch, direct launches, K={K} fwd+bwd"}
+        return {"value": iters / tot, "unit": "instance-iters/s",
+                "sample": f"{len(sample)} instances (seeded choice, n={sorted(int(probs[i].A.shape[1]) for i in sample)}), "
+                          f"each its own {'FP64' if precision == 'fp64' else 'mixed-precision (FP32)'} batch, "
+                          f"direct launches, K={K} fwd+bwd"}
+
+    plain = plain32 = None
+    if not args.no_plain:
+        plain = one_instance_form("fp64")
+        plain32 = one_instance_form("mixed")
 
     cpu = None
     if not args.no_cpu and args.workload == "maxcut":
-        cpu = cpu_oracle_sample(4, K, min(4, os.cpu_count() or 1))
+        ncpu = os.cpu_count() or 1
+        cpu = cpu_oracle_sample(16, K, min(16, ncpu))
+        cpu["host_cores"] = ncpu
 
     line = {"metric": spec["metric"], "value": value, "unit": "instance-iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -730,14 +755,25 @@ def main():
             "config": {"workload": spec["desc"], "instances_per_gpu": n_inst, "K": K,
                        "precision": "float iterates, double CG/residual/eigen-gap reductions",
                        "l2": "flushed between steps (256 MB write, outside the events)",
-                       "launch": ("one CUDA graph per forward / backward" if use_graph else
-                                  "direct launches on the current stream (CUDA graphs are the library "
-                                  "default; off here so per-kernel CUDA events can be recorded)"),
+                       "launch": ("one CUDA graph per forward / backward (the library default); the "
+                                  f"roofline kernel class ({dom}) timed by CUDA-event nodes inside the graphs"
+                                  if use_graph else "direct launches on the current stream"),
+                       "tuning": {"autotune": bool(opts.get("autotune", 0)), "tuned": tuning["tuned"],
+                                  "psd_classes": [f"p<={c['maxp']} x{c['count']}: {c['method']} "
+                                                  f"{c['threads']} threads" for c in tuning["classes"]],
+                                  "cg_kernel": tuning["cg_kernel"], "tune_ms": round(tuning["tune_ms"], 1)},
                        "parallelism": f"dp{world} (independent instances per GPU, no collective)"},
             "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
             "cpu_baseline": cpu, "plain_fp64": plain,
             "ratio_vs_plain_fp64": (value / world) / plain["value"] if plain else None,
+            "plain_fp32_one_instance": plain32,
+            "ratio_vs_plain_fp32_one_instance": (value / world) / plain32["value"] if plain32 else None,
+            "ratio_fp32_vs_fp64_one_instance": plain32["value"] / plain["value"] if plain else None,
             "kernel_ms_per_step": breakdown, "work": work, "wall_s_timed": t_wall}
+    if args.workload == "maxcut" and not args.no_linsys:
+        # the HBM-bound CG of the reduced system at App. B scale, its own
+        # timed region and clock record
+        line["linsys"] = linsys_record(args)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -437,8 +437,11 @@ cosmo_status cosmo_step_host(cosmo_batch* batch, int32_t K, double sigma, double
  * timing off, otherwise only launches of that kernel class are timed.
  * Classes: rho_check rho_rectify alpha_check precond rhs pcg post soc_fwd
  * psd_fwd residuals loss_seed bwd_gproj soc_bwd psd_bwd bwd_relax pcg_adj
- * bwd_solve rect_adjoint.  Timing applies to direct launches only
- * (options.use_graph = 0); launches replayed from a CUDA graph are not timed. */
+ * bwd_solve rect_adjoint.  With CUDA graphs (options.use_graph = 1) the
+ * events are recorded as event nodes of the graph and read back after each
+ * replay (the next forward / backward, or cosmo_profile_read, waits for the
+ * previous replay to finish); a change of what is timed drops the recorded
+ * graphs, which are recorded again at the next call. */
 cosmo_status cosmo_profile_enable(cosmo_batch* batch, const char* kernel);
 /* Sum of the timed durations (ms) and number of timed launches of `kernel`
  * (NULL = all classes) since the last reset; synchronises on the recorded

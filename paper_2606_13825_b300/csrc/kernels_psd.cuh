@@ -542,33 +542,27 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
   }
   __syncthreads();
   if (warm) {
-    // previous step's eigenvectors as rows, then one Newton-Schulz step
-    // Vt <- 1.5 Vt - 0.5 (Vt Vt') Vt to restore orthogonality
+    // previous step's eigenvectors as rows (orthogonal to rounding: every
+    // step hands over re-orthogonalised vectors, see below)
     const T* Up = U_prev + P.psd_uoff[blk];
     for (int e = threadIdx.x; e < p * p; e += NT) {
       const int j = e / p, i = e - j * p;
       Vt[j * ldv + i] = Up[e];
     }
-    __syncthreads();
-    smem_gemm_auto<T>(p, Vt, ldv, 1, Vt, 1, ldv, [&](int i, int j, T v) { X[i * lds + j] = v; });
-    __syncthreads();
-    smem_gemm_auto<T>(p, X, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
-    __syncthreads();
-    for (int e = threadIdx.x; e < p * p; e += NT) {
-      const int i = e / p, j = e - i * p;
-      Vt[i * ldv + j] = T(1.5) * Vt[i * ldv + j] - T(0.5) * S[i * lds + j];
+  }
+  // S = smat(v), v = alpha s~ + (1 - alpha) s + y / rho
+  auto load_S = [&]() {
+    for (int e = threadIdx.x; e < d; e += NT) {
+      int i, j;
+      svec_ij(e, i, j);
+      const int64_t r = row0 + e;
+      T v = al * io.st[r] + (T(1) - al) * io.s[r] + io.y[r] / rh;
+      if (i != j) v *= (T)kInvSqrt2;
+      S[i * lds + j] = v;
+      S[j * lds + i] = v;
     }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < d; e += NT) {
-    int i, j;
-    svec_ij(e, i, j);
-    const int64_t r = row0 + e;
-    T v = al * io.st[r] + (T(1) - al) * io.s[r] + io.y[r] / rh;
-    if (i != j) v *= (T)kInvSqrt2;
-    S[i * lds + j] = v;
-    S[j * lds + i] = v;
-  }
+  };
+  load_S();
   __syncthreads();
   if (warm) {
     // B = V' S V (upper triangle read below), nearly diagonal when the
@@ -608,14 +602,37 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
       atomicAdd(&stats[1], 1ull);
     }
   }
-  T* lamv = sm.lamv;
-  for (int s = threadIdx.x; s < pe; s += NT) {
-    const int i = jt_slot_index(0, s, np);
-    if (i < p) {
-      const int E = jt_tile(s >> 1, s >> 1);
-      lamv[i] = (s & 1) ? fin[3 * ntri + E] : fin[E];
-    }
+  (void)fin;   // the refinement below starts again from S and the rotated basis
+  // Refinement.  In FP32 the accumulated rotations leave Vt orthogonal only to
+  // about sqrt(#rotations) * eps (a few 1e-6 over a cold solve), which alone
+  // would put a few 1e-6 of relative error in the projection and in the
+  // Daleckii-Krein backward.  So (1) one Newton-Schulz step Vt <- 1.5 Vt -
+  // 0.5 (Vt Vt') Vt restores orthogonality to rounding; (2) a Rayleigh-Ritz
+  // step in that basis, A = Vt S Vt' (S formed again from the iterate), gives
+  // the eigenvalues as its diagonal L and leaves its off-diagonal E, of the
+  // size of the solver's stopping tolerance; (3) Pi(S) = Vt' (max(L, 0) +
+  // G o E) Vt (Eq. psd-proj), where G is the Loewner matrix of max(x, 0) at L
+  // (Eq. lowner: the Daleckii-Krein derivative the backward applies), which
+  // removes the O(||E||) error of dropping E.  G of two same-sign eigenvalues
+  // is 1 or 0 without a division, and of mixed signs l+ / (l+ - l-) (no
+  // cancellation).
+  smem_gemm_auto<T>(p, Vt, ldv, 1, Vt, 1, ldv, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  __syncthreads();
+  smem_gemm_auto<T>(p, X, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += NT) {
+    const int i = e / p, j = e - i * p;
+    Vt[i * ldv + j] = T(1.5) * Vt[i * ldv + j] - T(0.5) * S[i * lds + j];
   }
+  __syncthreads();
+  load_S();
+  __syncthreads();
+  smem_gemm_auto<T>(p, Vt, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  __syncthreads();
+  smem_gemm_auto<T>(p, X, lds, 1, Vt, 1, ldv, [&](int i, int j, T v) { S[i * lds + j] = v; });
+  __syncthreads();
+  T* lamv = sm.lamv;
+  for (int i = threadIdx.x; i < p; i += NT) lamv[i] = S[i * lds + i];
   __syncthreads();
   // tape: eigenvalues and eigenvectors (column-major per block: column k = row k of Vt)
   T* lam = lam_slot + P.psd_loff[blk];
@@ -625,40 +642,36 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
     const int k = e / p, i = e - k * p;
     U[e] = Vt[k * ldv + i];
   }
-  // reconstruction from the smaller of the positive / non-positive sets
-  int* sel = sm.sel;
-  if (threadIdx.x == 0) {
-    int npos = 0;
-    for (int k = 0; k < p; ++k) npos += lamv[k] > T(0);
-    const bool usepos = npos <= p - npos;
-    int c = 0;
-    for (int k = 0; k < p; ++k)
-      if ((lamv[k] > T(0)) == usepos) sel[c++] = k;
-    sel[p] = c;
-    sel[p + 1] = usepos;
-  }
-  __syncthreads();
-  const int nsel = sel[p];
-  const bool usepos = sel[p + 1] != 0;
+  // M = max(L, 0) + G o E in place of A (upper triangle read, both written)
   for (int e = threadIdx.x; e < d; e += NT) {
     int i, j;
     svec_ij(e, i, j);
-    T acc = T(0);
-    for (int q = 0; q < nsel; ++q) {
-      const int k = sel[q];
-      acc += lamv[k] * Vt[k * ldv + i] * Vt[k * ldv + j];
+    if (i == j) {
+      S[i * lds + i] = lamv[i] > T(0) ? lamv[i] : T(0);
+      continue;
     }
+    const T li = lamv[i], lj = lamv[j];
+    T g;
+    if (li > T(0) && lj > T(0)) g = T(1);
+    else if (!(li > T(0)) && !(lj > T(0))) g = T(0);
+    else g = li > T(0) ? li / (li - lj) : lj / (lj - li);
+    const T v = g * S[i * lds + j];
+    S[i * lds + j] = v;
+    S[j * lds + i] = v;
+  }
+  __syncthreads();
+  // W = M Vt into X, then Pi = Vt' W into S
+  smem_gemm_auto<T>(p, S, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  __syncthreads();
+  smem_gemm_auto<T>(p, Vt, 1, ldv, X, lds, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
+  __syncthreads();
+  for (int e = threadIdx.x; e < d; e += NT) {
+    int i, j;
+    svec_ij(e, i, j);
+    T out = S[i * lds + j];
+    if (i != j) out *= (T)kSqrt2;
     const int64_t r = row0 + e;
     const T sh = al * io.st[r] + (T(1) - al) * io.s[r];
-    T out;
-    if (usepos) {
-      out = acc;
-    } else {
-      T sij = sh + io.y[r] / rh;            // svec entry of S
-      if (i != j) sij *= (T)kInvSqrt2;
-      out = sij - acc;
-    }
-    if (i != j) out *= (T)kSqrt2;
     const T yn = io.y[r] + rh * (sh - out);
     io.sn[r] = out;
     io.yn[r] = yn;

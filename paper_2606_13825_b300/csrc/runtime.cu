@@ -457,8 +457,11 @@ struct ImplT : Impl {
   int prof_mode = 0;            // 0 off, 1 every kernel, 2 kernels whose tag == prof_tag
   std::string prof_tag;
   bool capturing = false;
-  struct Rec { const char* tag; cudaEvent_t e0, e1; };
+  // graph: the events are nodes of a recorded CUDA graph (recorded again at
+  // every replay; collected after each replay, never returned to the pool)
+  struct Rec { const char* tag; cudaEvent_t e0, e1; bool graph; };
   std::vector<Rec> prof_pending;
+  std::vector<Rec> cap_recs, gfwd_recs, gbwd_recs;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<std::string, std::pair<double, int64_t>>> prof_acc;
 
@@ -467,7 +470,9 @@ struct ImplT : Impl {
     if (sv_run_h) cudaFreeHost(sv_run_h);
     for (auto& bk : buckets) { if (bk.s) cudaStreamDestroy(bk.s); if (bk.done) cudaEventDestroy(bk.done); }
     if (ev_fork) cudaEventDestroy(ev_fork);
-    for (auto& r : prof_pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto& r : prof_pending) if (!r.graph) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto* v : {&gfwd_recs, &gbwd_recs})
+      for (auto& r : *v) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto e : ev_pool) cudaEventDestroy(e);
     if (gfwd) cudaGraphExecDestroy(gfwd);
     if (gbwd) cudaGraphExecDestroy(gbwd);
@@ -723,6 +728,8 @@ struct ImplT : Impl {
   void drop_graphs() {
     if (gfwd) { cudaGraphExecDestroy(gfwd); gfwd = nullptr; }
     if (gbwd) { cudaGraphExecDestroy(gbwd); gbwd = nullptr; }
+    release_recs(gfwd_recs);
+    release_recs(gbwd_recs);
     gfwd_key[0] = -1;
   }
   cosmo_status apply_tune(const TuneResult& r) {
@@ -911,8 +918,7 @@ struct ImplT : Impl {
   cosmo_status ensure_tape(int32_t newK) {
     int32_t c = opt.checkpoint_every > 0 ? std::min(opt.checkpoint_every, newK) : newK;
     if (newK == K && c == cK && xs) return COSMO_OK;
-    if (gfwd) { cudaGraphExecDestroy(gfwd); gfwd = nullptr; }
-    if (gbwd) { cudaGraphExecDestroy(gbwd); gbwd = nullptr; }
+    drop_graphs();
     CU(cudaDeviceSynchronize());
     tarena.release();
     tape_valid = false;
@@ -943,35 +949,43 @@ struct ImplT : Impl {
     return e;
   }
 
-  template <class Kern, class... Args>
-  void launch(const char* tag, Kern kern, int grid, int block, size_t smem, cudaStream_t st,
-              Args... args) {
-    const bool rec = prof_mode != 0 && !capturing && (prof_mode == 1 || prof_tag == tag);
-    Rec r{tag, nullptr, nullptr};
-    if (rec) {
+  // CUDA-event timing of a launch (or launch group) of class `tag`; inside a
+  // stream capture the events become event-record nodes of the graph
+  Rec rec_begin(const char* tag, cudaStream_t st) {
+    Rec r{tag, nullptr, nullptr, capturing};
+    if (prof_mode != 0 && (prof_mode == 1 || prof_tag == tag)) {
       r.e0 = get_event();
       r.e1 = get_event();
-      cudaEventRecord(r.e0, st);
+      if (capturing) cudaEventRecordWithFlags(r.e0, st, cudaEventRecordExternal);
+      else cudaEventRecord(r.e0, st);
     }
-    kern<<<grid, block, smem, st>>>(args...);
-    ++seq_kernels;
-    if (rec) {
+    return r;
+  }
+  void rec_end(const Rec& r, cudaStream_t st) {
+    if (!r.e0) return;
+    if (capturing) {
+      cudaEventRecordWithFlags(r.e1, st, cudaEventRecordExternal);
+      cap_recs.push_back(r);
+    } else {
       cudaEventRecord(r.e1, st);
       prof_pending.push_back(r);
     }
+  }
+
+  template <class Kern, class... Args>
+  void launch(const char* tag, Kern kern, int grid, int block, size_t smem, cudaStream_t st,
+              Args... args) {
+    const Rec r = rec_begin(tag, st);
+    kern<<<grid, block, smem, st>>>(args...);
+    ++seq_kernels;
+    rec_end(r, st);
   }
 
   // the same with a thread-block cluster of cs CTAs along x
   template <class Kern, class... Args>
   void launch_cluster(const char* tag, Kern kern, int grid, int block, size_t smem, cudaStream_t st, int cs,
                       Args... args) {
-    const bool rec = prof_mode != 0 && !capturing && (prof_mode == 1 || prof_tag == tag);
-    Rec r{tag, nullptr, nullptr};
-    if (rec) {
-      r.e0 = get_event();
-      r.e1 = get_event();
-      cudaEventRecord(r.e0, st);
-    }
+    const Rec r = rec_begin(tag, st);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -986,10 +1000,7 @@ struct ImplT : Impl {
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kern, args...);
     ++seq_kernels;
-    if (rec) {
-      cudaEventRecord(r.e1, st);
-      prof_pending.push_back(r);
-    }
+    rec_end(r, st);
   }
 
   // CG launch: one CTA or one cluster of cg_cs CTAs per instance
@@ -1050,13 +1061,7 @@ struct ImplT : Impl {
   // into st (captured as parallel graph branches).  Timed as one group.
   template <class F>
   void psd_group(const char* tag, cudaStream_t st, F launch_bucket) {
-    const bool rec = prof_mode != 0 && !capturing && (prof_mode == 1 || prof_tag == tag);
-    Rec r{tag, nullptr, nullptr};
-    if (rec) {
-      r.e0 = get_event();
-      r.e1 = get_event();
-      cudaEventRecord(r.e0, st);
-    }
+    const Rec r = rec_begin(tag, st);
     if (buckets.size() == 1) {
       launch_bucket(buckets[0], st);
       ++seq_kernels;
@@ -1070,17 +1075,18 @@ struct ImplT : Impl {
       }
       for (auto& bk : buckets) cudaStreamWaitEvent(st, bk.done, 0);
     }
-    if (rec) {
-      cudaEventRecord(r.e1, st);
-      prof_pending.push_back(r);
-    }
+    rec_end(r, st);
   }
 
+  // A change of what is timed drops the recorded graphs: the next forward /
+  // backward records them again with (or without) the event nodes.
   cosmo_status profile_enable(const char* tag) override {
     TRY(profile_collect());
-    if (!tag) { prof_mode = 1; prof_tag.clear(); }
-    else if (!*tag) { prof_mode = 0; prof_tag.clear(); }
-    else { prof_mode = 2; prof_tag = tag; }
+    const int mode = !tag ? 1 : (!*tag ? 0 : 2);
+    const std::string t = mode == 2 ? std::string(tag) : std::string();
+    if (mode != prof_mode || t != prof_tag) drop_graphs();
+    prof_mode = mode;
+    prof_tag = t;
     return COSMO_OK;
   }
   cosmo_status profile_collect() {
@@ -1092,8 +1098,10 @@ struct ImplT : Impl {
       for (auto& a : prof_acc)
         if (a.first == r.tag) { a.second.first += ms; a.second.second += 1; found = true; }
       if (!found) prof_acc.push_back(std::make_pair(std::string(r.tag), std::make_pair((double)ms, (int64_t)1)));
-      ev_pool.push_back(r.e0);
-      ev_pool.push_back(r.e1);
+      if (!r.graph) {
+        ev_pool.push_back(r.e0);
+        ev_pool.push_back(r.e1);
+      }
     }
     prof_pending.clear();
     return COSMO_OK;
@@ -1335,8 +1343,17 @@ struct ImplT : Impl {
   int final_cot = 0;
 
   // run `fn` either captured into a cached graph or directly on st
+  // graph recs: release (after collecting what is pending) when the graph goes
+  cosmo_status release_recs(std::vector<Rec>& recs) {
+    if (recs.empty()) return COSMO_OK;
+    TRY(profile_collect());
+    for (auto& r : recs) { ev_pool.push_back(r.e0); ev_pool.push_back(r.e1); }
+    recs.clear();
+    return COSMO_OK;
+  }
   template <class Fn>
-  cosmo_status run_seq(cudaGraphExec_t& exec, int64_t& nk, bool reuse, Fn fn, cudaStream_t st) {
+  cosmo_status run_seq(cudaGraphExec_t& exec, int64_t& nk, std::vector<Rec>& recs, bool reuse, Fn fn,
+                       cudaStream_t st) {
     if (!opt.use_graph) {
       seq_kernels = 0;
       fn(st);
@@ -1347,11 +1364,15 @@ struct ImplT : Impl {
     }
     if (!(exec && reuse)) {
       if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+      TRY(release_recs(recs));
       seq_kernels = 0;
+      cap_recs.clear();
       CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
       capturing = true;
       fn(cap);
       capturing = false;
+      recs = cap_recs;
+      cap_recs.clear();
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cap, &g);
       if (e != cudaSuccess) return fail(COSMO_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
@@ -1359,6 +1380,11 @@ struct ImplT : Impl {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) { exec = nullptr; return fail(COSMO_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e)); }
       nk = seq_kernels;
+    }
+    if (!recs.empty()) {
+      // the previous replay's events are read before they are recorded again
+      TRY(profile_collect());
+      for (auto& r : recs) prof_pending.push_back(r);
     }
     CU(cudaGraphLaunch(exec, st));
     launched += nk;
@@ -1395,7 +1421,7 @@ struct ImplT : Impl {
     const bool want_loss = loss != nullptr || tape;
     const bool reuse = gfwd_key[0] == K && gfwd_key[1] == (int)want_loss && gfwd_key[2] == (int)pol_mode &&
                        gfwd_sigma == sg;
-    TRY(run_seq(gfwd, gfwd_nk, reuse, [&](cudaStream_t s) { enqueue_forward(want_loss, s); }, st));
+    TRY(run_seq(gfwd, gfwd_nk, gfwd_recs, reuse, [&](cudaStream_t s) { enqueue_forward(want_loss, s); }, st));
     gfwd_key[0] = K; gfwd_key[1] = (int)want_loss; gfwd_key[2] = (int)pol_mode; gfwd_sigma = sg;
     seg_in_buffer = nseg - 1;
     tape_valid = tape != 0;
@@ -1443,7 +1469,7 @@ struct ImplT : Impl {
       CU(cudaMemsetAsync(rd, 0, sizeof(T) * n, st));
     }
     const bool reuse = gbwd_sigma == sigma_h && gbwd != nullptr;
-    TRY(run_seq(gbwd, gbwd_nk, reuse, [&](cudaStream_t s) { enqueue_backward(true, s); }, st));
+    TRY(run_seq(gbwd, gbwd_nk, gbwd_recs, reuse, [&](cudaStream_t s) { enqueue_backward(true, s); }, st));
     gbwd_sigma = sigma_h;
     seg_in_buffer = nseg > 1 ? 0 : nseg - 1;
     const int c = final_cot;  // each reverse step swaps the cotangent buffers
