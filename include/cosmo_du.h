@@ -454,6 +454,16 @@ cosmo_status cosmo_profile_read(cosmo_batch* batch, const char* kernel, double* 
  * device.  Returns COSMO_OK even when flags are set. */
 cosmo_status cosmo_status_sync(cosmo_batch* batch, int32_t* flags_host);
 
+/* Eigenvalues of every PSD block at unrolled step k of the last forward that
+ * kept a tape (the projection input of that step, Eq. psd-proj), copied into
+ * lam (device real, sum of p over blocks, block order as in the problem) on
+ * `stream`.  A diagnostic of the path: an eigenvalue near zero is a kink of
+ * the projection, where FP32 and FP64 trajectories may take different
+ * branches.  With checkpointing only the steps of the segment in the buffer
+ * (the last one after a forward) are available.  Errors: E_INVAL (k out of
+ * range, no PSD block), E_STATE (no tape, or step k not in the buffer). */
+cosmo_status cosmo_tape_eigenvalues(cosmo_batch* batch, int32_t k, void* lam, void* stream);
+
 /* ---- standalone kernels (each is one step of the path, usable alone) ---- */
 
 /* Matrix-free solve of the reduced system of Sec. 2.3, Eq. (reduced):

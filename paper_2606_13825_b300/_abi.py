@@ -118,6 +118,7 @@ _SIGS = {
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_status_sync": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "cosmo_tape_eigenvalues": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "cosmo_profile_enable": (c_int32, [c_void_p, c_char_p]),
     "cosmo_profile_read": (c_int32, [c_void_p, c_char_p, POINTER(c_double), POINTER(c_int64),
                                      c_int32]),

@@ -202,6 +202,14 @@ class CosmoBatch:
         t.tune_ms = float(tuning.get("tune_ms", 0.0))
         check(lib().cosmo_batch_set_tuning(self._h, byref(t)))
 
+    def tape_eigenvalues(self, k):
+        """Eigenvalues of every PSD block at step k of the last taped forward
+        (sum of p over blocks, problem order)."""
+        c = np.asarray(self.packed.cones).reshape(-1, 2)
+        lam = torch.empty(int(c[c[:, 0] == 4, 1].sum()), dtype=self.dtype, device=self.device)
+        check(lib().cosmo_tape_eigenvalues(self._h, int(k), _tp(lam), _stream()))
+        return lam
+
     def zeros(self, *shape, dtype=None):
         return torch.zeros(*shape, dtype=dtype or self.dtype, device=self.device)
 

@@ -98,15 +98,23 @@ def test_full_size_batched_maxcut(config2):
     xs_d, ss_d, ys_d = d["x"], d["s"], d["y"]
     ro, co = bm.packed.row_off, bm.packed.col_off
     # Mixed vs FP64 on every instance.  Objective: the 1e-4 gate, relative to
-    # the value (measured max 1.5e-5).  Residual norms: within 1e-4 of the
-    # OSQP-style normaliser (App. E; measured max 1.9e-5).  Strict
-    # value-relative residual/loss errors reach 1e-2 on instances whose
-    # residual is small, because FP32 iterates and an FP32 eigensolver carry
-    # an absolute error of eps32 * ||S||_F per step; they are reported, not
-    # asserted.  Gradients: the 1e-3 gate holds in the median over instances
-    # (measured 8e-4); single instances whose trajectory passes an
-    # eigenvalue through zero (a kink of the projection) differ by more.
-    errs = []
+    # the value.  Residual norms: within 1e-4 of the OSQP-style normaliser
+    # (App. E).  Strict value-relative residual/loss errors reach 1e-3 on
+    # instances whose residual is small (FP32 iterates carry an absolute error
+    # of about eps32 ||S||_F per step); they are reported, not asserted.
+    #
+    # Gradients, per instance: the 1e-3 gate.  The Daleckii-Krein backward
+    # multiplies by the Loewner matrix, whose mixed-sign entries l+ / (l+ - l-)
+    # carry the relative error of the smaller eigenvalue; the FP32 trajectory
+    # perturbs eigenvalues by about 1e-6 of the spectrum's scale, so where the
+    # trajectory brings an eigenvalue within 1e-3 of max|lambda| of zero the
+    # derivative itself is that ill-conditioned.  The margin of an instance is
+    # min over steps and eigenvalues of |lambda| / max(1, max|lambda|), from the
+    # FP64 run's tape.  Asserted: every instance with margin >= 1e-3 meets
+    # 1e-3; no instance takes another branch of the projection (the inertia of
+    # every block at every step is the FP64 run's); at least 98% of all
+    # instances meet 1e-3 and none exceeds 1e-2.
+    errs, erra = [], []
     for i in range(len(config2)):
         pr = config2[i]
         cs, rs = slice(co[i], co[i + 1]), slice(ro[i], ro[i + 1])
@@ -117,7 +125,26 @@ def test_full_size_batched_maxcut(config2):
         assert abs(math.sqrt(rp_m[i]) - math.sqrt(rp_d[i])) <= 1e-4 * scale_p, i
         assert abs(math.sqrt(rd_m[i]) - math.sqrt(rd_d[i])) <= 1e-4 * scale_d, i
         errs.append(rel_l2(grho_m[:, rs], grho_d[:, rs]))
-    assert np.median(errs) < 1e-3, np.median(errs)
+        erra.append(rel_l2(ga_m[:, i], ga_d[:, i]))
+    errs, erra = np.array(errs), np.array(erra)
+    ps = [pr.cones[1][1] for pr in config2]
+    off = np.concatenate([[0], np.cumsum(ps)])
+    margin = np.full(len(config2), np.inf)
+    for k in range(K):
+        lm = bm.tape_eigenvalues(k).double().cpu().numpy()
+        ld = bd.tape_eigenvalues(k).double().cpu().numpy()
+        for i in range(len(config2)):
+            a, b_ = lm[off[i]:off[i + 1]], ld[off[i]:off[i + 1]]
+            assert (a > 0).sum() == (b_ > 0).sum(), (k, i)
+            margin[i] = min(margin[i], np.abs(b_).min() / max(1.0, np.abs(b_).max()))
+    worst = np.maximum(errs, erra)
+    far = margin >= 1e-3
+    print(f"\nC2 gradients, mixed vs FP64 per instance: rho median {np.median(errs):.2e} max {errs.max():.2e}; "
+          f"alpha median {np.median(erra):.2e} max {erra.max():.2e}; {int((worst > 1e-3).sum())} of "
+          f"{len(worst)} above 1e-3 (margins {np.sort(margin[worst > 1e-3])}); {int(far.sum())} instances "
+          f"with margin >= 1e-3, max error there {worst[far].max():.2e}")
+    assert worst[far].max() <= 1e-3, worst[far].max()
+    assert (worst <= 1e-3).mean() >= 0.98 and worst.max() <= 1e-2, (np.sort(worst)[-5:])
     # sampled instances against the oracle (the smallest ones finish in seconds)
     order = np.argsort([p.meta["nv"] for p in config2], kind="stable")[:3]
     for i in order:
@@ -128,4 +155,5 @@ def test_full_size_batched_maxcut(config2):
         assert rel_l2(grho_d[:, ro[i]:ro[i + 1]], ora["grho"]) < 1e-5
         assert rel_l2(ga_d[:, i], ora["galpha"][:, 0]) < 1e-5
         assert abs(obj_m[i] - ora["obj"][0]) <= 1e-4 * abs(ora["obj"][0])
-        assert rel_l2(grho_m[:, ro[i]:ro[i + 1]], ora["grho"]) < 2e-2
+        assert rel_l2(grho_m[:, ro[i]:ro[i + 1]], ora["grho"]) < 1e-3
+        assert rel_l2(ga_m[:, i], ora["galpha"][:, 0]) < 1e-3
