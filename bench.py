@@ -39,23 +39,29 @@ WORKLOAD = ("batched differentiable max-cut SDPs: 256 instances, n ~ U{20..80}, 
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 148, 2032.0
 
 
-def problems(rank=0):
+def problems(rank=0, world=1):
+    """This rank's shard of the global batch of world x 256 instances (seeds
+    2000+j): instances split over the ranks by estimated cost (LPT), so the
+    per-GPU work stays that of 256 instances (weak scaling).  One rank: the
+    whole 256-instance batch."""
     from synth import maxcut_problem, random_graph_batch
-    graphs = random_graph_batch(N_INST, SEED0 + rank * N_INST, 20, 80, 0.1, 0.5)
-    return [maxcut_problem(nv, e) for nv, e in graphs]
+    from paper_2606_13825_b300.dist import shard
+    graphs = random_graph_batch(N_INST * world, SEED0, 20, 80, 0.1, 0.5)
+    probs = [maxcut_problem(nv, e) for nv, e in graphs]
+    return probs if world == 1 else shard(probs, rank, world)[1]
 
 
 # -------------------------------------------------------------- workloads --
 # Each workload: problems, unroll depth, batch options, whether the warm start
 # is learned, and a description.  "maxcut" is the headline metric; the others
 # are the paper's other problem classes at their stated sizes.
-def workload_spec(name, rank=0):
+def workload_spec(name, rank=0, world=1):
     from synth import (lovasz_problem, random_graph_batch, cycle_graph, complete_graph,
                        socp_problem, covsteer_problem)
     if name == "maxcut":
         # the library defaults (one CUDA graph per forward / backward) with the
         # autotuner choosing the Jacobi CTA sizes of the PSD size classes
-        return dict(probs=problems(rank), K=K_UNROLL, opts={"use_graph": 1, "autotune": 1}, value_type="f32",
+        return dict(probs=problems(rank, world), K=K_UNROLL, opts={"use_graph": 1, "autotune": 1}, value_type="f32",
                     learn_start=False, metric=METRIC, desc=WORKLOAD)
     if name == "lovasz":
         graphs = random_graph_batch(64, 3000 + rank * 64, 100, 200, 0.5, 0.5)
@@ -549,7 +555,7 @@ def main():
     from paper_2606_13825_b300 import CosmoBatch, lib
     from paper_2606_13825_b300.solver import unrolled_residual_loss
 
-    spec = workload_spec(args.workload, rank)
+    spec = workload_spec(args.workload, rank, world)
     probs, K = spec["probs"], spec["K"]
     n_inst = len(probs)
     opts = dict(spec["opts"])
@@ -625,7 +631,12 @@ def main():
         from paper_2606_13825_b300.dist import max_over_ranks
         total_ms = max_over_ranks(total_ms, device=dev)
     ms_per_step = total_ms / args.steps
-    value = world * n_inst * K * args.steps / (total_ms / 1e3)
+    n_total = n_inst
+    if dist:
+        tot = torch.tensor([n_inst], dtype=torch.int64, device=dev)
+        dist.all_reduce(tot)
+        n_total = int(tot)          # every rank's instances (their shards partition the batch)
+    value = n_total * K * args.steps / (total_ms / 1e3)
 
     if rank != 0:
         if dist:

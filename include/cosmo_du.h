@@ -454,6 +454,23 @@ cosmo_status cosmo_profile_read(cosmo_batch* batch, const char* kernel, double* 
  * device.  Returns COSMO_OK even when flags are set. */
 cosmo_status cosmo_status_sync(cosmo_batch* batch, int32_t* flags_host);
 
+/* Device memory of the tape of a K-step forward with a tape, and of the
+ * per-step parameters (states of one checkpoint segment, linear-solve
+ * solutions, slacks, eigen-decompositions, checkpoints, rectified rho, the
+ * preconditioner, the per-step gradient buffers): the memory cosmo_forward
+ * allocates for a new K unless the caller supplies it.  Computed on the host.
+ * Errors: E_INVAL. */
+cosmo_status cosmo_workspace_bytes(const cosmo_batch* batch, int32_t K, size_t* bytes);
+
+/* Caller-owned workspace for K-step forwards/backwards: ws (device memory of
+ * at least cosmo_workspace_bytes(K) bytes, any alignment) holds the tape of
+ * every later cosmo_forward / cosmo_policy_forward with this K, which then
+ * allocates nothing (a forward with another K uses library memory again).
+ * ws = NULL returns to library-owned memory.  The caller keeps ws alive and
+ * untouched while the batch may use it.  Drops the current tape and recorded
+ * graphs; synchronises the device.  Errors: E_INVAL (K < 1, bytes too small). */
+cosmo_status cosmo_batch_set_workspace(cosmo_batch* batch, int32_t K, void* ws, size_t bytes);
+
 /* Eigenvalues of every PSD block at unrolled step k of the last forward that
  * kept a tape (the projection input of that step, Eq. psd-proj), copied into
  * lam (device real, sum of p over blocks, block order as in the problem) on

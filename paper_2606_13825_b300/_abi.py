@@ -5,7 +5,7 @@ Loading fails loudly if the library is missing; there is no fallback path.
 """
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
+from ctypes import c_size_t, POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcosmo_du.so")
@@ -119,6 +119,8 @@ _SIGS = {
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_status_sync": (c_int32, [c_void_p, POINTER(c_int32)]),
     "cosmo_tape_eigenvalues": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    "cosmo_workspace_bytes": (c_int32, [c_void_p, c_int32, POINTER(c_size_t)]),
+    "cosmo_batch_set_workspace": (c_int32, [c_void_p, c_int32, c_void_p, c_size_t]),
     "cosmo_profile_enable": (c_int32, [c_void_p, c_char_p]),
     "cosmo_profile_read": (c_int32, [c_void_p, c_char_p, POINTER(c_double), POINTER(c_int64),
                                      c_int32]),

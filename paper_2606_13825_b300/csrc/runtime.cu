@@ -163,19 +163,39 @@ static cosmo_status validate(const cosmo_problem* pr) {
 }
 
 // --------------------------------------------------------- allocation ---
+// Device buffers of a batch.  Either owned (one cudaMalloc each), carved
+// from caller-owned memory (set_external: 256-byte aligned pieces, nothing
+// allocated), or only measured (set_measure: the bytes carving would need).
 struct DevArena {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
+  unsigned char* ext = nullptr;   // caller memory being carved
+  size_t ext_cap = 0, ext_used = 0;
+  bool measure = false;
   ~DevArena() { release(); }
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
     bytes = 0;
+    ext_used = 0;
   }
+  void set_external(void* base, size_t cap) { release(); ext = (unsigned char*)base; ext_cap = cap; measure = false; }
+  void set_owned() { release(); ext = nullptr; ext_cap = 0; measure = false; }
+  void set_measure() { release(); ext = nullptr; ext_cap = 0; measure = true; }
   template <class X>
   cosmo_status alloc(X** out, int64_t count) {
     *out = nullptr;
     if (count <= 0) return COSMO_OK;
+    if (measure || ext) {
+      const size_t off = (ext_used + 255) & ~(size_t)255, need = (size_t)count * sizeof(X);
+      ext_used = off + need;
+      bytes = (int64_t)ext_used;
+      if (measure) return COSMO_OK;
+      if (ext_used > ext_cap)
+        return fail(COSMO_E_INVAL, "workspace of %zu bytes too small (%zu needed)", ext_cap, ext_used);
+      *out = reinterpret_cast<X*>(ext + off);
+      return COSMO_OK;
+    }
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(X));
     if (e != cudaSuccess) {
@@ -383,6 +403,8 @@ struct Impl {
   virtual size_t real_size() const = 0;
   virtual void get_tuning(cosmo_tuning* t) const = 0;
   virtual cosmo_status tape_eigenvalues(int32_t k, void* lam, cudaStream_t st) = 0;
+  virtual size_t workspace_bytes(int32_t K) = 0;
+  virtual cosmo_status set_workspace_ext(int32_t K, void* ws, size_t bytes) = 0;
   virtual cosmo_status set_tuning(const cosmo_tuning& t) = 0;
 };
 
@@ -926,29 +948,93 @@ struct ImplT : Impl {
   }
 
   // (re)allocate the tape for K steps with checkpoint interval c
+  // caller-owned workspace for the tape of K-step forwards (cosmo_batch_set_workspace)
+  void* ws_ext = nullptr;
+  size_t ws_ext_bytes = 0;
+  int32_t ws_ext_K = 0;
+  bool tape_external = false;
+
+  // bytes of the K-step tape and step parameters (what ensure_tape places)
+  size_t tape_bytes(int32_t newK) {
+    DevArena a;
+    a.set_measure();
+    TapePtrs t;
+    tape_layout(a, newK, opt.checkpoint_every > 0 ? std::min(opt.checkpoint_every, newK) : newK, t);
+    return (size_t)a.bytes + 256;   // + alignment of an arbitrary base
+  }
+  size_t workspace_bytes(int32_t newK) override { return tape_bytes(newK); }
+  cosmo_status set_workspace_ext(int32_t newK, void* ws, size_t bytes) override { return set_workspace(newK, ws, bytes); }
+  cosmo_status set_workspace(int32_t newK, void* ws, size_t bytes) {
+    if (ws) {
+      if (newK < 1) return fail(COSMO_E_INVAL, "K must be >= 1");
+      if (bytes < tape_bytes(newK))
+        return fail(COSMO_E_INVAL, "workspace of %zu bytes, %zu needed for K = %d", bytes, tape_bytes(newK), newK);
+    }
+    CU(cudaDeviceSynchronize());
+    ws_ext = ws;
+    ws_ext_bytes = ws ? bytes : 0;
+    ws_ext_K = ws ? newK : 0;
+    // the next forward lays the tape out again
+    drop_graphs();
+    tarena.set_owned();
+    xs = nullptr;
+    K = 0;
+    tape_valid = false;
+    tape_external = false;
+    return COSMO_OK;
+  }
+
   cosmo_status ensure_tape(int32_t newK) {
     int32_t c = opt.checkpoint_every > 0 ? std::min(opt.checkpoint_every, newK) : newK;
-    if (newK == K && c == cK && xs) return COSMO_OK;
+    const bool use_ext = ws_ext && ws_ext_K == newK;
+    if (newK == K && c == cK && xs && use_ext == tape_external) return COSMO_OK;
     drop_graphs();
     CU(cudaDeviceSynchronize());
-    tarena.release();
+    if (use_ext) {
+      const uintptr_t base = (reinterpret_cast<uintptr_t>(ws_ext) + 255) & ~uintptr_t(255);
+      tarena.set_external(reinterpret_cast<void*>(base), ws_ext_bytes - (size_t)(base - reinterpret_cast<uintptr_t>(ws_ext)));
+    } else {
+      tarena.set_owned();
+    }
+    tape_external = use_ext;
     tape_valid = false;
     K = newK;
     cK = c;
     nseg = (K + cK - 1) / cK;
+    TapePtrs t;
+    TRY(tape_layout(tarena, K, cK, t));
+    lr_rd2 = t.lr_rd2; lr_rp2 = t.lr_rp2; sigma_dev = t.sigma_dev;
+    xs = t.xs; ss = t.ss; ys = t.ys; xts = t.xts; sts = t.sts; lams = t.lams; Us = t.Us;
+    ck_x = t.ck_x; ck_s = t.ck_s; ck_y = t.ck_y; ck_xt = t.ck_xt; ck_U = t.ck_U;
+    rho_in = t.rho_in; rho_rect = t.rho_rect; dinv = t.dinv; alpha_in = t.alpha_in;
+    grho_all = t.grho_all; galpha_all = t.galpha_all;
+    return COSMO_OK;
+  }
+
+  struct TapePtrs {
+    double *lr_rd2 = nullptr, *lr_rp2 = nullptr, *sigma_dev = nullptr;
+    T *xs = nullptr, *ss = nullptr, *ys = nullptr, *xts = nullptr, *sts = nullptr, *lams = nullptr, *Us = nullptr;
+    T *ck_x = nullptr, *ck_s = nullptr, *ck_y = nullptr, *ck_xt = nullptr, *ck_U = nullptr;
+    T *rho_in = nullptr, *rho_rect = nullptr, *dinv = nullptr, *alpha_in = nullptr, *grho_all = nullptr,
+      *galpha_all = nullptr;
+  };
+  cosmo_status tape_layout(DevArena& ta, int32_t K_, int32_t c_, TapePtrs& t) {
     const int64_t n = h.n, m = h.m, ni = h.ninst;
-    TRY(tarena.alloc(&lr_rd2, (int64_t)(K + 1) * ni)); TRY(tarena.alloc(&lr_rp2, (int64_t)(K + 1) * ni));
-    TRY(tarena.alloc(&xs, (cK + 1) * n)); TRY(tarena.alloc(&ss, (cK + 1) * m));
-    TRY(tarena.alloc(&ys, (cK + 1) * m));
-    TRY(tarena.alloc(&xts, (int64_t)cK * n)); TRY(tarena.alloc(&sts, (int64_t)cK * m));
-    TRY(tarena.alloc(&lams, (int64_t)cK * h.sum_p)); TRY(tarena.alloc(&Us, (int64_t)cK * h.sum_p2));
-    TRY(tarena.alloc(&ck_x, nseg * n)); TRY(tarena.alloc(&ck_s, nseg * m));
-    TRY(tarena.alloc(&ck_y, nseg * m)); TRY(tarena.alloc(&ck_xt, nseg * n));
-    TRY(tarena.alloc(&ck_U, (int64_t)nseg * h.sum_p2));
-    TRY(tarena.alloc(&rho_in, (int64_t)K * m)); TRY(tarena.alloc(&rho_rect, (int64_t)K * m));
-    TRY(tarena.alloc(&dinv, (int64_t)K * n)); TRY(tarena.alloc(&alpha_in, (int64_t)K * ni));
-    TRY(tarena.alloc(&grho_all, (int64_t)K * m)); TRY(tarena.alloc(&galpha_all, (int64_t)K * ni));
-    TRY(tarena.alloc(&sigma_dev, K));
+    const int32_t nseg_ = (K_ + c_ - 1) / c_;
+    const int32_t K = K_, cK = c_, nseg = nseg_;
+    DevArena& tarena = ta;
+    TRY(tarena.alloc(&t.lr_rd2, (int64_t)(K + 1) * ni)); TRY(tarena.alloc(&t.lr_rp2, (int64_t)(K + 1) * ni));
+    TRY(tarena.alloc(&t.xs, (cK + 1) * n)); TRY(tarena.alloc(&t.ss, (cK + 1) * m));
+    TRY(tarena.alloc(&t.ys, (cK + 1) * m));
+    TRY(tarena.alloc(&t.xts, (int64_t)cK * n)); TRY(tarena.alloc(&t.sts, (int64_t)cK * m));
+    TRY(tarena.alloc(&t.lams, (int64_t)cK * h.sum_p)); TRY(tarena.alloc(&t.Us, (int64_t)cK * h.sum_p2));
+    TRY(tarena.alloc(&t.ck_x, nseg * n)); TRY(tarena.alloc(&t.ck_s, nseg * m));
+    TRY(tarena.alloc(&t.ck_y, nseg * m)); TRY(tarena.alloc(&t.ck_xt, nseg * n));
+    TRY(tarena.alloc(&t.ck_U, (int64_t)nseg * h.sum_p2));
+    TRY(tarena.alloc(&t.rho_in, (int64_t)K * m)); TRY(tarena.alloc(&t.rho_rect, (int64_t)K * m));
+    TRY(tarena.alloc(&t.dinv, (int64_t)K * n)); TRY(tarena.alloc(&t.alpha_in, (int64_t)K * ni));
+    TRY(tarena.alloc(&t.grho_all, (int64_t)K * m)); TRY(tarena.alloc(&t.galpha_all, (int64_t)K * ni));
+    TRY(tarena.alloc(&t.sigma_dev, K));
     return COSMO_OK;
   }
 
@@ -1866,7 +1952,7 @@ struct ImplT : Impl {
     o->n_psd = (int32_t)h.psd_p.size();
     o->max_psd_p = h.max_p;
     o->psd_u_entries = h.sum_p2;
-    o->device_bytes = arena.bytes + tarena.bytes + sarena.bytes + warena.bytes + parena.bytes;
+    o->device_bytes = arena.bytes + (tape_external ? 0 : tarena.bytes) + sarena.bytes + warena.bytes + parena.bytes;
     o->last_K = K;
     o->tape_valid = tape_valid ? 1 : 0;
     o->kernels_launched = launched;
@@ -2139,6 +2225,19 @@ cosmo_status cosmo_profile_read(cosmo_batch* b, const char* kernel, double* tota
   BATCH_GUARD(b);
   if (!total_ms || !launches) return fail(COSMO_E_INVAL, "NULL output");
   return b->impl->profile_read(kernel, total_ms, launches, reset);
+}
+
+cosmo_status cosmo_workspace_bytes(const cosmo_batch* b, int32_t K, size_t* bytes) {
+  g_err.clear();
+  if (!b || !bytes) return fail(COSMO_E_INVAL, "null argument");
+  if (K < 1) return fail(COSMO_E_INVAL, "K must be >= 1");
+  *bytes = b->impl->workspace_bytes(K);
+  return COSMO_OK;
+}
+
+cosmo_status cosmo_batch_set_workspace(cosmo_batch* b, int32_t K, void* ws, size_t bytes) {
+  BATCH_GUARD(b);
+  return b->impl->set_workspace_ext(K, ws, bytes);
 }
 
 cosmo_status cosmo_tape_eigenvalues(cosmo_batch* b, int32_t k, void* lam, void* stream) {

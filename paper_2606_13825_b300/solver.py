@@ -202,6 +202,24 @@ class CosmoBatch:
         t.tune_ms = float(tuning.get("tune_ms", 0.0))
         check(lib().cosmo_batch_set_tuning(self._h, byref(t)))
 
+    def workspace_bytes(self, K):
+        """Bytes of the tape of a K-step forward (cosmo_workspace_bytes)."""
+        n = ctypes.c_size_t()
+        check(lib().cosmo_workspace_bytes(self._h, int(K), byref(n)))
+        return n.value
+
+    def set_workspace(self, K, ws=None):
+        """Use the caller's device tensor `ws` (at least workspace_bytes(K)
+        bytes) for the tape of K-step forwards, so that they allocate nothing;
+        ws=None returns to library memory.  The batch keeps a reference."""
+        if ws is None:
+            check(lib().cosmo_batch_set_workspace(self._h, int(K), None, 0))
+            self._ws = None
+            return
+        nbytes = ws.numel() * ws.element_size()
+        check(lib().cosmo_batch_set_workspace(self._h, int(K), _tp(ws), nbytes))
+        self._ws = ws
+
     def tape_eigenvalues(self, k):
         """Eigenvalues of every PSD block at step k of the last taped forward
         (sum of p over blocks, problem order)."""
