@@ -471,15 +471,18 @@ cosmo_status cosmo_workspace_bytes(const cosmo_batch* batch, int32_t K, size_t* 
  * graphs; synchronises the device.  Errors: E_INVAL (K < 1, bytes too small). */
 cosmo_status cosmo_batch_set_workspace(cosmo_batch* batch, int32_t K, void* ws, size_t bytes);
 
-/* Eigenvalues of every PSD block at unrolled step k of the last forward that
- * kept a tape (the projection input of that step, Eq. psd-proj), copied into
- * lam (device real, sum of p over blocks, block order as in the problem) on
- * `stream`.  A diagnostic of the path: an eigenvalue near zero is a kink of
- * the projection, where FP32 and FP64 trajectories may take different
- * branches.  With checkpointing only the steps of the segment in the buffer
- * (the last one after a forward) are available.  Errors: E_INVAL (k out of
- * range, no PSD block), E_STATE (no tape, or step k not in the buffer). */
-cosmo_status cosmo_tape_eigenvalues(cosmo_batch* batch, int32_t k, void* lam, void* stream);
+/* Eigen-decomposition of every PSD block at unrolled step k of the last
+ * forward that kept a tape (of the projection input of that step, Eq.
+ * psd-proj), copied on `stream` into lam (device real, sum of p over blocks)
+ * and U (device real, sum of p^2, column-major per block: column j is the
+ * eigenvector of lam[j]); either may be NULL.  Block order as in the
+ * problem.  A diagnostic of the path: an eigenvalue near zero is a kink of
+ * the projection, a collapsing gap between eigenvalues the place where an
+ * eigenvector-based backward fails and the Daleckii-Krein one does not.
+ * With checkpointing only the steps of the segment in the buffer (the last
+ * one after a forward) are available.  Errors: E_INVAL (k out of range, no
+ * PSD block), E_STATE (no tape, or step k not in the buffer). */
+cosmo_status cosmo_tape_eigen(cosmo_batch* batch, int32_t k, void* lam, void* U, void* stream);
 
 /* ---- standalone kernels (each is one step of the path, usable alone) ---- */
 

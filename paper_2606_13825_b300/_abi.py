@@ -118,7 +118,7 @@ _SIGS = {
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "cosmo_status_sync": (c_int32, [c_void_p, POINTER(c_int32)]),
-    "cosmo_tape_eigenvalues": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    "cosmo_tape_eigen": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "cosmo_workspace_bytes": (c_int32, [c_void_p, c_int32, POINTER(c_size_t)]),
     "cosmo_batch_set_workspace": (c_int32, [c_void_p, c_int32, c_void_p, c_size_t]),
     "cosmo_profile_enable": (c_int32, [c_void_p, c_char_p]),

@@ -402,7 +402,7 @@ struct Impl {
   virtual cosmo_status profile_read(const char* tag, double* ms, int64_t* n, int32_t reset) = 0;
   virtual size_t real_size() const = 0;
   virtual void get_tuning(cosmo_tuning* t) const = 0;
-  virtual cosmo_status tape_eigenvalues(int32_t k, void* lam, cudaStream_t st) = 0;
+  virtual cosmo_status tape_eigen(int32_t k, void* lam, void* U, cudaStream_t st) = 0;
   virtual size_t workspace_bytes(int32_t K) = 0;
   virtual cosmo_status set_workspace_ext(int32_t K, void* ws, size_t bytes) = 0;
   virtual cosmo_status set_tuning(const cosmo_tuning& t) = 0;
@@ -902,14 +902,15 @@ struct ImplT : Impl {
     }
     return COSMO_OK;
   }
-  cosmo_status tape_eigenvalues(int32_t k, void* lamo, cudaStream_t st) override {
+  cosmo_status tape_eigen(int32_t k, void* lamo, void* Uo, cudaStream_t st) override {
     if (!h.sum_p) return fail(COSMO_E_INVAL, "the batch has no PSD block");
     if (!tape_valid) return fail(COSMO_E_STATE, "no forward with a tape");
     if (k < 0 || k >= K) return fail(COSMO_E_INVAL, "step %d out of range [0, %d)", k, K);
     const int32_t seg = k / cK;
     if (seg != seg_in_buffer) return fail(COSMO_E_STATE, "step %d is not in the segment held in the buffer", k);
-    CU(cudaMemcpyAsync(lamo, lams + (int64_t)(k - seg * cK) * h.sum_p, sizeof(T) * h.sum_p,
-                       cudaMemcpyDeviceToDevice, st));
+    const int64_t sl = k - (int64_t)seg * cK;
+    if (lamo) CU(cudaMemcpyAsync(lamo, lams + sl * h.sum_p, sizeof(T) * h.sum_p, cudaMemcpyDeviceToDevice, st));
+    if (Uo) CU(cudaMemcpyAsync(Uo, Us + sl * h.sum_p2, sizeof(T) * h.sum_p2, cudaMemcpyDeviceToDevice, st));
     return COSMO_OK;
   }
   void get_tuning(cosmo_tuning* t) const override {
@@ -2240,10 +2241,9 @@ cosmo_status cosmo_batch_set_workspace(cosmo_batch* b, int32_t K, void* ws, size
   return b->impl->set_workspace_ext(K, ws, bytes);
 }
 
-cosmo_status cosmo_tape_eigenvalues(cosmo_batch* b, int32_t k, void* lam, void* stream) {
+cosmo_status cosmo_tape_eigen(cosmo_batch* b, int32_t k, void* lam, void* U, void* stream) {
   BATCH_GUARD(b);
-  if (!lam) return fail(COSMO_E_INVAL, "lam is NULL");
-  return b->impl->tape_eigenvalues(k, lam, (cudaStream_t)stream);
+  return b->impl->tape_eigen(k, lam, U, (cudaStream_t)stream);
 }
 
 cosmo_status cosmo_status_sync(cosmo_batch* b, int32_t* flags_host) {

@@ -220,13 +220,20 @@ class CosmoBatch:
         check(lib().cosmo_batch_set_workspace(self._h, int(K), _tp(ws), nbytes))
         self._ws = ws
 
-    def tape_eigenvalues(self, k):
-        """Eigenvalues of every PSD block at step k of the last taped forward
-        (sum of p over blocks, problem order)."""
+    def tape_eigen(self, k, vectors=False):
+        """Eigenvalues (and with vectors=True the eigenvectors, column-major per
+        block) of every PSD block at step k of the last taped forward: lam
+        [sum p] (and U [sum p^2]), problem order."""
         c = np.asarray(self.packed.cones).reshape(-1, 2)
-        lam = torch.empty(int(c[c[:, 0] == 4, 1].sum()), dtype=self.dtype, device=self.device)
-        check(lib().cosmo_tape_eigenvalues(self._h, int(k), _tp(lam), _stream()))
-        return lam
+        ps = c[c[:, 0] == 4, 1]
+        lam = torch.empty(int(ps.sum()), dtype=self.dtype, device=self.device)
+        U = torch.empty(int((ps ** 2).sum()), dtype=self.dtype, device=self.device) if vectors else None
+        check(lib().cosmo_tape_eigen(self._h, int(k), _tp(lam), _tp(U) if U is not None else None, _stream()))
+        return (lam, U) if vectors else lam
+
+    def tape_eigenvalues(self, k):
+        """Eigenvalues of every PSD block at step k of the last taped forward."""
+        return self.tape_eigen(k)
 
     def zeros(self, *shape, dtype=None):
         return torch.zeros(*shape, dtype=dtype or self.dtype, device=self.device)

@@ -19,6 +19,7 @@ from .generators import (erdos_renyi, maxcut_problem, lovasz_problem,
                          cycle_graph, complete_graph, empty_graph)
 from .classes import (lyapunov_problem, robust_kalman_problem, robust_mpc_problem,
                       hurwitz_matrix, kalman_matrices, mpc_tightening)
+from .steering import cs_problem, cs_double_integrator_problem, double_integrator
 
 __all__ = [
     "ConicProblem", "ZERO", "NONNEG", "BOX", "SOC", "PSD", "CONE_NAMES",
@@ -27,4 +28,5 @@ __all__ = [
     "clustered_symmetric", "random_graph_batch", "cycle_graph",
     "complete_graph", "empty_graph", "lyapunov_problem", "robust_kalman_problem",
     "robust_mpc_problem", "hurwitz_matrix", "kalman_matrices", "mpc_tightening",
+    "cs_problem", "cs_double_integrator_problem", "double_integrator",
 ]
