@@ -103,38 +103,71 @@ def cs_problem(As, Bs, rs, Ws, mu0, Sigma0, mu_goal, Sigma_des, Q, R, QN,
     SW = np.zeros((N * nx, N * nx))
     for t in range(N):
         SW[t * nx:(t + 1) * nx, t * nx:(t + 1) * nx] = Ws[t]
-    SWh = _sqrt_psd(SW)
-    # ---- cost: 1/2 z'Pz + q'z + const
-    P = np.zeros((n, n))
+    if np.count_nonzero(SW - np.diag(np.diag(SW))):
+        raise ValueError("the process-noise covariances must be diagonal")
+    sw = np.sqrt(np.diag(SW))                 # Sigma_W^(1/2), diagonal
+    SWh = np.diag(sw)
+    # ---- cost: 1/2 z'Pz + q'z + const.  With Sigma_W^(1/2) diagonal, the
+    # Frobenius terms || Qh G_t SWh ||_F^2 separate by noise component c:
+    #   column c of Qh G_t SWh = sw_c Qh (Dbar_t[:, c] + Bbar_t[:, K rows] K[:, c]),
+    # so K entries couple only with entries of the same column c of K.
+    Pr, Pc, Pv = [], [], []                   # COO pieces (duplicates are summed)
     q = np.zeros(n)
     const = 0.0
+
+    def addP(i, j, v):
+        Pr.append(np.array([i]))
+        Pc.append(np.array([j]))
+        Pv.append(np.array([v]))
+
+    def addP_block(zj, H):
+        Pr.append(np.repeat(zj, zj.size))
+        Pc.append(np.tile(zj, zj.size))
+        Pv.append(H.ravel())
+
+    kr_all = np.array([e[1] for e in Kent], dtype=np.int64)
+    kc_all = np.array([e[2] for e in Kent], dtype=np.int64)
+    zj_all = np.array([e[0] for e in Kent], dtype=np.int64)
+    bycol = {}
+    for idx, c in enumerate(kc_all):
+        bycol.setdefault(int(c), []).append(idx)
+    bycol = {c: np.array(ids, dtype=np.int64) for c, ids in bycol.items()}
+    Rh = _sqrt_psd(R)
+    Xs, C0s = [], []
     for t in range(N + 1):
         Qt = QN if t == N else Q
-        P[o_mu + t * nx:o_mu + (t + 1) * nx, o_mu + t * nx:o_mu + (t + 1) * nx] += 2.0 * Qt
+        for i in range(nx):
+            for k in range(nx):
+                if Qt[i, k] != 0.0:
+                    addP(o_mu + t * nx + i, o_mu + t * nx + k, 2.0 * Qt[i, k])
         const += float(np.trace(Qt @ Abar[t] @ Sigma0 @ Abar[t].T))
-        # tr(Qt G_t SW G_t') = || Qh G_t SWh ||_F^2,  G_t = Dbar_t + Bbar_t K
         Qh = _sqrt_psd(Qt)
-        c0 = (Qh @ Dbar[t] @ SWh).ravel()
-        L = np.zeros((c0.size, n))
-        for (j, kr, kc) in Kent:
-            L[:, j] = np.outer(Qh @ Bbar[t][:, kr], SWh[kc, :]).ravel()
-        P += 2.0 * L.T @ L
-        q += 2.0 * L.T @ c0
-        const += float(c0 @ c0)
+        Xs.append(Qh @ Bbar[t])                   # nx x N nu
+        C0s.append(Qh @ Dbar[t] * sw[None, :])    # nx x N nx: the K-free part, column by column
+    Xs, C0s = np.stack(Xs), np.stack(C0s)
+    const += float(np.sum(C0s * C0s))
+    tK = kr_all // nu                             # block row (time) of each K entry
+    for c, ids in bycol.items():
+        # sum over t of || sw_c Qh_t (Dbar_t[:, c] + Bbar_t[:, rows] K[rows, c]) ||^2
+        Xc = Xs[:, :, kr_all[ids]] * sw[c]        # (N+1) x nx x |ids|
+        H = 2.0 * np.einsum("tai,taj->ij", Xc, Xc)
+        np.add.at(q, zj_all[ids], 2.0 * np.einsum("tai,ta->i", Xc, C0s[:, :, c]))
+        # tr(R K_t SW K_t') = || Rh K_t SWh ||_F^2: entries of the same block row only
+        Y = Rh[:, kr_all[ids] % nu] * sw[c]       # nu x |ids|
+        H += 2.0 * (Y.T @ Y) * (tK[ids][:, None] == tK[ids][None, :])
+        addP_block(zj_all[ids], H)
     for t in range(N):
-        P[o_v + t * nu:o_v + (t + 1) * nu, o_v + t * nu:o_v + (t + 1) * nu] += 2.0 * R
-        # tr(R K_t SW K_t') = || Rh K_t SWh ||_F^2
-        Rh = _sqrt_psd(R)
-        L = np.zeros((nu * N * nx, n))
-        for (j, kr, kc) in Kent:
-            if kr // nu != t:
-                continue
-            L[:, j] = np.outer(Rh[:, kr - t * nu], SWh[kc, :]).ravel()
-        P += 2.0 * L.T @ L
+        for i in range(nu):
+            for k in range(nu):
+                if R[i, k] != 0.0:
+                    addP(o_v + t * nu + i, o_v + t * nu + k, 2.0 * R[i, k])
     if vc:
         q[o_e:o_e + N * nx] = lam_nu
-    P = 0.5 * (P + P.T)
-    P[np.abs(P) < 1e-300] = 0.0
+    P = sp.coo_matrix((np.concatenate(Pv), (np.concatenate(Pr).astype(np.int64), np.concatenate(Pc).astype(np.int64))),
+                      shape=(n, n)).tocsr()
+    P.sum_duplicates()
+    P = (0.5 * (P + P.T)).tocsr()
+    P.eliminate_zeros()
     # ---- constraints, rows in cone order
     rows, cols, vals, b, cones = [], [], [], [], []
     r = 0
@@ -229,7 +262,7 @@ def cs_problem(As, Bs, rs, Ws, mu0, Sigma0, mu_goal, Sigma_des, Q, R, QN,
                         "e": o_e if vc else None},
             "kidx": kidx, "Abar": Abar, "Bbar": Bbar, "Dbar": Dbar, "SW": SW, "Sigma0": Sigma0,
             "Q": Q, "R": R, "QN": QN, "Sigma_des": Sigma_des}
-    return ConicProblem(P=sp.csr_matrix(P), q=q, A=A, b=np.asarray(b, float), cones=cones, meta=meta).check()
+    return ConicProblem(P=P, q=q, A=A, b=np.asarray(b, float), cones=cones, meta=meta).check()
 
 
 def double_integrator(dt=0.1, sigma_a=0.5):
@@ -289,3 +322,65 @@ def terminal_covariance(problem, z):
         Kmat[t * nu:(t + 1) * nu, tau * nx:(tau + 1) * nx] = z[off:off + nu * nx].reshape(nu, nx)
     G = mt["Dbar"][N] + mt["Bbar"][N] @ Kmat
     return mt["Abar"][N] @ mt["Sigma0"] @ mt["Abar"][N].T + G @ mt["SW"] @ G.T
+
+
+# ------------------------------------------------------------- unicycle --
+# The kinematic unicycle of App. F: x = (p_x, p_y, theta), u = (v, omega),
+# x_{t+1} = x_t + f(x_t, u_t) dt with f = (v cos theta, v sin theta, omega).
+def unicycle_step(x, u, dt=0.1):
+    """One explicit-Euler step of the unicycle (x: [..., 3], u: [..., 2])."""
+    x = np.asarray(x, float)
+    u = np.asarray(u, float)
+    th = x[..., 2]
+    return x + dt * np.stack([u[..., 0] * np.cos(th), u[..., 0] * np.sin(th), u[..., 1]], axis=-1)
+
+
+def unicycle_linearization(x_ref, u_ref, dt=0.1):
+    """(A, B, r) of x_{t+1} ~ A x_t + B u_t + r around (x_ref, u_ref): the
+    Jacobians of the Euler step and the offset r = F(x_ref, u_ref) - A x_ref - B u_ref."""
+    th, v = float(x_ref[2]), float(u_ref[0])
+    A = np.eye(3)
+    A[0, 2] = -dt * v * np.sin(th)
+    A[1, 2] = dt * v * np.cos(th)
+    B = np.array([[dt * np.cos(th), 0.0], [dt * np.sin(th), 0.0], [0.0, dt]])
+    r = unicycle_step(x_ref, u_ref, dt) - A @ np.asarray(x_ref, float) - B @ np.asarray(u_ref, float)
+    return A, B, r
+
+
+def unicycle_scenario(seed: int, N: int = 30, dt: float = 0.1) -> dict:
+    """A nonlinear CS scenario of App. F: start at the origin with heading
+    U[-pi, pi], target mean U(-(5, 5, pi), (5, 5, pi)), sigma_0 ~ U(0.01, 0.05),
+    sigma_N ~ U(0.05, 0.25), W = diag(0.02^2, 0.02^2, 0.01^2) dt,
+    Q = diag(1, 1, 0.1), R = diag(0.1, 0.05), Q_N = 10 Q, lambda_nu = 1e4."""
+    rng = np.random.default_rng(seed)
+    mu0 = np.array([0.0, 0.0, rng.uniform(-np.pi, np.pi)])
+    goal = rng.uniform(-1.0, 1.0, 3) * np.array([5.0, 5.0, np.pi])
+    s0, sN = rng.uniform(0.01, 0.05), rng.uniform(0.05, 0.25)
+    Q = np.diag([1.0, 1.0, 0.1])
+    return dict(seed=seed, N=N, dt=dt, mu0=mu0, goal=goal, Sigma0=s0 ** 2 * np.eye(3), Sigma_des=sN ** 2 * np.eye(3),
+                W=np.diag([0.02 ** 2, 0.02 ** 2, 0.01 ** 2]) * dt, Q=Q, R=np.diag([0.1, 0.05]), QN=10.0 * Q,
+                lam_nu=1e4)
+
+
+def unicycle_initial_reference(scn):
+    """A straight-line reference from the start to the target mean (states
+    interpolated, controls from the Euler differences along it)."""
+    N, dt = scn["N"], scn["dt"]
+    s = np.linspace(0.0, 1.0, N + 1)[:, None]
+    mu = (1.0 - s) * scn["mu0"] + s * scn["goal"]
+    d = np.diff(mu, axis=0)
+    u = np.stack([np.hypot(d[:, 0], d[:, 1]) / dt, d[:, 2] / dt], axis=1)
+    return mu, u
+
+
+def unicycle_subproblem(scn, mu_ref, u_ref, rho_x, rho_u):
+    """The SCP subproblem of App. F linearised around (mu_ref, u_ref): the
+    conic program of cs_problem with the LTV data of the linearisation,
+    virtual control (lambda_nu) and trust regions rho_x, rho_u."""
+    N, dt = scn["N"], scn["dt"]
+    lin = [unicycle_linearization(mu_ref[t], u_ref[t], dt) for t in range(N)]
+    pr = cs_problem([a for a, _, _ in lin], [b_ for _, b_, _ in lin], [r for _, _, r in lin], [scn["W"]] * N,
+                    scn["mu0"], scn["Sigma0"], scn["goal"], scn["Sigma_des"], scn["Q"], scn["R"], scn["QN"],
+                    lam_nu=scn["lam_nu"], mu_ref=mu_ref, v_ref=u_ref, rho_x=rho_x, rho_u=rho_u)
+    pr.meta.update(system="unicycle", seed=scn["seed"])
+    return pr
