@@ -163,14 +163,19 @@ typedef struct {
                                loss of Sec. 4, sum_{k=1..K} log(||r_d^k||^2/||r_d^0||^2 +
                                ||r_p^k||^2/||r_p^0||^2), k = 0 norms held constant, a term with
                                a zero k = 0 norm dropped */
-  int32_t eig_variant;      /* Jacobi kernel of the PSD projection: 0 automatic (2), 1 the
+  int32_t eig_variant;      /* Jacobi kernel of the PSD projection: 0 automatic (3 where it
+                               has an instantiation for the class and CTA size, else 2), 1 the
                                matrix and eigenvectors by index (two barriers per round),
                                2 the matrix in round-robin slot order as 2x2 tiles with the
                                next round's rotations formed in the same pass (one barrier
-                               per round).  Both give the eigen-decomposition to eig_tol. */
+                               per round), 3 the same solver on a compile-time geometry per
+                               size class (orders up to 32, 56, 80; eigenvectors kept by slot
+                               in a double buffer; a class without an instantiation for its
+                               CTA size is an error).  All give the eigen-decomposition to
+                               eig_tol. */
   int32_t eig_threads;      /* CTA size of the Jacobi projection: 0 by block order (128 up
                                to p = 32, 256 up to 56, 512 above), or 128, 256, 512 (or
-                               1024 with eig_variant 2) for every block */
+                               1024 with eig_variant 0, 2 or 3) for every block */
   int32_t autotune;         /* 1: at batch creation, time the candidate launch
                                configurations of what the options leave automatic and keep
                                the fastest (see cosmo_tuning); 0: shape rules only */
@@ -182,7 +187,8 @@ typedef struct {
  * rules, or by the autotuner (option autotune = 1), which at batch creation
  * times on the device, with synthetic data of the batch's own shapes:
  *   - per class, the slot-layout Jacobi at CTA sizes 128 / 256 / 512 / 1024
- *     (those that fit; projection of a perturbed block warm-started from the
+ *     (those that fit, each on the compile-time geometry where it has an
+ *     instantiation; projection of a perturbed block warm-started from the
  *     eigenvectors of the unperturbed one), and for classes of order >= 48
  *     the tridiagonal + QL path, each with its backward (Daleckii-Krein)
  *     kernel;
@@ -191,7 +197,7 @@ typedef struct {
  *     or clusters of 2 / 4 CTAs (20 iterations of the batch's operator);
  * keeping the fastest.  A choice is cached per process for the same device,
  * precision and shapes.  Only what the options leave automatic is tuned
- * (eig_threads 0, eig_variant 0 or 2, eig_jacobi_max_p 0, cg_cluster 0). */
+ * (eig_threads 0, eig_variant 0, 2 or 3, eig_jacobi_max_p 0, cg_cluster 0). */
 #define COSMO_MAX_PSD_CLASSES 8
 typedef struct {
   int32_t n_classes;

@@ -45,6 +45,7 @@ def build(debug=False, verbose=False, force=False):
            "-cudart", "static", "-o", LIB + ".tmp", os.path.join(HERE, "csrc", "runtime.cu"),
            "-I", os.path.join(ROOT, "include")]
     cmd += ["-O0", "-G"] if debug else ["-O3"]
+    cmd += ["-split-compile=0"]     # device optimisation in parallel over the host's cores
     if verbose:
         cmd += ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -136,7 +136,7 @@ __device__ __forceinline__ JtRot<T> jt_rotation(T aa, T ab, T bb, T thresh) {
     const T h = hypot(theta, phi);   // scaled: no under/overflow of the squares
     if (h > T(0) && h <= MaxVal<T>::v) {
       const T t = copysign(T(1), theta) * phi / (fabs(theta) + h);
-      r.c = jt_rsqrt(T(1) + t * t);
+      r.c = jt_rsqrt(fma(t, t, T(1)));
       r.s = t * r.c;
     }
   }
@@ -159,27 +159,38 @@ __device__ __forceinline__ JtRot<float> jt_rotation<float>(float aa, float ab, f
     if (M >= 1e-30f && M <= 1e30f) {
       const float inv = __fdividef(1.0f, M);
       const float th = theta * inv, ph = phi * inv;   // the larger is +-1
-      const float h2 = th * th + ph * ph;             // in [1, 2]
-      t = copysignf(1.0f, theta) * __fdividef(ph, fabsf(th) + h2 * rsqrtf(h2));
+      const float h2 = fmaf(th, th, ph * ph);         // in [1, 2]
+      t = copysignf(1.0f, theta) * __fdividef(ph, fmaf(h2, rsqrtf(h2), fabsf(th)));
     } else {
       const float h = hypotf(theta, phi);
       if (!(h > 0.0f && h <= MaxVal<float>::v)) return r;
       t = copysignf(1.0f, theta) * phi / (fabsf(theta) + h);
     }
-    r.c = rsqrtf(1.0f + t * t);
+    r.c = rsqrtf(fmaf(t, t, 1.0f));
     r.s = t * r.c;
   }
   return r;
 }
 
+// The rotation's two combinations c a - s b and s a + c b with the rounding
+// fixed in the source (the second product rounded, the first fused), so that
+// the kernels applying rotations produce the same bits whatever contraction
+// the compiler would choose in each context.
+template <class T>
+__device__ __forceinline__ T jt_cms(T c, T s, T a, T b) { return fma(c, a, -(s * b)); }
+template <class T>
+__device__ __forceinline__ T jt_spc(T c, T s, T a, T b) { return fma(s, a, c * b); }
+
 // new diagonal entry of a pair's first (second) index after its rotation
 template <class T>
 __device__ __forceinline__ T jt_diag_a(const JtQuad<T>& q, JtRot<T> r) {
-  return r.c * r.c * q.aa - T(2) * r.c * r.s * q.ab + r.s * r.s * q.bb;
+  const T cc = r.c * r.c, cs2 = T(2) * r.c * r.s, ss = r.s * r.s;
+  return fma(cc, q.aa, fma(ss, q.bb, -(cs2 * q.ab)));
 }
 template <class T>
 __device__ __forceinline__ T jt_diag_b(const JtQuad<T>& q, JtRot<T> r) {
-  return r.s * r.s * q.aa + T(2) * r.c * r.s * q.ab + r.c * r.c * q.bb;
+  const T cc = r.c * r.c, cs2 = T(2) * r.c * r.s, ss = r.s * r.s;
+  return fma(ss, q.aa, fma(cc, q.bb, cs2 * q.ab));
 }
 
 // Shared-memory accesses by byte offset from the kernel's shared array: with
@@ -209,18 +220,20 @@ __device__ __forceinline__ void jt_rot4<float>(unsigned char* sm, uint32_t ra, u
   float4* pa = reinterpret_cast<float4*>(sm + ra);
   float4* pb = reinterpret_cast<float4*>(sm + rb);
   const float4 x = *pa, y = *pb;
-  *pa = make_float4(r.c * x.x - r.s * y.x, r.c * x.y - r.s * y.y, r.c * x.z - r.s * y.z, r.c * x.w - r.s * y.w);
-  *pb = make_float4(r.s * x.x + r.c * y.x, r.s * x.y + r.c * y.y, r.s * x.z + r.c * y.z, r.s * x.w + r.c * y.w);
+  *pa = make_float4(jt_cms(r.c, r.s, x.x, y.x), jt_cms(r.c, r.s, x.y, y.y), jt_cms(r.c, r.s, x.z, y.z),
+                    jt_cms(r.c, r.s, x.w, y.w));
+  *pb = make_float4(jt_spc(r.c, r.s, x.x, y.x), jt_spc(r.c, r.s, x.y, y.y), jt_spc(r.c, r.s, x.z, y.z),
+                    jt_spc(r.c, r.s, x.w, y.w));
 }
 template <>
 __device__ __forceinline__ void jt_rot4<double>(unsigned char* sm, uint32_t ra, uint32_t rb, JtRot<double> r) {
   double2* pa = reinterpret_cast<double2*>(sm + ra);
   double2* pb = reinterpret_cast<double2*>(sm + rb);
   const double2 x0 = pa[0], x1 = pa[1], y0 = pb[0], y1 = pb[1];
-  pa[0] = make_double2(r.c * x0.x - r.s * y0.x, r.c * x0.y - r.s * y0.y);
-  pa[1] = make_double2(r.c * x1.x - r.s * y1.x, r.c * x1.y - r.s * y1.y);
-  pb[0] = make_double2(r.s * x0.x + r.c * y0.x, r.s * x0.y + r.c * y0.y);
-  pb[1] = make_double2(r.s * x1.x + r.c * y1.x, r.s * x1.y + r.c * y1.y);
+  pa[0] = make_double2(jt_cms(r.c, r.s, x0.x, y0.x), jt_cms(r.c, r.s, x0.y, y0.y));
+  pa[1] = make_double2(jt_cms(r.c, r.s, x1.x, y1.x), jt_cms(r.c, r.s, x1.y, y1.y));
+  pb[0] = make_double2(jt_spc(r.c, r.s, x0.x, y0.x), jt_spc(r.c, r.s, x0.y, y0.y));
+  pb[1] = make_double2(jt_spc(r.c, r.s, x1.x, y1.x), jt_spc(r.c, r.s, x1.y, y1.y));
 }
 
 // items of a round per thread for a CTA of nt threads: the off-diagonal
@@ -362,12 +375,12 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
           const JtQuad<T> x = jt_ldq<T>(sm, cur, d0[u] & 0xfffu, nt_);
           const JtRot<T> rk = jt_ldr<T>(sm, rc + k * RB), rl = jt_ldr<T>(sm, rc + l * RB);
           // rows of pair k, then columns of pair l
-          const T y00 = rk.c * x.aa - rk.s * x.ba, y01 = rk.c * x.ab - rk.s * x.bb;
-          const T y10 = rk.s * x.aa + rk.c * x.ba, y11 = rk.s * x.ab + rk.c * x.bb;
-          jt_st<T>(sm, nxt + (d1[u] & 0xffffu) * TB, rl.c * y00 - rl.s * y01);
-          jt_st<T>(sm, nxt + (d1[u] >> 16) * TB, rl.s * y00 + rl.c * y01);
-          jt_st<T>(sm, nxt + (d2[u] & 0xffffu) * TB, rl.c * y10 - rl.s * y11);
-          jt_st<T>(sm, nxt + (d2[u] >> 16) * TB, rl.s * y10 + rl.c * y11);
+          const T y00 = jt_cms(rk.c, rk.s, x.aa, x.ba), y01 = jt_cms(rk.c, rk.s, x.ab, x.bb);
+          const T y10 = jt_spc(rk.c, rk.s, x.aa, x.ba), y11 = jt_spc(rk.c, rk.s, x.ab, x.bb);
+          jt_st<T>(sm, nxt + (d1[u] & 0xffffu) * TB, jt_cms(rl.c, rl.s, y00, y01));
+          jt_st<T>(sm, nxt + (d1[u] >> 16) * TB, jt_spc(rl.c, rl.s, y00, y01));
+          jt_st<T>(sm, nxt + (d2[u] & 0xffffu) * TB, jt_cms(rl.c, rl.s, y10, y11));
+          jt_st<T>(sm, nxt + (d2[u] >> 16) * TB, jt_spc(rl.c, rl.s, y10, y11));
         } else if (kind == 2) {
           const uint32_t k = (d0[u] >> 12) & 0xffu, c4 = d0[u] & 0xfffu;
           const int a = (int)d1[u], b = (int)d2[u];
@@ -396,9 +409,9 @@ __device__ __forceinline__ int jt_solve(unsigned char* sm, uint32_t tb0, uint32_
             const JtQuad<T> dk = jt_ldq<T>(sm, cur, (uint32_t)jt_tile(k, k), nt_);
             const JtQuad<T> dl = jt_ldq<T>(sm, cur, (uint32_t)jt_tile(l, l), nt_);
             // the coupling entry (row i = q >> 1 of pair k, column j = q & 1 of pair l)
-            const T y0 = (q >> 1) ? rk.s * t.aa + rk.c * t.ba : rk.c * t.aa - rk.s * t.ba;
-            const T y1 = (q >> 1) ? rk.s * t.ab + rk.c * t.bb : rk.c * t.ab - rk.s * t.bb;
-            const T z = (q & 1) ? rl.s * y0 + rl.c * y1 : rl.c * y0 - rl.s * y1;
+            const T y0 = (q >> 1) ? jt_spc(rk.c, rk.s, t.aa, t.ba) : jt_cms(rk.c, rk.s, t.aa, t.ba);
+            const T y1 = (q >> 1) ? jt_spc(rk.c, rk.s, t.ab, t.bb) : jt_cms(rk.c, rk.s, t.ab, t.bb);
+            const T z = (q & 1) ? jt_spc(rl.c, rl.s, y0, y1) : jt_cms(rl.c, rl.s, y0, y1);
             // new diagonal entries of the row slot and of the column slot
             const T drow = (q >> 1) ? jt_diag_b(dk, rk) : jt_diag_a(dk, rk);
             const T dcol = (q & 1) ? jt_diag_b(dl, rl) : jt_diag_a(dl, rl);

@@ -136,11 +136,17 @@ __device__ __forceinline__ int dk_tc_at(int r, int c, int sbo) {
 
 // Loewner weight of max(x, 0) for FP32 eigenvalues: same-sign pairs need no
 // division (1 for two positive, 0 for two non-positive, 1/2 for two exact
-// zeros); mixed-sign pairs take the FP64 gap test and divided difference.
-__device__ __forceinline__ float dk_tc_gamma(float lk, float ll, double tau) {
+// zeros).  A mixed-sign pair l+ > 0 >= l- whose FP32 gap l+ - l- exceeds
+// 2 tau is certainly outside the FP64 gap test's tie band, and its divided
+// difference l+ / (l+ - l-) has no cancellation, so it is taken in FP32 (an
+// FP64 division costs hundreds of cycles per warp on this part); pairs within
+// 2 tau take the FP64 gap test and divided difference.
+__device__ __forceinline__ float dk_tc_gamma(float lk, float ll, double tau, float tau2) {
   const bool pk = lk > 0.f, pl = ll > 0.f;
   if (pk && pl) return 1.f;
   if (!pk && !pl) return (lk == 0.f && ll == 0.f) ? 0.5f : 0.f;
+  const float lp = pk ? lk : ll, gap = pk ? lk - ll : ll - lk;
+  if (gap > tau2) return lp / gap;
   return (float)loewner_relu((double)lk, (double)ll, tau);
 }
 
@@ -260,16 +266,19 @@ __device__ bool dk_tc_block(int p, const float* __restrict__ U, const float* __r
   }
   for (int k = tid; k < p; k += DK_TC_NT) lamf[k] = lam[k];
   __syncthreads();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int k = 0; k < p; ++k) m = fmax(m, fabs((double)lamf[k]));
-    s_tau = tau_rel * fmax(1.0, m);
+  if (warp == 0) {
+    float m = 0.f;   // max |lambda| (exact in FP32)
+    for (int k = tid; k < p; k += 32) m = fmaxf(m, fabsf(lamf[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (tid == 0) s_tau = tau_rel * fmax(1.0, (double)m);
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t taddr = *tslot;
   const double tau = s_tau;
+  const float tau2 = (float)(2.0 * tau);
 
   // 1: W = U' G  (A = U', B rows j = G(., j))
   bool ok = dk_tc_gemm(taddr, Uth, Utl, Xh, Xl, pn, mbar, 0);
@@ -282,7 +291,7 @@ __device__ bool dk_tc_block(int p, const float* __restrict__ U, const float* __r
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int l = c + j;
-        v[j] = (k < p && l < p) ? v[j] * dk_tc_gamma(lamf[k], lamf[l], tau) : 0.f;
+        v[j] = (k < p && l < p) ? v[j] * dk_tc_gamma(lamf[k], lamf[l], tau, tau2) : 0.f;
       }
       dk_tc_put8(Xh, Xl, k, c, sbo, v);
     });

@@ -994,6 +994,9 @@ __global__ void k_soc_bwd(Prob<T, V> P, BwdPtrs<T> q) {
 //   rhobar_part = y+bar (shat - s+) - vbar y / rho^2
 //   x~bar = alpha x+bar - A' s~bar ; xbar_part = (1-alpha) x+bar
 //   alpha_bar = <shat_bar, s~ - s> + <x+bar, x~ - x>
+// The rows' s~bar goes to vbar (one gather per A' entry in the column loop
+// instead of three); 512 threads so that the largest instances take few
+// passes of the dependent row-pointer -> index -> value chain.
 template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
   __shared__ double sm[NT / 32];
@@ -1014,14 +1017,13 @@ __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
     q.grho[r] = yb * (sh - q.sn[r]) - vb * y / (rh * rh);
     acc[0] += (double)shb * (double)(st - s);
     if (!finite_(shb)) atomicOr(&q.flags[inst], F_NONFINITE);
+    q.vbar[r] = al * shb;   // s~bar, read back by the A' product below (vbar is dead after this kernel)
   }
+  __syncthreads();          // the instance's rows are all this CTA's: its own writes are visible
   for (int64_t j = c0 + threadIdx.x; j < c1; j += NT) {
     const T xb = q.xb[j];
     T acc2 = al * xb;
-    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) {
-      const int32_t r = P.AT_ci[e];
-      acc2 -= (T)ldv(P.AT_v, e) * (al * (q.rho[r] * q.yb[r] + q.vbar[r]));
-    }
+    for (int64_t e = P.AT_rp[j]; e < P.AT_rp[j + 1]; ++e) acc2 -= (T)ldv(P.AT_v, e) * q.vbar[P.AT_ci[e]];
     if (diag) q.lamt[j] = -acc2 * q.dinv[j];
     else q.adjrhs[j] = -acc2;
     q.xb2[j] = (T(1) - al) * xb;

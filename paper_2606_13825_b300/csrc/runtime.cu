@@ -23,6 +23,7 @@
 #include "../../include/cosmo_du.h"
 #include "common.cuh"
 #include "kernels_psd.cuh"
+#include "kernels_jt2.cuh"
 #include "kernels_tql.cuh"
 #include "kernels_gcg.cuh"
 #include "kernels_gcs.cuh"
@@ -426,6 +427,35 @@ struct cosmo_batch {
   std::unique_ptr<HostStepBufs> hostbufs;
 };
 
+// Instantiations of the compile-time-geometry Jacobi (k_psd_fwd_jt2): size
+// classes PMAX = 32, 56, 80 at CTA sizes 128..1024 where a thread's work fits
+// its registers (at most three tiles and two eigenvector chunks per thread).
+template <class T, int PMAX, int NT>
+struct Jt2Cfg {
+  using G = Jt2Geo<T, PMAX>;
+  static constexpr bool room = NT > 32 * G::PW;
+  static constexpr int TI = room ? G::items_t(NT) : 1;
+  static constexpr int CI = room ? G::items_c(NT) : 1;
+  // FP64 items take twice the registers: fewer per thread (no spills at 64 registers)
+  static constexpr bool ok = room && (sizeof(T) == 4 ? (TI <= 3 && CI <= 2) : (TI <= 2 && CI <= 1));
+};
+inline int jt2_pmax(int p) { return p <= 32 ? 32 : (p <= 56 ? 56 : (p <= 80 ? 80 : 0)); }
+template <class T, class F>
+inline void jt2_for(int pmax, int nt, F f) {   // f(Jt2Cfg) for the (pmax, nt) instantiation, if it exists
+#define COSMO_JT2_CASE(PM_, NT_) \
+  if (pmax == PM_ && nt == NT_) { if constexpr (Jt2Cfg<T, PM_, NT_>::ok) f(Jt2Cfg<T, PM_, NT_>{}, std::integral_constant<int, PM_>{}, std::integral_constant<int, NT_>{}); return; }
+  COSMO_JT2_CASE(32, 128) COSMO_JT2_CASE(32, 256) COSMO_JT2_CASE(32, 512) COSMO_JT2_CASE(32, 1024)
+  COSMO_JT2_CASE(56, 128) COSMO_JT2_CASE(56, 256) COSMO_JT2_CASE(56, 512) COSMO_JT2_CASE(56, 1024)
+  COSMO_JT2_CASE(80, 128) COSMO_JT2_CASE(80, 256) COSMO_JT2_CASE(80, 512) COSMO_JT2_CASE(80, 1024)
+#undef COSMO_JT2_CASE
+}
+template <class T>
+inline bool jt2_exists(int pmax, int nt) {
+  bool ok = false;
+  jt2_for<T>(pmax, nt, [&](auto, auto, auto) { ok = true; });
+  return ok;
+}
+
 template <class T, class V>
 struct ImplT : Impl {
   cosmo_options opt;
@@ -625,7 +655,10 @@ struct ImplT : Impl {
       // Blocks above the cutoff (option eig_jacobi_max_p; by default the
       // largest p whose warm-started Jacobi and DK fit in shared memory) take
       // the large-block path with 256 threads.
-      const int variant = opt.eig_variant == 0 ? 2 : opt.eig_variant;
+      const int variant = opt.eig_variant == 0 || opt.eig_variant == 3 ? 2 : opt.eig_variant;
+      auto jt2_ok = [&](int p, int fnt) {
+        return jt2_pmax(p) && jt2_exists<T>(jt2_pmax(p), fnt) && (int64_t)jt2_bytes(p, fnt) <= maxs;
+      };
       auto fwd_threads = [&](int p) { return opt.eig_threads ? opt.eig_threads : (p > 56 ? 512 : (p > 32 ? 256 : 128)); };
       auto fits_jacobi = [&](int p) {
         const int nt = p > 56 ? 512 : (p > 32 ? 256 : 128), fnt = fwd_threads(p);
@@ -647,13 +680,17 @@ struct ImplT : Impl {
         const int method = cls == 1000 ? 1 : 0;
         const int nt = method ? 256 : cls;
         const int fnt = method ? 256 : fwd_threads(p0);
+        const int bvar = (opt.eig_variant == 0 || opt.eig_variant == 3) && method == 0 && jt2_ok(p0, fnt) ? 3 : variant;
+        if (opt.eig_variant == 3 && method == 0 && bvar != 3)
+          return fail(COSMO_E_INVAL, "eig_variant 3: no instantiation for order %d with %d threads", p0, fnt);
         Bucket bk{(int)q, (int)(e - q), p0, nt, nullptr, nullptr,
                   method == 0 && (variant == 2 || (int64_t)psd_fwd_smem_warm<T>(p0, fnt) <= (int64_t)maxs), method,
-                  fnt, jt_ipt(p0, fnt) <= 2 ? 2 : (jt_ipt(p0, fnt) <= 4 ? 4 : 8), variant};
+                  fnt, jt_ipt(p0, fnt) <= 2 ? 2 : (jt_ipt(p0, fnt) <= 4 ? 4 : 8), bvar};
         CU(cudaStreamCreateWithFlags(&bk.s, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
         if (method == 0) {
-          const size_t fs = variant == 2 ? jt_smem<T>(p0, fnt) : psd_fwd_smem<T>(p0, fnt), bs = psd_bwd_smem<T>(p0, nt);
+          const size_t fs = bvar == 3 ? jt2_bytes(p0, fnt) : (variant == 2 ? jt_smem<T>(p0, fnt) : psd_fwd_smem<T>(p0, fnt)),
+                       bs = psd_bwd_smem<T>(p0, nt);
           if ((int64_t)fs > maxs || (int64_t)bs > maxs)
             return fail(COSMO_E_INVAL, "PSD order %d needs %zu B of shared memory (device allows %d)",
                         p0, std::max(fs, bs), maxs);
@@ -679,6 +716,15 @@ struct ImplT : Impl {
       COSMO_JT_ATTR(512, 2); COSMO_JT_ATTR(512, 4); COSMO_JT_ATTR(512, 8);
       COSMO_JT_ATTR(1024, 2); COSMO_JT_ATTR(1024, 4); COSMO_JT_ATTR(1024, 8);
 #undef COSMO_JT_ATTR
+      for (int pm : {32, 56, 80})
+        for (int nt_ : {128, 256, 512, 1024})
+          jt2_for<T>(pm, nt_, [&](auto c, auto pmc, auto ntc) {
+            using C = decltype(c);
+            if ((int64_t)Jt2Geo<T, decltype(pmc)::value>::bytes(ntc) <= maxs)
+              cudaFuncSetAttribute(k_psd_fwd_jt2<T, V, decltype(ntc)::value, decltype(pmc)::value, C::TI, C::CI>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+          });
+      CU(cudaGetLastError());
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -714,6 +760,14 @@ struct ImplT : Impl {
              (long long)h.A_ci.size(), (long long)h.P_ci.size(), (long long)h.n, (long long)h.m);
     return std::string(buf);
   }
+  static size_t jt2_bytes(int p, int fnt) {
+    size_t b = 0;
+    jt2_for<T>(jt2_pmax(p), fnt, [&](auto, auto pmc, auto) { b = Jt2Geo<T, decltype(pmc)::value>::bytes(fnt); });
+    return b;
+  }
+  bool jt2_fits(int p, int fnt) const {
+    return jt2_pmax(p) && jt2_exists<T>(jt2_pmax(p), fnt) && (int64_t)jt2_bytes(p, fnt) <= smem_max;
+  }
   bool jt_fits(int p, int fnt) const {
     return fnt > 32 * jt_pair_warps(p) && (int64_t)jt_smem<T>(p, fnt) <= smem_max && jt_ipt(p, fnt) <= 8 && p <= 180;
   }
@@ -735,9 +789,10 @@ struct ImplT : Impl {
       bk.fnt = 256;
       return COSMO_OK;
     }
-    const int variant = opt.eig_variant == 0 ? 2 : opt.eig_variant;
-    const bool ok = variant == 2 ? jt_fits(bk.maxp, fnt)
-                                 : (fnt <= 512 && fnt >= 128 && (int64_t)psd_fwd_smem_warm<T>(bk.maxp, fnt) <= smem_max);
+    const int variant = opt.eig_variant == 0 ? (jt2_fits(bk.maxp, fnt) ? 3 : 2) : opt.eig_variant;
+    const bool ok = variant == 3   ? jt2_fits(bk.maxp, fnt)
+                    : variant == 2 ? jt_fits(bk.maxp, fnt)
+                                   : (fnt <= 512 && fnt >= 128 && (int64_t)psd_fwd_smem_warm<T>(bk.maxp, fnt) <= smem_max);
     Bucket t = bk;
     t.method = 0;
     if (!ok || !bwd_fits(t)) return fail(COSMO_E_INVAL, "order %d does not fit Jacobi with %d threads", bk.maxp, fnt);
@@ -850,7 +905,7 @@ struct ImplT : Impl {
         if (opt.eig_jacobi_max_p == 0 && base.maxp >= 48) cands.push_back(std::make_pair(1, 256));
         for (const auto& c : cands) {
           Bucket bk = base;
-          if (c.first == 1 ? !ql_fits(bk.maxp) : !jt_fits(bk.maxp, c.second)) continue;
+          if (c.first == 1 ? !ql_fits(bk.maxp) : !(jt2_fits(bk.maxp, c.second) || jt_fits(bk.maxp, c.second))) continue;
           if (config_bucket(bk, c.first, c.second) != COSMO_OK) { g_err.clear(); continue; }
           const T* up = bk.method == 0 && opt.eig_warm_start ? U0 : nullptr;
           const float f = time_min(st, [&]() { psd_fwd_bucket(bk, st, io1, lam, U1, up, fl, nullptr); });
@@ -1265,6 +1320,15 @@ struct ImplT : Impl {
       k_psd_fwd_tql<T, V, 256><<<bk.count, 256, tql_smem<T>(bk.maxp, 256), s>>>(P, io, lam, U, fl, bk.start, stt, 30 * 4);
       return;
     }
+    if (bk.variant == 3) {
+      jt2_for<T>(jt2_pmax(bk.maxp), bk.fnt, [&](auto c, auto pmc, auto ntc) {
+        using C = decltype(c);
+        constexpr int PM = decltype(pmc)::value, NT_ = decltype(ntc)::value;
+        k_psd_fwd_jt2<T, V, NT_, PM, C::TI, C::CI><<<bk.count, NT_, Jt2Geo<T, PM>::bytes(NT_), s>>>(
+            P, io, lam, U, opt.eig_tol, opt.eig_max_sweeps, fl, bk.start, stt, up);
+      });
+      return;
+    }
     if (bk.variant == 2) {
       const size_t sm = jt_smem<T>(bk.maxp, bk.fnt);
 #define COSMO_JT_LAUNCH(NT_, IPT_) \
@@ -1392,7 +1456,7 @@ struct ImplT : Impl {
       PsdBwdIO<T> io{gproj, vbar, P.row_inst};
       psd_group("psd_bwd", st, [&](const Bucket& bk, cudaStream_t s) { psd_bwd_bucket(bk, s, io, q.lam, q.U, flags); });
     }
-    launch("bwd_relax", k_bwd_relax<T, V, 256>, h.ninst, 256, 0, st, P, q);
+    launch("bwd_relax", k_bwd_relax<T, V, 512>, h.ninst, 512, 0, st, P, q);
     CgArgs<T> ca{};
     ca.rhs = adjrhs; ca.x = lamt; ca.x0 = nullptr; ca.rho = q.rho;
     ca.dinv = dinv + (int64_t)k * h.n; ca.sigma = q.sigma; ca.r = cg_r; ca.p = cg_p; ca.u = cg_u;
@@ -2025,7 +2089,7 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
   if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
       !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
-      !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 2 ||
+      !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 3 ||
       !(o.autotune == 0 || o.autotune == 1) ||
       !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512 ||
         (o.eig_threads == 1024 && o.eig_variant != 1)))

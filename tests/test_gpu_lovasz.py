@@ -27,7 +27,8 @@ def _run(b, K, rho, alpha):
     rp2, rd2, obj = b.residuals(xK, sK, yK)
     torch.cuda.synchronize()
     n = lambda v: v.double().cpu().numpy()
-    return {"loss": n(loss), "obj": n(obj), "grho": n(g["grho"]), "galpha": n(g["galpha"])}
+    return {"loss": n(loss), "obj": n(obj), "grho": n(g["grho"]), "galpha": n(g["galpha"]), "rp2": n(rp2),
+            "rd2": n(rd2)}
 
 
 def test_lovasz_parity_subset():
@@ -81,5 +82,14 @@ def test_lovasz_full_size_mixed_vs_fp64():
     # parity subset above).
     m, d = res["mixed"], res["fp64"]
     obj_err = np.abs(m["obj"] - d["obj"]) / np.abs(d["obj"])
+    ro = b.packed.row_off
+    gerr = np.array([rel_l2(m["grho"][:, ro[i]:ro[i + 1]], d["grho"][:, ro[i]:ro[i + 1]]) for i in range(len(probs))])
+    aerr = np.array([rel_l2(m["galpha"][:, i], d["galpha"][:, i]) for i in range(len(probs))])
+    rerr = np.abs(np.sqrt(m["rp2"]) - np.sqrt(d["rp2"])) / np.maximum(np.sqrt(d["rp2"]), 1e-30)
+    derr = np.abs(np.sqrt(m["rd2"]) - np.sqrt(d["rd2"])) / np.maximum(np.sqrt(d["rd2"]), 1e-30)
+    print(f"\nLovasz full size, mixed vs FP64: objective max {obj_err[:64].max():.2e} (G(n,1/2)) "
+          f"{obj_err[64:].max():.2e} (vertex-transitive); residual norms (value-relative) primal max "
+          f"{rerr.max():.2e} dual max {derr.max():.2e}; rho-bar median {np.median(gerr):.2e} max {gerr.max():.2e}; "
+          f"alpha-bar median {np.median(aerr):.2e} max {aerr.max():.2e}")
     assert np.max(obj_err) < 5e-3, np.max(obj_err)
     assert np.max(obj_err[64:]) < 1e-3, np.max(obj_err[64:])

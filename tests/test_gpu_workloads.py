@@ -73,12 +73,13 @@ def _run(b, K, lr, ak):
     rho = b.rho_from_log(lr, 1e3)
     alpha = b.alpha_broadcast(ak)
     xK, sK, yK, loss = b.forward(K, rho, alpha)
-    g = b.backward(gloss=torch.ones(b.ninst, dtype=torch.float64, device="cuda"), want_start=False)
+    g = b.backward(gloss=torch.ones(b.ninst, dtype=torch.float64, device="cuda"), want_start=True)
     rp2, rd2, obj = b.residuals(xK, sK, yK)
     torch.cuda.synchronize()
     np_ = lambda t: t.double().cpu().numpy()
     return {"loss": np_(loss), "grho": np_(g["grho"]), "galpha": np_(g["galpha"]), "x": np_(xK),
-            "s": np_(sK), "y": np_(yK), "rp2": np_(rp2), "rd2": np_(rd2), "obj": np_(obj)}
+            "s": np_(sK), "y": np_(yK), "rp2": np_(rp2), "rd2": np_(rd2), "obj": np_(obj),
+            "gx0": np_(g["gx0"]), "gs0": np_(g["gs0"]), "gy0": np_(g["gy0"])}
 
 
 def test_full_size_batched_maxcut(config2):
@@ -114,7 +115,7 @@ def test_full_size_batched_maxcut(config2):
     # 1e-3; no instance takes another branch of the projection (the inertia of
     # every block at every step is the FP64 run's); at least 98% of all
     # instances meet 1e-3 and none exceeds 1e-2.
-    errs, erra = [], []
+    errs, erra, errz = [], [], []
     for i in range(len(config2)):
         pr = config2[i]
         cs, rs = slice(co[i], co[i + 1]), slice(ro[i], ro[i + 1])
@@ -126,7 +127,9 @@ def test_full_size_batched_maxcut(config2):
         assert abs(math.sqrt(rd_m[i]) - math.sqrt(rd_d[i])) <= 1e-4 * scale_d, i
         errs.append(rel_l2(grho_m[:, rs], grho_d[:, rs]))
         erra.append(rel_l2(ga_m[:, i], ga_d[:, i]))
-    errs, erra = np.array(errs), np.array(erra)
+        errz.append(max(rel_l2(m["gx0"][cs], d["gx0"][cs]), rel_l2(m["gs0"][rs], d["gs0"][rs]),
+                        rel_l2(m["gy0"][rs], d["gy0"][rs])))
+    errs, erra, errz = np.array(errs), np.array(erra), np.array(errz)
     ps = [pr.cones[1][1] for pr in config2]
     off = np.concatenate([[0], np.cumsum(ps)])
     margin = np.full(len(config2), np.inf)
@@ -140,10 +143,12 @@ def test_full_size_batched_maxcut(config2):
     worst = np.maximum(errs, erra)
     far = margin >= 1e-3
     print(f"\nC2 gradients, mixed vs FP64 per instance: rho median {np.median(errs):.2e} max {errs.max():.2e}; "
-          f"alpha median {np.median(erra):.2e} max {erra.max():.2e}; {int((worst > 1e-3).sum())} of "
+          f"alpha median {np.median(erra):.2e} max {erra.max():.2e}; start (x0, s0, y0) median "
+          f"{np.median(errz):.2e} max {errz.max():.2e}; {int((worst > 1e-3).sum())} of "
           f"{len(worst)} above 1e-3 (margins {np.sort(margin[worst > 1e-3])}); {int(far.sum())} instances "
           f"with margin >= 1e-3, max error there {worst[far].max():.2e}")
     assert worst[far].max() <= 1e-3, worst[far].max()
+    assert errz[far].max() <= 1e-2, np.sort(errz[far])[-5:]
     assert (worst <= 1e-3).mean() >= 0.98 and worst.max() <= 1e-2, (np.sort(worst)[-5:])
     # sampled instances against the oracle (the smallest ones finish in seconds)
     order = np.argsort([p.meta["nv"] for p in config2], kind="stable")[:3]
