@@ -560,6 +560,11 @@ def main():
     n_inst = len(probs)
     opts = dict(spec["opts"])
     use_graph = int(opts.pop("use_graph", 0))
+    if args.profile:
+        # the profiled command is deterministic: the shape rules' launch
+        # configuration (on this workload the one the autotuner keeps: Jacobi
+        # at 512 / 256 / 128 threads), no timed candidates before the step
+        opts["autotune"] = 0
     b = CosmoBatch(probs, precision="mixed", value_type=spec["value_type"], device=local,
                    use_graph=use_graph, **opts)
     lr = torch.full((K,), math.log(0.1), dtype=torch.float64, device=dev, requires_grad=True)

@@ -187,8 +187,8 @@ typedef struct {
  * rules, or by the autotuner (option autotune = 1), which at batch creation
  * times on the device, with synthetic data of the batch's own shapes:
  *   - per class, the slot-layout Jacobi at CTA sizes 128 / 256 / 512 / 1024
- *     (those that fit, each on the compile-time geometry where it has an
- *     instantiation; projection of a perturbed block warm-started from the
+ *     and, on the compile-time geometry of orders above 32, 384 (those that
+ *     fit, each on the compile-time geometry where it has an instantiation; projection of a perturbed block warm-started from the
  *     eigenvectors of the unperturbed one), and for classes of order >= 48
  *     the tridiagonal + QL path, each with its backward (Daleckii-Krein)
  *     kernel;

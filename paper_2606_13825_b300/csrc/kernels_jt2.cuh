@@ -73,6 +73,7 @@ struct Jt2Geo {
   static constexpr int items_t(int nt) { return (NPM * (NPM - 1) / 2 + (nt - 32 * PW) - 1) / (nt - 32 * PW); }
   static constexpr int items_c(int nt) { return (NPM * HC + (nt - 32 * PW) - 1) / (nt - 32 * PW); }
   static_assert(8 * PS >= PE * LDS, "the tile region doubles as the product buffer");
+  static_assert(LDV >= LDS, "a V buffer holds the transposed eigenvectors with the odd stride");
   static_assert((LDV * sizeof(T)) % 16 == 0 && (VBUF * sizeof(T)) % 16 == 0, "16-byte rows");
 };
 
@@ -379,7 +380,9 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
     // B = V' S V (upper triangle read below): C = Vt S into X, then C Vt' into S
     smem_gemm_auto<T>(p, V1, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
     __syncthreads();
-    smem_gemm_auto<T>(p, X, lds, 1, V1, 1, ldv, [&](int i, int j, T v) { S[i * lds + j] = v; });
+    // (X Vt')(i, j) formed as (Vt X')(j, i): the lanes then walk X with its odd
+    // row stride instead of Vt with its 16-byte-multiple one (no bank conflicts)
+    smem_gemm_auto<T>(p, V1, ldv, 1, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
     __syncthreads();
   }
   // round-0 tiles (slot layout, tile buffer 0) from the upper triangle of S,
@@ -424,11 +427,18 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
     Vt[jt_slot_index(0, s, np) * ldv + j] = Vs[e];
   }
   __syncthreads();
+  // Vt' with the odd row stride in the free buffer, for Vt Vt' below
+  T* const Vtt = Vs;
+  for (int e = threadIdx.x; e < p * p; e += NT) {
+    const int i = e / p, k = e - i * p;
+    Vtt[k * lds + i] = Vt[i * ldv + k];
+  }
+  __syncthreads();
   // Refinement (as in k_psd_fwd_jt): one Newton-Schulz step on Vt, the
   // Rayleigh-Ritz matrix A = Vt S Vt' of S formed again, eigenvalues
   // L = diag A, and Pi = Vt' (max(L, 0) + G o E) Vt with E the off-diagonal
   // of A and G the Loewner matrix of max(x, 0) at L (Eq. lowner).
-  smem_gemm_auto<T>(p, Vt, ldv, 1, Vt, 1, ldv, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  smem_gemm_auto<T>(p, Vt, ldv, 1, Vtt, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
   __syncthreads();
   smem_gemm_auto<T>(p, X, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
   __syncthreads();
@@ -441,7 +451,7 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
   __syncthreads();
   smem_gemm_auto<T>(p, Vt, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
   __syncthreads();
-  smem_gemm_auto<T>(p, X, lds, 1, Vt, 1, ldv, [&](int i, int j, T v) { S[i * lds + j] = v; });
+  smem_gemm_auto<T>(p, Vt, ldv, 1, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
   __syncthreads();
   for (int i = threadIdx.x; i < p; i += NT) lamv[i] = S[i * lds + i];
   __syncthreads();

@@ -228,26 +228,36 @@ __device__ bool dk_tc_block(int p, const float* __restrict__ U, const float* __r
   const uint32_t ncols = pn <= 32 ? 32u : (pn <= 64 ? 64u : 128u);
   if (warp == 0) tc::alloc(tslot, ncols);
   if (tid == 0) tc::mbar_init(mbar, 1);
-  // staging in destination order: thread f writes the 16-byte core-matrix
-  // row (r, c..c+3), consecutive threads consecutive rows of a core matrix
-  // (no bank conflicts); U is read from L2 with strided scalar loads
+  // Staging.  U (column-major, contiguous) and g (svec, contiguous) are first
+  // copied into shared memory with coalesced loads (U into the G buffer, g
+  // into the tail past the last operand buffer, which only the unused rows of
+  // a 128-row A operand read); the operands are then written in destination
+  // order from there: thread f writes the 16-byte core-matrix row (r,
+  // c..c+3), consecutive threads consecutive rows of a core matrix.
   const int q4 = pn / 4;
+  const int ps = (p * (p | 1) <= nb) ? (p | 1) : p;   // raw U stride (odd where it fits)
+  float* const Ur = Xh;                              // raw U: column k at Ur + k ps
+  float* const gr = Xl + nb;                         // raw svec g
+  {
+    const int d = p * (p + 1) / 2;
+#pragma unroll 4
+    for (int e = tid; e < p * p; e += DK_TC_NT) {
+      const int k = e / p, i = e - k * p;
+      Ur[k * ps + i] = U[e];
+    }
+#pragma unroll 4
+    for (int e = tid; e < d; e += DK_TC_NT) gr[e] = g[e];
+  }
+  __syncthreads();
   for (int f = tid; f < pn * q4; f += DK_TC_NT) {
     const int r = ((f >> 3) / q4) * 8 + (f & 7), c = ((f >> 3) % q4) * 4;
-    float ut[4], ur[4], gv[4];
+    float ut[4], ur[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int cc = c + j;
       const bool in = r < p && cc < p;
-      ut[j] = in ? U[r * p + cc] : 0.f;          // U'(r, cc) = U(cc, r)
-      ur[j] = in ? U[cc * p + r] : 0.f;          // U(r, cc)
-      float g0 = 0.f;
-      if (in) {
-        const int i = min(r, cc), jj = max(r, cc);
-        g0 = g[jj * (jj + 1) / 2 + i];
-        if (i != jj) g0 *= (float)kInvSqrt2;
-      }
-      gv[j] = g0;                                // G (symmetric)
+      ut[j] = in ? Ur[r * ps + cc] : 0.f;        // U'(r, cc) = U(cc, r)
+      ur[j] = in ? Ur[cc * ps + r] : 0.f;        // U(r, cc)
     }
     const int idx = dk_tc_at(r, c, sbo);
     float4 h, l;
@@ -259,8 +269,26 @@ __device__ bool dk_tc_block(int p, const float* __restrict__ U, const float* __r
     l = make_float4(tc::tf32(ur[0] - h.x), tc::tf32(ur[1] - h.y), tc::tf32(ur[2] - h.z), tc::tf32(ur[3] - h.w));
     *reinterpret_cast<float4*>(Urh + idx) = h;
     *reinterpret_cast<float4*>(Url + idx) = l;
-    h = make_float4(tc::tf32(gv[0]), tc::tf32(gv[1]), tc::tf32(gv[2]), tc::tf32(gv[3]));
-    l = make_float4(tc::tf32(gv[0] - h.x), tc::tf32(gv[1] - h.y), tc::tf32(gv[2] - h.z), tc::tf32(gv[3] - h.w));
+  }
+  __syncthreads();   // raw U is read: its buffer takes G
+  for (int f = tid; f < pn * q4; f += DK_TC_NT) {
+    const int r = ((f >> 3) / q4) * 8 + (f & 7), c = ((f >> 3) % q4) * 4;
+    float gv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = c + j;
+      float g0 = 0.f;
+      if (r < p && cc < p) {
+        const int i = min(r, cc), jj = max(r, cc);
+        g0 = gr[jj * (jj + 1) / 2 + i];
+        if (i != jj) g0 *= (float)kInvSqrt2;
+      }
+      gv[j] = g0;                                // G (symmetric)
+    }
+    const int idx = dk_tc_at(r, c, sbo);
+    const float4 h = make_float4(tc::tf32(gv[0]), tc::tf32(gv[1]), tc::tf32(gv[2]), tc::tf32(gv[3]));
+    const float4 l = make_float4(tc::tf32(gv[0] - h.x), tc::tf32(gv[1] - h.y), tc::tf32(gv[2] - h.z),
+                                 tc::tf32(gv[3] - h.w));
     *reinterpret_cast<float4*>(Xh + idx) = h;
     *reinterpret_cast<float4*>(Xl + idx) = l;
   }

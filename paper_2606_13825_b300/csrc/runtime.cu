@@ -445,8 +445,10 @@ inline void jt2_for(int pmax, int nt, F f) {   // f(Jt2Cfg) for the (pmax, nt) i
 #define COSMO_JT2_CASE(PM_, NT_) \
   if (pmax == PM_ && nt == NT_) { if constexpr (Jt2Cfg<T, PM_, NT_>::ok) f(Jt2Cfg<T, PM_, NT_>{}, std::integral_constant<int, PM_>{}, std::integral_constant<int, NT_>{}); return; }
   COSMO_JT2_CASE(32, 128) COSMO_JT2_CASE(32, 256) COSMO_JT2_CASE(32, 512) COSMO_JT2_CASE(32, 1024)
-  COSMO_JT2_CASE(56, 128) COSMO_JT2_CASE(56, 256) COSMO_JT2_CASE(56, 512) COSMO_JT2_CASE(56, 1024)
-  COSMO_JT2_CASE(80, 128) COSMO_JT2_CASE(80, 256) COSMO_JT2_CASE(80, 512) COSMO_JT2_CASE(80, 1024)
+  COSMO_JT2_CASE(56, 128) COSMO_JT2_CASE(56, 256) COSMO_JT2_CASE(56, 384) COSMO_JT2_CASE(56, 512)
+  COSMO_JT2_CASE(56, 1024)
+  COSMO_JT2_CASE(80, 128) COSMO_JT2_CASE(80, 256) COSMO_JT2_CASE(80, 384) COSMO_JT2_CASE(80, 512)
+  COSMO_JT2_CASE(80, 1024)
 #undef COSMO_JT2_CASE
 }
 template <class T>
@@ -717,7 +719,7 @@ struct ImplT : Impl {
       COSMO_JT_ATTR(1024, 2); COSMO_JT_ATTR(1024, 4); COSMO_JT_ATTR(1024, 8);
 #undef COSMO_JT_ATTR
       for (int pm : {32, 56, 80})
-        for (int nt_ : {128, 256, 512, 1024})
+        for (int nt_ : {128, 256, 384, 512, 1024})
           jt2_for<T>(pm, nt_, [&](auto c, auto pmc, auto ntc) {
             using C = decltype(c);
             if ((int64_t)Jt2Geo<T, decltype(pmc)::value>::bytes(ntc) <= maxs)
@@ -769,7 +771,7 @@ struct ImplT : Impl {
     return jt2_pmax(p) && jt2_exists<T>(jt2_pmax(p), fnt) && (int64_t)jt2_bytes(p, fnt) <= smem_max;
   }
   bool jt_fits(int p, int fnt) const {
-    return fnt > 32 * jt_pair_warps(p) && (int64_t)jt_smem<T>(p, fnt) <= smem_max && jt_ipt(p, fnt) <= 8 && p <= 180;
+    return (fnt == 128 || fnt == 256 || fnt == 512 || fnt == 1024) && fnt > 32 * jt_pair_warps(p) && (int64_t)jt_smem<T>(p, fnt) <= smem_max && jt_ipt(p, fnt) <= 8 && p <= 180;
   }
   bool ql_fits(int p) const { return (int64_t)tql_smem<T>(p, 256) <= smem_max; }
   bool bwd_fits(const Bucket& bk) const {
@@ -901,7 +903,7 @@ struct ImplT : Impl {
         float best = 3.0e38f;
         float bwd[2] = {-1.f, -1.f};
         std::vector<std::pair<int, int>> cands;
-        for (int fnt : {128, 256, 512, 1024}) cands.push_back(std::make_pair(0, fnt));
+        for (int fnt : {128, 256, 384, 512, 1024}) cands.push_back(std::make_pair(0, fnt));
         if (opt.eig_jacobi_max_p == 0 && base.maxp >= 48) cands.push_back(std::make_pair(1, 256));
         for (const auto& c : cands) {
           Bucket bk = base;
