@@ -169,12 +169,13 @@ typedef struct {
                                2 the matrix in round-robin slot order as 2x2 tiles with the
                                next round's rotations formed in the same pass (one barrier
                                per round), 3 the same solver on a compile-time geometry per
-                               size class (orders up to 32, 56, 80; eigenvectors kept by slot
+                               size class (orders up to 8, 16, 32, 56, 80; eigenvectors kept by slot
                                in a double buffer; a class without an instantiation for its
                                CTA size is an error).  All give the eigen-decomposition to
                                eig_tol. */
-  int32_t eig_threads;      /* CTA size of the Jacobi projection: 0 by block order (128 up
-                               to p = 32, 256 up to 56, 512 above), or 128, 256, 512 (or
+  int32_t eig_threads;      /* CTA size of the Jacobi projection: 0 by block order (64 up
+                               to p = 16 on the compile-time geometry, 128 up to 32, 256 up
+                               to 56, 512 above), or 128, 256, 512 (or
                                1024 with eig_variant 0, 2 or 3) for every block */
   int32_t autotune;         /* 1: at batch creation, time the candidate launch
                                configurations of what the options leave automatic and keep

@@ -42,6 +42,80 @@ __device__ __forceinline__ void jt2_rotv(double2& a, double2& b, JtRot<double> r
   b = make_double2(jt_spc(r.c, r.s, x.x, y.x), jt_spc(r.c, r.s, x.y, y.y));
 }
 
+// C = A B for A with 16-byte-aligned rows contiguous along k (the eigenvector
+// rows Vt): the warp-strided mapping of smem_gemm_w (warp w owns rows
+// w + TY a, lane owns columns lane + 32 b), A read a 16-byte vector (four
+// or two k) at a time.  The sum runs over k in the same order with the same
+// fused multiply-adds, so the result is the one smem_gemm_w gives.
+template <class T, int TM, int TN, class F>
+__device__ __forceinline__ void jt2_gemm_w(int p, const T* A, int ar, const T* B, int br, int bc, F f) {
+  using VT = typename Vec16<T>::type;
+  constexpr int VL = 16 / (int)sizeof(T);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, TY = blockDim.x >> 5;
+  const int pk = p & ~(VL - 1);
+  for (int i0 = w; i0 < p; i0 += TM * TY) {
+    for (int j0 = lane; j0 < p; j0 += TN * 32) {
+      T acc[TM][TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+      int ii[TM], jj[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) ii[a] = min(i0 + a * TY, p - 1);
+#pragma unroll
+      for (int b = 0; b < TN; ++b) jj[b] = min(j0 + b * 32, p - 1);
+      int k = 0;
+      for (; k < pk; k += VL) {
+        T av[TM][VL];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+          const VT v = *reinterpret_cast<const VT*>(A + ii[a] * ar + k);
+          const T* c = reinterpret_cast<const T*>(&v);
+#pragma unroll
+          for (int q = 0; q < VL; ++q) av[a][q] = c[q];
+        }
+#pragma unroll
+        for (int q = 0; q < VL; ++q) {
+          T bv[TN];
+#pragma unroll
+          for (int b = 0; b < TN; ++b) bv[b] = B[(k + q) * br + jj[b] * bc];
+#pragma unroll
+          for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a][q], bv[b], acc[a][b]);
+        }
+      }
+      for (; k < p; ++k) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = A[ii[a] * ar + k];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = B[k * br + jj[b] * bc];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b)
+          if (i0 + a * TY < p && j0 + b * 32 < p) f(i0 + a * TY, j0 + b * 32, acc[a][b]);
+    }
+  }
+}
+template <class T, class F>
+__device__ __forceinline__ void jt2_gemm(int p, const T* A, int ar, const T* B, int br, int bc, F f) {
+  if constexpr (sizeof(T) == 8) {   // FP64: the scalar form (the vector one spills at 64 registers)
+    smem_gemm_auto<T>(p, A, ar, 1, B, br, bc, f);
+    return;
+  }
+  if (blockDim.x >= 512) jt2_gemm_w<T, 5, 3>(p, A, ar, B, br, bc, f);
+  else if (blockDim.x >= 256) jt2_gemm_w<T, 7, 2>(p, A, ar, B, br, bc, f);
+  else jt2_gemm_w<T, 8, 1>(p, A, ar, B, br, bc, f);
+}
+
 // Geometry for orders p <= PMAX (byte offsets from the dynamic shared base):
 //   V   [2][PE][LDV]  eigenvectors by row, two buffers (index order outside
 //                     the solve, slot order inside it)
@@ -378,11 +452,11 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
   __syncthreads();
   if (warm) {
     // B = V' S V (upper triangle read below): C = Vt S into X, then C Vt' into S
-    smem_gemm_auto<T>(p, V1, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+    jt2_gemm<T>(p, V1, ldv, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
     __syncthreads();
     // (X Vt')(i, j) formed as (Vt X')(j, i): the lanes then walk X with its odd
     // row stride instead of Vt with its 16-byte-multiple one (no bank conflicts)
-    smem_gemm_auto<T>(p, V1, ldv, 1, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
+    jt2_gemm<T>(p, V1, ldv, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
     __syncthreads();
   }
   // round-0 tiles (slot layout, tile buffer 0) from the upper triangle of S,
@@ -438,7 +512,7 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
   // Rayleigh-Ritz matrix A = Vt S Vt' of S formed again, eigenvalues
   // L = diag A, and Pi = Vt' (max(L, 0) + G o E) Vt with E the off-diagonal
   // of A and G the Loewner matrix of max(x, 0) at L (Eq. lowner).
-  smem_gemm_auto<T>(p, Vt, ldv, 1, Vtt, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  jt2_gemm<T>(p, Vt, ldv, Vtt, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
   __syncthreads();
   smem_gemm_auto<T>(p, X, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
   __syncthreads();
@@ -449,9 +523,9 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
   __syncthreads();
   load_S();
   __syncthreads();
-  smem_gemm_auto<T>(p, Vt, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  jt2_gemm<T>(p, Vt, ldv, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
   __syncthreads();
-  smem_gemm_auto<T>(p, Vt, ldv, 1, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
+  jt2_gemm<T>(p, Vt, ldv, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
   __syncthreads();
   for (int i = threadIdx.x; i < p; i += NT) lamv[i] = S[i * lds + i];
   __syncthreads();

@@ -439,11 +439,12 @@ struct Jt2Cfg {
   // FP64 items take twice the registers: fewer per thread (no spills at 64 registers)
   static constexpr bool ok = room && (sizeof(T) == 4 ? (TI <= 3 && CI <= 2) : (TI <= 2 && CI <= 1));
 };
-inline int jt2_pmax(int p) { return p <= 32 ? 32 : (p <= 56 ? 56 : (p <= 80 ? 80 : 0)); }
+inline int jt2_pmax(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : (p <= 32 ? 32 : (p <= 56 ? 56 : (p <= 80 ? 80 : 0)))); }
 template <class T, class F>
 inline void jt2_for(int pmax, int nt, F f) {   // f(Jt2Cfg) for the (pmax, nt) instantiation, if it exists
 #define COSMO_JT2_CASE(PM_, NT_) \
   if (pmax == PM_ && nt == NT_) { if constexpr (Jt2Cfg<T, PM_, NT_>::ok) f(Jt2Cfg<T, PM_, NT_>{}, std::integral_constant<int, PM_>{}, std::integral_constant<int, NT_>{}); return; }
+  COSMO_JT2_CASE(8, 64) COSMO_JT2_CASE(8, 128) COSMO_JT2_CASE(16, 64) COSMO_JT2_CASE(16, 128)
   COSMO_JT2_CASE(32, 128) COSMO_JT2_CASE(32, 256) COSMO_JT2_CASE(32, 512) COSMO_JT2_CASE(32, 1024)
   COSMO_JT2_CASE(56, 128) COSMO_JT2_CASE(56, 256) COSMO_JT2_CASE(56, 384) COSMO_JT2_CASE(56, 512)
   COSMO_JT2_CASE(56, 1024)
@@ -661,7 +662,12 @@ struct ImplT : Impl {
       auto jt2_ok = [&](int p, int fnt) {
         return jt2_pmax(p) && jt2_exists<T>(jt2_pmax(p), fnt) && (int64_t)jt2_bytes(p, fnt) <= maxs;
       };
-      auto fwd_threads = [&](int p) { return opt.eig_threads ? opt.eig_threads : (p > 56 ? 512 : (p > 32 ? 256 : 128)); };
+      // (blocks of order <= 16 take 64 threads where the compile-time geometry has them)
+      auto fwd_threads = [&](int p) {
+        if (opt.eig_threads) return opt.eig_threads;
+        if (p <= 16 && opt.eig_variant != 1 && opt.eig_variant != 2 && jt2_exists<T>(jt2_pmax(p), 64)) return 64;
+        return p > 56 ? 512 : (p > 32 ? 256 : 128);
+      };
       auto fits_jacobi = [&](int p) {
         const int nt = p > 56 ? 512 : (p > 32 ? 256 : 128), fnt = fwd_threads(p);
         if ((int64_t)psd_bwd_smem<T>(p, nt) > maxs) return false;
@@ -718,8 +724,8 @@ struct ImplT : Impl {
       COSMO_JT_ATTR(512, 2); COSMO_JT_ATTR(512, 4); COSMO_JT_ATTR(512, 8);
       COSMO_JT_ATTR(1024, 2); COSMO_JT_ATTR(1024, 4); COSMO_JT_ATTR(1024, 8);
 #undef COSMO_JT_ATTR
-      for (int pm : {32, 56, 80})
-        for (int nt_ : {128, 256, 384, 512, 1024})
+      for (int pm : {8, 16, 32, 56, 80})
+        for (int nt_ : {64, 128, 256, 384, 512, 1024})
           jt2_for<T>(pm, nt_, [&](auto c, auto pmc, auto ntc) {
             using C = decltype(c);
             if ((int64_t)Jt2Geo<T, decltype(pmc)::value>::bytes(ntc) <= maxs)
@@ -903,7 +909,7 @@ struct ImplT : Impl {
         float best = 3.0e38f;
         float bwd[2] = {-1.f, -1.f};
         std::vector<std::pair<int, int>> cands;
-        for (int fnt : {128, 256, 384, 512, 1024}) cands.push_back(std::make_pair(0, fnt));
+        for (int fnt : {64, 128, 256, 384, 512, 1024}) cands.push_back(std::make_pair(0, fnt));
         if (opt.eig_jacobi_max_p == 0 && base.maxp >= 48) cands.push_back(std::make_pair(1, 256));
         for (const auto& c : cands) {
           Bucket bk = base;
