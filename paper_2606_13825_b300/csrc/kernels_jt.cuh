@@ -236,6 +236,112 @@ __device__ __forceinline__ void jt_rot4<double>(unsigned char* sm, uint32_t ra, 
   pb[1] = make_double2(jt_spc(r.c, r.s, x1.x, y1.x), jt_spc(r.c, r.s, x1.y, y1.y));
 }
 
+// ---------------------------------------------------------------------------
+// End of the refinement shared by the slot-layout kernels.  With X = Vt S (the
+// first Rayleigh-Ritz product, Vt orthonormal) the Rayleigh-Ritz matrix is
+// B = X Vt', its diagonal the eigenvalues L and its off-diagonal E.  The
+// projection Pi = Vt' M Vt with M = max(L, 0) + G o E (G the Loewner matrix of
+// max(x, 0), Eq. lowner) has M = 0 between two non-positive indices, so with
+// A the smaller of the positive and the non-positive index sets (size ns)
+//   Pi = sum_{a in A} v_a w_a' + z_a v_a',
+//   w_a = sum_j M_aj v_j,  z_a = sum_{j not in A} M_aj v_j
+// (v_j = row j of Vt) when A is the positive set, and Pi = S - (the same with
+// D = B - M, which vanishes between two positive indices) when A is the
+// non-positive one.  This needs the ns rows of B at A (ns p^2 fused
+// multiply-adds) instead of B and two p x p products (3 p^3).
+// ---------------------------------------------------------------------------
+
+// L_i = sum_k Vt(i, k) X(i, k): the fused multiply-adds, in the same order,
+// that form the diagonal of the full product X Vt'
+template <class T>
+__device__ __forceinline__ void jt_rr_diag(int p, const T* Vt, int ldv, const T* X, int ldx, T* lamv) {
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    T acc = T(0);
+    for (int k = 0; k < p; ++k) acc = fma(Vt[i * ldv + k], X[i * ldx + k], acc);
+    lamv[i] = acc;
+  }
+}
+
+// A in increasing order into sel[0 .. ns), ns into sel[cap], 1 into
+// sel[cap + 1] if A is the positive set (warp 0, ballot prefix sums)
+template <class T>
+__device__ __forceinline__ void jt_select(int p, const T* lamv, int* sel, int cap) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int npos = 0;
+    for (int k0 = 0; k0 < p; k0 += 32)
+      npos += __popc(__ballot_sync(0xffffffffu, k0 + lane < p && lamv[k0 + lane] > T(0)));
+    const bool usepos = npos <= p - npos;
+    int c = 0;
+    for (int k0 = 0; k0 < p; k0 += 32) {
+      const int k = k0 + lane;
+      const bool in = k < p && ((lamv[k] > T(0)) == usepos);
+      const unsigned b = __ballot_sync(0xffffffffu, in);
+      if (in) sel[c + __popc(b & ((1u << lane) - 1u))] = k;
+      c += __popc(b);
+    }
+    if (lane == 0) {
+      sel[cap] = c;
+      sel[cap + 1] = usepos ? 1 : 0;
+    }
+  }
+}
+
+// rows q < ns of M (A positive) or D = B - M (A non-positive) at A into R,
+// then w_q into X rows 0 .. ns and z_q into X rows ns .. 2 ns (X is read
+// first, so the CTA barrier in between is the caller's: call the two halves
+// with one between them)
+template <class T>
+__device__ __forceinline__ void jt_lowrank_rows(int p, const T* Vt, int ldv, const T* X, int ldx, T* R, int ldr,
+                                                const T* lamv, const int* sel, int ns, bool usepos) {
+  for (int idx = threadIdx.x; idx < ns * p; idx += blockDim.x) {
+    const int j = idx / ns, q = idx - j * ns, i = sel[q];
+    const T li = lamv[i], lj = lamv[j];
+    T r;
+    if (j == i) {
+      r = li;                                   // max(l, 0) on A positive, l - max(l, 0) on A non-positive
+    } else {
+      T b = T(0);
+      for (int k = 0; k < p; ++k) b = fma(Vt[j * ldv + k], X[i * ldx + k], b);
+      const bool pi = li > T(0), pj = lj > T(0);
+      if (pi == pj) {
+        r = b;                                  // G = 1 between positives (M), G = 0 between the others (D)
+      } else {
+        const T lp = pi ? li : lj, ln = pi ? lj : li;
+        r = (usepos ? lp : -ln) / (lp - ln) * b;  // G resp. 1 - G of a mixed pair, no cancellation
+      }
+    }
+    R[q * ldr + j] = r;
+  }
+}
+template <class T>
+__device__ __forceinline__ void jt_lowrank_wz(int p, const T* Vt, int ldv, T* X, int ldx, const T* R, int ldr,
+                                              const T* lamv, int ns, bool usepos) {
+  for (int idx = threadIdx.x; idx < ns * p; idx += blockDim.x) {
+    const int q = idx / p, c = idx - q * p;
+    T w = T(0), z = T(0);
+    for (int j = 0; j < p; ++j) {
+      const T m = R[q * ldr + j], v = Vt[j * ldv + c];
+      w = fma(m, v, w);
+      if ((lamv[j] > T(0)) != usepos) z = fma(m, v, z);
+    }
+    X[q * ldx + c] = w;
+    X[(ns + q) * ldx + c] = z;
+  }
+}
+// Pi(i, j) from w, z; sij = S(i, j) (used when A is the non-positive set)
+template <class T>
+__device__ __forceinline__ T jt_lowrank_entry(int i, int j, const T* Vt, int ldv, const T* X, int ldx,
+                                              const int* sel, int ns, bool usepos, T sij) {
+  T acc = T(0);
+  for (int q = 0; q < ns; ++q) {
+    const int a = sel[q];
+    acc = fma(Vt[a * ldv + i], X[q * ldx + j], acc);
+    acc = fma(X[(ns + q) * ldx + i], Vt[a * ldv + j], acc);
+  }
+  return usepos ? acc : sij - acc;
+}
+
 // items of a round per thread for a CTA of nt threads: the off-diagonal
 // tiles and the four-component chunks of the eigenvector rotation
 __host__ __device__ inline int jt_items(int p) {

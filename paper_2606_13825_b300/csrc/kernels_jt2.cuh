@@ -123,7 +123,8 @@ __device__ __forceinline__ void jt2_gemm(int p, const T* A, int ar, const T* B, 
 //   T   [2][4][PS]    tile buffers (four planes each); outside the solve the
 //                     product buffer X (PE x LDS fits: asserted)
 //   R   [2][NPM]      rotations of the current and the next round
-//   L   [PE]          eigenvalues, then the reduction scratch (doubles)
+//   L   [PE]          eigenvalues, the selected index set [PE + 2] int, then
+//                     the reduction scratch (doubles)
 template <class T, int PMAX>
 struct Jt2Geo {
   static constexpr int PE = PMAX + (PMAX & 1);
@@ -141,7 +142,8 @@ struct Jt2Geo {
   static constexpr uint32_t OT = (OS + (uint32_t)(PE * LDS) * (uint32_t)sizeof(T) + 15u) & ~15u;
   static constexpr uint32_t OR = OT + 2u * TBUF * (uint32_t)sizeof(T);
   static constexpr uint32_t OL = OR + 2u * NPM * (uint32_t)sizeof(JtRot<T>);
-  static constexpr uint32_t ORED = (OL + (uint32_t)PE * (uint32_t)sizeof(T) + 7u) & ~7u;
+  static constexpr uint32_t OI = (OL + (uint32_t)PE * (uint32_t)sizeof(T) + 3u) & ~3u;   // selected set [PE + 2] int
+  static constexpr uint32_t ORED = (OI + (uint32_t)(PE + 2) * 4u + 7u) & ~7u;
   static constexpr size_t bytes(int nt) { return (size_t)ORED + (size_t)(2 * (nt / 32) + 2) * 8; }
   // work items per thread of an NT-thread CTA at the largest order
   static constexpr int items_t(int nt) { return (NPM * (NPM - 1) / 2 + (nt - 32 * PW) - 1) / (nt - 32 * PW); }
@@ -525,10 +527,12 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
   __syncthreads();
   jt2_gemm<T>(p, Vt, ldv, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
   __syncthreads();
-  jt2_gemm<T>(p, Vt, ldv, X, 1, lds, [&](int j, int i, T v) { S[i * lds + j] = v; });
+  // X = Vt S: eigenvalues, the tape, the selected index set, then Pi from
+  // the rows of the Rayleigh-Ritz matrix at that set (kernels_jt.cuh)
+  int* const sel = reinterpret_cast<int*>(smraw + G::OI);
+  jt_rr_diag<T>(p, Vt, ldv, X, lds, lamv);
   __syncthreads();
-  for (int i = threadIdx.x; i < p; i += NT) lamv[i] = S[i * lds + i];
-  __syncthreads();
+  jt_select<T>(p, lamv, sel, G::PE);
   T* lam = lam_slot + P.psd_loff[blk];
   T* U = U_slot + P.psd_uoff[blk];
   for (int k = threadIdx.x; k < p; k += NT) lam[k] = lamv[k];
@@ -536,34 +540,22 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
     const int k = e / p, i = e - k * p;
     U[e] = Vt[k * ldv + i];
   }
-  for (int e = threadIdx.x; e < d; e += NT) {
-    int i, j;
-    svec_ij(e, i, j);
-    if (i == j) {
-      S[i * lds + i] = lamv[i] > T(0) ? lamv[i] : T(0);
-      continue;
-    }
-    const T li = lamv[i], lj = lamv[j];
-    T g;
-    if (li > T(0) && lj > T(0)) g = T(1);
-    else if (!(li > T(0)) && !(lj > T(0))) g = T(0);
-    else g = li > T(0) ? li / (li - lj) : lj / (lj - li);
-    const T v = g * S[i * lds + j];
-    S[i * lds + j] = v;
-    S[j * lds + i] = v;
-  }
   __syncthreads();
-  smem_gemm_auto<T>(p, S, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  const int ns = sel[G::PE];
+  const bool usepos = sel[G::PE + 1] != 0;
+  jt_lowrank_rows<T>(p, Vt, ldv, X, lds, S, lds, lamv, sel, ns, usepos);
   __syncthreads();
-  smem_gemm_auto<T>(p, Vt, 1, ldv, X, lds, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
+  jt_lowrank_wz<T>(p, Vt, ldv, X, lds, S, lds, lamv, ns, usepos);
   __syncthreads();
   for (int e = threadIdx.x; e < d; e += NT) {
     int i, j;
     svec_ij(e, i, j);
-    T out = S[i * lds + j];
-    if (i != j) out *= (T)kSqrt2;
     const int64_t r = row0 + e;
     const T sh = al * io.st[r] + (T(1) - al) * io.s[r];
+    T sij = sh + io.y[r] / rh;                       // S(i, j) (svec entry scaled back)
+    if (i != j) sij *= (T)kInvSqrt2;
+    T out = jt_lowrank_entry<T>(i, j, Vt, ldv, X, lds, sel, ns, usepos, sij);
+    if (i != j) out *= (T)kSqrt2;
     const T yn = io.y[r] + rh * (sh - out);
     io.sn[r] = out;
     io.yn[r] = yn;

@@ -629,12 +629,14 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
   __syncthreads();
   smem_gemm_auto<T>(p, Vt, ldv, 1, S, lds, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
   __syncthreads();
-  smem_gemm_auto<T>(p, X, lds, 1, Vt, 1, ldv, [&](int i, int j, T v) { S[i * lds + j] = v; });
-  __syncthreads();
+  // X = Vt S: eigenvalues, the tape, the selected index set, then Pi from the
+  // rows of the Rayleigh-Ritz matrix at that set (the routine of
+  // kernels_jt.cuh that k_psd_fwd_jt2 runs too: both give the same bits)
   T* lamv = sm.lamv;
-  for (int i = threadIdx.x; i < p; i += NT) lamv[i] = S[i * lds + i];
+  int* const sel = sm.sel;
+  jt_rr_diag<T>(p, Vt, ldv, X, lds, lamv);
   __syncthreads();
-  // tape: eigenvalues and eigenvectors (column-major per block: column k = row k of Vt)
+  jt_select<T>(p, lamv, sel, p);
   T* lam = lam_slot + P.psd_loff[blk];
   T* U = U_slot + P.psd_uoff[blk];
   for (int k = threadIdx.x; k < p; k += NT) lam[k] = lamv[k];
@@ -642,36 +644,22 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32)) k_psd_fwd_jt(Prob<T, V>
     const int k = e / p, i = e - k * p;
     U[e] = Vt[k * ldv + i];
   }
-  // M = max(L, 0) + G o E in place of A (upper triangle read, both written)
-  for (int e = threadIdx.x; e < d; e += NT) {
-    int i, j;
-    svec_ij(e, i, j);
-    if (i == j) {
-      S[i * lds + i] = lamv[i] > T(0) ? lamv[i] : T(0);
-      continue;
-    }
-    const T li = lamv[i], lj = lamv[j];
-    T g;
-    if (li > T(0) && lj > T(0)) g = T(1);
-    else if (!(li > T(0)) && !(lj > T(0))) g = T(0);
-    else g = li > T(0) ? li / (li - lj) : lj / (lj - li);
-    const T v = g * S[i * lds + j];
-    S[i * lds + j] = v;
-    S[j * lds + i] = v;
-  }
   __syncthreads();
-  // W = M Vt into X, then Pi = Vt' W into S
-  smem_gemm_auto<T>(p, S, lds, 1, Vt, ldv, 1, [&](int i, int j, T v) { X[i * lds + j] = v; });
+  const int ns = sel[p];
+  const bool usepos = sel[p + 1] != 0;
+  jt_lowrank_rows<T>(p, Vt, ldv, X, lds, S, lds, lamv, sel, ns, usepos);
   __syncthreads();
-  smem_gemm_auto<T>(p, Vt, 1, ldv, X, lds, 1, [&](int i, int j, T v) { S[i * lds + j] = v; });
+  jt_lowrank_wz<T>(p, Vt, ldv, X, lds, S, lds, lamv, ns, usepos);
   __syncthreads();
   for (int e = threadIdx.x; e < d; e += NT) {
     int i, j;
     svec_ij(e, i, j);
-    T out = S[i * lds + j];
-    if (i != j) out *= (T)kSqrt2;
     const int64_t r = row0 + e;
     const T sh = al * io.st[r] + (T(1) - al) * io.s[r];
+    T sij = sh + io.y[r] / rh;                       // S(i, j) (svec entry scaled back)
+    if (i != j) sij *= (T)kInvSqrt2;
+    T out = jt_lowrank_entry<T>(i, j, Vt, ldv, X, lds, sel, ns, usepos, sij);
+    if (i != j) out *= (T)kSqrt2;
     const T yn = io.y[r] + rh * (sh - out);
     io.sn[r] = out;
     io.yn[r] = yn;
