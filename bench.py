@@ -500,6 +500,39 @@ def run_policy(args):
 
 
 # --------------------------------------------------------------------- ours --
+PSD_TRAFFIC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "psd_fwd_traffic_maxcut256.txt")
+PSD_SOURCES = ("kernels_jt.cuh", "kernels_jt2.cuh", "kernels_psd.cuh")
+
+
+def psd_sources_sha16():
+    """Hash of the PSD projection kernels' sources: a DRAM-traffic figure taken
+    with ncu holds only for the sources it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in PSD_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2606_13825_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def psd_traffic():
+    """DRAM bytes (read + write) per forward launch group of the projection on
+    the max-cut workload, from the ncu capture summarised in profiles/, or None
+    when the kernels changed since it was taken."""
+    try:
+        kv = {}
+        with open(PSD_TRAFFIC) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha16") != psd_sources_sha16():
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def psd_flops(probs):
     """Algorithmic flops of one PSD-projection launch: symmetric eigen-
     decomposition with vectors 9 p^3 (Golub & Van Loan's count for symmetric
@@ -682,7 +715,11 @@ def main():
         peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"kernel": "psd_fwd (cyclic Jacobi eigensolver + reconstruction, CTA per block)",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": psd_traffic() if args.workload == "maxcut" else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the three size-class "
+                                  "launches of one forward iteration (profiles/psd_fwd_traffic_maxcut256.txt), "
+                                  "null when the kernel sources changed since the capture",
                 "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop/FMA x 2032 MHz",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches_timed": dom_n,
                 "algorithmic_count": "sum over blocks of 9p^3 (eigh) + 2p^3 (reconstruction)"}
