@@ -77,12 +77,15 @@ def workload_spec(name, rank=0, world=1):
                          "learnable log rho_k / alpha_k; loss ||r_p^K||^2+||r_d^K||^2")
     if name == "socp":
         probs = [socp_problem(4000 + rank * 64 + j) for j in range(64)]
-        # FP32 iterates reach a relative CG residual of about eps32 * kappa(M)
-        return dict(probs=probs, K=100, opts={"cg_tol": 1e-6}, value_type="bf16", learn_start=False,
+        # FP32 iterates reach a true relative CG residual of about eps32 * kappa(M)
+        # (kappa ~ 1e3-1e4); the recursively updated residual still falls below
+        # it, and stopping at 1e-7 instead of 1e-6 takes the worst per-instance
+        # rho-gradient error against the FP64 form from 8.0e-3 to 1.7e-3
+        return dict(probs=probs, K=100, opts={"cg_tol": 1e-7}, value_type="bf16", learn_start=False,
                     metric="unrolled fwd+bwd instance-iters/sec (sparse SOCP, batched mixed precision)",
                     desc="random sparse SOCPs: 64 instances (seeds 4000+j), n=5000, A 8000x5000 density 1e-3, "
                          "P=M'M+1e-3 I (M 500x5000 density 1e-3), 200 SOCs d ~ U{3..50} + orthant, planted "
-                         "solution; K=100; BF16 A values (P FP32), FP32 iterates, CG tol 1e-6; "
+                         "solution; K=100; BF16 A values (P FP32), FP32 iterates, CG tol 1e-7; "
                          "loss ||r_p^K||^2+||r_d^K||^2")
     if name in ("lyapunov", "kalman", "mpc"):
         from synth import lyapunov_problem, robust_kalman_problem, robust_mpc_problem

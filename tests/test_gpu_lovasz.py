@@ -73,13 +73,17 @@ def test_lovasz_full_size_mixed_vs_fp64():
         assert not (flags & (4 | 8)).any(), (prec, flags)
         for k in ("grho", "galpha", "loss"):
             assert np.all(np.isfinite(res[prec][k])), (prec, k)
-    # Mixed vs FP64.  Here the FP32 floor is worse than on max-cut: X has
-    # trace 1 (entries ~1/n) while ||S|| is dominated by y/rho = 10 y, so the
-    # eps32 ||S||_F error of each projection is large relative to X.
-    # Measured: objective error up to ~2e-3 on the G(n, 1/2) instances,
-    # up to ~7e-4 on the vertex-transitive ones; asserted: 5e-3 and 1e-3.  The 1e-4 gate
-    # at this size needs the FP64 form (checked against the oracle on the
-    # parity subset above).
+    # Mixed vs FP64.  The unrolled map of these SDPs amplifies the relative
+    # FP32 rounding of the dual iterate y: FP64 steps with only y rounded to
+    # FP32 in between already move the objective by several 1e-4
+    # (test_lovasz_fp32_iterate_storage_floor), so FP32 iterates cannot meet
+    # the 1e-4 gate here whatever the kernels do; a tighter CG tolerance, a
+    # cold-started eigensolver and an eigenvector refinement on the QL path
+    # left the error where it is (measured).  Measured: objective error up
+    # to 1.8e-3 on the G(n, 1/2) instances (median 1.4e-3), up to 4.4e-4 on
+    # the vertex-transitive ones; asserted: 5e-3 and 1e-3.  The 1e-4 gate at
+    # this size needs the FP64 form (checked against the oracle on the parity
+    # subset above).
     m, d = res["mixed"], res["fp64"]
     obj_err = np.abs(m["obj"] - d["obj"]) / np.abs(d["obj"])
     ro = b.packed.row_off
@@ -93,3 +97,58 @@ def test_lovasz_full_size_mixed_vs_fp64():
           f"alpha-bar median {np.median(aerr):.2e} max {aerr.max():.2e}")
     assert np.max(obj_err) < 5e-3, np.max(obj_err)
     assert np.max(obj_err[64:]) < 1e-3, np.max(obj_err[64:])
+
+
+def test_lovasz_fp32_iterate_storage_floor():
+    """Why the mixed form misses the 1e-4 objective gate on the Lovasz theta
+    workload: the FP64 path run one step at a time, with the state rounded to
+    FP32 between steps and nothing else changed, already misses it.  Rounding
+    only the dual iterate y of the PSD rows moves the objective at K = 30 by
+    several 1e-4 (measured: median 3.5e-4); rounding x, s, or y on the
+    equality rows alone moves it by 1e-9 .. 1e-7.  The projection sees y / rho
+    with rho = 0.1 on the PSD rows (Sec. 2.2), and the unrolled map of these
+    SDPs amplifies that relative rounding, so FP32 iterates (the workload's
+    precision) bound the objective error from below whatever the kernels do.
+    On max-cut the same experiment stays near 1e-8 (asserted below 1e-6)."""
+    _need_gpu()
+    from paper_2606_13825_b300 import CosmoBatch
+    from synth import ZERO, maxcut_problem
+    graphs = random_graph_batch(8, 3000, 100, 200, 0.5, 0.5)   # the workload's first eight graphs
+    probs = [lovasz_problem(nv, e) for nv, e in graphs]
+    K = 30
+
+    def floor(probs, K):
+        rho = torch.tensor(np.tile(np.concatenate([default_rho_rows(p) for p in probs]), (K, 1)), device="cuda")
+        alpha = torch.full((K, len(probs)), 1.6, dtype=torch.float64, device="cuda")
+        b = CosmoBatch(probs, precision="fp64", cg_tol=1e-12)
+        xK, sK, yK, _ = b.forward(K, rho, alpha, tape=False)
+        ref = b.residuals(xK, sK, yK)[2].cpu().numpy()
+        zero = torch.tensor(np.concatenate([p.row_types() == ZERO for p in probs]), device="cuda")
+
+        def stepwise(mask_x, mask_s, mask_y):
+            x = torch.zeros(b.n_total, dtype=torch.float64, device="cuda")
+            s = torch.zeros(b.m_total, dtype=torch.float64, device="cuda")
+            y = torch.zeros_like(s)
+            rnd = lambda v, msk: torch.where(msk, v.float().double(), v) if msk is not None else v
+            for k in range(K):
+                x, s, y, _ = b.forward(1, rho[k:k + 1], alpha[k:k + 1], x0=x, s0=s, y0=y, tape=False)
+                x, s, y = rnd(x, mask_x), rnd(s, mask_s), rnd(y, mask_y)
+            o = b.residuals(x, s, y)[2].cpu().numpy()
+            return np.abs(o - ref) / np.abs(ref)
+
+        allx = torch.ones(b.n_total, dtype=torch.bool, device="cuda")
+        allm = torch.ones(b.m_total, dtype=torch.bool, device="cuda")
+        return {"none": stepwise(None, None, None), "x": stepwise(allx, None, None),
+                "s": stepwise(None, allm, None), "y": stepwise(None, None, allm),
+                "y zero rows": stepwise(None, None, zero), "y cone rows": stepwise(None, None, ~zero)}
+
+    e = floor(probs, K)
+    print("\nLovasz, FP64 steps with FP32-rounded state: objective error median / max: " +
+          "; ".join(f"{k} {np.median(v):.2e} / {v.max():.2e}" for k, v in e.items()))
+    assert e["none"].max() <= 1e-10
+    assert max(e["x"].max(), e["s"].max()) <= 1e-7
+    assert np.median(e["y"]) >= 1e-4          # the gate is below the FP32-storage floor
+    assert np.median(e["y cone rows"]) >= 1e-4 and e["y zero rows"].max() <= 1e-6
+    mc = floor([maxcut_problem(nv, ed) for nv, ed in random_graph_batch(8, 2000, 20, 80, 0.1, 0.5)], 50)
+    print("max-cut, the same: " + "; ".join(f"{k} {np.median(v):.2e} / {v.max():.2e}" for k, v in mc.items()))
+    assert max(v.max() for v in mc.values()) <= 1e-6
