@@ -18,6 +18,13 @@ template <class T>
 __host__ __device__ inline size_t tql_smem(int p, int nt) {
   return (size_t)7 * p * sizeof(T) + (size_t)(p + 8) * sizeof(int) + (size_t)(2 * (nt / 32)) * sizeof(double) + 64;
 }
+// the same with the p x p working matrix in shared memory too (after the
+// scratch, 16-byte aligned): every phase then works on chip, and the
+// eigenvectors are copied to the tape once at the end
+template <class T>
+__host__ __device__ inline size_t tql_smem_z(int p, int nt) {
+  return ((tql_smem<T>(p, nt) + 15) & ~(size_t)15) + (size_t)p * p * sizeof(T);
+}
 
 // sum over the CTA of one double, broadcast (uses red[nt/32])
 __device__ __forceinline__ double cta_sum1(double v, double* red) {
@@ -237,11 +244,13 @@ __device__ bool tql_iterate(T* Z, int p, T* d, T* e, T* rc, T* rs, int* ctl, int
 }
 
 // a7 for large blocks: fused relaxation / projection / dual update like
-// k_psd_fwd, with the tridiagonal + QL eigensolver.
+// k_psd_fwd, with the tridiagonal + QL eigensolver.  zsm: the working matrix
+// lives in shared memory (launched with tql_smem_z bytes) instead of the
+// block's tape slot; the arithmetic and its order are the same either way.
 template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_psd_fwd_tql(Prob<T, V> P, PsdIterIO<T> io, T* lam_slot,
                                                     T* U_slot, int32_t* flags, int sched_off,
-                                                    unsigned long long* stats, int maxit) {
+                                                    unsigned long long* stats, int maxit, int zsm) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int blk = P.psd_sched[sched_off + blockIdx.x];
   const int p = P.psd_p[blk];
@@ -258,7 +267,8 @@ __global__ void __launch_bounds__(NT) k_psd_fwd_tql(Prob<T, V> P, PsdIterIO<T> i
   double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(sel + p) + 7) & ~uintptr_t(7));
   const int inst = io.row_inst[row0];
   const T al = io.alpha[inst], rh = io.rho[row0];
-  T* Z = U_slot + P.psd_uoff[blk];
+  T* const Ut = U_slot + P.psd_uoff[blk];
+  T* Z = zsm ? reinterpret_cast<T*>(smraw + ((tql_smem<T>(p, NT) + 15) & ~(size_t)15)) : Ut;
   // S (full, symmetric) into Z
   for (int q = threadIdx.x; q < p * p; q += NT) {
     const int j = q / p, i = q - j * p;
@@ -278,6 +288,8 @@ __global__ void __launch_bounds__(NT) k_psd_fwd_tql(Prob<T, V> P, PsdIterIO<T> i
   }
   T* lam = lam_slot + P.psd_loff[blk];
   for (int k = threadIdx.x; k < p; k += NT) lam[k] = d[k];
+  if (zsm)
+    for (int q = threadIdx.x; q < p * p; q += NT) Ut[q] = Z[q];
   if (threadIdx.x == 0) {
     int npos = 0;
     for (int k = 0; k < p; ++k) npos += d[k] > T(0);

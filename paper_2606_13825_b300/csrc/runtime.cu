@@ -1325,7 +1325,10 @@ struct ImplT : Impl {
   void psd_fwd_bucket(const Bucket& bk, cudaStream_t s, const PsdIterIO<T>& io, T* lam, T* U, const T* up,
                       int32_t* fl, unsigned long long* stt) {
     if (bk.method == 1) {
-      k_psd_fwd_tql<T, V, 256><<<bk.count, 256, tql_smem<T>(bk.maxp, 256), s>>>(P, io, lam, U, fl, bk.start, stt, 30 * 4);
+      // the working matrix in shared memory when the class's largest block fits
+      const int zsm = (int64_t)tql_smem_z<T>(bk.maxp, 256) <= (int64_t)smem_max ? 1 : 0;
+      k_psd_fwd_tql<T, V, 256><<<bk.count, 256, zsm ? tql_smem_z<T>(bk.maxp, 256) : tql_smem<T>(bk.maxp, 256), s>>>(
+          P, io, lam, U, fl, bk.start, stt, 30 * 4, zsm);
       return;
     }
     if (bk.variant == 3) {
