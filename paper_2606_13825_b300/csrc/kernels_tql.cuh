@@ -7,6 +7,8 @@
 // (global memory, column-major, L2-resident), so any p fits.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels_psd.cuh"
 
@@ -66,8 +68,18 @@ __device__ void householder_tridiag(T* Z, int p, T* d, T* e, T* vh, T* wv, T* be
       // p = beta A_sub v (thread per row r of the trailing block; coalesced)
       double pv = 0.0;
       for (int r = tid; r < n1; r += nt) {
-        T acc = T(0);
-        for (int c = 0; c < n1; ++c) acc = fma(Z[(size_t)(k + 1 + c) * p + (k + 1 + r)], vh[c], acc);
+        // four partial sums (columns c = 0, 1, 2, 3 mod 4) break the FMA chain
+        const T* zr = Z + (size_t)(k + 1) * p + (k + 1 + r);
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int c = 0;
+        for (; c + 3 < n1; c += 4) {
+          a0 = fma(zr[(size_t)c * p], vh[c], a0);
+          a1 = fma(zr[(size_t)(c + 1) * p], vh[c + 1], a1);
+          a2 = fma(zr[(size_t)(c + 2) * p], vh[c + 2], a2);
+          a3 = fma(zr[(size_t)(c + 3) * p], vh[c + 3], a3);
+        }
+        for (; c < n1; ++c) a0 = fma(zr[(size_t)c * p], vh[c], a0);
+        const T acc = (a0 + a1) + (a2 + a3);
         const T pr = bet * acc;
         wv[r] = pr;
         pv += (double)pr * (double)vh[r];
@@ -122,14 +134,27 @@ __device__ void form_q(T* Z, int p, const T* beta, T* vh, T* wv) {
     for (int i = tid; i < n1; i += nt) vh[i] = Z[(size_t)k * p + k + 1 + i];
     __syncthreads();
     if (bet != T(0)) {
-      // u_c = v' Q[k+1:, k+1+c]: one warp per column, lanes over rows
-      for (int c = w; c < n1; c += nw) {
-        const T* colc = Z + (size_t)(k + 1 + c) * p + (k + 1);
-        T acc = T(0);
-        for (int r = lane; r < n1; r += 32) acc = fma(vh[r], colc[r], acc);
+      // u_c = v' Q[k+1:, k+1+c]: four columns per warp at a time (their
+      // warp reductions interleave), lanes over rows
+      for (int c0 = 4 * w; c0 < n1; c0 += 4 * nw) {
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int r = lane; r < n1; r += 32) {
+          const T vr = vh[r];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) wv[c] = bet * acc;
+          for (int q = 0; q < 4; ++q)
+            if (c0 + q < n1) acc[q] = fma(vr, Z[(size_t)(k + 1 + c0 + q) * p + (k + 1) + r], acc[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        if (lane < 4 && c0 + lane < n1) {
+          T a = acc[0];
+#pragma unroll
+          for (int q = 1; q < 4; ++q)
+            if (lane == q) a = acc[q];
+          wv[c0 + lane] = bet * a;
+        }
       }
       __syncthreads();
       for (int c = 0; c < n1; ++c) {
@@ -146,6 +171,20 @@ __device__ void form_q(T* Z, int p, const T* beta, T* vh, T* wv) {
 }
 
 template <class T> __device__ __forceinline__ T pythag_(T a, T b) { return hypot_(a, b); }
+
+// The plane rotation of a QL step: r = hypot(f, g), s = f / r, c = g / r;
+// false (r = 0) if f = g = 0.  (A reciprocal-square-root form with a Newton
+// step was measured: the sweep got faster but the vertex-transitive Lovasz
+// blocks, whose spectra are highly repeated, lost an order of magnitude of
+// objective accuracy in FP32, so the IEEE quotients stay.)
+template <class T>
+__device__ __forceinline__ bool tql_rot(T f, T g, T& r, T& s, T& c) {
+  r = pythag_(f, g);
+  if (r == T(0)) return false;
+  s = f / r;
+  c = g / r;
+  return true;
+}
 
 // Implicit-shift QL on the symmetric tridiagonal (d, e), rotations applied to
 // the columns of Z (so Z Q_ql holds the eigenvectors).  Thread 0 runs the
@@ -182,26 +221,31 @@ __device__ bool tql_iterate(T* Z, int p, T* d, T* e, T* rc, T* rs, int* ctl, int
         T s = T(1), c = T(1), pp = T(0);
         int i = m - 1;
         bool early = false;
+        // step i reads e[i], d[i + 1], d[i] and writes e[i + 1], d[i + 1]:
+        // d[i] and the next e, d are carried in registers (loaded ahead)
+        T ei = e[i], di1 = d[i + 1], di = d[i];
         for (; i >= l; --i) {
-          T f = s * e[i];
-          const T b = c * e[i];
-          r = pythag_(f, g);
-          e[i + 1] = r;
-          if (r == T(0)) {          // deflation inside the sweep
-            d[i + 1] -= pp;
+          const T e_nx = i > l ? e[i - 1] : T(0), d_nx = i > l ? d[i - 1] : T(0);
+          T f = s * ei;
+          const T b = c * ei;
+          if (!tql_rot(f, g, r, s, c)) {   // r = 0: deflation inside the sweep
+            e[i + 1] = r;
+            d[i + 1] = di1 - pp;
             e[m] = T(0);
             early = true;
             break;
           }
-          s = f / r;
-          c = g / r;
-          g = d[i + 1] - pp;
-          r = (d[i] - g) * s + T(2) * c * b;
+          e[i + 1] = r;
+          g = di1 - pp;
+          r = (di - g) * s + T(2) * c * b;
           pp = s * r;
           d[i + 1] = g + pp;
           g = c * r - b;
           rc[i] = c;
           rs[i] = s;
+          ei = e_nx;
+          di1 = di;
+          di = d_nx;
         }
         if (!early) {
           d[l] -= pp;
