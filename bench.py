@@ -626,6 +626,11 @@ def main():
 
     has_psd = any(ct == 4 for p in probs for (ct, _) in p.cones)
     dom = "psd_fwd" if has_psd else "pcg"          # dominant kernel class
+    persist = has_psd and bool(b.info()["fwd_persistent"])
+    if persist:
+        # the persistent forward: one launch per size class runs every step of
+        # a segment (right-hand side, relaxation, projections, dual update)
+        dom = "fwd_persist"
     # CUDA events around every launch group of the dominant class: with CUDA
     # graphs they are event nodes of the recorded graphs, read back after
     # each replay, so the roofline kernel is timed inside the timed region
@@ -714,18 +719,27 @@ def main():
     avg_s = dom_ms / max(dom_n, 1) / 1e3
     if has_psd:
         flops = psd_flops(probs)
+        kern = "psd_fwd (cyclic Jacobi eigensolver + reconstruction, CTA per block)"
+        if persist:
+            # one launch group covers the steps of one forward segment
+            c = int(opts.get("checkpoint_every", 0) or 0)
+            nseg = -(-K // c) if c > 0 else 1
+            flops *= K / nseg
+            kern = ("fwd_persist (per CTA one instance for every step of a segment: right-hand side, "
+                    "relaxation, separable projections, cyclic Jacobi eigensolver + reconstruction, dual update)")
         achieved = flops / avg_s / 1e12
         peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"kernel": "psd_fwd (cyclic Jacobi eigensolver + reconstruction, CTA per block)",
+        roof = {"kernel": kern,
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": psd_traffic() if args.workload == "maxcut" else None,
+                "traffic": psd_traffic() if args.workload == "maxcut" and not persist else None,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the three size-class "
                                   "launches of one forward iteration (profiles/psd_fwd_traffic_maxcut256.txt), "
                                   "null when the kernel sources changed since the capture",
                 "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop/FMA x 2032 MHz",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3, "launches_timed": dom_n,
-                "algorithmic_count": "sum over blocks of 9p^3 (eigh) + 2p^3 (reconstruction)"}
+                "algorithmic_count": "sum over blocks of 9p^3 (eigh) + 2p^3 (reconstruction)"
+                                     + (", times the steps of a launch" if persist else "")}
     else:
         # CG: every iteration streams A, A' and P once (value + column index)
         # plus ~8 n-vectors of 4 bytes; iterations counted on the device

@@ -180,6 +180,16 @@ typedef struct {
   int32_t autotune;         /* 1: at batch creation, time the candidate launch
                                configurations of what the options leave automatic and keep
                                the fastest (see cosmo_tuning); 0: shape rules only */
+  int32_t fwd_persistent;   /* 1: in MIXED precision with FP32 values, where every instance
+                               has a diagonal reduced system and exactly one PSD block (its
+                               other rows zero, nonnegative or box; no SOC) and every size
+                               class runs the compile-time-geometry Jacobi, one launch per
+                               size class runs all steps of a forward segment (one CTA per
+                               instance: a3..a8 step after step, no per-step launches; the
+                               open-loop forward with loss_kind 0 only); results equal the
+                               per-step launches bit for bit.  0 (default): per-step
+                               launches (measured faster on the batched max-cut workload
+                               in graph mode: 13.0 against 15.0 ms per forward). */
 } cosmo_options;
 
 /* Launch configuration of a batch: the PSD size classes (blocks sorted by
@@ -228,6 +238,8 @@ typedef struct {
   int64_t eig_sweeps, eig_blocks;       /* Jacobi sweeps summed over PSD-block projections */
   int64_t cg_iters, cg_solves;          /* forward CG iterations / solves (per instance) */
   int64_t adj_cg_iters, adj_cg_solves;  /* adjoint CG iterations / solves */
+  int32_t fwd_persistent;   /* 1 if the batch's forward runs persistent (option
+                               fwd_persistent and the batch qualifies), else 0 */
 } cosmo_batch_info;
 
 typedef struct cosmo_batch cosmo_batch;
@@ -243,7 +255,7 @@ const char* cosmo_last_error(void);
  * cg_max_iter 500; checkpoint_every 0; dk_gap_tau 1e-12; eig_jacobi_max_p 0
  * (Jacobi wherever it fits in shared memory); 30 sweeps; eig_tol 1e-6 (MIXED) / 1e-14 (FP64);
  * use_graph 1; device 0; eig_warm_start 1; dk_tensor_cores 1; cg_cluster 0; loss_kind 0;
- * eig_variant 0; eig_threads 0; autotune 0.
+ * eig_variant 0; eig_threads 0; autotune 0; fwd_persistent 0.
  * Returns COSMO_E_INVAL for an unknown precision. */
 cosmo_status cosmo_options_default(cosmo_options* opt, int32_t precision);
 

@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
                 ("eig_max_sweeps", c_int32), ("eig_tol", c_double), ("use_graph", c_int32),
                 ("device", c_int32), ("eig_warm_start", c_int32), ("dk_tensor_cores", c_int32),
                 ("cg_cluster", c_int32), ("loss_kind", c_int32), ("eig_variant", c_int32),
-                ("eig_threads", c_int32), ("autotune", c_int32)]
+                ("eig_threads", c_int32), ("autotune", c_int32),
+                ("fwd_persistent", c_int32)]
 
 
 MAX_PSD_CLASSES = 8
@@ -69,7 +70,8 @@ class BatchInfo(ctypes.Structure):
                 ("psd_u_entries", c_int64), ("device_bytes", c_int64), ("last_K", c_int32),
                 ("tape_valid", c_int32), ("kernels_launched", c_int64),
                 ("eig_sweeps", c_int64), ("eig_blocks", c_int64), ("cg_iters", c_int64),
-                ("cg_solves", c_int64), ("adj_cg_iters", c_int64), ("adj_cg_solves", c_int64)]
+                ("cg_solves", c_int64), ("adj_cg_iters", c_int64), ("adj_cg_solves", c_int64),
+                ("fwd_persistent", c_int32)]
 
 
 PCG_PHASES = ("R stage", "R stream (warp 0)", "R stream rest + cluster barrier", "R epilogue",

@@ -404,14 +404,16 @@ __device__ __forceinline__ int jt2_solve(unsigned char* sm, int p, double tol, i
 // of k_psd_fwd_jt, on the geometry of Jt2Geo<T, PMAX> (one CTA per block of
 // order p <= PMAX).  Outside the solve the eigenvectors are rows of Vt in
 // index order; the solve runs on the slot-ordered copy in the other buffer.
+// The projection of block blk by the whole CTA, in the CTA's dynamic shared
+// memory (Jt2Geo<T, PMAX>::bytes(NT) of it); shared by the per-step kernel
+// below and the persistent forward of kernels_persist.cuh.
 template <class T, class V, int NT, int PMAX, int TI, int CI>
-__global__ void __launch_bounds__(NT, 32768 / (NT * 32))
-    k_psd_fwd_jt2(Prob<T, V> P, PsdIterIO<T> io, T* lam_slot, T* U_slot, double tol, int max_sweeps,
-                  int32_t* flags, int sched_off, unsigned long long* stats, const T* U_prev) {
+__device__ __forceinline__ void jt2_project(const Prob<T, V>& P, const PsdIterIO<T>& io, T* lam_slot, T* U_slot,
+                                            double tol, int max_sweeps, int32_t* flags, int blk,
+                                            unsigned long long* stats, const T* U_prev) {
   using G = Jt2Geo<T, PMAX>;
   constexpr int ldv = G::LDV, lds = G::LDS;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int blk = P.psd_sched[sched_off + blockIdx.x];
   const int p = P.psd_p[blk];
   const int pe = p + (p & 1), np = pe / 2;
   const int64_t row0 = P.psd_row0[blk];
@@ -561,6 +563,14 @@ __global__ void __launch_bounds__(NT, 32768 / (NT * 32))
     io.yn[r] = yn;
     if (!finite_(yn)) atomicOr(&flags[inst], F_NONFINITE);
   }
+}
+
+template <class T, class V, int NT, int PMAX, int TI, int CI>
+__global__ void __launch_bounds__(NT, 32768 / (NT * 32))
+    k_psd_fwd_jt2(Prob<T, V> P, PsdIterIO<T> io, T* lam_slot, T* U_slot, double tol, int max_sweeps,
+                  int32_t* flags, int sched_off, unsigned long long* stats, const T* U_prev) {
+  jt2_project<T, V, NT, PMAX, TI, CI>(P, io, lam_slot, U_slot, tol, max_sweeps, flags,
+                                      P.psd_sched[sched_off + blockIdx.x], stats, U_prev);
 }
 
 }  // namespace cosmo

@@ -32,6 +32,7 @@
 #include "kernels_ws.cuh"
 #include "kernels_pol.cuh"
 #include "kernels_ws_tc.cuh"
+#include "kernels_persist.cuh"
 
 using namespace cosmo;
 
@@ -728,9 +729,13 @@ struct ImplT : Impl {
         for (int nt_ : {64, 128, 256, 384, 512, 1024})
           jt2_for<T>(pm, nt_, [&](auto c, auto pmc, auto ntc) {
             using C = decltype(c);
-            if ((int64_t)Jt2Geo<T, decltype(pmc)::value>::bytes(ntc) <= maxs)
+            if ((int64_t)Jt2Geo<T, decltype(pmc)::value>::bytes(ntc) <= maxs) {
               cudaFuncSetAttribute(k_psd_fwd_jt2<T, V, decltype(ntc)::value, decltype(pmc)::value, C::TI, C::CI>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+              if constexpr (std::is_same<T, float>::value && std::is_same<V, float>::value)
+                cudaFuncSetAttribute(k_fwd_persist_jt2<T, V, decltype(ntc)::value, decltype(pmc)::value, C::TI, C::CI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+            }
           });
       CU(cudaGetLastError());
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -741,7 +746,27 @@ struct ImplT : Impl {
                                 (int)dk_tc_smem(DK_TC_MAXP)));
     }
     if (opt.autotune) TRY(tune());
+    // persistent forward (kernels_persist.cuh): FP32 batches (FP32 values)
+    // of diagonal instances with exactly one PSD block each and no SOC rows
+    if constexpr (std::is_same<T, float>::value && std::is_same<V, float>::value) {
+      persist_shape = opt.fwd_persistent == 1 && P.nsoc == 0 && P.n_cg == 0 && h.ninst > 0 &&
+                      h.psd_p.size() == (size_t)h.ninst;
+      if (persist_shape) {
+        std::vector<int32_t> cnt(h.ninst, 0);
+        for (int64_t r0 : h.psd_row0) ++cnt[h.row_inst[r0]];
+        for (int32_t c : cnt) persist_shape = persist_shape && c == 1;
+      }
+    }
     return COSMO_OK;
+  }
+  bool persist_shape = false;
+  // the persistent forward applies now: open loop, squared-residual loss,
+  // every size class on the compile-time-geometry Jacobi
+  bool persist_now() const {
+    if (!persist_shape || pol_mode || opt.loss_kind != 0 || buckets.empty()) return false;
+    for (const auto& bk : buckets)
+      if (bk.method != 0 || bk.variant != 3) return false;
+    return true;
   }
 
   // ------------------------------------------------------------- tuning --
@@ -1388,6 +1413,28 @@ struct ImplT : Impl {
   // run steps [k0, k1) of segment seg (slot 0 holds z^{k0})
   void enqueue_segment(int32_t seg, cudaStream_t st) {
     const int32_t k0 = seg * cK, k1 = std::min(K, k0 + cK);
+    if constexpr (std::is_same<T, float>::value && std::is_same<V, float>::value) {
+      if (persist_now()) {
+        // one launch per size class for the whole segment (kernels_persist.cuh)
+        PersistArgs<T> a{};
+        a.k0 = k0; a.k1 = k1;
+        a.rho = rho_rect; a.alpha = alpha_in; a.sigma = sigma_dev; a.dinv = dinv;
+        a.xs = xs; a.ss = ss; a.ys = ys; a.xts = xts; a.sts = sts; a.lams = lams; a.Us = Us;
+        a.U_warm = k0 > 0 ? ck_U + (int64_t)seg * h.sum_p2 : nullptr;
+        a.sum_p = h.sum_p; a.sum_p2 = h.sum_p2;
+        a.tol = opt.eig_tol; a.max_sweeps = opt.eig_max_sweeps; a.flags = flags; a.stats = stats;
+        psd_group("fwd_persist", st, [&](const Bucket& bk, cudaStream_t s) {
+          const int warm = (opt.eig_warm_start && bk.warm_fits) ? 1 : 0;
+          jt2_for<T>(jt2_pmax(bk.maxp), bk.fnt, [&](auto c, auto pmc, auto ntc) {
+            using C = decltype(c);
+            constexpr int PM = decltype(pmc)::value, NT_ = decltype(ntc)::value;
+            k_fwd_persist_jt2<T, V, NT_, PM, C::TI, C::CI><<<bk.count, NT_, Jt2Geo<T, PM>::bytes(NT_), s>>>(
+                P, a, bk.start, warm);
+          });
+        });
+        return;
+      }
+    }
     for (int32_t k = k0; k < k1; ++k) {
       const int slot = k - k0;
       const T* warm = nullptr;
@@ -2032,6 +2079,7 @@ struct ImplT : Impl {
     o->last_K = K;
     o->tape_valid = tape_valid ? 1 : 0;
     o->kernels_launched = launched;
+    o->fwd_persistent = persist_now() ? 1 : 0;
     unsigned long long st6[6] = {0, 0, 0, 0, 0, 0};
     if (cudaDeviceSynchronize() == cudaSuccess &&
         cudaMemcpy(st6, stats, sizeof(st6), cudaMemcpyDeviceToHost) == cudaSuccess) {
@@ -2076,6 +2124,7 @@ cosmo_status cosmo_options_default(cosmo_options* o, int32_t precision) {
   o->eig_variant = 0;
   o->eig_threads = 0;
   o->autotune = 0;
+  o->fwd_persistent = 0;
   o->loss_kind = 0;
   return COSMO_OK;
 }
@@ -2101,7 +2150,7 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
       !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
       !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 3 ||
-      !(o.autotune == 0 || o.autotune == 1) ||
+      !(o.autotune == 0 || o.autotune == 1) || !(o.fwd_persistent == 0 || o.fwd_persistent == 1) ||
       !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512 ||
         (o.eig_threads == 1024 && o.eig_variant != 1)))
     return fail(COSMO_E_INVAL, "invalid options");

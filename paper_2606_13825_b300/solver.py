@@ -384,7 +384,7 @@ class CosmoBatch:
         return out
 
     KERNEL_CLASSES = ("rho_check", "rho_rectify", "alpha_check", "precond", "rhs", "pcg", "post",
-                      "soc_fwd", "psd_fwd", "residuals", "loss_seed", "bwd_gproj", "soc_bwd",
+                      "soc_fwd", "psd_fwd", "fwd_persist", "residuals", "loss_seed", "bwd_gproj", "soc_bwd",
                       "psd_bwd", "bwd_relax", "pcg_adj", "bwd_solve", "rect_adjoint", "ws_feat", "ws_fwd",
                       "ws_bwd", "ws_grad", "pol_fwd", "pol_bwd")
 

@@ -35,7 +35,7 @@ def test_version_and_defaults(L):
     assert o.eig_warm_start == 1 and o.dk_tensor_cores == 1 and o.cg_cluster == 0 and o.loss_kind == 0
     # the ctypes struct and the C struct agree in size (every field marshalled)
     assert ctypes.sizeof(_abi.Options) == 88
-    assert o.eig_variant == 0 and o.eig_threads == 0 and o.autotune == 0
+    assert o.eig_variant == 0 and o.eig_threads == 0 and o.autotune == 0 and o.fwd_persistent == 0
     assert ctypes.sizeof(_abi.Tuning) == 152     # 4 + 4 x 8 x 4 + 4 + 4, then the double at 144
     o = default_options("fp64")
     assert o.precision == _abi.PREC_FP64 and o.cg_tol == 1e-10
