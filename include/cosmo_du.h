@@ -215,7 +215,12 @@ typedef struct {
   int32_t class_maxp[COSMO_MAX_PSD_CLASSES];     /* largest order of the class */
   int32_t class_count[COSMO_MAX_PSD_CLASSES];    /* blocks in the class */
   int32_t class_method[COSMO_MAX_PSD_CLASSES];   /* 0 Jacobi in shared memory (eig_variant),
-                                                    1 tridiagonal + implicit QL */
+                                                    1 tridiagonal + implicit QL,
+                                                    2 one block per thread (MIXED, orders
+                                                    <= 8: serial cyclic Jacobi with the same
+                                                    refinement, CUDA-core DK backward); the
+                                                    shape rules choose 2 for such classes
+                                                    when eig_variant and eig_threads are 0 */
   int32_t class_threads[COSMO_MAX_PSD_CLASSES];  /* CTA size of the projection */
   int32_t cg_kernel;        /* 0 the shape rule (or no CG), else a cg_cluster value */
   int32_t tuned;            /* 1 if the autotuner chose this configuration */

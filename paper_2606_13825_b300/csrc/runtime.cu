@@ -33,6 +33,7 @@
 #include "kernels_pol.cuh"
 #include "kernels_ws_tc.cuh"
 #include "kernels_persist.cuh"
+#include "kernels_tpb.cuh"
 
 using namespace cosmo;
 
@@ -708,6 +709,13 @@ struct ImplT : Impl {
           if ((int64_t)tql_smem<T>(p0, nt) > maxs)
             return fail(COSMO_E_INVAL, "PSD order %d too large", p0);
         }
+        // classes of order <= TPB_MAXP in FP32: one block per thread (kernels_tpb.cuh)
+        if (std::is_same<T, float>::value && method == 0 && p0 <= TPB_MAXP && opt.eig_variant == 0 &&
+            opt.eig_threads == 0) {
+          bk.method = 2;
+          bk.fnt = TPB_NT;
+          bk.warm_fits = true;
+        }
         buckets.push_back(bk);
         q = e;
       }
@@ -738,6 +746,8 @@ struct ImplT : Impl {
             }
           });
       CU(cudaGetLastError());
+      CU(cudaFuncSetAttribute(k_psd_fwd_tpb<T, V, TPB_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+      CU(cudaFuncSetAttribute(k_psd_bwd_tpb<T, V, TPB_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
       CU(cudaFuncSetAttribute(k_psd_bwd<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -813,8 +823,17 @@ struct ImplT : Impl {
     const int i = jt_ipt(p, fnt);
     return i <= 2 ? 2 : (i <= 4 ? 4 : 8);
   }
-  // a class's configuration: method 0 = Jacobi (this batch's variant), 1 = QL
+  // a class's configuration: method 0 = Jacobi (this batch's variant), 1 = QL,
+  // 2 = one block per thread (FP32, orders <= TPB_MAXP)
   cosmo_status config_bucket(Bucket& bk, int method, int fnt) {
+    if (method == 2) {
+      if (!std::is_same<T, float>::value || bk.maxp > TPB_MAXP)
+        return fail(COSMO_E_INVAL, "order %d does not fit the one-block-per-thread path", bk.maxp);
+      bk.method = 2;
+      bk.fnt = TPB_NT;
+      bk.warm_fits = true;
+      return COSMO_OK;
+    }
     if (method == 1) {
       if (!ql_fits(bk.maxp)) return fail(COSMO_E_INVAL, "order %d does not fit the QL path", bk.maxp);
       if (!dk_work) TRY(arena.alloc(&dk_work, 2 * h.sum_p2));
@@ -932,15 +951,18 @@ struct ImplT : Impl {
         psd_fwd_bucket(base, st, io0, lam, U0, nullptr, fl, nullptr);
         CU(cudaGetLastError());
         float best = 3.0e38f;
-        float bwd[2] = {-1.f, -1.f};
+        float bwd[3] = {-1.f, -1.f, -1.f};
         std::vector<std::pair<int, int>> cands;
         for (int fnt : {64, 128, 256, 384, 512, 1024}) cands.push_back(std::make_pair(0, fnt));
         if (opt.eig_jacobi_max_p == 0 && base.maxp >= 48) cands.push_back(std::make_pair(1, 256));
+        if (std::is_same<T, float>::value && opt.eig_variant == 0 && base.maxp <= TPB_MAXP)
+          cands.push_back(std::make_pair(2, TPB_NT));
         for (const auto& c : cands) {
           Bucket bk = base;
-          if (c.first == 1 ? !ql_fits(bk.maxp) : !(jt2_fits(bk.maxp, c.second) || jt_fits(bk.maxp, c.second))) continue;
+          if (c.first == 1 ? !ql_fits(bk.maxp)
+                           : c.first == 0 && !(jt2_fits(bk.maxp, c.second) || jt_fits(bk.maxp, c.second))) continue;
           if (config_bucket(bk, c.first, c.second) != COSMO_OK) { g_err.clear(); continue; }
-          const T* up = bk.method == 0 && opt.eig_warm_start ? U0 : nullptr;
+          const T* up = bk.method != 1 && opt.eig_warm_start ? U0 : nullptr;
           const float f = time_min(st, [&]() { psd_fwd_bucket(bk, st, io1, lam, U1, up, fl, nullptr); });
           CU(cudaGetLastError());
           if (bwd[bk.method] < 0.f) {
@@ -1019,7 +1041,7 @@ struct ImplT : Impl {
       return fail(COSMO_E_INVAL, "tuning has %d classes, the batch %zu", t.n_classes, buckets.size());
     for (size_t i = 0; i < buckets.size(); ++i)
       if (t.class_maxp[i] != buckets[i].maxp || t.class_count[i] != buckets[i].count ||
-          !(t.class_method[i] == 0 || t.class_method[i] == 1))
+          !(t.class_method[i] == 0 || t.class_method[i] == 1 || t.class_method[i] == 2))
         return fail(COSMO_E_INVAL, "tuning class %zu does not match the batch", i);
     const int cg = t.cg_kernel;
     if (!(cg >= -3 && cg <= 4 && cg != 3) || (cg == -1 && cg_smem_bytes() > CG_SMEM_MAX) ||
@@ -1349,6 +1371,11 @@ struct ImplT : Impl {
   // the forward projection of one PSD class (kernel chosen by the class's method / variant / CTA size)
   void psd_fwd_bucket(const Bucket& bk, cudaStream_t s, const PsdIterIO<T>& io, T* lam, T* U, const T* up,
                       int32_t* fl, unsigned long long* stt) {
+    if (bk.method == 2) {
+      k_psd_fwd_tpb<T, V, TPB_NT><<<(bk.count + TPB_NT - 1) / TPB_NT, TPB_NT, tpb_smem<T>(TPB_NT), s>>>(
+          P, io, lam, U, opt.eig_tol, opt.eig_max_sweeps, fl, bk.start, bk.count, stt, up);
+      return;
+    }
     if (bk.method == 1) {
       // the working matrix in shared memory when the class's largest block fits
       const int zsm = (int64_t)tql_smem_z<T>(bk.maxp, 256) <= (int64_t)smem_max ? 1 : 0;
@@ -1391,6 +1418,11 @@ struct ImplT : Impl {
   // the Daleckii-Krein backward of one PSD class
   void psd_bwd_bucket(const Bucket& bk, cudaStream_t s, const PsdBwdIO<T>& io, const T* lam, const T* U,
                       int32_t* fl) {
+    if (bk.method == 2) {
+      k_psd_bwd_tpb<T, V, TPB_NT><<<(bk.count + TPB_NT - 1) / TPB_NT, TPB_NT, tpb_smem<T>(TPB_NT), s>>>(
+          P, io, lam, U, opt.dk_gap_tau, bk.start, bk.count);
+      return;
+    }
     if (bk.method == 1) {
       k_psd_bwd_global<T, V, 256><<<bk.count, 256, 0, s>>>(P, io, lam, U, dk_work, opt.dk_gap_tau, bk.start);
       return;

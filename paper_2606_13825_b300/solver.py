@@ -182,7 +182,7 @@ class CosmoBatch:
         check(lib().cosmo_batch_get_tuning(self._h, byref(t)))
         k = t.n_classes
         return {"classes": [{"maxp": t.class_maxp[i], "count": t.class_count[i],
-                             "method": "jacobi" if t.class_method[i] == 0 else "ql",
+                             "method": ("jacobi", "ql", "thread")[t.class_method[i]],
                              "threads": t.class_threads[i]} for i in range(k)],
                 "cg_kernel": t.cg_kernel, "tuned": bool(t.tuned), "tune_ms": t.tune_ms}
 
@@ -195,7 +195,7 @@ class CosmoBatch:
         for i, c in enumerate(cl):
             t.class_maxp[i] = c["maxp"]
             t.class_count[i] = c["count"]
-            t.class_method[i] = 0 if c["method"] == "jacobi" else 1
+            t.class_method[i] = {"jacobi": 0, "ql": 1, "thread": 2}[c["method"]]
             t.class_threads[i] = c["threads"]
         t.cg_kernel = tuning["cg_kernel"]
         t.tuned = 1 if tuning.get("tuned") else 0
