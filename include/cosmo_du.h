@@ -157,7 +157,11 @@ typedef struct {
                                forced: -1 vectors in shared memory, -2 vectors and the
                                instance's A, A' and P in shared memory, -3 global-memory
                                vectors (-1 / -2 fail with E_INVAL at creation when the
-                               data does not fit in 200 KB) */
+                               data does not fit in 200 KB); -4 one warp per instance
+                               over global vectors (offered to the autotuner when every
+                               CG instance has n_i + m_i <= 4096 and nnz(A_i) + nnz(P_i)
+                               <= 16384; measured slower than -2 on the covariance-
+                               steering instances, so never the shape rules' choice) */
   int32_t loss_kind;        /* per-instance loss of cosmo_forward / cotangent of
                                cosmo_backward: 0 ||r_p^K||^2 + ||r_d^K||^2; 1 the log-residual
                                loss of Sec. 4, sum_{k=1..K} log(||r_d^k||^2/||r_d^0||^2 +

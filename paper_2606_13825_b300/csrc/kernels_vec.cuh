@@ -350,6 +350,159 @@ __global__ void __launch_bounds__(NT) k_pcg(Prob<T, V> P, CgArgs<T> a) {
   }
 }
 
+// out[row] = f(row, sum_e val[e] x[ci[e]]) for rows [r0, r1), one warp,
+// lane l taking rows r0 + l, r0 + l + 32, ...: two rows per lane in flight,
+// each read in chunks of 8 entries (indices and values, then the gathers);
+// the sum runs along the row in entry order.
+template <class T, class V, class F>
+__device__ __forceinline__ void warp_csr_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              const V* __restrict__ val, const T* __restrict__ x, int64_t r0,
+                                              int64_t r1, int lane, F f) {
+  constexpr int U = 8;
+  for (int64_t rb = r0 + lane; rb < r1; rb += 64) {
+    int64_t e[2], eend[2];
+    T acc[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t r = rb + u * 32;
+      const bool ok = r < r1;
+      e[u] = ok ? rp[r] : 0;
+      eend[u] = ok ? rp[r + 1] : 0;
+      acc[u] = T(0);
+    }
+    while (e[0] < eend[0] || e[1] < eend[1]) {
+      int32_t c[2][U];
+      T v[2][U];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          const int64_t idx = e[u] + k;
+          const bool ok = idx < eend[u];
+          c[u][k] = ok ? ci[idx] : -1;
+          v[u][k] = ok ? (T)ldv(val, idx) : T(0);
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+          if (c[u][k] >= 0) acc[u] += v[u][k] * x[c[u][k]];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) e[u] = min(e[u] + U, eend[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t r = rb + u * 32;
+      if (r < r1) f(r, acc[u]);
+    }
+  }
+}
+
+// a4 / b5 for many small instances: the Jacobi-PCG of k_pcg with one WARP per
+// instance (WPB warps per CTA, option cg_cluster = -4).  A warp needs no CTA
+// barrier or block reduction: its phases are ordered by __syncwarp (which
+// also orders the warp's global writes), and the inner products are double
+// warp sums by shuffles.  The same iteration, stopping rule, warm start, cap
+// and flags as k_pcg; the inner products are summed in another order, so
+// iterates agree with k_pcg to rounding, not bit for bit.  Measured on the
+// covariance-steering workload (512 instances, n + m ~ 1,850): 20.5 ms of CG
+// per step against 12.1 for k_pcg_local -- one warp's chains of gathers
+// through L2 hide less latency than a CTA with the instance's matrices staged
+// in shared memory -- so it is an option and an autotuner candidate only.
+template <class T, class V, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k_pcg_warp(Prob<T, V> P, CgArgs<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int cid = blockIdx.x * WPB + (threadIdx.x >> 5);
+  if (cid >= P.n_cg) return;                 // whole warps: no CTA barrier below
+  const int32_t inst = P.cg_sched[cid];
+  const int64_t c0 = P.col_off[inst], c1 = P.col_off[inst + 1];
+  const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
+  if (c1 == c0) return;
+  T* __restrict__ x = a.x;
+  T* __restrict__ r = a.r;
+  T* __restrict__ p = a.p;
+  T* __restrict__ u = a.u;
+  T* __restrict__ t = a.t;
+  const T* __restrict__ rho = a.rho;
+  const T sig = (T)a.sigma;
+  // u = M v = sigma v + P v + A' (rho o (A v)) on this instance
+  auto matvec = [&](const T* __restrict__ v) {
+    warp_csr_rows<T, V>(P.A_rp, P.A_ci, P.A_v, v, r0, r1, lane, [&](int64_t q, T acc) { t[q] = rho[q] * acc; });
+    __syncwarp();
+    if (P.P_rp) {
+      warp_csr_rows<T, T>(P.P_rp, P.P_ci, P.P_v, v, c0, c1, lane, [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+      warp_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1, lane, [&](int64_t j, T acc) { u[j] += acc; });
+    } else {
+      warp_csr_rows<T, V>(P.AT_rp, P.AT_ci, P.AT_v, (const T*)t, c0, c1, lane,
+                          [&](int64_t j, T acc) { u[j] = sig * v[j] + acc; });
+    }
+    __syncwarp();
+  };
+  if (a.zero_start) {
+    for (int64_t j = c0 + lane; j < c1; j += 32) x[j] = T(0);
+  } else {
+    if (a.x0 && a.x0 != a.x)
+      for (int64_t j = c0 + lane; j < c1; j += 32) x[j] = a.x0[j];
+    __syncwarp();
+    matvec(x);
+  }
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t j = c0 + lane; j < c1; j += 32) {
+    const T bj = a.rhs[j];
+    const T rj = a.zero_start ? bj : bj - u[j];
+    const T zj = a.dinv[j] * rj;
+    r[j] = rj;
+    p[j] = zj;
+    rz += (double)rj * (double)zj;
+    rr += (double)rj * (double)rj;
+    bb += (double)bj * (double)bj;
+  }
+  rz = warp_sum(rz);
+  rr = warp_sum(rr);
+  bb = warp_sum(bb);
+  __syncwarp();
+  const double thr = a.tol * a.tol * bb;
+  int32_t it = 0;
+  if (bb == 0.0) {
+    for (int64_t j = c0 + lane; j < c1; j += 32) x[j] = T(0);
+    rr = 0.0;
+  }
+  while (rr > thr && it < a.maxit) {
+    matvec(p);
+    double pu = 0.0;
+    for (int64_t j = c0 + lane; j < c1; j += 32) pu += (double)p[j] * (double)u[j];
+    pu = warp_sum(pu);
+    if (!(pu > 0.0)) break;                  // breakdown: stop, flagged below
+    const T al = (T)(rz / pu);
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t j = c0 + lane; j < c1; j += 32) {
+      x[j] += al * p[j];
+      const T rj = r[j] - al * u[j];
+      r[j] = rj;
+      const T zj = a.dinv[j] * rj;
+      s0 += (double)rj * (double)zj;
+      s1 += (double)rj * (double)rj;
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    const T be = (T)(s0 / rz);
+    rz = s0;
+    rr = s1;
+    for (int64_t j = c0 + lane; j < c1; j += 32) p[j] = a.dinv[j] * r[j] + be * p[j];
+    __syncwarp();
+    ++it;
+  }
+  if (lane == 0) {
+    if (rr > thr) atomicOr(&a.flags[inst], a.flag_bit);
+    if (!(rr == rr)) atomicOr(&a.flags[inst], F_NONFINITE);
+    if (a.iters) a.iters[inst] = it;
+    if (a.stats) {
+      atomicAdd(&a.stats[0], (unsigned long long)it);
+      atomicAdd(&a.stats[1], 1ull);
+    }
+  }
+}
+
 // cta_csr_rows_c with the gathered vector in shared memory: entry c of the
 // instance-local vector xl is column (c + base) of the batch
 template <class T, class V, class F>

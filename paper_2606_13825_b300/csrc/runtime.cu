@@ -239,6 +239,8 @@ struct HostPlan {
   int32_t cg_nt = 256;      // threads of a CG CTA
   int64_t cg_vec = 0;       // max over CG instances of 5 n_i + m_i (reals of the shared-memory CG)
   int32_t cg_cs = 1;        // CTAs per instance (thread-block cluster) in the CG
+  bool cg_small = false;    // every CG instance small: n_i + m_i <= 4096, nnz(A_i) + nnz(P_i) <= 16384
+                            // (the autotuner then also times one warp per instance)
   int64_t sum_p = 0, sum_p2 = 0;
   int32_t max_p = 0;
 };
@@ -357,6 +359,13 @@ static void build_plan(const cosmo_problem* pr, HostPlan& h) {
       cg_max = std::max(cg_max, (h.row_off[i + 1] - h.row_off[i]) + (h.col_off[i + 1] - h.col_off[i]));
       h.cg_vec = std::max(h.cg_vec, 5 * (h.col_off[i + 1] - h.col_off[i]) + (h.row_off[i + 1] - h.row_off[i]));
     }
+  h.cg_small = !h.cg_sched.empty();
+  for (int32_t i : h.cg_sched) {
+    const int64_t nz = (h.A_rp[h.row_off[i + 1]] - h.A_rp[h.row_off[i]]) +
+                       (h.has_P ? h.P_rp[h.col_off[i + 1]] - h.P_rp[h.col_off[i]] : 0);
+    if ((h.row_off[i + 1] - h.row_off[i]) + (h.col_off[i + 1] - h.col_off[i]) > 4096 || nz > 16384)
+      h.cg_small = false;
+  }
   // large instances take 512-thread CG CTAs (more rows in flight per SpMV);
   // many small ones 256 (two CTAs resident per SM)
   h.cg_nt = cg_max >= 8192 ? 512 : 256;
@@ -995,6 +1004,7 @@ struct ImplT : Impl {
       ca.r = cg_r; ca.p = cg_p; ca.u = cg_u; ca.t = cg_t; ca.tol = 1e-30; ca.maxit = 20; ca.zero_start = 1;
       ca.flag_bit = F_CG_CAP; ca.flags = fl; ca.iters = nullptr; ca.stats = nullptr;
       std::vector<int> cands;
+      if (h.cg_small) cands.push_back(-4);
       if (cg_local <= CG_SMEM_MAX) cands.push_back(-2);
       if (cg_smem_bytes() <= CG_SMEM_MAX) cands.push_back(-1);
       cands.push_back(-3);
@@ -1044,7 +1054,7 @@ struct ImplT : Impl {
           !(t.class_method[i] == 0 || t.class_method[i] == 1 || t.class_method[i] == 2))
         return fail(COSMO_E_INVAL, "tuning class %zu does not match the batch", i);
     const int cg = t.cg_kernel;
-    if (!(cg >= -3 && cg <= 4 && cg != 3) || (cg == -1 && cg_smem_bytes() > CG_SMEM_MAX) ||
+    if (!(cg >= -4 && cg <= 4 && cg != 3) || (cg == -1 && cg_smem_bytes() > CG_SMEM_MAX) ||
         (cg == -2 && cg_local > CG_SMEM_MAX))
       return fail(COSMO_E_INVAL, "tuning: CG kernel %d not available", cg);
     std::vector<Bucket> nb = buckets;
@@ -1229,6 +1239,10 @@ struct ImplT : Impl {
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
     const size_t smb = cg_smem_bytes();
     const int mode = opt.cg_cluster != 0 ? opt.cg_cluster : cg_mode;
+    if (mode == -4) {   // one warp per instance
+      launch(tag, k_pcg_warp<T, V, 1>, P.n_cg, 32, 0, st, P, ca);
+      return;
+    }
     if (mode == -1) {
       if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
       else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
@@ -2180,7 +2194,7 @@ cosmo_status cosmo_batch_create(const cosmo_problem* prob, const cosmo_options* 
     return fail(COSMO_E_INVAL, "unknown value type %d", o.value_type);
   if (!(o.cg_tol > 0.0) || o.cg_max_iter < 1 || o.checkpoint_every < 0 || !(o.dk_gap_tau >= 0.0) ||
       o.eig_max_sweeps < 1 || !(o.eig_tol > 0.0) ||
-      !(o.cg_cluster >= -3 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
+      !(o.cg_cluster >= -4 && o.cg_cluster <= 4 && o.cg_cluster != 3) ||
       !(o.loss_kind == 0 || o.loss_kind == 1) || o.eig_variant < 0 || o.eig_variant > 3 ||
       !(o.autotune == 0 || o.autotune == 1) || !(o.fwd_persistent == 0 || o.fwd_persistent == 1) ||
       !(o.eig_threads == 0 || o.eig_threads == 128 || o.eig_threads == 256 || o.eig_threads == 512 ||

@@ -46,7 +46,7 @@ def test_tuned_configuration_is_bit_identical_to_forcing_it(kind):
         for c in ta["classes"]:
             assert c["method"] in ("jacobi", "ql") and c["threads"] in (64, 128, 256, 384, 512, 1024)
     else:
-        assert ta["cg_kernel"] in (-3, -2, -1, 2, 4)
+        assert ta["cg_kernel"] in (-4, -3, -2, -1, 2, 4)
     ra = _run(a, rho, alpha, x0, s0, y0)
     b = CosmoBatch(probs, precision="mixed", autotune=0)
     b.set_tuning(ta)

@@ -182,6 +182,23 @@ def test_socp_cg_on_clusters(precision, cs):
     compare(gpu, ora, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_socp_cg_warp_per_instance(precision):
+    """The CG with one warp per instance (cg_cluster = -4, an option and an
+    autotuner candidate for small instances), forced on instances with more
+    rows and columns than a warp has lanes many times over, warm-started:
+    forward and every gradient against the oracle."""
+    _need_gpu()
+    probs = socp_batch(2, seed=4151, n=300, m=500) + socp_batch(2, seed=4153)
+    K = 4
+    rho, alpha, x0, s0, y0 = random_inputs(probs, K, seed=23)
+    ora = oracle_batch(probs, rho, alpha, 1e-6, x0, s0, y0)
+    gpu = run_gpu(probs, rho, alpha, x0, s0, y0, precision, cg_cluster=-4,
+                  cg_tol=1e-12 if precision == "fp64" else 1e-8)
+    assert not (gpu["flags"] & 3).any(), gpu["flags"]
+    compare(gpu, ora, precision)
+
+
 def test_socp_bf16_values_vs_rounded_oracle():
     """BF16 storage of A: parity against the oracle run on the same
     bf16-rounded A (the rounding is the input, not an error).  P stays in the
