@@ -42,35 +42,61 @@ __host__ __device__ constexpr size_t tpb_smem(int nt) {
   return (size_t)3 * TPB_MAXP * TPB_MAXP * nt * sizeof(T);
 }
 
-// C = A B (p x p), C distinct from A and B
+// C = A B (p x p), C distinct from A and B.  The TPB_MAXP outputs of a row
+// are formed together (their FMA chains interleave; entries beyond p are
+// skipped by predicate); each sum runs over k in order.
 template <class T, int NT>
 __device__ __forceinline__ void tpb_mm(int p, TpbMat<T, NT> A, TpbMat<T, NT> B, TpbMat<T, NT> C) {
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) {
-      T acc = T(0);
-      for (int k = 0; k < p; ++k) acc = fma(A(i, k), B(k, j), acc);
-      C(i, j) = acc;
+  for (int i = 0; i < p; ++i) {
+    T acc[TPB_MAXP];
+#pragma unroll
+    for (int j = 0; j < TPB_MAXP; ++j) acc[j] = T(0);
+    for (int k = 0; k < p; ++k) {
+      const T a = A(i, k);
+#pragma unroll
+      for (int j = 0; j < TPB_MAXP; ++j)
+        if (j < p) acc[j] = fma(a, B(k, j), acc[j]);
     }
+#pragma unroll
+    for (int j = 0; j < TPB_MAXP; ++j)
+      if (j < p) C(i, j) = acc[j];
+  }
 }
 // C = A B'
 template <class T, int NT>
 __device__ __forceinline__ void tpb_mmt(int p, TpbMat<T, NT> A, TpbMat<T, NT> B, TpbMat<T, NT> C) {
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) {
-      T acc = T(0);
-      for (int k = 0; k < p; ++k) acc = fma(A(i, k), B(j, k), acc);
-      C(i, j) = acc;
+  for (int i = 0; i < p; ++i) {
+    T acc[TPB_MAXP];
+#pragma unroll
+    for (int j = 0; j < TPB_MAXP; ++j) acc[j] = T(0);
+    for (int k = 0; k < p; ++k) {
+      const T a = A(i, k);
+#pragma unroll
+      for (int j = 0; j < TPB_MAXP; ++j)
+        if (j < p) acc[j] = fma(a, B(j, k), acc[j]);
     }
+#pragma unroll
+    for (int j = 0; j < TPB_MAXP; ++j)
+      if (j < p) C(i, j) = acc[j];
+  }
 }
 // C = A' B
 template <class T, int NT>
 __device__ __forceinline__ void tpb_mtm(int p, TpbMat<T, NT> A, TpbMat<T, NT> B, TpbMat<T, NT> C) {
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) {
-      T acc = T(0);
-      for (int k = 0; k < p; ++k) acc = fma(A(k, i), B(k, j), acc);
-      C(i, j) = acc;
+  for (int i = 0; i < p; ++i) {
+    T acc[TPB_MAXP];
+#pragma unroll
+    for (int j = 0; j < TPB_MAXP; ++j) acc[j] = T(0);
+    for (int k = 0; k < p; ++k) {
+      const T a = A(k, i);
+#pragma unroll
+      for (int j = 0; j < TPB_MAXP; ++j)
+        if (j < p) acc[j] = fma(a, B(k, j), acc[j]);
     }
+#pragma unroll
+    for (int j = 0; j < TPB_MAXP; ++j)
+      if (j < p) C(i, j) = acc[j];
+  }
 }
 
 // sum over the warp's converged lanes of one counter, added by the first of them
@@ -143,8 +169,9 @@ __global__ void __launch_bounds__(NT) k_psd_fwd_tpb(Prob<T, V> P, PsdIterIO<T> i
         x.aa = A(a, a); x.ab = A(a, b); x.ba = x.ab; x.bb = A(b, b);
         const JtRot<T> r = jt_rotation(x.aa, x.ab, x.bb, thresh);
         if (r.s == T(0)) continue;
-        for (int k = 0; k < p; ++k) {
-          if (k == a || k == b) continue;
+#pragma unroll
+        for (int k = 0; k < TPB_MAXP; ++k) {
+          if (k >= p || k == a || k == b) continue;
           const T ka = A(k, a), kb = A(k, b);
           const T na = jt_cms(r.c, r.s, ka, kb), nb = jt_spc(r.c, r.s, ka, kb);
           A(k, a) = na; A(a, k) = na;
@@ -153,7 +180,9 @@ __global__ void __launch_bounds__(NT) k_psd_fwd_tpb(Prob<T, V> P, PsdIterIO<T> i
         A(a, a) = jt_diag_a(x, r);
         A(b, b) = jt_diag_b(x, r);
         A(a, b) = T(0); A(b, a) = T(0);
-        for (int k = 0; k < p; ++k) {
+#pragma unroll
+        for (int k = 0; k < TPB_MAXP; ++k) {
+          if (k >= p) continue;
           const T va = Vt(a, k), vb = Vt(b, k);
           Vt(a, k) = jt_cms(r.c, r.s, va, vb);
           Vt(b, k) = jt_spc(r.c, r.s, va, vb);
