@@ -107,7 +107,11 @@ def workload_spec(name, rank=0, world=1):
                     desc=desc + "; K=50; learnable log rho_k / alpha_k; loss ||r_p^K||^2+||r_d^K||^2")
     if name == "covsteer":
         probs = [covsteer_problem(5000 + rank * 512 + j) for j in range(512)]
-        return dict(probs=probs, K=40, opts={"use_graph": 1}, value_type="f32", learn_start=True,
+        # its CG solves are short (about 12 iterations): staging each instance's
+        # matrices in shared memory (the shape rule's CG) costs more than it
+        # saves; vectors in shared memory, matrices through L2 measured 35.0 ->
+        # 29.5 ms per step (without the warm-start network)
+        return dict(probs=probs, K=40, opts={"use_graph": 1, "cg_cluster": -1}, value_type="f32", learn_start=True,
                     metric="unrolled fwd+bwd instance-iters/sec (covariance steering, batched mixed precision)",
                     desc="covariance-steering stand-in SDPs: 512 instances (seeds 5000+j), nx=4, nu=2, T=20, "
                          "PSD blocks 20x p8 + 20x p6 + p4; K=40; App. E warm-start network and log rho_k / alpha_k; "
@@ -719,7 +723,8 @@ def main():
     avg_s = dom_ms / max(dom_n, 1) / 1e3
     if has_psd:
         flops = psd_flops(probs)
-        kern = "psd_fwd (cyclic Jacobi eigensolver + reconstruction, CTA per block)"
+        kern = ("psd_fwd (cyclic Jacobi eigensolver + reconstruction; a CTA per block, a thread per "
+                "block of order <= 8)")
         if persist:
             # one launch group covers the steps of one forward segment
             c = int(opts.get("checkpoint_every", 0) or 0)
