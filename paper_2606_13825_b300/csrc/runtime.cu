@@ -367,8 +367,9 @@ static void build_plan(const cosmo_problem* pr, HostPlan& h) {
       h.cg_small = false;
   }
   // large instances take 512-thread CG CTAs (more rows in flight per SpMV);
-  // many small ones 256 (two CTAs resident per SM)
-  h.cg_nt = cg_max >= 8192 ? 512 : 256;
+  // many small ones 256 (two CTAs resident per SM), the smallest (fewer than
+  // 1024 rows + columns) 128: fewer warps behind every barrier and reduction
+  h.cg_nt = cg_max >= 8192 ? 512 : (cg_max < 1024 ? 128 : 256);
   // few large instances: a cluster of 2 or 4 CTAs per instance, so that the
   // CG of e.g. 64 SOCP instances spreads over more than 64 SMs
   const int64_t ncg = (int64_t)h.cg_sched.size();
@@ -634,6 +635,8 @@ struct ImplT : Impl {
     TRY(arena.alloc(&xi, n)); TRY(arena.alloc(&cg_r, n)); TRY(arena.alloc(&cg_p, n));
     TRY(arena.alloc(&cg_u, n)); TRY(arena.alloc(&cg_t, m));
     // the shared-memory CG may take up to CG_SMEM_MAX bytes (set outside any graph capture)
+    CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
+    CU(cudaFuncSetAttribute(k_pcg_local<T, V, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     CU(cudaFuncSetAttribute(k_pcg_smem<T, V, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
     CU(cudaFuncSetAttribute(k_pcg_local<T, V, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG_SMEM_MAX));
@@ -1237,6 +1240,12 @@ struct ImplT : Impl {
   // forced variant that does not fit.
   int cg_mode = 0;   // the CG kernel chosen by tuning (a cg_cluster value; 0: the shape rule)
   void launch_pcg(const char* tag, cudaStream_t st, const CgArgs<T>& ca) {
+#define COSMO_CG_NT(KER, SMB)                                                      \
+  {                                                                                \
+    if (h.cg_nt == 512) launch(tag, KER<T, V, 512>, P.n_cg, 512, SMB, st, P, ca);  \
+    else if (h.cg_nt == 128) launch(tag, KER<T, V, 128>, P.n_cg, 128, SMB, st, P, ca); \
+    else launch(tag, KER<T, V, 256>, P.n_cg, 256, SMB, st, P, ca);                 \
+  }
     const size_t smb = cg_smem_bytes();
     const int mode = opt.cg_cluster != 0 ? opt.cg_cluster : cg_mode;
     if (mode == -4) {   // one warp per instance
@@ -1244,39 +1253,33 @@ struct ImplT : Impl {
       return;
     }
     if (mode == -1) {
-      if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
-      else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
+      COSMO_CG_NT(k_pcg_smem, smb);
       return;
     }
     if (mode == -2) {
-      if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
-      else launch(tag, k_pcg_local<T, V, 256>, P.n_cg, 256, cg_local, st, P, ca);
+      COSMO_CG_NT(k_pcg_local, cg_local);
       return;
     }
     if (mode == -3) {
-      if (h.cg_nt == 512) launch(tag, k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
-      else launch(tag, k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+      COSMO_CG_NT(k_pcg, 0);
       return;
     }
     const int cs = mode > 0 ? mode : (smb <= CG_SMEM_MAX ? 1 : h.cg_cs);
     if (cs == 1 && cg_local <= CG_SMEM_MAX) {
-      if (h.cg_nt == 512) launch(tag, k_pcg_local<T, V, 512>, P.n_cg, 512, cg_local, st, P, ca);
-      else launch(tag, k_pcg_local<T, V, 256>, P.n_cg, 256, cg_local, st, P, ca);
+      COSMO_CG_NT(k_pcg_local, cg_local);
       return;
     }
     if (cs == 1 && smb <= CG_SMEM_MAX) {
-      if (h.cg_nt == 512) launch(tag, k_pcg_smem<T, V, 512>, P.n_cg, 512, smb, st, P, ca);
-      else launch(tag, k_pcg_smem<T, V, 256>, P.n_cg, 256, smb, st, P, ca);
+      COSMO_CG_NT(k_pcg_smem, smb);
       return;
     }
     if (cs == 4)
       launch_cluster(tag, k_pcg<T, V, 512, 4>, P.n_cg * 4, 512, 0, st, 4, P, ca);
     else if (cs == 2)
       launch_cluster(tag, k_pcg<T, V, 512, 2>, P.n_cg * 2, 512, 0, st, 2, P, ca);
-    else if (h.cg_nt == 512)
-      launch(tag, k_pcg<T, V, 512>, P.n_cg, 512, 0, st, P, ca);
     else
-      launch(tag, k_pcg<T, V, 256>, P.n_cg, 256, 0, st, P, ca);
+      COSMO_CG_NT(k_pcg, 0);
+#undef COSMO_CG_NT
   }
 
   // Fork one launch per PSD bucket onto the bucket streams and join them back
