@@ -41,6 +41,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// The butterfly within aligned groups of L lanes (L a power of two <= 32);
+// every lane of a group ends with the group's sum.  L = 32 is warp_sum.
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (L == 32) return 0xffffffffu;
+  else return ((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1));
+}
+template <int L>
+__device__ __forceinline__ double group_sum(double v) {
+  const unsigned mask = group_mask<L>();
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
 // Same butterfly in the value's own type.  On this GPU an FP64 warp
 // instruction costs about 16 SM cycles (two FP64 lanes per clock per SM), so
 // per-row sums of float data stay in float.

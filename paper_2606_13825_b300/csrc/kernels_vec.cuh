@@ -32,23 +32,24 @@ __global__ void k_rho_copy_check(Prob<T, V> P, int32_t K, const T* __restrict__ 
   }
 }
 
-// one warp per (step, SOC/PSD block): replace the rows by their mean
-template <class T, class V>
+// L lanes per (step, SOC/PSD block) -- a warp, or 8 lanes when every block
+// has at most 64 rows: replace the rows by their mean
+template <class T, class V, int L>
 __global__ void k_rho_rectify(Prob<T, V> P, int32_t K, const T* __restrict__ rho_in,
                               T* __restrict__ rho_rect) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= (int64_t)K * P.nrect) return;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
+  const int lane = threadIdx.x % L;
+  if (w >= (int64_t)K * P.nrect) return;   // whole lane groups
   const int32_t k = (int32_t)(w / P.nrect), c = (int32_t)(w % P.nrect);
   const int64_t r0 = P.rect_row0[c];
   const int32_t nr = P.rect_rows[c];
   const T* src = rho_in + (int64_t)k * P.m_total + r0;
   double acc = 0.0;
-  for (int32_t i = lane; i < nr; i += 32) acc += (double)src[i];
-  acc = warp_sum(acc);
+  for (int32_t i = lane; i < nr; i += L) acc += (double)src[i];
+  acc = group_sum<L>(acc);
   const T mean = (T)(acc / (double)nr);
   T* dst = rho_rect + (int64_t)k * P.m_total + r0;
-  for (int32_t i = lane; i < nr; i += 32) dst[i] = mean;
+  for (int32_t i = lane; i < nr; i += L) dst[i] = mean;
 }
 
 template <class T, class V>
@@ -1209,21 +1210,22 @@ __global__ void k_bwd_solve(Prob<T, V> P, BwdPtrs<T> q) {
 }
 
 // b6: adjoint of the rectification over all K steps: every row of a SOC/PSD
-// block receives the block mean of rho-bar.  One warp per (step, block).
-template <class T, class V>
+// block receives the block mean of rho-bar.  L lanes per (step, block), as
+// k_rho_rectify.
+template <class T, class V, int L>
 __global__ void k_rect_adjoint(Prob<T, V> P, int32_t K, T* __restrict__ g) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= (int64_t)K * P.nrect) return;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
+  const int lane = threadIdx.x % L;
+  if (w >= (int64_t)K * P.nrect) return;   // whole lane groups
   const int32_t k = (int32_t)(w / P.nrect), c = (int32_t)(w % P.nrect);
   T* dst = g + (int64_t)k * P.m_total + P.rect_row0[c];
   const int32_t nr = P.rect_rows[c];
   double acc = 0.0;
-  for (int32_t i = lane; i < nr; i += 32) acc += (double)dst[i];
-  acc = warp_sum(acc);
-  __syncwarp();
+  for (int32_t i = lane; i < nr; i += L) acc += (double)dst[i];
+  acc = group_sum<L>(acc);
+  __syncwarp(group_mask<L>());             // the group's reads before its writes
   const T mean = (T)(acc / (double)nr);
-  for (int32_t i = lane; i < nr; i += 32) dst[i] = mean;
+  for (int32_t i = lane; i < nr; i += L) dst[i] = mean;
 }
 
 // ---------------------------------------------------------------------------

@@ -768,6 +768,8 @@ struct ImplT : Impl {
                                 (int)dk_tc_smem(DK_TC_MAXP)));
     }
     if (opt.autotune) TRY(tune());
+    rect_small = !h.rect_rows.empty();
+    for (int32_t nr : h.rect_rows) rect_small = rect_small && nr <= 64;
     // persistent forward (kernels_persist.cuh): FP32 batches (FP32 values)
     // of diagonal instances with exactly one PSD block each and no SOC rows
     if constexpr (std::is_same<T, float>::value && std::is_same<V, float>::value) {
@@ -782,6 +784,9 @@ struct ImplT : Impl {
     return COSMO_OK;
   }
   bool persist_shape = false;
+  // every SOC / PSD block has at most 64 rows: the rectification kernels take
+  // 8 lanes per block instead of a warp
+  bool rect_small = false;
   // the persistent forward applies now: open loop, squared-residual loss,
   // every size class on the compile-time-geometry Jacobi
   bool persist_now() const {
@@ -1348,7 +1353,10 @@ struct ImplT : Impl {
   void enqueue_prep(cudaStream_t st) {
     const int64_t Km = (int64_t)K * h.m;
     launch("rho_check", k_rho_copy_check<T, V>, grid_for(Km, 256), 256, 0, st, P, K, (const T*)rho_in, rho_rect, flags);
-    if (P.nrect) launch("rho_rectify", k_rho_rectify<T, V>, grid_for((int64_t)K * P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, K, (const T*)rho_in, rho_rect);
+    if (P.nrect) {
+      if (rect_small) launch("rho_rectify", k_rho_rectify<T, V, 8>, grid_for((int64_t)K * P.nrect * 8, 256, INT32_MAX), 256, 0, st, P, K, (const T*)rho_in, rho_rect);
+      else launch("rho_rectify", k_rho_rectify<T, V, 32>, grid_for((int64_t)K * P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, K, (const T*)rho_in, rho_rect);
+    }
     launch("alpha_check", k_alpha_check<T, V>, grid_for((int64_t)K * h.ninst, 256), 256, 0, st, P, K, (const T*)alpha_in, flags);
     launch("precond", k_precond<T, V>, grid_for((int64_t)K * h.n, 256), 256, 0, st, P, K, (const double*)sigma_dev, (const T*)rho_rect, dinv);
   }
@@ -1606,7 +1614,10 @@ struct ImplT : Impl {
         cur ^= 1;
       }
     }
-    if (P.nrect) launch("rect_adjoint", k_rect_adjoint<T, V>, grid_for((int64_t)K * P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, K, grho_all);
+    if (P.nrect) {
+      if (rect_small) launch("rect_adjoint", k_rect_adjoint<T, V, 8>, grid_for((int64_t)K * P.nrect * 8, 256, INT32_MAX), 256, 0, st, P, K, grho_all);
+      else launch("rect_adjoint", k_rect_adjoint<T, V, 32>, grid_for((int64_t)K * P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, K, grho_all);
+    }
     final_cot = cur;
   }
   int final_cot = 0;
@@ -1987,7 +1998,7 @@ struct ImplT : Impl {
     launch("rho_check", k_rho_copy_check<T, V>, grid_for(h.m, 256), 256, 0, st, P, 1, (const T*)(rho_in + om),
            rho_rect + om, flags);
     if (P.nrect)
-      launch("rho_rectify", k_rho_rectify<T, V>, grid_for((int64_t)P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, 1,
+      launch("rho_rectify", k_rho_rectify<T, V, 32>, grid_for((int64_t)P.nrect * 32, 256, INT32_MAX), 256, 0, st, P, 1,
              (const T*)(rho_in + om), rho_rect + om);
     launch("precond", k_precond<T, V>, grid_for(h.n, 256), 256, 0, st, P, 1, (const double*)(sigma_dev + k),
            (const T*)(rho_rect + om), dinv + (int64_t)k * h.n);
