@@ -1151,6 +1151,36 @@ __global__ void k_soc_bwd(Prob<T, V> P, BwdPtrs<T> q) {
 // The rows' s~bar goes to vbar (one gather per A' entry in the column loop
 // instead of three); 512 threads so that the largest instances take few
 // passes of the dependent row-pointer -> index -> value chain.
+// A thread's running sum of products a*b, for the per-instance double
+// reductions of the backward.  FP32: each product split exactly into
+// p + e by a fused multiply-add (TwoProduct), both added with Neumaier's
+// compensated summation in FP32, converted to double once -- the double
+// accumulation of the exact products to within a few units of 2^-48 of the
+// sum of the magnitudes, without an FP64 operation per element (slow on this
+// part).  FP64: the plain double sum.
+template <class T>
+struct CompSum {
+  double d = 0.0;
+  __device__ __forceinline__ void add_prod(T a, T b) { d += (double)a * (double)b; }
+  __device__ __forceinline__ double value() const { return d; }
+};
+template <>
+struct CompSum<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add1(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    add1(p);
+    c += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <class T, class V, int NT>
 __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
   __shared__ double sm[NT / 32];
@@ -1159,7 +1189,7 @@ __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
   const int64_t r0 = P.row_off[inst], r1 = P.row_off[inst + 1];
   const T al = q.alpha[inst];
   const bool diag = P.diag_inst[inst] != 0;
-  double acc[1] = {0.0};
+  CompSum<T> acc0;
   for (int64_t r = r0 + threadIdx.x; r < r1; r += NT) {
     const T rh = q.rho[r];
     const T yb = q.yb[r], vb = q.vbar[r];
@@ -1169,7 +1199,7 @@ __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
     q.yb2[r] = yb + vb / rh;
     q.sb2[r] = (T(1) - al) * shb;
     q.grho[r] = yb * (sh - q.sn[r]) - vb * y / (rh * rh);
-    acc[0] += (double)shb * (double)(st - s);
+    acc0.add_prod(shb, st - s);
     if (!finite_(shb)) atomicOr(&q.flags[inst], F_NONFINITE);
     q.vbar[r] = al * shb;   // s~bar, read back by the A' product below (vbar is dead after this kernel)
   }
@@ -1181,8 +1211,9 @@ __global__ void __launch_bounds__(NT) k_bwd_relax(Prob<T, V> P, BwdPtrs<T> q) {
     if (diag) q.lamt[j] = -acc2 * q.dinv[j];
     else q.adjrhs[j] = -acc2;
     q.xb2[j] = (T(1) - al) * xb;
-    acc[0] += (double)xb * (double)(q.xt[j] - q.x[j]);
+    acc0.add_prod(xb, q.xt[j] - q.x[j]);
   }
+  double acc[1] = {acc0.value()};
   block_sum<1>(acc, sm);
   if (threadIdx.x == 0) q.galpha[inst] = (T)acc[0];
 }
